@@ -1,0 +1,276 @@
+"""Occupations, subsystem eigensolver, subsystem SCF and the freeze-and-thaw cycle.
+
+Test infrastructure only (see ``oracle/__init__.py``).
+
+* Occupations 0 <= n_jk <= 1 with 2 sum_k w_k sum_j n_jk = N_I (Sec. 2; reading: the
+  printed constraint sum_j n_jk = N_I double counts the factor 2 of the density).
+  Smeared (metallic) subsystems use Fermi-Dirac occupations with the chemical
+  potential found by bisection; molecular subsystems use integer occupations
+  (Computational Details: smearing only for the metallic subsystems).  The Mermin
+  entropy term sigma S, S = -2 sum_k w_k sum_j [n ln n + (1-n) ln(1-n)], is reported.
+* Eigenpairs of H_I (Eq. KS): the lowest n_b eigenpairs by ARPACK's Lanczos
+  (scipy ``eigsh``) on the FFT-form H_I psi, or by LAPACK ``eigh`` of the dense matrix;
+  either is independent of the Davidson iteration the CUDA library runs.
+* Subsystem SCF with the other densities frozen, Pulay (DIIS) density mixing
+  (history 8, linear weight 0.3; the paper is silent on mixing).
+* Freeze-and-thaw (Fig. 1b caption): each subsystem's SCF runs to self-consistency
+  before the densities are exchanged.  Reading: Jacobi order, every subsystem solves
+  against the densities frozen at the start of the cycle, then rho is refreshed.
+
+Parity unpinned beyond the invariants: the absolute energies of the synthetic cells
+have no external value; they are pinned by the N_S = 1 reduction to plain KS, by the
+agreement of the three energy forms and by the eigensolver pin against dense LAPACK.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.linalg
+import scipy.sparse.linalg
+from scipy.special import expit
+
+from paper_1406_7803_gb300 import workloads
+
+
+# ---------------------------------------------------------------- occupations
+def occupations(eigs, wk, nelec, smearing):
+    """Occupations per k, chemical potential and entropy S (dimensionless)."""
+    eigs = [np.asarray(e, dtype=np.float64) for e in eigs]
+    wk = np.asarray(wk, dtype=np.float64)
+    if smearing <= 0.0:
+        nocc = nelec / 2.0
+        if len(eigs) != 1 or abs(nocc - round(nocc)) > 1e-12 or round(nocc) > eigs[0].size:
+            raise ValueError("integer occupations need one k-point and N_I/2 <= n_b bands")
+        nocc = int(round(nocc))
+        occ = np.zeros(eigs[0].size)
+        order = np.argsort(eigs[0], kind="stable")
+        occ[order[:nocc]] = 1.0
+        mu = float(eigs[0][order[nocc - 1]]) if nocc else float(eigs[0].min())
+        return [occ], mu, 0.0
+
+    def count(mu):
+        return sum(2.0 * w * float(np.sum(expit(-(e - mu) / smearing))) for w, e in zip(wk, eigs))
+
+    lo = min(e.min() for e in eigs) - 40.0 * smearing
+    hi = max(e.max() for e in eigs) + 40.0 * smearing
+    for _ in range(300):
+        mu = 0.5 * (lo + hi)
+        n = count(mu)
+        if abs(n - nelec) < 1e-13:
+            break
+        if n < nelec:
+            lo = mu
+        else:
+            hi = mu
+    occ = [expit(-(e - mu) / smearing) for e in eigs]
+    S = 0.0
+    for w, n in zip(wk, occ):
+        with np.errstate(divide="ignore", invalid="ignore"):
+            t = np.where(n > 0, n * np.log(np.where(n > 0, n, 1.0)), 0.0) \
+                + np.where(n < 1, (1 - n) * np.log(np.where(n < 1, 1 - n, 1.0)), 0.0)
+        S += -2.0 * w * float(np.sum(t))
+    return occ, mu, S
+
+
+# ---------------------------------------------------------------- eigensolvers
+def eig_dense(system, I, k, veff_I, nb):
+    H = system.dense_h(I, k, veff_I)
+    w, v = scipy.linalg.eigh(H, subset_by_index=[0, nb - 1])
+    return w, v.T.copy()
+
+
+def eig_lanczos(system, I, k, veff_I, nb, guess=None, tol=1e-13):
+    mil, kin = system.basis[I][k]
+    npw = mil.shape[0]
+
+    def mv(x):
+        return system.apply_h(I, k, x.reshape(1, -1), veff_I).reshape(-1)
+
+    op = scipy.sparse.linalg.LinearOperator((npw, npw), matvec=mv, dtype=np.complex128)
+    v0 = None
+    if guess is not None:
+        v0 = np.asarray(guess).sum(axis=0)
+    ncv = min(npw, max(2 * nb + 20, 40))
+    w, v = scipy.sparse.linalg.eigsh(op, k=nb, which="SA", tol=tol, v0=v0, ncv=ncv, maxiter=20000)
+    order = np.argsort(w)
+    return w[order], v[:, order].T.copy()
+
+
+def eigensolve(system, I, k, veff_I, nb, guess=None, dense_max=0):
+    npw = system.basis[I][k][0].shape[0]
+    if npw <= dense_max or npw <= nb + 2:
+        return eig_dense(system, I, k, veff_I, nb)
+    return eig_lanczos(system, I, k, veff_I, nb, guess)
+
+
+# ---------------------------------------------------------------- state
+class State:
+    """Orbitals, eigenvalues, occupations and densities of every subsystem."""
+
+    def __init__(self, system, coefs, occ, eigs, rhos, entropy):
+        self.coefs = coefs
+        self.occ = occ
+        self.eigs = eigs
+        self.rhos = rhos
+        self.entropy = entropy
+
+
+def initial_state(system, seed=None, density="atoms"):
+    """Initial orbitals from the seeded raw draws.  The initial density is the seeded
+    superposition of atom-centred Gaussians of ``workloads.initial_density``
+    (density="atoms"), or the density of the initial orbitals with equal occupations
+    N_I / (2 n_b) on every band (density="orbitals")."""
+    wl = system.wl
+    seed = wl.seed if seed is None else seed
+    coefs, occ, eigs, rhos = [], [], [], []
+    for I, s in enumerate(wl.subsystems):
+        ck = []
+        for k in range(s.nk):
+            npw = system.basis[I][k][0].shape[0]
+            raw = workloads.raw_orbitals(seed, I, k, s.nbands, npw)
+            ck.append(system.initial_orbitals(I, k, raw))
+        oc = [np.full(s.nbands, s.nelec / (2.0 * s.nbands)) for _ in range(s.nk)]
+        coefs.append(ck)
+        occ.append(oc)
+        eigs.append([np.zeros(s.nbands) for _ in range(s.nk)])
+        if density == "atoms":
+            rhos.append(workloads.initial_density(wl, I))
+        else:
+            rhos.append(system.density(I, ck, oc))
+    return State(system, coefs, occ, eigs, np.array(rhos), np.zeros(len(rhos)))
+
+
+def initial_density(system, I, seed):
+    s = system.subs[I]
+    ck = []
+    for k in range(s.nk):
+        npw = system.basis[I][k][0].shape[0]
+        ck.append(system.initial_orbitals(I, k, workloads.raw_orbitals(seed, I, k, s.nbands, npw)))
+    oc = [np.full(s.nbands, s.nelec / (2.0 * s.nbands)) for _ in range(s.nk)]
+    return ck, system.density(I, ck, oc)
+
+
+# ---------------------------------------------------------------- SCF
+class Pulay:
+    """DIIS on the density: minimise |sum c_i R_i| with sum c_i = 1, then
+    rho_next = sum c_i (rho_in_i + beta R_i)."""
+
+    def __init__(self, beta=0.3, history=8):
+        self.beta = beta
+        self.history = history
+        self.rin, self.res = [], []
+
+    def __call__(self, rho_in, rho_out):
+        self.rin.append(rho_in.copy())
+        self.res.append(rho_out - rho_in)
+        if len(self.rin) > self.history:
+            self.rin.pop(0)
+            self.res.pop(0)
+        m = len(self.res)
+        A = np.zeros((m + 1, m + 1))
+        for i in range(m):
+            for j in range(m):
+                A[i, j] = float(np.sum(self.res[i] * self.res[j]))
+        A[m, :m] = A[:m, m] = 1.0
+        b = np.zeros(m + 1)
+        b[m] = 1.0
+        try:
+            c = np.linalg.solve(A, b)[:m]
+        except np.linalg.LinAlgError:
+            c = np.zeros(m)
+            c[-1] = 1.0
+        return sum(ci * (r + self.beta * d) for ci, r, d in zip(c, self.rin, self.res))
+
+
+def solve_subsystem(system, I, rhos_frozen, rho_in, guess, tol, max_scf=100, dense_max=0,
+                    others=None, log=None):
+    """SCF of subsystem I with every other density frozen (one freeze step).
+
+    ``others`` = (coefs, occ) of the frozen subsystems, used only for the energy.
+    Converged when the FDE free energy changes by less than tol between iterations and
+    the density residual int|rho_out - rho_in| is below sqrt(tol)."""
+    s = system.subs[I]
+    mixer = Pulay()
+    rhos = np.array(rhos_frozen, copy=True)
+    E_prev = None
+    coefs = guess
+    for it in range(1, max_scf + 1):
+        rhos[I] = rho_in
+        pot = system.build_veff(rhos)
+        veff = pot["veff"][I]
+        eigs, new = [], []
+        for k in range(s.nk):
+            w, v = eigensolve(system, I, k, veff, s.nbands, coefs[k] if coefs else None, dense_max)
+            eigs.append(w)
+            new.append(v)
+        coefs = new
+        occ, mu, S = occupations(eigs, s.wk, s.nelec, s.smearing)
+        rho_out = system.density(I, coefs, occ)
+        rhos_out = rhos.copy()
+        rhos_out[I] = rho_out
+        oc_all = [None] * len(rhos)
+        cf_all = [None] * len(rhos)
+        ent = np.zeros(len(rhos))
+        for J in range(len(rhos)):
+            if J == I:
+                cf_all[J], oc_all[J] = coefs, occ
+                ent[J] = s.smearing * S
+            else:
+                cf_all[J], oc_all[J] = others[0][J], others[1][J]
+                ent[J] = others[2][J]
+        en = system.energies(cf_all, oc_all, rhos_out, entropy=ent)
+        dres = float(np.sum(np.abs(rho_out - rho_in))) * system.omega / system.nr
+        dE = None if E_prev is None else en["F_fde"] - E_prev
+        if log is not None:
+            log.append(dict(sub=I, it=it, F=en["F_fde"], dE=dE, dres=dres))
+        if E_prev is not None and abs(dE) < tol and dres < np.sqrt(tol):
+            return dict(coefs=coefs, occ=occ, eigs=eigs, rho=rho_out, S=S, mu=mu,
+                        iters=it, energies=en, converged=True)
+        E_prev = en["F_fde"]
+        rho_in = mixer(rho_in, rho_out)
+    return dict(coefs=coefs, occ=occ, eigs=eigs, rho=rho_out, S=S, mu=mu, iters=max_scf,
+                energies=en, converged=False)
+
+
+def freeze_thaw_cycle(system, state, tol=None, max_scf=100, dense_max=0, log=None):
+    """One Jacobi freeze-and-thaw cycle; returns the new state and the energies of the
+    refreshed total density."""
+    wl = system.wl
+    tol = wl.tol if tol is None else tol
+    rhos0 = np.array(state.rhos)
+    ent0 = np.array(state.entropy)
+    results = []
+    for I in range(len(rhos0)):
+        r = solve_subsystem(system, I, rhos0, rhos0[I], state.coefs[I], tol, max_scf,
+                            dense_max, others=(state.coefs, state.occ, ent0), log=log)
+        results.append(r)
+    coefs = [r["coefs"] for r in results]
+    occ = [r["occ"] for r in results]
+    eigs = [r["eigs"] for r in results]
+    rhos = np.array([r["rho"] for r in results])
+    ent = np.array([system.subs[I].smearing * r["S"] for I, r in enumerate(results)])
+    new = State(system, coefs, occ, eigs, rhos, ent)
+    en = system.energies(coefs, occ, rhos, entropy=ent)
+    en["converged"] = all(r["converged"] for r in results)
+    en["iters"] = [r["iters"] for r in results]
+    en["sub_energies"] = [r["energies"]["F_fde"] for r in results]
+    return new, en
+
+
+def freeze_thaw(system, state, tol=None, max_cycles=30, max_scf=100, dense_max=0, log=None):
+    """Freeze-and-thaw cycles until the FDE free energy changes by less than tol."""
+    wl = system.wl
+    tol = wl.tol if tol is None else tol
+    E_prev = None
+    history = []
+    for c in range(max_cycles):
+        state, en = freeze_thaw_cycle(system, state, tol, max_scf, dense_max, log)
+        history.append(en["F_fde"])
+        if E_prev is not None and abs(en["F_fde"] - E_prev) < tol:
+            en["cycles"] = c + 1
+            en["history"] = history
+            return state, en
+        E_prev = en["F_fde"]
+    en["cycles"] = max_cycles
+    en["history"] = history
+    en["converged"] = False
+    return state, en
