@@ -1,0 +1,229 @@
+/*
+ * fde.h -- C ABI of the GB300 periodic frozen-density-embedding (subsystem DFT) library.
+ *
+ * The library computes the data-parallel hot path of periodic subsystem DFT
+ * (Genova, Ceresoli & Pavanello, "Periodic Subsystem Density-Functional Theory",
+ * arXiv:1406.7803): the embedded plane-wave Kohn-Sham apply H_I psi for every subsystem I,
+ * the embedding-potential build that feeds it, the subsystem eigensolver and the
+ * freeze-and-thaw cycle around them.  Everything on that path runs in the library's own
+ * CUDA kernels on one GPU.
+ *
+ * Units: Hartree atomic units (bohr, Hartree).
+ *
+ * Conventions shared by every call:
+ *   - grid functions are real arrays in C order [n1][n2][n3] (n3 fastest); grid point
+ *     (i1,i2,i3) sits at sum_j (i_j/n_j) a_j.
+ *   - orbitals u_jk(r) = Omega^{-1/2} sum_G c_G e^{iG.r}, sum_G |c_G|^2 = 1; a block of
+ *     orbitals is band-major [nb][npw] of interleaved complex (re, im).  The sphere of one
+ *     k-point holds every G with |k+G|^2/2 <= ecut (FP64 test on the integer Miller
+ *     indices) sorted lexicographically by signed (m1, m2, m3) (fde_get_basis).
+ *   - forward transform f(G) = (1/N_r) sum_r f(r) e^{-iG.r}; Nyquist planes (m_j = -n_j/2,
+ *     n_j even) are zeroed in every reciprocal-space filter (Poisson, local potential,
+ *     gradient, divergence).
+ *
+ * Memory: pointers named d_* are device pointers owned by the caller (the library never
+ * frees or keeps them); pointers named h_* are host pointers owned by the caller.  The
+ * library owns its context memory (allocated with cudaMalloc at fde_create /
+ * fde_add_subsystem / first use, released by fde_destroy).  All device work is enqueued on
+ * the stream given to fde_create; calls that return host values synchronise that stream.
+ *
+ * Errors: no exception crosses the ABI.  Every call returns an fde_status; on failure the
+ * context keeps a message readable with fde_last_error.  A device-side status word is
+ * checked at the end of each synchronising call and maps to FDE_ENONFINITE.
+ */
+#ifndef FDE_H
+#define FDE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fde_ctx fde_ctx;
+
+typedef enum {
+  FDE_OK = 0,
+  FDE_EINVAL = -1,        /* bad argument (null pointer, index out of range, bad size) */
+  FDE_ENOMEM = -2,        /* device or host allocation failed */
+  FDE_ECUDA = -3,         /* a CUDA runtime call failed */
+  FDE_ENOCONV = -4,       /* an iteration reached its cap before its tolerance */
+  FDE_ENONFINITE = -5,    /* a density, potential or energy became NaN/Inf */
+  FDE_ETIMEOUT = -6,      /* reserved: bounded device waits that ran out */
+  FDE_EUNSUPPORTED = -7   /* a size or option outside what the kernels handle */
+} fde_status;
+
+typedef enum {
+  FDE_PREC_FP64 = 0,  /* everything in FP64 */
+  FDE_PREC_MIXED = 1  /* FP32 orbitals, FFTs and grid arithmetic; FP64 dense algebra,
+                         densities and energies */
+} fde_prec;
+
+enum { FDE_XC_LDA = 0, FDE_XC_PBE = 1 };                         /* exchange-correlation */
+enum { FDE_KEDF_TF = 0, FDE_KEDF_REVAPBEK = 1, FDE_KEDF_LC94 = 2 };  /* kinetic functional */
+enum { FDE_PRECOND_TPA = 0 };                                    /* Davidson preconditioner */
+
+/* Cell, shared real-space grid and wavefunction cutoff (Sec. 2: one shared grid holds rho
+ * and every potential, Eq. meth:1).  lattice rows are a_1, a_2, a_3 (bohr); the cell must
+ * be orthorhombic (diagonal lattice) -- other cells return FDE_EUNSUPPORTED.  Each grid
+ * size must factor into 2, 3 and 5 and be at most 512. */
+typedef struct {
+  double lattice[3][3];
+  int grid[3];
+  double ecut_ha;
+} fde_cell_desc;
+
+/* Functionals (Computational Details: PBE xc with LC94 or revAPBEK nonadditive kinetic
+ * energy; LDA and Thomas-Fermi are the simpler members of the same families). rho_cut:
+ * points with rho < rho_cut contribute no energy density and no potential. */
+typedef struct {
+  int xc;
+  int kedf;
+  double rho_cut;
+} fde_func_desc;
+
+/* One subsystem (Sec. 2: subsystem density with BZ integral and fractional occupations;
+ * Appendix: subsystem-specific projectors).  pos [natoms][3] bohr, Z [natoms]; every atom
+ * carries the local potential -Z erf(|r-R|/rc)/|r-R| and nproj_per_atom Gaussian s-type
+ * Kleinman-Bylander projectors of widths proj_sigma [nproj_per_atom] (bohr) coupled by
+ * proj_D [nproj_per_atom][nproj_per_atom] (Ha, symmetric).  kpts [nk][3] in crystal
+ * coordinates with weights wk [nk] summing to 1.  smearing_ha > 0: Fermi-Dirac occupations;
+ * 0: integer occupations (then nk must be 1 and nelec/2 an integer <= nbands).
+ * All arrays are host memory and are copied. */
+typedef struct {
+  int natoms;
+  const double* pos;
+  const double* Z;
+  double rc;
+  int nproj_per_atom;
+  const double* proj_sigma;
+  const double* proj_D;
+  int nbands;
+  int nk;
+  const double* kpts;
+  const double* wk;
+  double nelec;
+  double smearing_ha;
+} fde_subsys_desc;
+
+/* Energy terms of Eq. E_FDE (Sec. 2) for the current densities and orbitals:
+ *   E_fde = E_kin + E_nl + E_loc + E_H + E_xc + T_nad + E_nn
+ * with E_kin = sum_I T_J[rho_I] (Janak), E_nl the subsystem-specific nonlocal energy,
+ * E_loc = int v_loc rho (all nuclei), E_H = E_H[rho], E_xc = E_xc[rho],
+ * T_nad = T~[rho] - sum_I T~[rho_I], E_nn the Ewald nuclear repulsion.  TS = sum_I sigma_I S_I
+ * (Mermin entropy of smeared subsystems) and F_fde = E_fde - TS.  E_xc_nad and E_H_nad are
+ * the nonadditive parts E[rho] - sum_I E[rho_I].  E_band_form is E_fde evaluated by the
+ * band-energy ("deband") recast of the Appendix from the stored eigenvalues.  iters is the
+ * number of inner iterations the call made; dE the last energy change. */
+typedef struct {
+  double E_fde, F_fde, TS;
+  double E_kin, E_nl, E_loc, E_H, E_xc, T_nad, E_xc_nad, E_H_nad, E_nn;
+  double E_band_form;
+  int iters;
+  double dE;
+} fde_energies;
+
+/* Create a context on the current CUDA device.  cuda_stream is a cudaStream_t (NULL: the
+ * legacy default stream).  Errors: FDE_EINVAL (null/invalid descriptor), FDE_EUNSUPPORTED
+ * (non-orthorhombic cell, grid sizes), FDE_ENOMEM/FDE_ECUDA. */
+fde_status fde_create(const fde_cell_desc* cell, const fde_func_desc* func, fde_prec prec,
+                      void* cuda_stream, fde_ctx** out);
+
+/* Add a subsystem (copies every host array); builds its plane-wave spheres, FFT column
+ * maps and projector tables on the device.  *sub_id receives its index (0, 1, ...).
+ * The first call also fixes the set of atoms grouped in the all-nuclei local potential;
+ * adding subsystems after fde_build_vemb has run returns FDE_EINVAL. */
+fde_status fde_add_subsystem(fde_ctx* ctx, const fde_subsys_desc* desc, int* sub_id);
+
+/* Number of plane waves of (sub, k) and, if h_miller is not NULL, their Miller indices
+ * [npw][3] (host int) in the library's order. */
+fde_status fde_get_basis(fde_ctx* ctx, int sub, int k, int* npw, int* h_miller);
+
+/* Set the density rho_I of a subsystem from a real grid [n1][n2][n3] (FP64).  on_device:
+ * 1 if rho is a device pointer, 0 if host. */
+fde_status fde_set_density(fde_ctx* ctx, int sub, const double* rho, int on_device);
+
+/* Copy rho_I (sub >= 0) or rho = sum_I rho_I (sub = -1) to a caller device buffer. */
+fde_status fde_get_density(fde_ctx* ctx, int sub, double* d_rho);
+
+/* Recast effective potentials of every subsystem (Appendix, recast effective potential):
+ * V_eff^I = V_eN (all nuclei) + V_H[rho] + V_XC[rho_I] + V_XC^nad + V_kin^nad
+ *         = v_loc + v_H[rho] + v_xc[rho] + v~_kin[rho] - v~_kin[rho_I],
+ * with rho = sum_I rho_I (Eq. meth:1), v_H(G) = 4 pi rho(G)/|G|^2 (FFT Poisson solve),
+ * GGA gradients and divergences through FFTs and v~_kin from the Appendix's GGA derivative.
+ * Stored in the context for fde_apply_h.  d_veff_out (nullable): device [nsub][N_r] FP64
+ * copy.  e (nullable, synchronising): receives the grid energy terms E_loc, E_H, E_xc,
+ * T_nad, E_xc_nad, E_H_nad, E_nn (the orbital terms are left 0). */
+fde_status fde_build_vemb(fde_ctx* ctx, double* d_veff_out, fde_energies* e);
+
+/* Overwrite V_eff^I of one subsystem with a caller grid (device, FP64) -- for tests and
+ * for callers that build their own potentials. */
+fde_status fde_set_veff(fde_ctx* ctx, int sub, const double* d_veff);
+
+/* H_I psi for a block of nb orbitals of (sub, k) (Eq. KS with the nonlocal projectors of
+ * the atoms of I only, Appendix):
+ *   (H psi)(G) = |k+G|^2/2 psi(G) + P_sphere FFT[V_eff^I(r) . IFFT psi](G)
+ *              + sum_{a in I} sum_ij beta_ai(k+G) D_ij <beta_aj|psi>.
+ * d_psi, d_hpsi: device [nb][npw] complex, double2 in FDE_PREC_FP64 contexts and float2 in
+ * FDE_PREC_MIXED contexts; they must not overlap.  Asynchronous on the context stream. */
+fde_status fde_apply_h(fde_ctx* ctx, int sub, int k, const void* d_psi, void* d_hpsi, int nb);
+
+/* Same as fde_apply_h with host buffers (complex double [nb][npw] in both precisions);
+ * copies in and out through pinned staging inside the call; synchronising. */
+fde_status fde_apply_h_host(fde_ctx* ctx, int sub, int k, const double* h_psi, double* h_hpsi,
+                            int nb);
+
+/* H psi for every band of every (subsystem, k) of the context's stored orbitals, written
+ * into the context's H psi buffers: one batched pass of the hot path.  Asynchronous. */
+fde_status fde_apply_h_all(fde_ctx* ctx);
+
+/* Initial orbitals of (sub, k) from raw complex draws h_raw [nbands][npw][2] (host):
+ * c_G = raw_G / (1 + |k+G|^2/2), then orthonormalised on the device. */
+fde_status fde_init_orbitals(fde_ctx* ctx, int sub, int k, const double* h_raw);
+
+/* Replace / read the stored orbitals of (sub, k): device complex double [nbands][npw].
+ * h_eig, h_occ (nullable): host [nbands] eigenvalues and occupations. */
+fde_status fde_set_orbitals(fde_ctx* ctx, int sub, int k, const double* d_psi);
+fde_status fde_get_orbitals(fde_ctx* ctx, int sub, int k, double* d_psi, double* h_eig,
+                            double* h_occ);
+
+/* Block Davidson on (sub, k) with the current V_eff^I (Eq. KS): refines the stored orbitals
+ * and eigenvalues until every band's residual norm |H psi - eps psi| < tol or max_iter
+ * iterations.  *iters (nullable) receives the iteration count.  FDE_ENOCONV if not
+ * converged (the best orbitals are kept). */
+fde_status fde_subspace_solve(fde_ctx* ctx, int sub, int k, double tol, int max_iter,
+                              int precond, int* iters);
+
+/* Occupations of subsystem sub from its stored eigenvalues (Fermi-Dirac with bisection
+ * for the chemical potential, or integer filling), then rho_I = 2 sum_k w_k sum_j n_jk
+ * |u_jk|^2 (Sec. 2) from the stored orbitals.  The new density replaces rho_I. */
+fde_status fde_update_density(fde_ctx* ctx, int sub);
+
+/* Every energy term of the current state (synchronising). */
+fde_status fde_energy(fde_ctx* ctx, fde_energies* out);
+
+/* Self-consistent field of one subsystem with every other density frozen: repeat
+ * {build V_eff^I, Davidson on every k, occupations and density, Pulay mixing} until the
+ * FDE free energy changes by less than tol_ha and int|rho_out - rho_in| < sqrt(tol_ha).
+ * out (nullable) gets the energies. FDE_ENOCONV after max_scf iterations. */
+fde_status fde_scf_subsystem(fde_ctx* ctx, int sub, double tol_ha, int max_scf,
+                             fde_energies* out);
+
+/* One Jacobi freeze-and-thaw cycle (Fig. 1b: each subsystem's SCF runs to self-consistency
+ * before the densities are exchanged): every subsystem runs fde_scf_subsystem against the
+ * densities frozen at the start of the cycle, then every rho_I is refreshed together.
+ * out (nullable) receives the energies of the refreshed state. */
+fde_status fde_freeze_thaw_cycle(fde_ctx* ctx, double tol_ha, int max_scf, fde_energies* out);
+
+/* Synchronise the context stream and check the device status word. */
+fde_status fde_sync(fde_ctx* ctx);
+
+/* Message of the last failing call on this context ("" if none). */
+const char* fde_last_error(const fde_ctx* ctx);
+
+/* Release every device and host resource of the context. */
+fde_status fde_destroy(fde_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FDE_H */

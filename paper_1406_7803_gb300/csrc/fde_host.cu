@@ -1,0 +1,1320 @@
+// fde_host.cu -- context, plane-wave bases, plans and the C ABI of include/fde.h.
+//
+// Host code orchestrates the device work of one GPU: it builds the plane-wave spheres and
+// their FFT column maps, the twiddle tables, the projector tables and the work buffers,
+// and runs the block-Davidson eigensolver, the subsystem SCF and the freeze-and-thaw
+// cycle, whose every grid-, band- and subspace-sized step is a kernel of this library.
+// Only scalars (eigenvalues, norms, energies, DIIS coefficients) travel to the host.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "fde.h"
+#include "grid_kernels.h"
+#include "kernels.h"
+#include "small.h"
+
+namespace fde {
+
+struct Err {
+  fde_status st;
+  std::string msg;
+};
+
+#define CK(x)                                                                                   \
+  do {                                                                                          \
+    cudaError_t e_ = (x);                                                                       \
+    if (e_ != cudaSuccess) throw Err{FDE_ECUDA, std::string(#x) + ": " + cudaGetErrorString(e_)}; \
+  } while (0)
+#define REQ(c, s, m)              \
+  do {                            \
+    if (!(c)) throw Err{(s), (m)}; \
+  } while (0)
+
+template <typename X> struct DBuf {
+  X* p = nullptr;
+  size_t n = 0;
+  DBuf() = default;
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  DBuf(DBuf&& o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+  DBuf& operator=(DBuf&& o) noexcept {
+    if (this != &o) { release(); p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+    return *this;
+  }
+  ~DBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  void alloc(size_t count) {
+    release();
+    if (count) {
+      cudaError_t e = cudaMalloc(&p, count * sizeof(X));
+      if (e != cudaSuccess) { p = nullptr; throw Err{FDE_ENOMEM, "cudaMalloc failed"}; }
+      n = count;
+    }
+  }
+  void ensure(size_t count) {
+    if (count > n) alloc(count);
+  }
+};
+
+static const long double kPiL = 3.141592653589793238462643383279502884L;
+
+template <typename T> struct Plans {
+  DBuf<cplx<T>> tw[3];
+  FftPlans<T> fp;
+};
+
+static void factorize(int n, int* radix, int* nst) {
+  int m = n, k = 0;
+  while (m % 4 == 0 && k < kMaxStages) { radix[k++] = 4; m /= 4; }
+  while (m % 2 == 0 && k < kMaxStages) { radix[k++] = 2; m /= 2; }
+  while (m % 3 == 0 && k < kMaxStages) { radix[k++] = 3; m /= 3; }
+  while (m % 5 == 0 && k < kMaxStages) { radix[k++] = 5; m /= 5; }
+  REQ(m == 1, FDE_EUNSUPPORTED, "grid sizes must factor into 2, 3 and 5");
+  *nst = k;
+}
+
+template <typename T> static void make_plans(Plans<T>& P, const int grid[3], cudaStream_t) {
+  LinePlan<T>* lp[3] = {&P.fp.p1, &P.fp.p2, &P.fp.p3};
+  for (int a = 0; a < 3; ++a) {
+    const int n = grid[a];
+    std::vector<cplx<T>> h(n);
+    for (int m = 0; m < n; ++m) {
+      const long double ang = 2.0L * kPiL * (long double)m / (long double)n;
+      h[m] = mk<T>((T)cosl(ang), (T)(-sinl(ang)));
+    }
+    P.tw[a].alloc(n);
+    CK(cudaMemcpy(P.tw[a].p, h.data(), n * sizeof(cplx<T>), cudaMemcpyHostToDevice));
+    lp[a]->n = n;
+    factorize(n, lp[a]->radix, &lp[a]->nstages);
+    lp[a]->tw = P.tw[a].p;
+  }
+}
+
+// ---- host-side physics that is not on the data path ---------------------------------------
+// Ewald sum of point charges with a neutralising background (nuclear repulsion V_NN).
+static double ewald_energy(const double A[3][3], const double B[3][3], double omega, const std::vector<double>& pos,
+                           const std::vector<double>& Z) {
+  const int n = (int)Z.size();
+  const double eta = sqrt(M_PI) / cbrt(omega);
+  const double x = sqrt(-log(1e-16));
+  const double rmax = x / eta + 1.0, gmax = 2.0 * eta * x + 1.0;
+  int nl[3], ng[3];
+  for (int j = 0; j < 3; ++j) {
+    const double bn = sqrt(B[j][0] * B[j][0] + B[j][1] * B[j][1] + B[j][2] * B[j][2]);
+    const double an = sqrt(A[j][0] * A[j][0] + A[j][1] * A[j][1] + A[j][2] * A[j][2]);
+    nl[j] = (int)ceil(rmax * bn / (2 * M_PI)) + 1;
+    ng[j] = (int)ceil(gmax * an / (2 * M_PI)) + 1;
+  }
+  double er = 0.0;
+  for (int a = -nl[0]; a <= nl[0]; ++a)
+    for (int b = -nl[1]; b <= nl[1]; ++b)
+      for (int c = -nl[2]; c <= nl[2]; ++c) {
+        double L[3];
+        for (int d = 0; d < 3; ++d) L[d] = a * A[0][d] + b * A[1][d] + c * A[2][d];
+        for (int i = 0; i < n; ++i)
+          for (int j = 0; j < n; ++j) {
+            if (a == 0 && b == 0 && c == 0 && i == j) continue;
+            double r2 = 0;
+            for (int d = 0; d < 3; ++d) {
+              const double dd = pos[3 * i + d] - pos[3 * j + d] + L[d];
+              r2 += dd * dd;
+            }
+            const double r = sqrt(r2);
+            if (r < rmax) er += 0.5 * Z[i] * Z[j] * erfc(eta * r) / r;
+          }
+      }
+  double eg = 0.0;
+  for (int a = -ng[0]; a <= ng[0]; ++a)
+    for (int b = -ng[1]; b <= ng[1]; ++b)
+      for (int c = -ng[2]; c <= ng[2]; ++c) {
+        double G[3];
+        for (int d = 0; d < 3; ++d) G[d] = a * B[0][d] + b * B[1][d] + c * B[2][d];
+        const double g2 = G[0] * G[0] + G[1] * G[1] + G[2] * G[2];
+        if (g2 <= 0 || g2 >= gmax * gmax) continue;
+        double sr = 0, si = 0;
+        for (int i = 0; i < n; ++i) {
+          const double ph = G[0] * pos[3 * i] + G[1] * pos[3 * i + 1] + G[2] * pos[3 * i + 2];
+          sr += Z[i] * cos(ph);
+          si += Z[i] * sin(ph);
+        }
+        eg += exp(-g2 / (4 * eta * eta)) / g2 * (sr * sr + si * si);
+      }
+  eg *= 2.0 * M_PI / omega;
+  double z2 = 0, zs = 0;
+  for (int i = 0; i < n; ++i) { z2 += Z[i] * Z[i]; zs += Z[i]; }
+  return er + eg - eta / sqrt(M_PI) * z2 - M_PI * zs * zs / (2.0 * omega * eta * eta);
+}
+
+static inline double fermi(double x) {  // 1 / (1 + e^x)
+  if (x > 0) { const double e = exp(-x); return e / (1.0 + e); }
+  return 1.0 / (1.0 + exp(x));
+}
+
+// ---- per-(subsystem, k) and per-subsystem state ---------------------------------------------
+template <typename T> struct KP {
+  int npw = 0;
+  double kfrac[3] = {0, 0, 0}, kc[3] = {0, 0, 0};
+  std::vector<int> miller;
+  std::vector<double> kin;
+  DBuf<int> cols;
+  SphereDev sp{};
+  DBuf<T> kin_d;
+  DBuf<cplx<T>> beta;
+  DBuf<cplx<T>> X, HX;
+  std::vector<double> eig, occ;
+  bool have_orbitals = false;
+  bool have_eig = false;
+};
+
+template <typename T> struct Sub {
+  int natoms = 0, nproj_atom = 0, nproj = 0, nb = 0, nk = 0;
+  double rc = 0, nelec = 0, smearing = 0;
+  std::vector<double> pos, Z, sigma, D, kpts, wk;
+  std::vector<KP<T>> kp;
+  DBuf<double2> Dfull;
+  DBuf<double> rho, veff;
+  DBuf<T> vplane;
+  double entropy = 0, mu = 0;
+};
+
+struct EnergyParts {
+  double Eloc = 0, EH = 0, Exc = 0, Ttot = 0, Tsub = 0, Exc_sub = 0, EH_sub = 0;
+};
+
+// ---- the engine ------------------------------------------------------------------------------
+struct Engine {
+  virtual ~Engine() = default;
+  virtual int add_subsystem(const fde_subsys_desc* d) = 0;
+  virtual void get_basis(int sub, int k, int* npw, int* miller) = 0;
+  virtual void set_density(int sub, const double* rho, int on_device) = 0;
+  virtual void get_density(int sub, double* d_rho) = 0;
+  virtual void build_vemb(double* d_out, fde_energies* e) = 0;
+  virtual void set_veff(int sub, const double* d_v) = 0;
+  virtual void apply_h(int sub, int k, const void* psi, void* hpsi, int nb) = 0;
+  virtual void apply_h_host(int sub, int k, const double* psi, double* hpsi, int nb) = 0;
+  virtual void apply_h_all() = 0;
+  virtual void init_orbitals(int sub, int k, const double* raw) = 0;
+  virtual void set_orbitals(int sub, int k, const double* d_psi) = 0;
+  virtual void get_orbitals(int sub, int k, double* d_psi, double* eig, double* occ) = 0;
+  virtual fde_status subspace_solve(int sub, int k, double tol, int max_iter, int* iters) = 0;
+  virtual void update_density(int sub) = 0;
+  virtual void energy(fde_energies* out) = 0;
+  virtual fde_status scf_subsystem(int sub, double tol, int max_scf, fde_energies* out) = 0;
+  virtual fde_status freeze_thaw(double tol, int max_scf, fde_energies* out) = 0;
+  virtual void sync() = 0;
+};
+
+template <typename T> struct EngineT : Engine {
+  using C = cplx<T>;
+  cudaStream_t st;
+  double A[3][3], B[3][3], omega;
+  int grid[3];
+  GridDims g;
+  long long nr;
+  CellDev cell;
+  double ecut;
+  fde_func_desc func;
+  Plans<T> plans;
+  Plans<double> plans64;
+  std::vector<std::unique_ptr<Sub<T>>> subs;
+  bool locked = false;  // no more subsystems once the local potential exists
+  DBuf<double> vloc;
+  double enn = 0;
+  // grid work
+  DBuf<C> cb[5];
+  DBuf<double2> cvl;
+  DBuf<double> rho_tot, vcommon, vpart, vtmp, partial, scal;
+  DBuf<unsigned> status;
+  // band work
+  DBuf<C> scratch;
+  DBuf<double2> gwork, Pm, Qm;
+  DBuf<C> V, HV, V2, HV2, R;
+  DBuf<double2> S, Hs, L, Li, Ht, Y, Cc, tmp, jwork;
+  DBuf<double> wv, dnorm, deps, dtb;
+  DBuf<int> didx;
+  DBuf<double> rho_plane, occw;
+  // Pulay history and freeze-and-thaw copies
+  std::vector<DBuf<double>> hist_in, hist_res;
+  DBuf<double> rho_in, frozen, fresh;
+  DBuf<const double*> dptrs;
+  DBuf<double> dcoef;
+  // host staging
+  double* pin = nullptr;
+  size_t pin_n = 0;
+
+  EngineT(const fde_cell_desc* c, const fde_func_desc* f, cudaStream_t s) : st(s) {
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        A[i][j] = c->lattice[i][j];
+        if (i != j) REQ(c->lattice[i][j] == 0.0, FDE_EUNSUPPORTED, "only orthorhombic (diagonal) lattices");
+      }
+    for (int i = 0; i < 3; ++i) {
+      REQ(A[i][i] > 0, FDE_EINVAL, "lattice diagonal must be positive");
+      REQ(c->grid[i] >= 2 && c->grid[i] <= kMaxLine, FDE_EUNSUPPORTED, "grid sizes must be in [2, 320]");
+      grid[i] = c->grid[i];
+    }
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) B[i][j] = (i == j) ? 2.0 * M_PI * (1.0 / A[i][i]) : 0.0;
+    omega = A[0][0] * A[1][1] * A[2][2];
+    g = GridDims{grid[0], grid[1], grid[2]};
+    nr = (long long)grid[0] * grid[1] * grid[2];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) cell.b[i][j] = B[i][j];
+    cell.omega = omega;
+    ecut = c->ecut_ha;
+    REQ(ecut > 0, FDE_EINVAL, "ecut must be positive");
+    func = *f;
+    REQ(func.xc == FDE_XC_LDA || func.xc == FDE_XC_PBE, FDE_EINVAL, "unknown xc");
+    REQ(func.kedf >= 0 && func.kedf <= 2, FDE_EINVAL, "unknown kinetic functional");
+    REQ((size_t)g.n1 * (g.n2 + 1) * sizeof(C) <= 227 * 1024, FDE_EUNSUPPORTED,
+        "an (x, y) plane must fit in shared memory");
+    REQ(g.n1 <= kMaxPlane && g.n2 <= kMaxPlane, FDE_EUNSUPPORTED, "n1 and n2 must be at most 160");
+    make_plans(plans, grid, st);
+    make_plans(plans64, grid, st);
+    for (auto& b : cb) b.alloc(nr);
+    rho_tot.alloc(nr);
+    vcommon.alloc(nr);
+    vpart.alloc(nr);
+    vtmp.alloc(nr);
+    partial.alloc(64 * (size_t)grid_red_blocks());
+    scal.alloc(128);
+    status.alloc(1);
+    CK(cudaMemsetAsync(status.p, 0, sizeof(unsigned), st));
+    rho_plane.alloc(nr);
+  }
+  ~EngineT() override {
+    if (pin) cudaFreeHost(pin);
+  }
+
+  Sub<T>& sub(int i) {
+    REQ(i >= 0 && i < (int)subs.size(), FDE_EINVAL, "subsystem index out of range");
+    return *subs[i];
+  }
+  KP<T>& kpt(int i, int k) {
+    Sub<T>& s = sub(i);
+    REQ(k >= 0 && k < s.nk, FDE_EINVAL, "k-point index out of range");
+    return s.kp[k];
+  }
+  void sync() override {
+    CK(cudaStreamSynchronize(st));
+    unsigned h = 0;
+    CK(cudaMemcpy(&h, status.p, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    if (h & ST_NONFINITE) {
+      CK(cudaMemset(status.p, 0, sizeof(unsigned)));
+      throw Err{FDE_ENONFINITE, "non-finite value on the device"};
+    }
+  }
+
+  // ---- basis ------------------------------------------------------------------------------
+  void build_sphere(KP<T>& q) {
+    for (int c = 0; c < 3; ++c) q.kc[c] = q.kfrac[0] * B[0][c] + q.kfrac[1] * B[1][c] + q.kfrac[2] * B[2][c];
+    const double knorm = sqrt(q.kc[0] * q.kc[0] + q.kc[1] * q.kc[1] + q.kc[2] * q.kc[2]);
+    const double qmax = sqrt(2.0 * ecut) + knorm;
+    int lim[3];
+    for (int j = 0; j < 3; ++j) lim[j] = (int)ceil(qmax * A[j][j] / (2.0 * M_PI)) + 1;
+    q.miller.clear();
+    q.kin.clear();
+    for (int m1 = -lim[0]; m1 <= lim[0]; ++m1)
+      for (int m2 = -lim[1]; m2 <= lim[1]; ++m2)
+        for (int m3 = -lim[2]; m3 <= lim[2]; ++m3) {
+          double qv[3];
+          for (int c = 0; c < 3; ++c) {
+            const double gc = (double)m1 * B[0][c] + (double)m2 * B[1][c] + (double)m3 * B[2][c];
+            qv[c] = q.kc[c] + gc;
+          }
+          const double kk = 0.5 * (qv[0] * qv[0] + qv[1] * qv[1] + qv[2] * qv[2]);
+          if (kk <= ecut) {
+            q.miller.push_back(m1);
+            q.miller.push_back(m2);
+            q.miller.push_back(m3);
+            q.kin.push_back(kk);
+          }
+        }
+    q.npw = (int)q.kin.size();
+    REQ(q.npw > 0, FDE_EINVAL, "empty plane-wave sphere");
+    for (int j = 0; j < 3; ++j) {
+      int lo = 1 << 30, hi = -(1 << 30);
+      for (int p = 0; p < q.npw; ++p) { lo = std::min(lo, q.miller[3 * p + j]); hi = std::max(hi, q.miller[3 * p + j]); }
+      REQ(hi - lo + 1 <= grid[j], FDE_EINVAL, "plane-wave sphere does not fit the grid");
+    }
+    // columns (m1, m2) with contiguous m3 runs (enumeration order is already sorted)
+    std::vector<int> cs, m3lo, ci1, ci2;
+    for (int p = 0; p < q.npw; ++p) {
+      const int m1 = q.miller[3 * p], m2 = q.miller[3 * p + 1];
+      if (p == 0 || m1 != q.miller[3 * (p - 1)] || m2 != q.miller[3 * (p - 1) + 1]) {
+        cs.push_back(p);
+        m3lo.push_back(q.miller[3 * p + 2]);
+        ci1.push_back(((m1 % grid[0]) + grid[0]) % grid[0]);
+        ci2.push_back(((m2 % grid[1]) + grid[1]) % grid[1]);
+      }
+    }
+    const int ncol = (int)m3lo.size();
+    cs.push_back(q.npw);
+    std::vector<int> rows;
+    for (int c = 0; c < ncol; ++c)
+      if (std::find(rows.begin(), rows.end(), ci1[c]) == rows.end()) rows.push_back(ci1[c]);
+    std::vector<int> all;
+    all.insert(all.end(), cs.begin(), cs.end());
+    all.insert(all.end(), m3lo.begin(), m3lo.end());
+    all.insert(all.end(), ci1.begin(), ci1.end());
+    all.insert(all.end(), ci2.begin(), ci2.end());
+    all.insert(all.end(), rows.begin(), rows.end());
+    q.cols.alloc(all.size());
+    CK(cudaMemcpy(q.cols.p, all.data(), all.size() * sizeof(int), cudaMemcpyHostToDevice));
+    q.sp.npw = q.npw;
+    q.sp.ncol = ncol;
+    q.sp.nrow = (int)rows.size();
+    q.sp.col_start = q.cols.p;
+    q.sp.col_m3lo = q.cols.p + (ncol + 1);
+    q.sp.col_i1 = q.cols.p + (2 * ncol + 1);
+    q.sp.col_i2 = q.cols.p + (3 * ncol + 1);
+    q.sp.row_i1 = q.cols.p + (4 * ncol + 1);
+    std::vector<T> kt(q.npw);
+    for (int p = 0; p < q.npw; ++p) kt[p] = (T)q.kin[p];
+    q.kin_d.alloc(q.npw);
+    CK(cudaMemcpy(q.kin_d.p, kt.data(), q.npw * sizeof(T), cudaMemcpyHostToDevice));
+  }
+
+  void build_projectors(Sub<T>& s, KP<T>& q) {
+    if (s.nproj == 0) return;
+    std::vector<C> h((size_t)s.nproj * q.npw);
+    for (int p = 0; p < q.npw; ++p) {
+      double qv[3];
+      for (int c = 0; c < 3; ++c)
+        qv[c] = q.kc[c] + ((double)q.miller[3 * p] * B[0][c] + (double)q.miller[3 * p + 1] * B[1][c] +
+                           (double)q.miller[3 * p + 2] * B[2][c]);
+      const double q2 = qv[0] * qv[0] + qv[1] * qv[1] + qv[2] * qv[2];
+      for (int a = 0; a < s.natoms; ++a) {
+        const double ph = qv[0] * s.pos[3 * a] + qv[1] * s.pos[3 * a + 1] + qv[2] * s.pos[3 * a + 2];
+        const double cr = cos(ph), ci = -sin(ph);
+        for (int i = 0; i < s.nproj_atom; ++i) {
+          const double sg = s.sigma[i];
+          const double amp = pow(omega, -0.5) * pow(pow(M_PI, 1.5) * sg * sg * sg, -0.5) * pow(2.0 * M_PI * sg * sg, 1.5) *
+                             exp(-q2 * sg * sg / 2.0);
+          h[(size_t)(a * s.nproj_atom + i) * q.npw + p] = mk<T>((T)(amp * cr), (T)(amp * ci));
+        }
+      }
+    }
+    q.beta.alloc(h.size());
+    CK(cudaMemcpy(q.beta.p, h.data(), h.size() * sizeof(C), cudaMemcpyHostToDevice));
+  }
+
+  int add_subsystem(const fde_subsys_desc* d) override {
+    REQ(d, FDE_EINVAL, "null subsystem descriptor");
+    REQ(!locked, FDE_EINVAL, "subsystems must be added before the potentials are built");
+    REQ(d->natoms >= 0 && d->nbands > 0 && d->nk > 0, FDE_EINVAL, "bad subsystem sizes");
+    REQ(d->natoms == 0 || (d->pos && d->Z), FDE_EINVAL, "null atom arrays");
+    REQ(d->kpts && d->wk, FDE_EINVAL, "null k-point arrays");
+    REQ(d->nproj_per_atom >= 0 && (d->nproj_per_atom == 0 || (d->proj_sigma && d->proj_D)), FDE_EINVAL,
+        "null projector arrays");
+    if (d->smearing_ha <= 0) {
+      const double no = d->nelec / 2.0;
+      REQ(d->nk == 1 && fabs(no - round(no)) < 1e-12 && round(no) <= d->nbands && no >= 0, FDE_EINVAL,
+          "integer occupations need one k-point and nelec/2 <= nbands");
+    }
+    auto s = std::make_unique<Sub<T>>();
+    s->natoms = d->natoms;
+    s->nproj_atom = d->nproj_per_atom;
+    s->nproj = d->natoms * d->nproj_per_atom;
+    s->nb = d->nbands;
+    s->nk = d->nk;
+    s->rc = d->rc;
+    s->nelec = d->nelec;
+    s->smearing = d->smearing_ha;
+    s->pos.assign(d->pos, d->pos + 3 * d->natoms);
+    s->Z.assign(d->Z, d->Z + d->natoms);
+    if (s->nproj_atom) {
+      s->sigma.assign(d->proj_sigma, d->proj_sigma + s->nproj_atom);
+      s->D.assign(d->proj_D, d->proj_D + s->nproj_atom * s->nproj_atom);
+    }
+    s->kpts.assign(d->kpts, d->kpts + 3 * d->nk);
+    s->wk.assign(d->wk, d->wk + d->nk);
+    if (!subs.empty()) REQ(subs[0]->rc == s->rc, FDE_EINVAL, "one r_c for every atom");
+    s->kp.resize(s->nk);
+    for (int k = 0; k < s->nk; ++k) {
+      KP<T>& q = s->kp[k];
+      for (int c = 0; c < 3; ++c) q.kfrac[c] = s->kpts[3 * k + c];
+      build_sphere(q);
+      build_projectors(*s, q);
+      q.X.alloc((size_t)s->nb * q.npw);
+      q.HX.alloc((size_t)s->nb * q.npw);
+      q.eig.assign(s->nb, 0.0);
+      q.occ.assign(s->nb, 0.0);
+    }
+    if (s->nproj) {
+      std::vector<double2> Df((size_t)s->nproj * s->nproj, make_double2(0, 0));
+      for (int a = 0; a < s->natoms; ++a)
+        for (int i = 0; i < s->nproj_atom; ++i)
+          for (int j = 0; j < s->nproj_atom; ++j)
+            Df[(size_t)(a * s->nproj_atom + i) * s->nproj + a * s->nproj_atom + j] =
+                make_double2(s->D[i * s->nproj_atom + j], 0.0);
+      s->Dfull.alloc(Df.size());
+      CK(cudaMemcpy(s->Dfull.p, Df.data(), Df.size() * sizeof(double2), cudaMemcpyHostToDevice));
+    }
+    s->rho.alloc(nr);
+    s->veff.alloc(nr);
+    s->vplane.alloc(nr);
+    CK(cudaMemsetAsync(s->rho.p, 0, nr * sizeof(double), st));
+    CK(cudaMemsetAsync(s->veff.p, 0, nr * sizeof(double), st));
+    CK(cudaMemsetAsync(s->vplane.p, 0, nr * sizeof(T), st));
+    subs.push_back(std::move(s));
+    return (int)subs.size() - 1;
+  }
+
+  void get_basis(int i, int k, int* npw, int* miller) override {
+    KP<T>& q = kpt(i, k);
+    REQ(npw, FDE_EINVAL, "null npw");
+    *npw = q.npw;
+    if (miller) memcpy(miller, q.miller.data(), q.miller.size() * sizeof(int));
+  }
+
+  // ---- local potential of all nuclei and nuclear repulsion (once per geometry) -----------------
+  void ensure_vloc() {
+    if (locked) return;
+    REQ(!subs.empty(), FDE_EINVAL, "no subsystems");
+    std::vector<double> pos, Z;
+    for (auto& s : subs) {
+      pos.insert(pos.end(), s->pos.begin(), s->pos.end());
+      Z.insert(Z.end(), s->Z.begin(), s->Z.end());
+    }
+    vloc.alloc(nr);
+    cvl.alloc(nr);
+    const int na = (int)Z.size();
+    DBuf<double> dp, dz;
+    dp.alloc(std::max(1, 3 * na));
+    dz.alloc(std::max(1, na));
+    if (na) {
+      CK(cudaMemcpyAsync(dp.p, pos.data(), 3 * na * sizeof(double), cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(dz.p, Z.data(), na * sizeof(double), cudaMemcpyHostToDevice, st));
+    }
+    grid_vloc_g(cvl.p, g, cell, dp.p, dz.p, na, subs[0]->rc, st);
+    launch_fft3d<double>(cvl.p, g, plans64.fp, +1, st);
+    grid_c_to_real<double>(cvl.p, vloc.p, nr, st);
+    CK(cudaStreamSynchronize(st));
+    cvl.release();
+    enn = ewald_energy(A, B, omega, pos, Z);
+    locked = true;
+  }
+
+  // ---- densities ----------------------------------------------------------------------------
+  void set_density(int i, const double* rho, int on_device) override {
+    REQ(rho, FDE_EINVAL, "null density");
+    Sub<T>& s = sub(i);
+    CK(cudaMemcpyAsync(s.rho.p, rho, nr * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    if (!on_device) CK(cudaStreamSynchronize(st));
+  }
+  void sum_densities() {
+    CK(cudaMemcpyAsync(rho_tot.p, subs[0]->rho.p, nr * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    for (size_t I = 1; I < subs.size(); ++I)
+      grid_combine<T>(rho_tot.p, subs[I]->rho.p, nullptr, nullptr, 0.0, rho_tot.p, nr, st);
+  }
+  void get_density(int i, double* d_rho) override {
+    REQ(d_rho, FDE_EINVAL, "null output");
+    if (i == -1) {
+      REQ(!subs.empty(), FDE_EINVAL, "no subsystems");
+      sum_densities();
+      CK(cudaMemcpyAsync(d_rho, rho_tot.p, nr * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    } else {
+      CK(cudaMemcpyAsync(d_rho, sub(i).rho.p, nr * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    }
+  }
+
+  // ---- embedding-potential build --------------------------------------------------------------
+  bool gga_xc() const { return func.xc == FDE_XC_PBE; }
+  bool gga_kin() const { return func.kedf != FDE_KEDF_TF; }
+
+  // Gradient of the density held (forward-transformed, unscaled) in cb[0] into cb[2..4] (real).
+  void gradient_from_cb0() {
+    grid_gradient_g<T>(cb[0].p, cb[2].p, cb[3].p, cb[4].p, g, cell, st);
+    for (int c = 2; c < 5; ++c) launch_fft3d<T>(cb[c].p, g, plans.fp, +1, st);
+  }
+  // Divergence of h held (real) in cb[2..4]; result (real part) in cb[2].
+  void divergence_cb234() {
+    for (int c = 2; c < 5; ++c) launch_fft3d<T>(cb[c].p, g, plans.fp, -1, st);
+    grid_divergence_g<T>(cb[2].p, cb[3].p, cb[4].p, g, cell, st);
+    launch_fft3d<T>(cb[2].p, g, plans.fp, +1, st);
+  }
+
+  // Builds the potentials (want_pot) of the subsystems in `which` (-1 all) and/or the grid
+  // energy terms (want_e); slots of scal: 0 E_H, 1/2 E_xc/T_tot, 3 E_loc, then per
+  // subsystem 4+3I: E_H[rho_I], 5+3I: E_xc[rho_I], 6+3I: T[rho_I].
+  EnergyParts grid_pass(bool want_pot, bool want_e, int which) {
+    ensure_vloc();
+    REQ(4 + 3 * subs.size() <= 120, FDE_EUNSUPPORTED, "too many subsystems for one energy pass");
+    const int nrb = grid_red_blocks();
+    const double dv = omega / (double)nr;
+    sum_densities();
+    grid_real_to_c<T>(rho_tot.p, cb[0].p, nr, st);
+    launch_fft3d<T>(cb[0].p, g, plans.fp, -1, st);
+    grid_poisson<T>(cb[0].p, want_pot ? cb[1].p : nullptr, g, cell, partial.p, st);
+    grid_finalize(partial.p, 1, 0.5 * omega, scal.p + 0, st);
+    if (want_pot) launch_fft3d<T>(cb[1].p, g, plans.fp, +1, st);
+    const bool grad = gga_xc() || gga_kin();
+    if (grad) gradient_from_cb0();
+    grid_pointwise<T>(rho_tot.p, grad ? cb[2].p : nullptr, grad ? cb[3].p : nullptr, grad ? cb[4].p : nullptr, nr,
+                      func.xc, 1, func.kedf, func.rho_cut, want_pot ? vpart.p : nullptr, partial.p, st);
+    grid_finalize(partial.p, 2, dv, scal.p + 1, st);
+    grid_dot_partial(vloc.p, rho_tot.p, nr, 0, partial.p, st);
+    grid_finalize(partial.p, 1, dv, scal.p + 3, st);
+    if (want_pot) {
+      grid_combine<T>(vloc.p, vpart.p, nullptr, cb[1].p, 1.0, vcommon.p, nr, st);
+      if (grad) {
+        divergence_cb234();
+        grid_combine<T>(vcommon.p, nullptr, nullptr, cb[2].p, -1.0, vcommon.p, nr, st);
+      }
+    }
+    for (size_t I = 0; I < subs.size(); ++I) {
+      const bool pot_I = want_pot && (which < 0 || which == (int)I);
+      if (!pot_I && !want_e) continue;
+      Sub<T>& s = *subs[I];
+      grid_real_to_c<T>(s.rho.p, cb[0].p, nr, st);
+      launch_fft3d<T>(cb[0].p, g, plans.fp, -1, st);
+      if (want_e) {
+        grid_poisson<T>(cb[0].p, nullptr, g, cell, partial.p, st);
+        grid_finalize(partial.p, 1, 0.5 * omega, scal.p + 4 + 3 * I, st);
+      }
+      const bool gI = gga_kin() || (want_e && gga_xc());
+      if (gI) gradient_from_cb0();
+      grid_pointwise<T>(s.rho.p, gI ? cb[2].p : nullptr, gI ? cb[3].p : nullptr, gI ? cb[4].p : nullptr, nr,
+                        want_e ? func.xc : -1, 0, func.kedf, func.rho_cut, pot_I ? vpart.p : nullptr, partial.p, st);
+      grid_finalize(partial.p, 2, dv, scal.p + 5 + 3 * I, st);
+      if (pot_I) {
+        // v_eff^I = v_common - v~_kin[rho_I] = v_common - vpart_I + div h_I
+        CK(cudaMemcpyAsync(s.veff.p, vcommon.p, nr * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        grid_axpy(s.veff.p, vpart.p, -1.0, nr, st);
+        if (gga_kin()) {
+          divergence_cb234();
+          grid_combine<T>(s.veff.p, nullptr, nullptr, cb[2].p, 1.0, s.veff.p, nr, st);
+        }
+        grid_nonfinite(s.veff.p, nr, status.p, st);
+        to_plane(s);
+      }
+    }
+    (void)nrb;
+    EnergyParts ep;
+    if (want_e) {
+      std::vector<double> h(4 + 3 * subs.size());
+      CK(cudaMemcpyAsync(h.data(), scal.p, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+      sync();
+      ep.EH = h[0];
+      ep.Exc = h[1];
+      ep.Ttot = h[2];
+      ep.Eloc = h[3];
+      for (size_t I = 0; I < subs.size(); ++I) {
+        ep.EH_sub += h[4 + 3 * I];
+        ep.Exc_sub += h[5 + 3 * I];
+        ep.Tsub += h[6 + 3 * I];
+      }
+    }
+    return ep;
+  }
+  void neg_add(double* a, const double* b) { grid_axpy(a, b, -1.0, nr, st); }
+  void to_plane(Sub<T>& s) {
+    launch_transpose<double, T>(s.veff.p, s.vplane.p, (int)((long long)g.n1 * g.n2), g.n3, 0, st);
+  }
+
+  void build_vemb(double* d_out, fde_energies* e) override {
+    locked = false;
+    ensure_vloc();
+    EnergyParts ep = grid_pass(true, e != nullptr, -1);
+    if (d_out)
+      for (size_t I = 0; I < subs.size(); ++I)
+        CK(cudaMemcpyAsync(d_out + I * nr, subs[I]->veff.p, nr * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if (e) {
+      memset(e, 0, sizeof(*e));
+      e->E_loc = ep.Eloc;
+      e->E_H = ep.EH;
+      e->E_xc = ep.Exc;
+      e->T_nad = ep.Ttot - ep.Tsub;
+      e->E_xc_nad = ep.Exc - ep.Exc_sub;
+      e->E_H_nad = ep.EH - ep.EH_sub;
+      e->E_nn = enn;
+    }
+  }
+
+  void set_veff(int i, const double* d_v) override {
+    REQ(d_v, FDE_EINVAL, "null potential");
+    Sub<T>& s = sub(i);
+    CK(cudaMemcpyAsync(s.veff.p, d_v, nr * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    to_plane(s);
+  }
+
+  // ---- H psi ----------------------------------------------------------------------------------
+  void apply_h_dev(Sub<T>& s, KP<T>& q, const C* psi, C* hpsi, int nb) {
+    scratch.ensure((size_t)nb * g.n3 * q.sp.ncol);
+    launch_hpsi_local<T>(psi, q.npw, hpsi, q.npw, nb, q.kin_d.p, s.vplane.p, scratch.p, q.sp, g, plans.fp, st);
+    if (s.nproj) {
+      gwork.ensure(gemm_hn_work(s.nproj, nb, q.npw));
+      Pm.ensure((size_t)s.nproj * nb);
+      Qm.ensure((size_t)s.nproj * nb);
+      launch_gemm_hn<T>(q.beta.p, q.npw, psi, q.npw, s.nproj, nb, q.npw, Pm.p, nb, gwork.p, st);
+      launch_gemm_rot<double>(Pm.p, nb, s.Dfull.p, s.nproj, s.nproj, s.nproj, nb, Qm.p, nb, 1.0, 0.0, st);
+      launch_gemm_rot<T>(q.beta.p, q.npw, Qm.p, nb, s.nproj, nb, q.npw, hpsi, q.npw, 1.0, 1.0, st);
+    }
+  }
+  void apply_h(int i, int k, const void* psi, void* hpsi, int nb) override {
+    REQ(psi && hpsi, FDE_EINVAL, "null orbital buffers");
+    REQ(nb > 0, FDE_EINVAL, "nb must be positive");
+    Sub<T>& s = sub(i);
+    KP<T>& q = kpt(i, k);
+    apply_h_dev(s, q, (const C*)psi, (C*)hpsi, nb);
+  }
+  void apply_h_host(int i, int k, const double* psi, double* hpsi, int nb) override {
+    REQ(psi && hpsi && nb > 0, FDE_EINVAL, "bad host buffers");
+    Sub<T>& s = sub(i);
+    KP<T>& q = kpt(i, k);
+    const size_t n = (size_t)nb * q.npw;
+    if (pin_n < 2 * n) {
+      if (pin) cudaFreeHost(pin);
+      pin = nullptr;
+      CK(cudaMallocHost(&pin, 2 * n * sizeof(double2)));
+      pin_n = 2 * n;
+    }
+    V.ensure(n);
+    V2.ensure(n);
+    DBuf<double2>& d64 = S;  // staging in FP64 complex
+    d64.ensure(n);
+    memcpy(pin, psi, n * sizeof(double2));
+    CK(cudaMemcpyAsync(d64.p, pin, n * sizeof(double2), cudaMemcpyHostToDevice, st));
+    convert_in(d64.p, V.p, n);
+    apply_h_dev(s, q, V.p, V2.p, nb);
+    convert_out(V2.p, d64.p, n);
+    CK(cudaMemcpyAsync(pin + 2 * n, d64.p, n * sizeof(double2), cudaMemcpyDeviceToHost, st));
+    sync();
+    memcpy(hpsi, pin + 2 * n, n * sizeof(double2));
+  }
+  void convert_in(const double2* a, C* b, size_t n);
+  void convert_out(const C* a, double2* b, size_t n);
+
+  void apply_h_all() override {
+    for (auto& sp : subs)
+      for (auto& q : sp->kp) apply_h_dev(*sp, q, q.X.p, q.HX.p, sp->nb);
+  }
+
+  // ---- orbitals -------------------------------------------------------------------------------
+  void init_orbitals(int i, int k, const double* raw) override {
+    REQ(raw, FDE_EINVAL, "null raw draws");
+    Sub<T>& s = sub(i);
+    KP<T>& q = kpt(i, k);
+    const size_t n = (size_t)s.nb * q.npw;
+    DBuf<double2> tmpd;
+    tmpd.alloc(n);
+    CK(cudaMemcpyAsync(tmpd.p, raw, n * sizeof(double2), cudaMemcpyHostToDevice, st));
+    convert_in(tmpd.p, q.X.p, n);
+    launch_shape_init<T>(q.X.p, q.npw, q.kin_d.p, s.nb, q.npw, st);
+    orthonormalize(q, s.nb);
+    CK(cudaStreamSynchronize(st));
+    q.have_orbitals = true;
+    q.have_eig = false;
+  }
+  // X <- X L^{-H} with S = X^H X = L L^H (Cholesky-QR)
+  void orthonormalize(KP<T>& q, int nb) {
+    ensure_small(nb);
+    V2.ensure((size_t)nb * q.npw);
+    gwork.ensure(gemm_hn_work(nb, nb, q.npw));
+    launch_gemm_hn<T>(q.X.p, q.npw, q.X.p, q.npw, nb, nb, q.npw, S.p, nb, gwork.p, st);
+    launch_hermitize(S.p, nb, st);
+    launch_cholesky_inv(S.p, nb, L.p, Li.p, status.p, st);
+    check_cholesky();
+    // U[i][j] = conj(Li[j][i])
+    launch_small_gemm(Li.p, nb, 1, identity(nb), nb, 0, nb, nb, nb, Cc.p, nb, st);
+    launch_gemm_rot<T>(q.X.p, q.npw, Cc.p, nb, nb, nb, q.npw, V2.p, q.npw, 1.0, 0.0, st);
+    CK(cudaMemcpyAsync(q.X.p, V2.p, (size_t)nb * q.npw * sizeof(C), cudaMemcpyDeviceToDevice, st));
+  }
+  DBuf<double2> eye;
+  int eye_n = 0;
+  const double2* identity(int n) {
+    if (eye_n != n) {
+      std::vector<double2> h((size_t)n * n, make_double2(0, 0));
+      for (int i = 0; i < n; ++i) h[(size_t)i * n + i] = make_double2(1, 0);
+      eye.alloc(h.size());
+      CK(cudaMemcpy(eye.p, h.data(), h.size() * sizeof(double2), cudaMemcpyHostToDevice));
+      eye_n = n;
+    }
+    REQ(eye_n == n, FDE_EINVAL, "identity size");
+    return eye.p;
+  }
+  void check_cholesky() {
+    unsigned h = 0;
+    CK(cudaMemcpyAsync(&h, status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (h & ST_CHOLESKY) {
+      CK(cudaMemsetAsync(status.p, 0, sizeof(unsigned), st));
+      throw Err{FDE_ENOCONV, "overlap matrix is not positive definite (linearly dependent vectors)"};
+    }
+  }
+  void ensure_small(int n) {
+    const size_t n2 = (size_t)n * n;
+    S.ensure(n2); Hs.ensure(n2); L.ensure(n2); Li.ensure(n2); Ht.ensure(n2); Y.ensure(n2); Cc.ensure(n2);
+    tmp.ensure(n2); jwork.ensure(n2);
+    wv.ensure(n); dnorm.ensure(n); deps.ensure(n); dtb.ensure(n); didx.ensure(n);
+  }
+
+  void set_orbitals(int i, int k, const double* d_psi) override {
+    REQ(d_psi, FDE_EINVAL, "null orbitals");
+    Sub<T>& s = sub(i);
+    KP<T>& q = kpt(i, k);
+    convert_in((const double2*)d_psi, q.X.p, (size_t)s.nb * q.npw);
+    q.have_orbitals = true;
+    q.have_eig = false;
+  }
+  void get_orbitals(int i, int k, double* d_psi, double* eig, double* occ) override {
+    Sub<T>& s = sub(i);
+    KP<T>& q = kpt(i, k);
+    if (d_psi) convert_out(q.X.p, (double2*)d_psi, (size_t)s.nb * q.npw);
+    if (eig) memcpy(eig, q.eig.data(), s.nb * sizeof(double));
+    if (occ) memcpy(occ, q.occ.data(), s.nb * sizeof(double));
+    CK(cudaStreamSynchronize(st));
+  }
+
+  // ---- Rayleigh-Ritz on the n rows of V / HV; keeps the lowest nb pairs in V2 / HV2 ------------
+  void rayleigh_ritz(KP<T>& q, int n, int nb, std::vector<double>& eps) {
+    const int K = q.npw;
+    gwork.ensure(gemm_hn_work(n, n, K));
+    launch_gemm_hn<T>(V.p, K, V.p, K, n, n, K, S.p, n, gwork.p, st);
+    launch_gemm_hn<T>(V.p, K, HV.p, K, n, n, K, Hs.p, n, gwork.p, st);
+    launch_hermitize(S.p, n, st);
+    launch_hermitize(Hs.p, n, st);
+    launch_cholesky_inv(S.p, n, L.p, Li.p, status.p, st);
+    check_cholesky();
+    launch_small_gemm(Li.p, n, 0, Hs.p, n, 0, n, n, n, tmp.p, n, st);
+    launch_small_gemm(tmp.p, n, 0, Li.p, n, 1, n, n, n, Ht.p, n, st);
+    launch_hermitize(Ht.p, n, st);
+    launch_jacobi_eig(Ht.p, n, wv.p, Y.p, jwork.p, st);
+    launch_small_gemm(Li.p, n, 1, Y.p, n, 0, n, n, n, Cc.p, n, st);
+    launch_gemm_rot<T>(V.p, K, Cc.p, n, n, nb, K, V2.p, K, 1.0, 0.0, st);
+    launch_gemm_rot<T>(HV.p, K, Cc.p, n, n, nb, K, HV2.p, K, 1.0, 0.0, st);
+    eps.resize(n);
+    CK(cudaMemcpyAsync(eps.data(), wv.p, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    eps.resize(nb);
+  }
+
+  fde_status subspace_solve(int i, int k, double tol, int max_iter, int* iters) override {
+    Sub<T>& s = sub(i);
+    KP<T>& q = kpt(i, k);
+    REQ(q.have_orbitals, FDE_EINVAL, "orbitals of this (subsystem, k) are not set");
+    const int nb = s.nb, K = q.npw;
+    const size_t rowsz = (size_t)K * sizeof(C);
+    V.ensure((size_t)2 * nb * K);
+    HV.ensure((size_t)2 * nb * K);
+    V2.ensure((size_t)2 * nb * K);
+    HV2.ensure((size_t)2 * nb * K);
+    R.ensure((size_t)nb * K);
+    ensure_small(2 * nb);
+    std::vector<double> eps;
+    // Rayleigh-Ritz on the current orbitals
+    CK(cudaMemcpyAsync(V.p, q.X.p, nb * rowsz, cudaMemcpyDeviceToDevice, st));
+    apply_h_dev(s, q, V.p, HV.p, nb);
+    rayleigh_ritz(q, nb, nb, eps);
+    CK(cudaMemcpyAsync(V.p, V2.p, nb * rowsz, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(HV.p, HV2.p, nb * rowsz, cudaMemcpyDeviceToDevice, st));
+    int it = 0;
+    bool conv = false;
+    std::vector<double> rn(nb), tb(nb), sc(nb);
+    for (;;) {
+      CK(cudaMemcpyAsync(deps.p, eps.data(), nb * sizeof(double), cudaMemcpyHostToDevice, st));
+      launch_residual<T>(HV.p, V.p, deps.p, nb, K, K, R.p, K, st);
+      launch_row_norms<T>(R.p, K, nb, K, nullptr, dnorm.p, nullptr, st);
+      CK(cudaMemcpyAsync(rn.data(), dnorm.p, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      std::vector<int> sel;
+      for (int j = 0; j < nb; ++j) {
+        REQ(std::isfinite(rn[j]), FDE_ENONFINITE, "non-finite residual");
+        if (sqrt(rn[j]) >= tol) sel.push_back(j);
+      }
+      if (sel.empty()) { conv = true; break; }
+      if (it >= max_iter) break;
+      ++it;
+      const int m = (int)sel.size();
+      CK(cudaMemcpyAsync(didx.p, sel.data(), m * sizeof(int), cudaMemcpyHostToDevice, st));
+      C* W = V.p + (size_t)nb * K;
+      launch_gather_rows<T>(R.p, K, didx.p, m, K, W, K, st);
+      // band kinetic energies of the selected bands -> TPA preconditioner
+      launch_row_norms<T>(V.p, K, nb, K, q.kin_d.p, dnorm.p, nullptr, st);
+      CK(cudaMemcpyAsync(tb.data(), dnorm.p, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      std::vector<double> tsel(m);
+      for (int a = 0; a < m; ++a) tsel[a] = tb[sel[a]];
+      CK(cudaMemcpyAsync(dtb.p, tsel.data(), m * sizeof(double), cudaMemcpyHostToDevice, st));
+      launch_tpa<T>(W, K, q.kin_d.p, dtb.p, m, K, W, K, st);
+      // orthogonalise against the current orbitals and normalise
+      gwork.ensure(gemm_hn_work(nb, m, K));
+      launch_gemm_hn<T>(V.p, K, W, K, nb, m, K, Cc.p, m, gwork.p, st);
+      launch_gemm_rot<T>(V.p, K, Cc.p, m, nb, m, K, W, K, -1.0, 1.0, st);
+      launch_row_norms<T>(W, K, m, K, nullptr, dnorm.p, nullptr, st);
+      CK(cudaMemcpyAsync(sc.data(), dnorm.p, m * sizeof(double), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      for (int a = 0; a < m; ++a) sc[a] = 1.0 / sqrt(std::max(sc[a], 1e-300));
+      CK(cudaMemcpyAsync(dtb.p, sc.data(), m * sizeof(double), cudaMemcpyHostToDevice, st));
+      launch_scale_rows<T>(W, K, m, K, dtb.p, st);
+      apply_h_dev(s, q, W, HV.p + (size_t)nb * K, m);
+      try {
+        rayleigh_ritz(q, nb + m, nb, eps);
+      } catch (Err& e) {
+        if (e.st != FDE_ENOCONV) throw;
+        break;  // dependent search directions: keep the current orbitals
+      }
+      CK(cudaMemcpyAsync(V.p, V2.p, nb * rowsz, cudaMemcpyDeviceToDevice, st));
+      CK(cudaMemcpyAsync(HV.p, HV2.p, nb * rowsz, cudaMemcpyDeviceToDevice, st));
+    }
+    CK(cudaMemcpyAsync(q.X.p, V.p, nb * rowsz, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(q.HX.p, HV.p, nb * rowsz, cudaMemcpyDeviceToDevice, st));
+    q.eig = eps;
+    q.have_eig = true;
+    CK(cudaStreamSynchronize(st));
+    if (iters) *iters = it;
+    return conv ? FDE_OK : FDE_ENOCONV;
+  }
+
+  // ---- occupations and density ----------------------------------------------------------------
+  void occupations(Sub<T>& s) {
+    if (s.smearing <= 0) {
+      const int no = (int)llround(s.nelec / 2.0);
+      KP<T>& q = s.kp[0];
+      std::vector<int> order(s.nb);
+      for (int j = 0; j < s.nb; ++j) order[j] = j;
+      std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return q.eig[a] < q.eig[b]; });
+      q.occ.assign(s.nb, 0.0);
+      for (int j = 0; j < no; ++j) q.occ[order[j]] = 1.0;
+      s.entropy = 0.0;
+      s.mu = no ? q.eig[order[no - 1]] : q.eig[order[0]];
+      return;
+    }
+    double lo = 1e300, hi = -1e300;
+    for (auto& q : s.kp)
+      for (double e : q.eig) { lo = std::min(lo, e); hi = std::max(hi, e); }
+    lo -= 40.0 * s.smearing;
+    hi += 40.0 * s.smearing;
+    double mu = 0.5 * (lo + hi);
+    for (int it = 0; it < 300; ++it) {
+      mu = 0.5 * (lo + hi);
+      double n = 0;
+      for (int k = 0; k < s.nk; ++k)
+        for (double e : s.kp[k].eig) n += 2.0 * s.wk[k] * fermi((e - mu) / s.smearing);
+      if (fabs(n - s.nelec) < 1e-13) break;
+      if (n < s.nelec) lo = mu; else hi = mu;
+    }
+    double S = 0;
+    for (int k = 0; k < s.nk; ++k) {
+      KP<T>& q = s.kp[k];
+      q.occ.resize(s.nb);
+      for (int j = 0; j < s.nb; ++j) {
+        const double n = fermi((q.eig[j] - mu) / s.smearing);
+        q.occ[j] = n;
+        double t = 0;
+        if (n > 0) t += n * log(n);
+        if (n < 1) t += (1 - n) * log(1 - n);
+        S -= 2.0 * s.wk[k] * t;
+      }
+    }
+    s.mu = mu;
+    s.entropy = s.smearing * S;
+  }
+
+  void density_from_orbitals(Sub<T>& s, double* out) {
+    occw.ensure(s.nb);
+    for (int k = 0; k < s.nk; ++k) {
+      KP<T>& q = s.kp[k];
+      std::vector<double> w(s.nb);
+      for (int j = 0; j < s.nb; ++j) w[j] = 2.0 * s.wk[k] * q.occ[j] / omega;
+      CK(cudaMemcpyAsync(occw.p, w.data(), s.nb * sizeof(double), cudaMemcpyHostToDevice, st));
+      scratch.ensure((size_t)s.nb * g.n3 * q.sp.ncol);
+      launch_density<T>(q.X.p, q.npw, s.nb, occw.p, scratch.p, rho_plane.p, k > 0, q.sp, g, plans.fp, st);
+      CK(cudaStreamSynchronize(st));  // occw is reused by the next k
+    }
+    launch_transpose<double, double>(rho_plane.p, out, g.n3, (int)((long long)g.n1 * g.n2), 0, st);
+    grid_nonfinite(out, nr, status.p, st);
+  }
+
+  void update_density(int i) override {
+    Sub<T>& s = sub(i);
+    for (auto& q : s.kp) REQ(q.have_eig, FDE_EINVAL, "eigenvalues not available: run fde_subspace_solve first");
+    occupations(s);
+    density_from_orbitals(s, s.rho.p);
+    sync();
+  }
+
+  // ---- energies ---------------------------------------------------------------------------------
+  // Janak kinetic and nonlocal energies of one subsystem's stored orbitals.
+  void band_terms(Sub<T>& s, double* T_J, double* E_nl) {
+    *T_J = 0;
+    *E_nl = 0;
+    std::vector<double> t(s.nb);
+    for (int k = 0; k < s.nk; ++k) {
+      KP<T>& q = s.kp[k];
+      if (!q.have_orbitals) continue;
+      dnorm.ensure(s.nb);
+      launch_row_norms<T>(q.X.p, q.npw, s.nb, q.npw, q.kin_d.p, dnorm.p, nullptr, st);
+      CK(cudaMemcpyAsync(t.data(), dnorm.p, s.nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      for (int j = 0; j < s.nb; ++j) *T_J += 2.0 * s.wk[k] * q.occ[j] * t[j];
+      if (s.nproj) {
+        gwork.ensure(gemm_hn_work(s.nproj, s.nb, q.npw));
+        Pm.ensure((size_t)s.nproj * s.nb);
+        launch_gemm_hn<T>(q.beta.p, q.npw, q.X.p, q.npw, s.nproj, s.nb, q.npw, Pm.p, s.nb, gwork.p, st);
+        std::vector<double2> P((size_t)s.nproj * s.nb);
+        CK(cudaMemcpyAsync(P.data(), Pm.p, P.size() * sizeof(double2), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        for (int j = 0; j < s.nb; ++j) {
+          double e = 0;
+          for (int a = 0; a < s.natoms; ++a)
+            for (int p1 = 0; p1 < s.nproj_atom; ++p1)
+              for (int p2 = 0; p2 < s.nproj_atom; ++p2) {
+                const double2 x = P[(size_t)(a * s.nproj_atom + p1) * s.nb + j];
+                const double2 y = P[(size_t)(a * s.nproj_atom + p2) * s.nb + j];
+                e += s.D[p1 * s.nproj_atom + p2] * (x.x * y.x + x.y * y.y);
+              }
+          *E_nl += 2.0 * s.wk[k] * q.occ[j] * e;
+        }
+      }
+    }
+  }
+
+  double integrate_product(const double* a, const double* b) {
+    grid_dot_partial(a, b, nr, 0, partial.p, st);
+    grid_finalize(partial.p, 1, omega / (double)nr, scal.p + 127, st);
+    double h = 0;
+    CK(cudaMemcpyAsync(&h, scal.p + 127, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return h;
+  }
+  double integrate_absdiff(const double* a, const double* b) {
+    grid_dot_partial(a, b, nr, 1, partial.p, st);
+    grid_finalize(partial.p, 1, omega / (double)nr, scal.p + 127, st);
+    double h = 0;
+    CK(cudaMemcpyAsync(&h, scal.p + 127, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return h;
+  }
+
+  void energy(fde_energies* out) override {
+    REQ(out, FDE_EINVAL, "null output");
+    memset(out, 0, sizeof(*out));
+    ensure_vloc();
+    EnergyParts ep = grid_pass(false, true, -1);
+    double TJ = 0, Enl = 0, TS = 0, band = 0, deband = 0;
+    for (auto& sp : subs) {
+      double t, e;
+      band_terms(*sp, &t, &e);
+      TJ += t;
+      Enl += e;
+      TS += sp->entropy;
+      for (int k = 0; k < sp->nk; ++k)
+        for (int j = 0; j < sp->nb; ++j) band += 2.0 * sp->wk[k] * sp->kp[k].occ[j] * sp->kp[k].eig[j];
+      deband -= integrate_product(sp->veff.p, sp->rho.p);
+    }
+    out->E_kin = TJ;
+    out->E_nl = Enl;
+    out->E_loc = ep.Eloc;
+    out->E_H = ep.EH;
+    out->E_xc = ep.Exc;
+    out->T_nad = ep.Ttot - ep.Tsub;
+    out->E_xc_nad = ep.Exc - ep.Exc_sub;
+    out->E_H_nad = ep.EH - ep.EH_sub;
+    out->E_nn = enn;
+    out->E_fde = TJ + Enl + ep.Eloc + ep.EH + ep.Exc + out->T_nad + enn;
+    out->TS = TS;
+    out->F_fde = out->E_fde - TS;
+    out->E_band_form = band + deband + ep.Eloc + ep.EH + ep.Exc + out->T_nad + enn;
+  }
+
+  // ---- Pulay mixing -----------------------------------------------------------------------------
+  int hist_len = 0, hist_head = 0;
+  void pulay_reset() { hist_len = 0; hist_head = 0; }
+  // rho_in <- DIIS mix of the history extended by (rho_in, rho_out - rho_in)
+  void pulay(double* rin, const double* rout) {
+    const int H = 8;
+    const double beta = 0.3;
+    if (hist_in.size() < (size_t)H) {
+      hist_in.resize(H);
+      hist_res.resize(H);
+      for (int h = 0; h < H; ++h) { hist_in[h].ensure(nr); hist_res[h].ensure(nr); }
+    }
+    const int slot = (hist_head + hist_len) % H;
+    if (hist_len == H) hist_head = (hist_head + 1) % H; else ++hist_len;
+    CK(cudaMemcpyAsync(hist_in[slot].p, rin, nr * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    // res = rout - rin
+    CK(cudaMemcpyAsync(hist_res[slot].p, rout, nr * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    neg_add(hist_res[slot].p, rin);
+    const int m = hist_len;
+    std::vector<int> sl(m);
+    for (int a = 0; a < m; ++a) sl[a] = (hist_head + a) % H;
+    std::vector<double> Am((m + 1) * (m + 1), 0.0), b(m + 1, 0.0);
+    for (int a = 0; a < m; ++a)
+      for (int c = a; c < m; ++c) {
+        const double v = integrate_product(hist_res[sl[a]].p, hist_res[sl[c]].p) * (double)nr / omega;
+        Am[a * (m + 1) + c] = Am[c * (m + 1) + a] = v;
+      }
+    for (int a = 0; a < m; ++a) Am[a * (m + 1) + m] = Am[m * (m + 1) + a] = 1.0;
+    b[m] = 1.0;
+    std::vector<double> coef(m, 0.0);
+    if (!solve_dense(Am, b, m + 1)) { coef.assign(m, 0.0); coef[m - 1] = 1.0; }
+    else for (int a = 0; a < m; ++a) coef[a] = b[a];
+    std::vector<const double*> pi(m), pr(m);
+    for (int a = 0; a < m; ++a) { pi[a] = hist_in[sl[a]].p; pr[a] = hist_res[sl[a]].p; }
+    dptrs.ensure(2 * m);
+    dcoef.ensure(m);
+    CK(cudaMemcpyAsync(dptrs.p, pi.data(), m * sizeof(double*), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(dptrs.p + m, pr.data(), m * sizeof(double*), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(dcoef.p, coef.data(), m * sizeof(double), cudaMemcpyHostToDevice, st));
+    grid_lincomb(dptrs.p, dptrs.p + m, dcoef.p, m, beta, nr, rin, st);
+    CK(cudaStreamSynchronize(st));
+  }
+  // Gaussian elimination with partial pivoting; solution returned in b.
+  static bool solve_dense(std::vector<double>& Am, std::vector<double>& b, int n) {
+    for (int c = 0; c < n; ++c) {
+      int p = c;
+      for (int r = c + 1; r < n; ++r) if (fabs(Am[r * n + c]) > fabs(Am[p * n + c])) p = r;
+      if (fabs(Am[p * n + c]) < 1e-300) return false;
+      if (p != c) { for (int k = 0; k < n; ++k) std::swap(Am[c * n + k], Am[p * n + k]); std::swap(b[c], b[p]); }
+      for (int r = c + 1; r < n; ++r) {
+        const double f = Am[r * n + c] / Am[c * n + c];
+        for (int k = c; k < n; ++k) Am[r * n + k] -= f * Am[c * n + k];
+        b[r] -= f * b[c];
+      }
+    }
+    for (int c = n - 1; c >= 0; --c) {
+      double v = b[c];
+      for (int k = c + 1; k < n; ++k) v -= Am[c * n + k] * b[k];
+      b[c] = v / Am[c * n + c];
+    }
+    return true;
+  }
+
+  // ---- subsystem SCF and freeze-and-thaw ------------------------------------------------------
+  double davidson_tol(double tol) const { return sizeof(T) == 8 ? std::max(1e-9, std::min(1e-6, 0.1 * sqrt(tol))) : 3e-5; }
+
+  fde_status scf_subsystem(int I, double tol, int max_scf, fde_energies* out) override {
+    Sub<T>& s = sub(I);
+    for (auto& q : s.kp) REQ(q.have_orbitals, FDE_EINVAL, "orbitals of the subsystem are not set");
+    ensure_vloc();
+    rho_in.ensure(nr);
+    CK(cudaMemcpyAsync(rho_in.p, s.rho.p, nr * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    // frozen band terms of the other subsystems
+    double TJo = 0, Enlo = 0, TSo = 0;
+    for (size_t J = 0; J < subs.size(); ++J) {
+      if ((int)J == I) continue;
+      double t, e;
+      band_terms(*subs[J], &t, &e);
+      TJo += t;
+      Enlo += e;
+      TSo += subs[J]->entropy;
+    }
+    pulay_reset();
+    double Eprev = 0;
+    bool have_prev = false;
+    const double dtol = davidson_tol(tol);
+    fde_energies en{};
+    for (int it = 1; it <= max_scf; ++it) {
+      CK(cudaMemcpyAsync(s.rho.p, rho_in.p, nr * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      grid_pass(true, false, I);
+      for (int k = 0; k < s.nk; ++k) {
+        int its = 0;
+        subspace_solve(I, k, dtol, 60, &its);
+      }
+      occupations(s);
+      density_from_orbitals(s, s.rho.p);
+      sync();
+      // energy of the output density with the others frozen
+      EnergyParts ep = grid_pass(false, true, -1);
+      double t, e;
+      band_terms(s, &t, &e);
+      en.E_kin = TJo + t;
+      en.E_nl = Enlo + e;
+      en.E_loc = ep.Eloc;
+      en.E_H = ep.EH;
+      en.E_xc = ep.Exc;
+      en.T_nad = ep.Ttot - ep.Tsub;
+      en.E_xc_nad = ep.Exc - ep.Exc_sub;
+      en.E_H_nad = ep.EH - ep.EH_sub;
+      en.E_nn = enn;
+      en.E_fde = en.E_kin + en.E_nl + en.E_loc + en.E_H + en.E_xc + en.T_nad + enn;
+      en.TS = TSo + s.entropy;
+      en.F_fde = en.E_fde - en.TS;
+      en.iters = it;
+      const double dres = integrate_absdiff(s.rho.p, rho_in.p);
+      en.dE = have_prev ? en.F_fde - Eprev : 0.0;
+      REQ(std::isfinite(en.F_fde), FDE_ENONFINITE, "non-finite energy");
+      if (have_prev && fabs(en.dE) < tol && dres < sqrt(tol)) {
+        if (out) *out = en;
+        return FDE_OK;
+      }
+      Eprev = en.F_fde;
+      have_prev = true;
+      pulay(rho_in.p, s.rho.p);
+    }
+    if (out) *out = en;
+    return FDE_ENOCONV;
+  }
+
+  fde_status freeze_thaw(double tol, int max_scf, fde_energies* out) override {
+    REQ(!subs.empty(), FDE_EINVAL, "no subsystems");
+    ensure_vloc();
+    const size_t ns = subs.size();
+    frozen.ensure(ns * nr);
+    fresh.ensure(ns * nr);
+    for (size_t I = 0; I < ns; ++I)
+      CK(cudaMemcpyAsync(frozen.p + I * nr, subs[I]->rho.p, nr * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    fde_status worst = FDE_OK;
+    int iters = 0;
+    for (size_t I = 0; I < ns; ++I) {
+      for (size_t J = 0; J < ns; ++J)
+        CK(cudaMemcpyAsync(subs[J]->rho.p, frozen.p + J * nr, nr * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      fde_energies e{};
+      const fde_status r = scf_subsystem((int)I, tol, max_scf, &e);
+      if (r != FDE_OK) worst = r;
+      iters += e.iters;
+      CK(cudaMemcpyAsync(fresh.p + I * nr, subs[I]->rho.p, nr * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    }
+    for (size_t I = 0; I < ns; ++I)
+      CK(cudaMemcpyAsync(subs[I]->rho.p, fresh.p + I * nr, nr * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    // potentials of the refreshed densities, then every energy term
+    grid_pass(true, false, -1);
+    if (out) {
+      energy(out);
+      out->iters = iters;
+    }
+    sync();
+    return worst;
+  }
+};
+
+template <> void EngineT<double>::convert_in(const double2* a, double2* b, size_t n) {
+  launch_convert_c<double, double>(a, b, n, st);
+}
+template <> void EngineT<float>::convert_in(const double2* a, float2* b, size_t n) {
+  launch_convert_c<double, float>(a, b, n, st);
+}
+template <> void EngineT<double>::convert_out(const double2* a, double2* b, size_t n) {
+  launch_convert_c<double, double>(a, b, n, st);
+}
+template <> void EngineT<float>::convert_out(const float2* a, double2* b, size_t n) {
+  launch_convert_c<float, double>(a, b, n, st);
+}
+}  // namespace fde
+
+// ---- C ABI ------------------------------------------------------------------------------------
+struct fde_ctx {
+  std::unique_ptr<fde::Engine> eng;
+  std::string err;
+  fde_prec prec;
+};
+
+template <typename F> static fde_status guard(fde_ctx* c, F&& f) {
+  if (!c) return FDE_EINVAL;
+  try {
+    c->err.clear();
+    return f();
+  } catch (fde::Err& e) {
+    c->err = e.msg;
+    return e.st;
+  } catch (std::exception& e) {
+    c->err = e.what();
+    return FDE_ENOMEM;
+  }
+}
+
+extern "C" {
+
+fde_status fde_create(const fde_cell_desc* cell, const fde_func_desc* func, fde_prec prec, void* cuda_stream,
+                      fde_ctx** out) {
+  if (!cell || !func || !out) return FDE_EINVAL;
+  *out = nullptr;
+  if (prec != FDE_PREC_FP64 && prec != FDE_PREC_MIXED) return FDE_EINVAL;
+  fde_ctx* c = new fde_ctx();
+  c->prec = prec;
+  fde_status s = guard(c, [&]() {
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (prec == FDE_PREC_FP64) c->eng.reset(new fde::EngineT<double>(cell, func, st));
+    else c->eng.reset(new fde::EngineT<float>(cell, func, st));
+    return FDE_OK;
+  });
+  if (s != FDE_OK) {
+    fprintf(stderr, "fde_create: %s\n", c->err.c_str());
+    delete c;
+    return s;
+  }
+  *out = c;
+  return FDE_OK;
+}
+
+fde_status fde_add_subsystem(fde_ctx* c, const fde_subsys_desc* d, int* id) {
+  return guard(c, [&]() {
+    const int i = c->eng->add_subsystem(d);
+    if (id) *id = i;
+    return FDE_OK;
+  });
+}
+fde_status fde_get_basis(fde_ctx* c, int sub, int k, int* npw, int* miller) {
+  return guard(c, [&]() { c->eng->get_basis(sub, k, npw, miller); return FDE_OK; });
+}
+fde_status fde_set_density(fde_ctx* c, int sub, const double* rho, int on_device) {
+  return guard(c, [&]() { c->eng->set_density(sub, rho, on_device); return FDE_OK; });
+}
+fde_status fde_get_density(fde_ctx* c, int sub, double* d_rho) {
+  return guard(c, [&]() { c->eng->get_density(sub, d_rho); return FDE_OK; });
+}
+fde_status fde_build_vemb(fde_ctx* c, double* d_out, fde_energies* e) {
+  return guard(c, [&]() { c->eng->build_vemb(d_out, e); return FDE_OK; });
+}
+fde_status fde_set_veff(fde_ctx* c, int sub, const double* d_v) {
+  return guard(c, [&]() { c->eng->set_veff(sub, d_v); return FDE_OK; });
+}
+fde_status fde_apply_h(fde_ctx* c, int sub, int k, const void* psi, void* hpsi, int nb) {
+  return guard(c, [&]() { c->eng->apply_h(sub, k, psi, hpsi, nb); return FDE_OK; });
+}
+fde_status fde_apply_h_host(fde_ctx* c, int sub, int k, const double* psi, double* hpsi, int nb) {
+  return guard(c, [&]() { c->eng->apply_h_host(sub, k, psi, hpsi, nb); return FDE_OK; });
+}
+fde_status fde_apply_h_all(fde_ctx* c) {
+  return guard(c, [&]() { c->eng->apply_h_all(); return FDE_OK; });
+}
+fde_status fde_init_orbitals(fde_ctx* c, int sub, int k, const double* raw) {
+  return guard(c, [&]() { c->eng->init_orbitals(sub, k, raw); return FDE_OK; });
+}
+fde_status fde_set_orbitals(fde_ctx* c, int sub, int k, const double* d_psi) {
+  return guard(c, [&]() { c->eng->set_orbitals(sub, k, d_psi); return FDE_OK; });
+}
+fde_status fde_get_orbitals(fde_ctx* c, int sub, int k, double* d_psi, double* eig, double* occ) {
+  return guard(c, [&]() { c->eng->get_orbitals(sub, k, d_psi, eig, occ); return FDE_OK; });
+}
+fde_status fde_subspace_solve(fde_ctx* c, int sub, int k, double tol, int max_iter, int precond, int* iters) {
+  return guard(c, [&]() {
+    if (precond != FDE_PRECOND_TPA) throw fde::Err{FDE_EUNSUPPORTED, "unknown preconditioner"};
+    return c->eng->subspace_solve(sub, k, tol, max_iter, iters);
+  });
+}
+fde_status fde_update_density(fde_ctx* c, int sub) {
+  return guard(c, [&]() { c->eng->update_density(sub); return FDE_OK; });
+}
+fde_status fde_energy(fde_ctx* c, fde_energies* out) {
+  return guard(c, [&]() { c->eng->energy(out); return FDE_OK; });
+}
+fde_status fde_scf_subsystem(fde_ctx* c, int sub, double tol, int max_scf, fde_energies* out) {
+  return guard(c, [&]() { return c->eng->scf_subsystem(sub, tol, max_scf, out); });
+}
+fde_status fde_freeze_thaw_cycle(fde_ctx* c, double tol, int max_scf, fde_energies* out) {
+  return guard(c, [&]() { return c->eng->freeze_thaw(tol, max_scf, out); });
+}
+fde_status fde_sync(fde_ctx* c) {
+  return guard(c, [&]() { c->eng->sync(); return FDE_OK; });
+}
+const char* fde_last_error(const fde_ctx* c) { return c ? c->err.c_str() : "null context"; }
+fde_status fde_destroy(fde_ctx* c) {
+  if (!c) return FDE_EINVAL;
+  delete c;
+  return FDE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,489 @@
+// grid.cu -- the embedding-potential build on the shared real-space grid:
+//   rho = sum_I rho_I (Eq. meth:1), full 3D FFTs, the FFT Poisson solve for v_H, the
+//   erf local potential of all nuclei, gradients and divergences through FFTs, and the
+//   pointwise exchange-correlation and GGA kinetic functionals (Appendix: kinetic energy
+//   functional and potential), with FP64 energy reductions in a fixed order.
+#include <math.h>
+
+#include "fft.cuh"
+#include "grid_kernels.h"
+
+namespace fde {
+
+// ---- full 3D transforms, one axis per pass ---------------------------------------------
+// Element (o, e, t) of a pass sits at (o * N + e) * I + t: N is the transformed length, I
+// the product of the faster axes.  A CTA holds kLinesPerCta lines (one warp each).
+constexpr int kLinesPerCta = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(kLinesPerCta * 32)
+k_fft_axis(cplx<T>* __restrict__ data, long long nlines, int N, long long I, LinePlan<T> p, int sign) {
+  using C = cplx<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* lines = reinterpret_cast<C*>(smem_raw);
+  const int lp = N + 1;
+  const long long l0 = (long long)blockIdx.x * kLinesPerCta;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nl = (int)min((long long)kLinesPerCta, nlines - l0);
+  for (int idx = threadIdx.x; idx < kLinesPerCta * N; idx += blockDim.x) {
+    int tl, e;
+    if (I == 1) { tl = idx / N; e = idx - tl * N; } else { e = idx / kLinesPerCta; tl = idx - e * kLinesPerCta; }
+    if (tl < nl) {
+      const long long l = l0 + tl, o = l / I, t = l - o * I;
+      lines[tl * lp + e] = data[(o * N + e) * I + t];
+    }
+  }
+  __syncthreads();
+  if (w < nl) fft_line<T>(lines + w * lp, 1, p, lane, sign);
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < kLinesPerCta * N; idx += blockDim.x) {
+    int tl, e;
+    if (I == 1) { tl = idx / N; e = idx - tl * N; } else { e = idx / kLinesPerCta; tl = idx - e * kLinesPerCta; }
+    if (tl < nl) {
+      const long long l = l0 + tl, o = l / I, t = l - o * I;
+      data[(o * N + e) * I + t] = lines[tl * lp + e];
+    }
+  }
+}
+
+template <typename T>
+void launch_fft3d(cplx<T>* data, const GridDims& g, const FftPlans<T>& fp, int sign, cudaStream_t st) {
+  const long long nr = (long long)g.n1 * g.n2 * g.n3;
+  struct Ax { int N; long long I; const LinePlan<T>* p; } ax[3] = {
+      {g.n3, 1, &fp.p3}, {g.n2, g.n3, &fp.p2}, {g.n1, (long long)g.n2 * g.n3, &fp.p1}};
+  for (int a = 0; a < 3; ++a) {
+    const long long nlines = nr / ax[a].N;
+    const size_t sm = (size_t)kLinesPerCta * (ax[a].N + 1) * sizeof(cplx<T>);
+    k_fft_axis<T><<<(unsigned)((nlines + kLinesPerCta - 1) / kLinesPerCta), kLinesPerCta * 32, sm, st>>>(
+        data, nlines, ax[a].N, ax[a].I, *ax[a].p, sign);
+  }
+}
+
+// ---- reciprocal-space helpers -----------------------------------------------------------
+struct Gpt {
+  double gx, gy, gz, g2;
+  bool nyq;
+};
+
+__device__ __forceinline__ Gpt gvec(long long idx, const GridDims& g, const CellDev& c) {
+  const int i3 = (int)(idx % g.n3);
+  const long long r = idx / g.n3;
+  const int i2 = (int)(r % g.n2), i1 = (int)(r / g.n2);
+  const int m1 = (i1 < (g.n1 + 1) / 2) ? i1 : i1 - g.n1;
+  const int m2 = (i2 < (g.n2 + 1) / 2) ? i2 : i2 - g.n2;
+  const int m3 = (i3 < (g.n3 + 1) / 2) ? i3 : i3 - g.n3;
+  Gpt p;
+  p.gx = m1 * c.b[0][0] + m2 * c.b[1][0] + m3 * c.b[2][0];
+  p.gy = m1 * c.b[0][1] + m2 * c.b[1][1] + m3 * c.b[2][1];
+  p.gz = m1 * c.b[0][2] + m2 * c.b[1][2] + m3 * c.b[2][2];
+  p.g2 = p.gx * p.gx + p.gy * p.gy + p.gz * p.gz;
+  p.nyq = ((g.n1 % 2 == 0) && m1 == -g.n1 / 2) || ((g.n2 % 2 == 0) && m2 == -g.n2 / 2) ||
+          ((g.n3 % 2 == 0) && m3 == -g.n3 / 2);
+  return p;
+}
+
+constexpr int kRedBlocks = 304;  // 2 x 152 SMs
+constexpr int kRedThreads = 256;
+
+__device__ __forceinline__ void block_sum_store(double v, double* out_slot) {
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+    *out_slot = t;
+  }
+  __syncthreads();
+}
+
+// v_H(G) = 4 pi rho(G) / |G|^2 from the unscaled forward transform F = N_r rho(G); writes
+// the potential coefficients (scaled to f(G)) and per-block partial sums of
+// |rho(G)|^2 4 pi / G^2 (E_H = Omega/2 times their sum).
+template <typename T>
+__global__ void k_poisson(const cplx<T>* __restrict__ F, cplx<T>* __restrict__ V, GridDims g, CellDev c,
+                          double inv_nr, double* partial) {
+  const long long nr = (long long)g.n1 * g.n2 * g.n3;
+  double acc = 0;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < nr; idx += (long long)gridDim.x * blockDim.x) {
+    const Gpt p = gvec(idx, g, c);
+    cplx<T> o = mk<T>(0, 0);
+    if (p.g2 > 0 && !p.nyq) {
+      const double re = (double)F[idx].x * inv_nr, im = (double)F[idx].y * inv_nr;
+      const double f = 4.0 * M_PI / p.g2;
+      if (V) o = mk<T>((T)(f * re), (T)(f * im));
+      acc += f * (re * re + im * im);
+    }
+    if (V) V[idx] = o;
+  }
+  block_sum_store(acc, partial + blockIdx.x);
+}
+
+// out_c = i G_c F / N_r (c = x, y, z), Nyquist planes zero.
+template <typename T>
+__global__ void k_grad_g(const cplx<T>* __restrict__ F, cplx<T>* __restrict__ ox, cplx<T>* __restrict__ oy,
+                         cplx<T>* __restrict__ oz, GridDims g, CellDev c, double inv_nr) {
+  const long long nr = (long long)g.n1 * g.n2 * g.n3;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < nr; idx += (long long)gridDim.x * blockDim.x) {
+    const Gpt p = gvec(idx, g, c);
+    const double re = (double)F[idx].x * inv_nr, im = (double)F[idx].y * inv_nr;
+    if (p.nyq) {
+      ox[idx] = oy[idx] = oz[idx] = mk<T>(0, 0);
+    } else {
+      ox[idx] = mk<T>((T)(-p.gx * im), (T)(p.gx * re));
+      oy[idx] = mk<T>((T)(-p.gy * im), (T)(p.gy * re));
+      oz[idx] = mk<T>((T)(-p.gz * im), (T)(p.gz * re));
+    }
+  }
+}
+
+// out = sum_c i G_c H_c / N_r, Nyquist planes zero (written into hx).
+template <typename T>
+__global__ void k_div_g(cplx<T>* __restrict__ hx, const cplx<T>* __restrict__ hy, const cplx<T>* __restrict__ hz,
+                        GridDims g, CellDev c, double inv_nr) {
+  const long long nr = (long long)g.n1 * g.n2 * g.n3;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < nr; idx += (long long)gridDim.x * blockDim.x) {
+    const Gpt p = gvec(idx, g, c);
+    if (p.nyq) {
+      hx[idx] = mk<T>(0, 0);
+      continue;
+    }
+    const double re = p.gx * hx[idx].x + p.gy * hy[idx].x + p.gz * hz[idx].x;
+    const double im = p.gx * hx[idx].y + p.gy * hy[idx].y + p.gz * hz[idx].y;
+    hx[idx] = mk<T>((T)(-im * inv_nr), (T)(re * inv_nr));
+  }
+}
+
+// Local potential of all nuclei in reciprocal space (FP64):
+// v(G) = (1/Omega) sum_a -4 pi Z_a / G^2 exp(-G^2 rc^2/4) exp(-i G.R_a), G != 0;
+// v(0) = (1/Omega) sum_a pi Z_a rc^2; Nyquist planes zero.
+__global__ void k_vloc_g(double2* __restrict__ V, GridDims g, CellDev c, const double* __restrict__ pos,
+                         const double* __restrict__ Z, int natoms, double rc) {
+  const long long nr = (long long)g.n1 * g.n2 * g.n3;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < nr; idx += (long long)gridDim.x * blockDim.x) {
+    const Gpt p = gvec(idx, g, c);
+    double re = 0, im = 0;
+    if (p.g2 == 0) {
+      for (int a = 0; a < natoms; ++a) re += M_PI * Z[a] * rc * rc;
+    } else if (!p.nyq) {
+      const double f = -4.0 * M_PI / p.g2 * exp(-p.g2 * rc * rc / 4.0);
+      for (int a = 0; a < natoms; ++a) {
+        const double ph = p.gx * pos[3 * a] + p.gy * pos[3 * a + 1] + p.gz * pos[3 * a + 2];
+        double sn, cs;
+        sincos(ph, &sn, &cs);
+        re += f * Z[a] * cs;
+        im -= f * Z[a] * sn;
+      }
+    }
+    V[idx] = make_double2(re / c.omega, im / c.omega);
+  }
+}
+
+// ---- pointwise functionals ------------------------------------------------------------------
+// Values with their derivatives along rho and sigma = |grad rho|^2 (forward-mode dual
+// numbers), so the potentials follow from the energy densities exactly.
+template <typename T> struct Dual {
+  T v, r, s;
+};
+template <typename T> __device__ __forceinline__ Dual<T> dc(T v) { return {v, 0, 0}; }
+template <typename T> __device__ __forceinline__ Dual<T> operator+(Dual<T> a, Dual<T> b) { return {a.v + b.v, a.r + b.r, a.s + b.s}; }
+template <typename T> __device__ __forceinline__ Dual<T> operator-(Dual<T> a, Dual<T> b) { return {a.v - b.v, a.r - b.r, a.s - b.s}; }
+template <typename T> __device__ __forceinline__ Dual<T> operator*(Dual<T> a, Dual<T> b) {
+  return {a.v * b.v, a.r * b.v + a.v * b.r, a.s * b.v + a.v * b.s};
+}
+template <typename T> __device__ __forceinline__ Dual<T> operator/(Dual<T> a, Dual<T> b) {
+  const T iv = (T)1 / b.v, q = a.v * iv;
+  return {q, (a.r - q * b.r) * iv, (a.s - q * b.s) * iv};
+}
+template <typename T> __device__ __forceinline__ Dual<T> operator*(T k, Dual<T> a) { return {k * a.v, k * a.r, k * a.s}; }
+template <typename T> __device__ __forceinline__ Dual<T> operator+(T k, Dual<T> a) { return {k + a.v, a.r, a.s}; }
+template <typename T> __device__ __forceinline__ Dual<T> dlog(Dual<T> a) { const T iv = (T)1 / a.v; return {log(a.v), a.r * iv, a.s * iv}; }
+template <typename T> __device__ __forceinline__ Dual<T> dexp(Dual<T> a) { const T e = exp(a.v); return {e, a.r * e, a.s * e}; }
+template <typename T> __device__ __forceinline__ Dual<T> dsqrt(Dual<T> a) {
+  const T q = sqrt(a.v), h = (T)0.5 / q;
+  return {q, a.r * h, a.s * h};
+}
+template <typename T> __device__ __forceinline__ Dual<T> dpow(Dual<T> a, T p) {
+  const T q = pow(a.v, p), d = p * q / a.v;
+  return {q, a.r * d, a.s * d};
+}
+
+// Slater exchange + PW92 correlation energy per volume of the uniform gas at rho.
+template <typename T> __device__ __forceinline__ Dual<T> lda_xc(Dual<T> rho, Dual<T>* eps_c_out) {
+  const T third = (T)(1.0 / 3.0);
+  const Dual<T> ex = (T)(-0.75 * 0.98474502184269654) * dpow(rho, (T)(4.0 / 3.0));  // (3/pi)^{1/3}
+  // rs = (3 / (4 pi rho))^{1/3} with derivative through rho
+  const Dual<T> rsd = dpow(dc<T>((T)(3.0 / (4.0 * M_PI))) / rho, third);
+  const T A = (T)0.031091, a1 = (T)0.21370;
+  const T b1 = (T)7.5957, b2 = (T)3.5876, b3 = (T)1.6382, b4 = (T)0.49294;
+  const Dual<T> srs = dsqrt(rsd);
+  const Dual<T> den = ((T)2 * A) * (b1 * srs + b2 * rsd + b3 * (rsd * srs) + b4 * (rsd * rsd));
+  const Dual<T> ec = ((T)-2 * A) * (((T)1 + a1 * rsd) * dlog((T)1 + dc<T>(1) / den));
+  *eps_c_out = ec;
+  return ex + rho * ec;
+}
+
+template <typename T> __device__ __forceinline__ Dual<T> pbe_xc(Dual<T> rho, Dual<T> sig) {
+  const T kappa = (T)0.804, mu = (T)0.2195149727645171;
+  const T beta = (T)0.06672455060314922, gamma = (T)((1.0 - 0.69314718055994530942) / (M_PI * M_PI));
+  Dual<T> ec;
+  const Dual<T> ex_unif = (T)(-0.75 * 0.98474502184269654) * dpow(rho, (T)(4.0 / 3.0));
+  (void)lda_xc(rho, &ec);
+  const Dual<T> kf = dpow((T)(3.0 * M_PI * M_PI) * rho, (T)(1.0 / 3.0));
+  const Dual<T> s2 = sig / ((T)4 * (kf * kf * rho * rho));
+  const Dual<T> fx = ((T)1 + kappa) + dc<T>(0) - kappa * (dc<T>(1) / ((T)1 + (mu / kappa) * s2));
+  const Dual<T> ks = dsqrt((T)(4.0 / M_PI) * kf);
+  const Dual<T> t2 = sig / ((T)4 * (ks * ks * rho * rho));
+  const T bg = beta / gamma;
+  const Dual<T> Aa = bg * (dc<T>(1) / (dexp(((T)-1 / gamma) * ec) - dc<T>(1)));
+  const Dual<T> At2 = Aa * t2;
+  const Dual<T> H = gamma * dlog((T)1 + bg * (t2 * (((T)1 + At2) / ((T)1 + At2 + At2 * At2))));
+  return ex_unif * fx + rho * (ec + H);
+}
+
+// Kinetic enhancement factors F(s) and F'(s).
+template <typename T> __device__ __forceinline__ void kedf_F(int kind, T s, T* F, T* dF) {
+  if (kind == 0) { *F = 1; *dF = 0; return; }
+  if (kind == 1) {  // revAPBEK
+    const T k = (T)1.245, mu = (T)0.23889;
+    const T d = (T)1 + mu * s * s / k;
+    *F = (T)1 + k - k / d;
+    *dF = (T)2 * mu * s / (d * d);
+    return;
+  }
+  // LC94 (PW91 form)
+  const T a = (T)0.093907, b = (T)76.32, c = (T)0.26608, dd = (T)-0.0809615, al = (T)100, f = (T)0.000057767;
+  const T ash = asinh(b * s), ex = exp(-al * s * s);
+  const T num = (T)1 + a * s * ash + (c + dd * ex) * s * s;
+  const T den = (T)1 + a * s * ash + f * s * s * s * s;
+  const T dash = a * ash + a * s * b / sqrt((T)1 + b * b * s * s);
+  const T dnum = dash + (T)2 * s * (c + dd * ex) - (T)2 * al * dd * s * s * s * ex;
+  const T dden = dash + (T)4 * f * s * s * s;
+  *F = num / den;
+  *dF = (dnum * den - num * dden) / (den * den);
+}
+
+// One point of a functional evaluation.  xc_mode: -1 none, 0 LDA, 1 PBE.  kedf: -1 none,
+// 0 TF, 1 revAPBEK, 2 LC94.  Returns the local potential part (d e/d rho of both), the
+// coefficient multiplying grad rho in the divergence term, and the two energy densities.
+template <typename T>
+__device__ __forceinline__ void point_functional(T rho, T gx, T gy, T gz, int xc_mode, int xc_pot, int kedf,
+                                                 T rho_cut, T* vloc, T* hcoef, double* exc, double* ekin) {
+  *vloc = 0; *hcoef = 0; *exc = 0; *ekin = 0;
+  if (!(rho >= rho_cut)) return;
+  const T sig = gx * gx + gy * gy + gz * gz;
+  if (xc_mode == 0) {
+    Dual<T> ec;
+    const Dual<T> e = lda_xc(Dual<T>{rho, 1, 0}, &ec);
+    if (xc_pot) *vloc += e.r;
+    *exc = e.v;
+  } else if (xc_mode == 1) {
+    const Dual<T> e = pbe_xc(Dual<T>{rho, 1, 0}, Dual<T>{sig, 0, 1});
+    if (xc_pot) {
+      *vloc += e.r;
+      *hcoef += (T)2 * e.s;
+    }
+    *exc = e.v;
+  }
+  if (kedf >= 0) {
+    const T ctf = (T)2.8712340001881918;   // (3/10)(3 pi^2)^{2/3}
+    const T cs = (T)0.16162045967399548;   // 1 / (2 (3 pi^2)^{1/3})
+    const T r13 = cbrt(rho), r23 = r13 * r13, r43 = rho * r13;
+    const T gn = sqrt(sig);
+    const T s = cs * gn / r43;
+    T F, dF;
+    kedf_F<T>(kedf, s, &F, &dF);
+    *ekin = (double)(ctf * rho * r23 * F);
+    *vloc += ctf * r23 * ((T)(5.0 / 3.0) * F - (T)(4.0 / 3.0) * s * dF);
+    if (kedf > 0) *hcoef += ctf * cs * r13 * dF / (gn > (T)1e-30 ? gn : (T)1e-30);
+  }
+}
+
+// Pointwise pass over a density: rho (FP64 master), gradient in g[xyz] (real parts of
+// complex grids; NULL when no GGA), writes vpart (FP64) and overwrites g[xyz] with
+// h = hcoef * grad rho; per-block partial energies in partial[0][blk] (xc), [1][blk] (kin).
+// xc_pot = 0: the xc functional contributes its energy only (not vpart or h).
+template <typename T>
+__global__ void k_pointwise(const double* __restrict__ rho, cplx<T>* gx, cplx<T>* gy, cplx<T>* gz, long long nr,
+                            int xc_mode, int xc_pot, int kedf, double rho_cut, double* __restrict__ vpart,
+                            double* partial) {
+  double ax = 0, ak = 0;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < nr; idx += (long long)gridDim.x * blockDim.x) {
+    const T r = (T)rho[idx];
+    T x = 0, y = 0, z = 0;
+    if (gx) { x = gx[idx].x; y = gy[idx].x; z = gz[idx].x; }
+    T v, h;
+    double ex, ek;
+    point_functional<T>(r, x, y, z, xc_mode, xc_pot, kedf, (T)rho_cut, &v, &h, &ex, &ek);
+    if (vpart) vpart[idx] = (double)v;
+    if (gx) {
+      gx[idx] = mk<T>(h * x, 0);
+      gy[idx] = mk<T>(h * y, 0);
+      gz[idx] = mk<T>(h * z, 0);
+    }
+    ax += ex;
+    ak += ek;
+  }
+  block_sum_store(ax, partial + blockIdx.x);
+  block_sum_store(ak, partial + kRedBlocks + blockIdx.x);
+}
+
+// ---- small elementwise kernels -----------------------------------------------------------
+template <typename T>
+__global__ void k_real_to_c(const double* __restrict__ a, cplx<T>* __restrict__ c, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    c[i] = mk<T>((T)a[i], 0);
+}
+
+template <typename T>
+__global__ void k_c_to_real(const cplx<T>* __restrict__ c, double* __restrict__ a, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    a[i] = (double)c[i].x;
+}
+
+// out = a + b + c - Re(d) (any of b, c, d may be NULL).
+template <typename T>
+__global__ void k_combine(const double* a, const double* b, const double* c, const cplx<T>* d, double sd,
+                          double* out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double v = a ? a[i] : 0.0;
+    if (b) v += b[i];
+    if (c) v += c[i];
+    if (d) v += sd * (double)d[i].x;
+    out[i] = v;
+  }
+}
+
+__global__ void k_sum_rows(const double* __restrict__ a, int nrows, long long n, double* __restrict__ out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double v = 0;
+    for (int r = 0; r < nrows; ++r) v += a[(size_t)r * n + i];
+    out[i] = v;
+  }
+}
+
+// partial sums of a[i] * b[i] (b NULL: a[i]; absdiff: |a - b|)
+__global__ void k_dot_partial(const double* __restrict__ a, const double* __restrict__ b, long long n, int mode,
+                              double* partial) {
+  double acc = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    if (mode == 0) acc += b ? a[i] * b[i] : a[i];
+    else acc += fabs(a[i] - b[i]);
+  }
+  block_sum_store(acc, partial + blockIdx.x);
+}
+
+__global__ void k_finalize(const double* __restrict__ partial, int nblk, int nq, double scale, double* out) {
+  const int q = threadIdx.x;
+  if (q >= nq) return;
+  double t = 0;
+  for (int b = 0; b < nblk; ++b) t += partial[(size_t)q * nblk + b];
+  out[q] = t * scale;
+}
+
+// out = sum_k c[k] * (a_k + beta * r_k) for the Pulay step; coefs on the device.
+__global__ void k_lincomb(const double* const* __restrict__ ins, const double* const* __restrict__ res,
+                          const double* __restrict__ coef, int m, double beta, long long n, double* out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double v = 0;
+    for (int k = 0; k < m; ++k) v += coef[k] * (ins[k][i] + beta * res[k][i]);
+    out[i] = v;
+  }
+}
+
+__global__ void k_axpy(double* __restrict__ a, const double* __restrict__ b, double alpha, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    a[i] += alpha * b[i];
+}
+
+__global__ void k_nonfinite(const double* __restrict__ a, long long n, unsigned* status) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    if (!isfinite(a[i])) { atomicOr(status, ST_NONFINITE); return; }
+}
+
+// ---- launch wrappers ------------------------------------------------------------------------
+static int gs(long long n) {
+  long long b = (n + 255) / 256;
+  return (int)(b < 4096 ? (b > 0 ? b : 1) : 4096);
+}
+
+template <typename T>
+void grid_poisson(const cplx<T>* F, cplx<T>* V, const GridDims& g, const CellDev& c, double* partial, cudaStream_t st) {
+  k_poisson<T><<<kRedBlocks, kRedThreads, 0, st>>>(F, V, g, c, 1.0 / ((double)g.n1 * g.n2 * g.n3), partial);
+}
+template <typename T>
+void grid_gradient_g(const cplx<T>* F, cplx<T>* ox, cplx<T>* oy, cplx<T>* oz, const GridDims& g, const CellDev& c,
+                     cudaStream_t st) {
+  const long long nr = (long long)g.n1 * g.n2 * g.n3;
+  k_grad_g<T><<<gs(nr), 256, 0, st>>>(F, ox, oy, oz, g, c, 1.0 / (double)nr);
+}
+template <typename T>
+void grid_divergence_g(cplx<T>* hx, const cplx<T>* hy, const cplx<T>* hz, const GridDims& g, const CellDev& c,
+                       cudaStream_t st) {
+  const long long nr = (long long)g.n1 * g.n2 * g.n3;
+  k_div_g<T><<<gs(nr), 256, 0, st>>>(hx, hy, hz, g, c, 1.0 / (double)nr);
+}
+void grid_vloc_g(double2* V, const GridDims& g, const CellDev& c, const double* pos, const double* Z, int natoms,
+                 double rc, cudaStream_t st) {
+  const long long nr = (long long)g.n1 * g.n2 * g.n3;
+  k_vloc_g<<<gs(nr), 256, 0, st>>>(V, g, c, pos, Z, natoms, rc);
+}
+template <typename T>
+void grid_pointwise(const double* rho, cplx<T>* gx, cplx<T>* gy, cplx<T>* gz, long long nr, int xc_mode, int xc_pot,
+                    int kedf, double rho_cut, double* vpart, double* partial, cudaStream_t st) {
+  k_pointwise<T><<<kRedBlocks, kRedThreads, 0, st>>>(rho, gx, gy, gz, nr, xc_mode, xc_pot, kedf, rho_cut, vpart,
+                                                      partial);
+}
+template <typename T>
+void grid_real_to_c(const double* a, cplx<T>* c, long long n, cudaStream_t st) {
+  k_real_to_c<T><<<gs(n), 256, 0, st>>>(a, c, n);
+}
+template <typename T>
+void grid_c_to_real(const cplx<T>* c, double* a, long long n, cudaStream_t st) {
+  k_c_to_real<T><<<gs(n), 256, 0, st>>>(c, a, n);
+}
+template <typename T>
+void grid_combine(const double* a, const double* b, const double* c, const cplx<T>* d, double sd, double* out,
+                  long long n, cudaStream_t st) {
+  k_combine<T><<<gs(n), 256, 0, st>>>(a, b, c, d, sd, out, n);
+}
+void grid_sum_rows(const double* a, int nrows, long long n, double* out, cudaStream_t st) {
+  k_sum_rows<<<gs(n), 256, 0, st>>>(a, nrows, n, out);
+}
+void grid_dot_partial(const double* a, const double* b, long long n, int mode, double* partial, cudaStream_t st) {
+  k_dot_partial<<<kRedBlocks, kRedThreads, 0, st>>>(a, b, n, mode, partial);
+}
+void grid_finalize(const double* partial, int nq, double scale, double* out, cudaStream_t st) {
+  k_finalize<<<1, 32, 0, st>>>(partial, kRedBlocks, nq, scale, out);
+}
+void grid_lincomb(const double* const* ins, const double* const* res, const double* coef, int m, double beta,
+                  long long n, double* out, cudaStream_t st) {
+  k_lincomb<<<gs(n), 256, 0, st>>>(ins, res, coef, m, beta, n, out);
+}
+void grid_axpy(double* a, const double* b, double alpha, long long n, cudaStream_t st) {
+  k_axpy<<<gs(n), 256, 0, st>>>(a, b, alpha, n);
+}
+void grid_nonfinite(const double* a, long long n, unsigned* status, cudaStream_t st) {
+  k_nonfinite<<<gs(n), 256, 0, st>>>(a, n, status);
+}
+int grid_red_blocks() { return kRedBlocks; }
+
+#define FDE_GRID_INST(T)                                                                                     \
+  template void launch_fft3d<T>(cplx<T>*, const GridDims&, const FftPlans<T>&, int, cudaStream_t);           \
+  template void grid_poisson<T>(const cplx<T>*, cplx<T>*, const GridDims&, const CellDev&, double*,          \
+                                cudaStream_t);                                                               \
+  template void grid_gradient_g<T>(const cplx<T>*, cplx<T>*, cplx<T>*, cplx<T>*, const GridDims&,            \
+                                   const CellDev&, cudaStream_t);                                            \
+  template void grid_divergence_g<T>(cplx<T>*, const cplx<T>*, const cplx<T>*, const GridDims&,              \
+                                     const CellDev&, cudaStream_t);                                          \
+  template void grid_pointwise<T>(const double*, cplx<T>*, cplx<T>*, cplx<T>*, long long, int, int, int,     \
+                                  double, double*, double*, cudaStream_t);                                   \
+  template void grid_real_to_c<T>(const double*, cplx<T>*, long long, cudaStream_t);                         \
+  template void grid_c_to_real<T>(const cplx<T>*, double*, long long, cudaStream_t);                         \
+  template void grid_combine<T>(const double*, const double*, const double*, const cplx<T>*, double, double*, \
+                                long long, cudaStream_t);
+FDE_GRID_INST(float)
+FDE_GRID_INST(double)
+
+}  // namespace fde

@@ -1,0 +1,99 @@
+// kernels.h -- launch wrappers of the library's CUDA kernels (internal interface between
+// the host orchestration in fde_host.cu and the kernel translation units).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace fde {
+
+// Columns of one plane-wave sphere on the FFT grid.  A column is a fixed (m1, m2) with a
+// contiguous run of m3 values; sphere order puts each column's run contiguously.
+struct SphereDev {
+  int npw, ncol, nrow;
+  const int* col_start;  // [ncol + 1] offsets into the sphere
+  const int* col_m3lo;   // [ncol] signed m3 of the first point
+  const int* col_i1;     // [ncol] grid index i1 = m1 mod n1
+  const int* col_i2;     // [ncol] grid index i2 = m2 mod n2
+  const int* row_i1;     // [nrow] distinct i1 holding at least one column
+};
+
+struct GridDims {
+  int n1, n2, n3;
+};
+
+template <typename T> struct FftPlans {
+  LinePlan<T> p1, p2, p3;
+};
+
+// ---- H psi local part and densities (hpsi.cu) -----------------------------------------
+// scratch: [nb][n3][ncol] complex T.  vplane: [n3][n1][n2] real T.
+template <typename T>
+void launch_hpsi_local(const cplx<T>* psi, int ldpsi, cplx<T>* hpsi, int ldh, int nb,
+                       const T* kin, const T* vplane, cplx<T>* scratch, const SphereDev& sp,
+                       const GridDims& g, const FftPlans<T>& fp, cudaStream_t st);
+
+// rho_plane[n3][n1][n2] (+)= sum_b weight[b] |u_b(r)|^2 for the block of nb orbitals.
+template <typename T>
+void launch_density(const cplx<T>* psi, int ldpsi, int nb, const double* weight,
+                    cplx<T>* scratch, double* rho_plane, int accumulate, const SphereDev& sp,
+                    const GridDims& g, const FftPlans<T>& fp, cudaStream_t st);
+
+// out[j][i] = (Tout) in[i][j], in is [rows][cols]; with optional accumulate.
+template <typename Tin, typename Tout>
+void launch_transpose(const Tin* in, Tout* out, int rows, int cols, int accumulate, cudaStream_t st);
+
+// ---- dense complex algebra (linalg.cu) --------------------------------------------------
+// C[i][j] = sum_g conj(A[i][g]) B[j][g], A [m][K] (lda), B [n][K] (ldb); C [m][n] FP64
+// complex (ldc).  work: at least gemm_hn_work(m, n, K) double2 elements.
+size_t gemm_hn_work(int m, int n, int K);
+template <typename T>
+void launch_gemm_hn(const cplx<T>* A, int lda, const cplx<T>* B, int ldb, int m, int n, int K,
+                    double2* C, int ldc, double2* work, cudaStream_t st);
+
+// Y[j][g] = alpha * sum_i U[i][j] X[i][g] + beta * Y[j][g]; X [m][K] (ldx), U [m][n] FP64
+// complex (ldu), Y [n][K] (ldy).  alpha/beta real.
+template <typename T>
+void launch_gemm_rot(const cplx<T>* X, int ldx, const double2* U, int ldu, int m, int n, int K,
+                     cplx<T>* Y, int ldy, double alpha, double beta, cudaStream_t st);
+
+// Cholesky S = L L^H (n x n, FP64 complex, lower, in place into L) and Linv = L^{-1};
+// sets status bit ST_CHOLESKY on a non-positive pivot.
+void launch_cholesky_inv(const double2* S, int n, double2* L, double2* Linv, unsigned* status,
+                         cudaStream_t st);
+
+// Hermitian eigenproblem by cyclic Jacobi: A (n x n, destroyed) -> eigenvalues w[n]
+// ascending and eigenvectors V (column j = vector j), FP64.
+void launch_jacobi_eig(double2* A, int n, double* w, double2* V, double2* work, cudaStream_t st);
+
+// Row-wise helpers on [nb][K] blocks.
+template <typename T>
+void launch_residual(const cplx<T>* HX, const cplx<T>* X, const double* eps, int nb, int K, int ld,
+                     cplx<T>* R, int ldr, cudaStream_t st);
+template <typename T>
+void launch_row_norms(const cplx<T>* X, int ld, int nb, int K, const T* weight, double* out,
+                      double* work, cudaStream_t st);
+template <typename T>
+void launch_tpa(const cplx<T>* R, int ldr, const T* kin, const double* tband, int nb, int K,
+                cplx<T>* W, int ldw, cudaStream_t st);
+template <typename T>
+void launch_scale_rows(cplx<T>* X, int ld, int nb, int K, const double* s, cudaStream_t st);
+template <typename Ta, typename Tb>
+void launch_convert_c(const cplx<Ta>* a, cplx<Tb>* b, size_t n, cudaStream_t st);
+template <typename T>
+void launch_shape_init(cplx<T>* X, int ld, const T* kin, int nb, int K, cudaStream_t st);
+void launch_hermitize(double2* A, int n, cudaStream_t st);
+
+// ---- grid kernels (grid.cu) -------------------------------------------------------------
+// Full 3D transforms of complex grids [n1][n2][n3] in place: sign -1 forward (scaled by
+// 1/N_r), +1 inverse (unscaled).
+template <typename T>
+void launch_fft3d(cplx<T>* data, const GridDims& g, const FftPlans<T>& fp, int sign, cudaStream_t st);
+
+struct CellDev {
+  double b[3][3];  // reciprocal rows
+  double omega;
+};
+
+}  // namespace fde

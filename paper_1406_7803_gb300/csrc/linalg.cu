@@ -1,0 +1,522 @@
+// linalg.cu -- dense complex algebra of the subspace eigensolver (Eq. KS solved by block
+// Davidson): band-block inner products (Gram / subspace Hamiltonian / projector
+// contractions), band-block rotations, FP64 Cholesky with triangular inverse, FP64 cyclic
+// Jacobi for the small Hermitian eigenproblem, and the row-wise residual / preconditioner
+// helpers.
+#include <math.h>
+
+#include "kernels.h"
+
+namespace fde {
+
+// ---- C = A^H B over a long K ------------------------------------------------------------
+// 32 x 32 output tile per CTA (256 threads, 2 x 2 outputs each), K split over gridDim.z;
+// each split writes its partial tile, a second kernel sums the splits in a fixed order.
+constexpr int kGT = 32, kGK = 32;
+
+template <typename T, typename Acc>
+__global__ void __launch_bounds__(256)
+k_gemm_hn_partial(const cplx<T>* __restrict__ A, int lda, const cplx<T>* __restrict__ B, int ldb, int m, int n,
+                  int K, int kchunk, double2* __restrict__ part) {
+  using C = cplx<T>;
+  __shared__ C As[kGT][kGK + 1];
+  __shared__ C Bs[kGT][kGK + 1];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int i0 = blockIdx.x * kGT, j0 = blockIdx.y * kGT;
+  const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
+  Acc re[2][2] = {{0, 0}, {0, 0}}, im[2][2] = {{0, 0}, {0, 0}};
+  for (int k0 = kb; k0 < ke; k0 += kGK) {
+    for (int idx = threadIdx.x; idx < kGT * kGK; idx += 256) {
+      const int r = idx / kGK, kk = idx % kGK;
+      const int g = k0 + kk;
+      const bool ok = g < ke;
+      As[r][kk] = (ok && i0 + r < m) ? A[(size_t)(i0 + r) * lda + g] : mk<T>(0, 0);
+      Bs[r][kk] = (ok && j0 + r < n) ? B[(size_t)(j0 + r) * ldb + g] : mk<T>(0, 0);
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < kGK; ++kk) {
+      C a0 = As[ty][kk], a1 = As[ty + 16][kk];
+      C b0 = Bs[tx][kk], b1 = Bs[tx + 16][kk];
+      // conj(a) * b
+      re[0][0] += (Acc)a0.x * b0.x + (Acc)a0.y * b0.y; im[0][0] += (Acc)a0.x * b0.y - (Acc)a0.y * b0.x;
+      re[0][1] += (Acc)a0.x * b1.x + (Acc)a0.y * b1.y; im[0][1] += (Acc)a0.x * b1.y - (Acc)a0.y * b1.x;
+      re[1][0] += (Acc)a1.x * b0.x + (Acc)a1.y * b0.y; im[1][0] += (Acc)a1.x * b0.y - (Acc)a1.y * b0.x;
+      re[1][1] += (Acc)a1.x * b1.x + (Acc)a1.y * b1.y; im[1][1] += (Acc)a1.x * b1.y - (Acc)a1.y * b1.x;
+    }
+    __syncthreads();
+  }
+  double2* P = part + (size_t)blockIdx.z * m * n;
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const int i = i0 + ty + 16 * a, j = j0 + tx + 16 * b;
+      if (i < m && j < n) P[(size_t)i * n + j] = make_double2((double)re[a][b], (double)im[a][b]);
+    }
+}
+
+__global__ void k_gemm_hn_reduce(const double2* __restrict__ part, int nsplit, int m, int n, double2* C, int ldc) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= m * n) return;
+  double re = 0, im = 0;
+  for (int s = 0; s < nsplit; ++s) {
+    const double2 v = part[(size_t)s * m * n + idx];
+    re += v.x;
+    im += v.y;
+  }
+  const int i = idx / n, j = idx % n;
+  C[(size_t)i * ldc + j] = make_double2(re, im);
+}
+
+static int gemm_hn_splits(int m, int n, int K) {
+  const int tiles = ceil_div(m, kGT) * ceil_div(n, kGT);
+  int s = ceil_div(4 * 152, tiles);
+  const int smax = ceil_div(K, 512);
+  if (s > smax) s = smax;
+  if (s < 1) s = 1;
+  return s;
+}
+
+size_t gemm_hn_work(int m, int n, int K) { return (size_t)gemm_hn_splits(m, n, K) * m * n; }
+
+template <typename T>
+void launch_gemm_hn(const cplx<T>* A, int lda, const cplx<T>* B, int ldb, int m, int n, int K, double2* C,
+                    int ldc, double2* work, cudaStream_t st) {
+  if (m <= 0 || n <= 0) return;
+  const int s = gemm_hn_splits(m, n, K);
+  int kchunk = ceil_div(K, s);
+  kchunk = ((kchunk + kGK - 1) / kGK) * kGK;
+  const int ns = ceil_div(K, kchunk > 0 ? kchunk : 1);
+  const dim3 grid(ceil_div(m, kGT), ceil_div(n, kGT), ns > 0 ? ns : 1);
+  k_gemm_hn_partial<T, T><<<grid, 256, 0, st>>>(A, lda, B, ldb, m, n, K, kchunk, work);
+  k_gemm_hn_reduce<<<ceil_div((long long)m * n, 256), 256, 0, st>>>(work, grid.z, m, n, C, ldc);
+}
+
+// ---- Y = alpha * U^T-combination of rows of X + beta * Y -----------------------------------
+// CTA: 64 columns g x 32 output rows j; each of the 256 threads owns one g and 8 rows.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_gemm_rot(const cplx<T>* __restrict__ X, int ldx, const double2* __restrict__ U, int ldu, int m, int n, int K,
+           cplx<T>* __restrict__ Y, int ldy, T alpha, T beta) {
+  using C = cplx<T>;
+  __shared__ C Xs[16][64];
+  __shared__ C Us[16][32];
+  const int tg = threadIdx.x & 63, tj = threadIdx.x >> 6;
+  const int g0 = blockIdx.x * 64, j0 = blockIdx.y * 32;
+  const int g = g0 + tg;
+  T re[8], im[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) re[q] = im[q] = 0;
+  for (int i0 = 0; i0 < m; i0 += 16) {
+    for (int idx = threadIdx.x; idx < 16 * 64; idx += 256) {
+      const int ii = idx / 64, gg = idx % 64;
+      Xs[ii][gg] = (i0 + ii < m && g0 + gg < K) ? X[(size_t)(i0 + ii) * ldx + g0 + gg] : mk<T>(0, 0);
+    }
+    for (int idx = threadIdx.x; idx < 16 * 32; idx += 256) {
+      const int ii = idx / 32, jj = idx % 32;
+      if (i0 + ii < m && j0 + jj < n) {
+        const double2 u = U[(size_t)(i0 + ii) * ldu + j0 + jj];
+        Us[ii][jj] = mk<T>((T)u.x, (T)u.y);
+      } else {
+        Us[ii][jj] = mk<T>(0, 0);
+      }
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int ii = 0; ii < 16; ++ii) {
+      const C x = Xs[ii][tg];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const C u = Us[ii][tj + 4 * q];
+        re[q] += u.x * x.x - u.y * x.y;
+        im[q] += u.x * x.y + u.y * x.x;
+      }
+    }
+    __syncthreads();
+  }
+  if (g >= K) return;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int j = j0 + tj + 4 * q;
+    if (j < n) {
+      C* y = Y + (size_t)j * ldy + g;
+      C o;
+      if (beta != (T)0) {
+        const C old = *y;
+        o.x = alpha * re[q] + beta * old.x;
+        o.y = alpha * im[q] + beta * old.y;
+      } else {
+        o.x = alpha * re[q];
+        o.y = alpha * im[q];
+      }
+      *y = o;
+    }
+  }
+}
+
+template <typename T>
+void launch_gemm_rot(const cplx<T>* X, int ldx, const double2* U, int ldu, int m, int n, int K, cplx<T>* Y,
+                     int ldy, double alpha, double beta, cudaStream_t st) {
+  if (n <= 0 || K <= 0) return;
+  const dim3 grid(ceil_div(K, 64), ceil_div(n, 32));
+  k_gemm_rot<T><<<grid, 256, 0, st>>>(X, ldx, U, ldu, m, n, K, Y, ldy, (T)alpha, (T)beta);
+}
+
+// ---- Cholesky and triangular inverse (one CTA) -------------------------------------------
+__global__ void __launch_bounds__(512)
+k_cholesky_inv(const double2* __restrict__ S, int n, double2* __restrict__ L, double2* __restrict__ Li,
+               unsigned* status) {
+  __shared__ int fail;
+  if (threadIdx.x == 0) fail = 0;
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int i = idx / n, j = idx % n;
+    L[idx] = (j <= i) ? S[idx] : make_double2(0, 0);
+  }
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    const double d = L[(size_t)j * n + j].x;
+    if (!(d > 0.0)) {
+      if (threadIdx.x == 0) { fail = 1; atomicOr(status, ST_CHOLESKY); }
+      break;
+    }
+    const double sd = sqrt(d);
+    const double inv = 1.0 / sd;
+    __syncthreads();
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) {
+      double2 v = L[(size_t)i * n + j];
+      v.x *= inv;
+      v.y *= inv;
+      L[(size_t)i * n + j] = v;
+    }
+    if (threadIdx.x == 0) L[(size_t)j * n + j] = make_double2(sd, 0.0);
+    __syncthreads();
+    const int rem = n - j - 1;
+    for (int idx = threadIdx.x; idx < rem * rem; idx += blockDim.x) {
+      const int i = j + 1 + idx / rem, k = j + 1 + idx % rem;
+      if (k <= i) {
+        const double2 a = L[(size_t)i * n + j], b = L[(size_t)k * n + j];
+        double2 v = L[(size_t)i * n + k];
+        // v -= a * conj(b)
+        v.x -= a.x * b.x + a.y * b.y;
+        v.y -= a.y * b.x - a.x * b.y;
+        L[(size_t)i * n + k] = v;
+      }
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  if (fail) return;
+  // Li = L^{-1}: column c by forward substitution, one thread per column.
+  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    for (int i = 0; i < c; ++i) Li[(size_t)i * n + c] = make_double2(0, 0);
+    for (int i = c; i < n; ++i) {
+      double re = (i == c) ? 1.0 : 0.0, im = 0.0;
+      for (int k = c; k < i; ++k) {
+        const double2 l = L[(size_t)i * n + k], x = Li[(size_t)k * n + c];
+        re -= l.x * x.x - l.y * x.y;
+        im -= l.x * x.y + l.y * x.x;
+      }
+      const double dd = L[(size_t)i * n + i].x;
+      Li[(size_t)i * n + c] = make_double2(re / dd, im / dd);
+    }
+  }
+}
+
+void launch_cholesky_inv(const double2* S, int n, double2* L, double2* Linv, unsigned* status, cudaStream_t st) {
+  k_cholesky_inv<<<1, 512, 0, st>>>(S, n, L, Linv, status);
+}
+
+// ---- Hermitian cyclic Jacobi (one CTA, round-robin parallel ordering) ----------------------
+constexpr int kJacobiMaxN = 1024;
+
+__global__ void __launch_bounds__(1024)
+k_jacobi(double2* __restrict__ A, int n, double* __restrict__ w, double2* __restrict__ Vout,
+         double2* __restrict__ V) {
+  __shared__ int pp[kJacobiMaxN / 2], qq[kJacobiMaxN / 2];
+  __shared__ double cc[kJacobiMaxN / 2], ss[kJacobiMaxN / 2];
+  __shared__ double2 uu[kJacobiMaxN / 2];
+  __shared__ double red[32];
+  __shared__ double offn, diagn;
+  const int ne = (n % 2) ? n + 1 : n;  // odd n: a dummy index n sits out each round
+  const int half = ne / 2;
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int i = idx / n, j = idx % n;
+    V[idx] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+  }
+  __syncthreads();
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    // convergence test: off-diagonal vs diagonal Frobenius norms
+    double lo = 0, ld = 0;
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+      const int i = idx / n, j = idx % n;
+      const double2 a = A[idx];
+      const double m2 = a.x * a.x + a.y * a.y;
+      if (i == j) ld += m2; else lo += m2;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      lo += __shfl_xor_sync(0xffffffffu, lo, o);
+      ld += __shfl_xor_sync(0xffffffffu, ld, o);
+    }
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = lo;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0;
+      for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+      offn = t;
+    }
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ld;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0;
+      for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+      diagn = t;
+    }
+    __syncthreads();
+    if (offn <= 1e-30 * (diagn + 1e-300) || offn < 1e-300) break;
+    for (int r = 0; r < ne - 1; ++r) {
+      for (int k = threadIdx.x; k < half; k += blockDim.x) {
+        const int a0 = (k == 0) ? 0 : 1 + ((k - 1 + r) % (ne - 1));
+        const int kb = ne - 1 - k;
+        const int b0 = 1 + ((kb - 1 + r) % (ne - 1));
+        int p = min(a0, b0), q = max(a0, b0);
+        double c = 1.0, s = 0.0;
+        double2 u = make_double2(1.0, 0.0);
+        if (q < n) {
+          const double2 apq = A[(size_t)p * n + q];
+          const double bb = sqrt(apq.x * apq.x + apq.y * apq.y);
+          const double app = A[(size_t)p * n + p].x, aqq = A[(size_t)q * n + q].x;
+          if (bb > 1e-300 && bb > 1e-18 * (fabs(app) + fabs(aqq))) {
+            u = make_double2(apq.x / bb, apq.y / bb);
+            const double th = (aqq - app) / (2.0 * bb);
+            const double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+            c = 1.0 / sqrt(t * t + 1.0);
+            s = t * c;
+          }
+        } else {
+          q = -1;
+        }
+        pp[k] = p;
+        qq[k] = q;
+        cc[k] = c;
+        ss[k] = s;
+        uu[k] = u;
+      }
+      __syncthreads();
+      // columns: A J and V J with J_pp = c, J_pq = s, J_qp = -s conj(u), J_qq = c conj(u)
+      for (int idx = threadIdx.x; idx < n * half; idx += blockDim.x) {
+        const int k = idx / n, i = idx % n;
+        const int p = pp[k], q = qq[k];
+        if (q < 0 || ss[k] == 0.0) continue;
+        const double c = cc[k], s = ss[k];
+        const double2 uc = make_double2(uu[k].x, -uu[k].y);
+        {
+          const double2 x = A[(size_t)i * n + p], y = A[(size_t)i * n + q];
+          const double2 yu = cmul(y, uc);
+          A[(size_t)i * n + p] = make_double2(c * x.x - s * yu.x, c * x.y - s * yu.y);
+          A[(size_t)i * n + q] = make_double2(s * x.x + c * yu.x, s * x.y + c * yu.y);
+        }
+        {
+          const double2 x = V[(size_t)i * n + p], y = V[(size_t)i * n + q];
+          const double2 yu = cmul(y, uc);
+          V[(size_t)i * n + p] = make_double2(c * x.x - s * yu.x, c * x.y - s * yu.y);
+          V[(size_t)i * n + q] = make_double2(s * x.x + c * yu.x, s * x.y + c * yu.y);
+        }
+      }
+      __syncthreads();
+      // rows: J^H (A J): row p = c row_p - s u row_q, row q = s row_p + c u row_q
+      for (int idx = threadIdx.x; idx < n * half; idx += blockDim.x) {
+        const int k = idx / n, j = idx % n;
+        const int p = pp[k], q = qq[k];
+        if (q < 0 || ss[k] == 0.0) continue;
+        const double c = cc[k], s = ss[k];
+        const double2 u = uu[k];
+        const double2 x = A[(size_t)p * n + j], y = A[(size_t)q * n + j];
+        const double2 yu = cmul(y, u);
+        A[(size_t)p * n + j] = make_double2(c * x.x - s * yu.x, c * x.y - s * yu.y);
+        A[(size_t)q * n + j] = make_double2(s * x.x + c * yu.x, s * x.y + c * yu.y);
+      }
+      __syncthreads();
+      for (int k = threadIdx.x; k < half; k += blockDim.x) {
+        const int p = pp[k], q = qq[k];
+        if (q < 0 || ss[k] == 0.0) continue;
+        A[(size_t)p * n + q] = make_double2(0, 0);
+        A[(size_t)q * n + p] = make_double2(0, 0);
+        A[(size_t)p * n + p].y = 0.0;
+        A[(size_t)q * n + q].y = 0.0;
+      }
+      __syncthreads();
+    }
+  }
+  // sort ascending by rank (ties by index) and permute the vectors
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double di = A[(size_t)i * n + i].x;
+    int rank = 0;
+    for (int j = 0; j < n; ++j) {
+      const double dj = A[(size_t)j * n + j].x;
+      rank += (dj < di) || (dj == di && j < i);
+    }
+    w[rank] = di;
+    for (int r = 0; r < n; ++r) Vout[(size_t)r * n + rank] = V[(size_t)r * n + i];
+  }
+}
+
+void launch_jacobi_eig(double2* A, int n, double* w, double2* V, double2* work, cudaStream_t st) {
+  k_jacobi<<<1, 1024, 0, st>>>(A, n, w, V, work);
+}
+
+__global__ void k_hermitize(double2* A, int n) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * n) return;
+  const int i = idx / n, j = idx % n;
+  if (j < i) return;
+  const double2 a = A[(size_t)i * n + j], b = A[(size_t)j * n + i];
+  const double2 h = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
+  A[(size_t)i * n + j] = h;
+  A[(size_t)j * n + i] = make_double2(h.x, -h.y);
+  if (i == j) A[(size_t)i * n + i].y = 0.0;
+}
+
+void launch_hermitize(double2* A, int n, cudaStream_t st) {
+  k_hermitize<<<ceil_div((long long)n * n, 256), 256, 0, st>>>(A, n);
+}
+
+// ---- row-wise helpers ----------------------------------------------------------------------
+template <typename T>
+__global__ void k_residual(const cplx<T>* __restrict__ HX, const cplx<T>* __restrict__ X, const double* eps, int K,
+                           int ld, cplx<T>* __restrict__ R, int ldr) {
+  const int j = blockIdx.y;
+  const T e = (T)eps[j];
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < K; g += gridDim.x * blockDim.x) {
+    const cplx<T> h = HX[(size_t)j * ld + g], x = X[(size_t)j * ld + g];
+    R[(size_t)j * ldr + g] = mk<T>(h.x - e * x.x, h.y - e * x.y);
+  }
+}
+
+template <typename T>
+void launch_residual(const cplx<T>* HX, const cplx<T>* X, const double* eps, int nb, int K, int ld, cplx<T>* R,
+                     int ldr, cudaStream_t st) {
+  if (nb <= 0) return;
+  k_residual<T><<<dim3(ceil_div(K, 256 * 4), nb), 256, 0, st>>>(HX, X, eps, K, ld, R, ldr);
+}
+
+// out[j] = sum_g weight[g] |X[j][g]|^2 (weight NULL: 1); one CTA per row, fixed order.
+template <typename T>
+__global__ void k_row_norms(const cplx<T>* __restrict__ X, int ld, int K, const T* __restrict__ weight,
+                            double* out) {
+  __shared__ double red[32];
+  const int j = blockIdx.x;
+  double acc = 0;
+  for (int g = threadIdx.x; g < K; g += blockDim.x) {
+    const cplx<T> x = X[(size_t)j * ld + g];
+    const double m2 = (double)x.x * x.x + (double)x.y * x.y;
+    acc += weight ? (double)weight[g] * m2 : m2;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+    out[j] = t;
+  }
+}
+
+template <typename T>
+void launch_row_norms(const cplx<T>* X, int ld, int nb, int K, const T* weight, double* out, double*,
+                      cudaStream_t st) {
+  if (nb <= 0) return;
+  k_row_norms<T><<<nb, 512, 0, st>>>(X, ld, K, weight, out);
+}
+
+// Teter-Payne-Allan kinetic preconditioner: W = K(x) R with x = |k+G|^2/2 / T_band,
+// K(x) = (27 + 18x + 12x^2 + 8x^3) / (27 + 18x + 12x^2 + 8x^3 + 16x^4).
+template <typename T>
+__global__ void k_tpa(const cplx<T>* __restrict__ R, int ldr, const T* __restrict__ kin, const double* tband, int K,
+                      cplx<T>* __restrict__ W, int ldw) {
+  const int j = blockIdx.y;
+  const T tb = (T)fmax(tband[j], 1e-12);
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < K; g += gridDim.x * blockDim.x) {
+    const T x = kin[g] / tb;
+    const T p = (T)27 + x * ((T)18 + x * ((T)12 + x * (T)8));
+    const T f = p / (p + (T)16 * x * x * x * x);
+    const cplx<T> r = R[(size_t)j * ldr + g];
+    W[(size_t)j * ldw + g] = mk<T>(f * r.x, f * r.y);
+  }
+}
+
+template <typename T>
+void launch_tpa(const cplx<T>* R, int ldr, const T* kin, const double* tband, int nb, int K, cplx<T>* W, int ldw,
+                cudaStream_t st) {
+  if (nb <= 0) return;
+  k_tpa<T><<<dim3(ceil_div(K, 256 * 4), nb), 256, 0, st>>>(R, ldr, kin, tband, K, W, ldw);
+}
+
+template <typename T>
+__global__ void k_scale_rows(cplx<T>* X, int ld, int K, const double* s) {
+  const int j = blockIdx.y;
+  const T f = (T)s[j];
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < K; g += gridDim.x * blockDim.x) {
+    cplx<T> x = X[(size_t)j * ld + g];
+    x.x *= f;
+    x.y *= f;
+    X[(size_t)j * ld + g] = x;
+  }
+}
+
+template <typename T>
+void launch_scale_rows(cplx<T>* X, int ld, int nb, int K, const double* s, cudaStream_t st) {
+  if (nb <= 0) return;
+  k_scale_rows<T><<<dim3(ceil_div(K, 256 * 4), nb), 256, 0, st>>>(X, ld, K, s);
+}
+
+template <typename Ta, typename Tb>
+__global__ void k_convert_c(const cplx<Ta>* a, cplx<Tb>* b, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    b[i] = mk<Tb>((Tb)a[i].x, (Tb)a[i].y);
+}
+
+template <typename Ta, typename Tb>
+void launch_convert_c(const cplx<Ta>* a, cplx<Tb>* b, size_t n, cudaStream_t st) {
+  if (!n) return;
+  k_convert_c<Ta, Tb><<<(int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096), 256, 0, st>>>(a, b, n);
+}
+
+template <typename T>
+__global__ void k_shape_init(cplx<T>* X, int ld, const T* kin, int K) {
+  const int j = blockIdx.y;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < K; g += gridDim.x * blockDim.x) {
+    cplx<T> x = X[(size_t)j * ld + g];
+    const T f = (T)1 / ((T)1 + kin[g]);
+    x.x *= f;
+    x.y *= f;
+    X[(size_t)j * ld + g] = x;
+  }
+}
+
+template <typename T>
+void launch_shape_init(cplx<T>* X, int ld, const T* kin, int nb, int K, cudaStream_t st) {
+  if (nb <= 0) return;
+  k_shape_init<T><<<dim3(ceil_div(K, 256 * 4), nb), 256, 0, st>>>(X, ld, kin, K);
+}
+
+#define FDE_INST_T(T)                                                                                            \
+  template void launch_gemm_hn<T>(const cplx<T>*, int, const cplx<T>*, int, int, int, int, double2*, int,        \
+                                  double2*, cudaStream_t);                                                       \
+  template void launch_gemm_rot<T>(const cplx<T>*, int, const double2*, int, int, int, int, cplx<T>*, int,       \
+                                   double, double, cudaStream_t);                                                \
+  template void launch_residual<T>(const cplx<T>*, const cplx<T>*, const double*, int, int, int, cplx<T>*, int,  \
+                                   cudaStream_t);                                                                \
+  template void launch_row_norms<T>(const cplx<T>*, int, int, int, const T*, double*, double*, cudaStream_t);    \
+  template void launch_tpa<T>(const cplx<T>*, int, const T*, const double*, int, int, cplx<T>*, int,             \
+                              cudaStream_t);                                                                     \
+  template void launch_scale_rows<T>(cplx<T>*, int, int, int, const double*, cudaStream_t);                      \
+  template void launch_shape_init<T>(cplx<T>*, int, const T*, int, int, cudaStream_t);
+FDE_INST_T(float)
+FDE_INST_T(double)
+template void launch_convert_c<double, float>(const double2*, float2*, size_t, cudaStream_t);
+template void launch_convert_c<float, double>(const float2*, double2*, size_t, cudaStream_t);
+template void launch_convert_c<double, double>(const double2*, double2*, size_t, cudaStream_t);
+
+}  // namespace fde

@@ -1,0 +1,274 @@
+"""Thin ctypes binding of the C ABI in ``include/fde.h`` (argument marshalling only).
+
+Every computation happens inside ``libfde.so``; this module converts Python/NumPy/torch
+arguments into the plain pointers and sizes the ABI takes.  Device buffers are passed as
+torch CUDA tensors (``data_ptr()``), the stream as ``torch.cuda.current_stream()``.
+There is no fallback: if the library is missing or fails to load, importing the entry
+points raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import workloads
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libfde.so")
+
+FDE_OK, FDE_EINVAL, FDE_ENOMEM, FDE_ECUDA, FDE_ENOCONV, FDE_ENONFINITE, FDE_ETIMEOUT, FDE_EUNSUPPORTED = \
+    0, -1, -2, -3, -4, -5, -6, -7
+FDE_PREC_FP64, FDE_PREC_MIXED = 0, 1
+FDE_PRECOND_TPA = 0
+STATUS_NAMES = {0: "FDE_OK", -1: "FDE_EINVAL", -2: "FDE_ENOMEM", -3: "FDE_ECUDA", -4: "FDE_ENOCONV",
+                -5: "FDE_ENONFINITE", -6: "FDE_ETIMEOUT", -7: "FDE_EUNSUPPORTED"}
+
+
+class CellDesc(C.Structure):
+    _fields_ = [("lattice", (C.c_double * 3) * 3), ("grid", C.c_int * 3), ("ecut_ha", C.c_double)]
+
+
+class FuncDesc(C.Structure):
+    _fields_ = [("xc", C.c_int), ("kedf", C.c_int), ("rho_cut", C.c_double)]
+
+
+class SubsysDesc(C.Structure):
+    _fields_ = [("natoms", C.c_int), ("pos", C.POINTER(C.c_double)), ("Z", C.POINTER(C.c_double)),
+                ("rc", C.c_double), ("nproj_per_atom", C.c_int), ("proj_sigma", C.POINTER(C.c_double)),
+                ("proj_D", C.POINTER(C.c_double)), ("nbands", C.c_int), ("nk", C.c_int),
+                ("kpts", C.POINTER(C.c_double)), ("wk", C.POINTER(C.c_double)), ("nelec", C.c_double),
+                ("smearing_ha", C.c_double)]
+
+
+class Energies(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("E_fde", "F_fde", "TS", "E_kin", "E_nl", "E_loc", "E_H", "E_xc",
+                                          "T_nad", "E_xc_nad", "E_H_nad", "E_nn", "E_band_form")] + \
+               [("iters", C.c_int), ("dE", C.c_double)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+EXPORTS = {
+    "fde_create": (C.c_int, [C.POINTER(CellDesc), C.POINTER(FuncDesc), C.c_int, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "fde_add_subsystem": (C.c_int, [C.c_void_p, C.POINTER(SubsysDesc), C.POINTER(C.c_int)]),
+    "fde_get_basis": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_int), C.c_void_p]),
+    "fde_set_density": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int]),
+    "fde_get_density": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "fde_build_vemb": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Energies)]),
+    "fde_set_veff": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "fde_apply_h": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int]),
+    "fde_apply_h_host": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int]),
+    "fde_apply_h_all": (C.c_int, [C.c_void_p]),
+    "fde_init_orbitals": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p]),
+    "fde_set_orbitals": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p]),
+    "fde_get_orbitals": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "fde_subspace_solve": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_int, C.c_int,
+                                     C.POINTER(C.c_int)]),
+    "fde_update_density": (C.c_int, [C.c_void_p, C.c_int]),
+    "fde_energy": (C.c_int, [C.c_void_p, C.POINTER(Energies)]),
+    "fde_scf_subsystem": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_int, C.POINTER(Energies)]),
+    "fde_freeze_thaw_cycle": (C.c_int, [C.c_void_p, C.c_double, C.c_int, C.POINTER(Energies)]),
+    "fde_sync": (C.c_int, [C.c_void_p]),
+    "fde_last_error": (C.c_char_p, [C.c_void_p]),
+    "fde_destroy": (C.c_int, [C.c_void_p]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libfde.so and declare every exported entry point; raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} (run paper_1406_7803_gb300/build.py)")
+    lib = C.CDLL(path)
+    for name, (res, args) in EXPORTS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class FDEError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _dptr(t):
+    """Device pointer of a torch CUDA tensor (or None)."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _hptr(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _dbl(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+class Context:
+    """One library context (cell, grid, functionals, subsystems) on the current device."""
+
+    def __init__(self, lattice, grid, ecut, xc, kedf, rho_cut=1e-10, prec="fp64", stream=None):
+        self.lib = load()
+        cell = CellDesc()
+        for i in range(3):
+            for j in range(3):
+                cell.lattice[i][j] = float(lattice[i][j])
+            cell.grid[i] = int(grid[i])
+        cell.ecut_ha = float(ecut)
+        func = FuncDesc(int(xc), int(kedf), float(rho_cut))
+        self.prec = FDE_PREC_MIXED if prec == "mixed" else FDE_PREC_FP64
+        h = C.c_void_p()
+        st = C.c_void_p(stream) if stream else None
+        s = self.lib.fde_create(C.byref(cell), C.byref(func), self.prec, st, C.byref(h))
+        if s != FDE_OK:
+            raise FDEError(s, "fde_create failed (see stderr)")
+        self.h = h
+        self.grid = tuple(int(n) for n in grid)
+        self.nsub = 0
+        self._keep = []
+
+    def _check(self, s, what):
+        if s != FDE_OK and s != FDE_ENOCONV:
+            raise FDEError(s, f"{what}: {self.lib.fde_last_error(self.h).decode()}")
+        return s
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.fde_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- setup --------------------------------------------------------------------------
+    def add_subsystem(self, pos, Z, rc, nbands, kpts, wk, nelec, smearing, proj_sigma=(), proj_D=()):
+        pos, ppos = _dbl(np.asarray(pos).reshape(-1, 3))
+        Z, pZ = _dbl(Z)
+        kpts, pk = _dbl(np.asarray(kpts).reshape(-1, 3))
+        wk, pw = _dbl(wk)
+        sig, psig = _dbl(proj_sigma if len(proj_sigma) else [0.0])
+        D, pD = _dbl(np.asarray(proj_D).reshape(-1) if len(proj_sigma) else [0.0])
+        d = SubsysDesc(int(Z.size), ppos, pZ, float(rc), int(len(proj_sigma)), psig, pD, int(nbands),
+                       int(kpts.shape[0]), pk, pw, float(nelec), float(smearing))
+        sid = C.c_int()
+        self._check(self.lib.fde_add_subsystem(self.h, C.byref(d), C.byref(sid)), "fde_add_subsystem")
+        self.nsub += 1
+        return sid.value
+
+    def basis(self, sub, k):
+        n = C.c_int()
+        self._check(self.lib.fde_get_basis(self.h, sub, k, C.byref(n), None), "fde_get_basis")
+        mil = np.zeros((n.value, 3), dtype=np.int32)
+        self._check(self.lib.fde_get_basis(self.h, sub, k, C.byref(n), _hptr(mil)), "fde_get_basis")
+        return mil
+
+    # ---- data path ----------------------------------------------------------------------
+    def set_density(self, sub, rho):
+        if hasattr(rho, "is_cuda"):
+            return self._check(self.lib.fde_set_density(self.h, sub, _dptr(rho), 1), "fde_set_density")
+        a = np.ascontiguousarray(rho, dtype=np.float64)
+        return self._check(self.lib.fde_set_density(self.h, sub, _hptr(a), 0), "fde_set_density")
+
+    def get_density(self, sub, out):
+        return self._check(self.lib.fde_get_density(self.h, sub, _dptr(out)), "fde_get_density")
+
+    def build_vemb(self, out=None, energies=False):
+        e = Energies() if energies else None
+        self._check(self.lib.fde_build_vemb(self.h, _dptr(out), C.byref(e) if e is not None else None),
+                    "fde_build_vemb")
+        return e.as_dict() if e is not None else None
+
+    def set_veff(self, sub, v):
+        return self._check(self.lib.fde_set_veff(self.h, sub, _dptr(v)), "fde_set_veff")
+
+    def apply_h(self, sub, k, psi, hpsi, nb):
+        return self._check(self.lib.fde_apply_h(self.h, sub, k, _dptr(psi), _dptr(hpsi), int(nb)), "fde_apply_h")
+
+    def apply_h_host(self, sub, k, psi, hpsi, nb):
+        return self._check(self.lib.fde_apply_h_host(self.h, sub, k, _hptr(psi), _hptr(hpsi), int(nb)),
+                           "fde_apply_h_host")
+
+    def apply_h_all(self):
+        return self._check(self.lib.fde_apply_h_all(self.h), "fde_apply_h_all")
+
+    def init_orbitals(self, sub, k, raw):
+        a = np.ascontiguousarray(raw, dtype=np.complex128)
+        return self._check(self.lib.fde_init_orbitals(self.h, sub, k, _hptr(a)), "fde_init_orbitals")
+
+    def set_orbitals(self, sub, k, psi):
+        return self._check(self.lib.fde_set_orbitals(self.h, sub, k, _dptr(psi)), "fde_set_orbitals")
+
+    def get_orbitals(self, sub, k, out, nbands):
+        eig = np.zeros(nbands)
+        occ = np.zeros(nbands)
+        self._check(self.lib.fde_get_orbitals(self.h, sub, k, _dptr(out), _hptr(eig), _hptr(occ)),
+                    "fde_get_orbitals")
+        return eig, occ
+
+    def subspace_solve(self, sub, k, tol, max_iter=100, precond=FDE_PRECOND_TPA):
+        it = C.c_int()
+        s = self._check(self.lib.fde_subspace_solve(self.h, sub, k, float(tol), int(max_iter), int(precond),
+                                                    C.byref(it)), "fde_subspace_solve")
+        return s, it.value
+
+    def update_density(self, sub):
+        return self._check(self.lib.fde_update_density(self.h, sub), "fde_update_density")
+
+    def energy(self):
+        e = Energies()
+        self._check(self.lib.fde_energy(self.h, C.byref(e)), "fde_energy")
+        return e.as_dict()
+
+    def scf_subsystem(self, sub, tol, max_scf=100):
+        e = Energies()
+        s = self._check(self.lib.fde_scf_subsystem(self.h, sub, float(tol), int(max_scf), C.byref(e)),
+                        "fde_scf_subsystem")
+        return s, e.as_dict()
+
+    def freeze_thaw_cycle(self, tol, max_scf=100):
+        e = Energies()
+        s = self._check(self.lib.fde_freeze_thaw_cycle(self.h, float(tol), int(max_scf), C.byref(e)),
+                        "fde_freeze_thaw_cycle")
+        return s, e.as_dict()
+
+    def sync(self):
+        return self._check(self.lib.fde_sync(self.h), "fde_sync")
+
+
+def context_from_workload(wl: workloads.Workload, prec="fp64", stream=None) -> Context:
+    """Create a context and add every subsystem of a synthetic workload (marshalling only)."""
+    ctx = Context(wl.lattice, wl.grid, wl.ecut, wl.xc, wl.kedf, wl.rho_cut, prec, stream)
+    for s in wl.subsystems:
+        ctx.add_subsystem(s.pos, s.Z, s.rc, s.nbands, s.kpts, s.wk, s.nelec, s.smearing,
+                          s.proj_sigma, s.proj_D)
+    return ctx
+
+
+def seed_workload(ctx: Context, wl: workloads.Workload, seed=None):
+    """Give every (subsystem, k) its seeded initial orbitals and every subsystem its seeded
+    starting density (both generated by ``workloads``)."""
+    seed = wl.seed if seed is None else seed
+    for I, s in enumerate(wl.subsystems):
+        for k in range(s.nk):
+            npw = ctx.basis(I, k).shape[0]
+            ctx.init_orbitals(I, k, workloads.raw_orbitals(seed, I, k, s.nbands, npw))
+        ctx.set_density(I, workloads.initial_density(wl, I))

@@ -1,0 +1,182 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle, element by element.
+
+Tolerances: FP64 path 1e-10 relative on H psi and 1e-8 Ha on energies; mixed FP32 path
+1e-5 relative on H psi.  Sizes span several tiles (many z-columns per CTA, many planes) and
+ragged tails (sphere columns that do not fill the last CTA, odd grid sizes)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from oracle import basis, fde as ofde, scf as oscf  # noqa: E402
+from paper_1406_7803_gb300 import fde, workloads  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1406_7803_gb300 import build
+    build.build()
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+
+
+def _smooth_potential(sy, seed=5):
+    rng = np.random.default_rng(seed)
+    r = basis.grid_points(sy.lattice, sy.grid)
+    B = basis.reciprocal(sy.lattice)
+    v = np.full(sy.grid, -0.3)
+    for _ in range(6):
+        m = rng.integers(-3, 4, size=3)
+        v += 0.2 * rng.standard_normal() * np.cos(r @ (m @ B) + rng.uniform(0, 6.28))
+    return v
+
+
+def _dev(a, dtype=torch.complex128):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
+
+
+WL_SMALL = [workloads.plain_fde_32, workloads.molecule_on_slab_small]
+
+
+@pytest.mark.parametrize("make", WL_SMALL)
+def test_basis_bit_exact(make):
+    wl = make()
+    sy = ofde.System(wl)
+    ctx = fde.context_from_workload(wl)
+    for I, s in enumerate(wl.subsystems):
+        for k in range(s.nk):
+            assert np.array_equal(ctx.basis(I, k), sy.basis[I][k][0])
+
+
+def test_basis_bit_exact_full_size_slab():
+    wl = workloads.molecule_on_slab()
+    ctx = fde.context_from_workload(wl)
+    for k in (0, 3):
+        mil, _ = basis.sphere(wl.lattice, wl.grid, wl.subsystems[0].kpts[k], wl.ecut)
+        assert np.array_equal(ctx.basis(0, k), mil)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("mixed", 1e-5)])
+@pytest.mark.parametrize("make", WL_SMALL)
+def test_apply_h_matches_oracle(make, prec, tol):
+    wl = make()
+    sy = ofde.System(wl)
+    ctx = fde.context_from_workload(wl, prec=prec)
+    v = _smooth_potential(sy)
+    ctdt = torch.complex128 if prec == "fp64" else torch.complex64
+    for I, s in enumerate(wl.subsystems):
+        ctx.set_veff(I, _dev(v, torch.float64))
+        for k in range(s.nk):
+            npw = sy.basis[I][k][0].shape[0]
+            nb = s.nbands + 3  # a block that is not a multiple of anything
+            c = workloads.raw_orbitals(7, I, k, nb, npw)
+            want = sy.apply_h(I, k, c, v)
+            psi = _dev(c, ctdt)
+            hpsi = torch.zeros_like(psi)
+            ctx.apply_h(I, k, psi, hpsi, nb)
+            torch.cuda.synchronize()
+            got = hpsi.to(torch.complex128).cpu().numpy()
+            err = np.abs(got - want).max() / np.abs(want).max()
+            assert err < tol, (I, k, err)
+
+
+def test_apply_h_host_path_matches_device_path():
+    wl = workloads.molecule_on_slab_small()
+    sy = ofde.System(wl)
+    ctx = fde.context_from_workload(wl)
+    v = _smooth_potential(sy)
+    ctx.set_veff(0, _dev(v, torch.float64))
+    npw = sy.basis[0][1][0].shape[0]
+    c = workloads.raw_orbitals(3, 0, 1, 5, npw)
+    out = np.zeros_like(c)
+    ctx.apply_h_host(0, 1, c, out, 5)
+    want = sy.apply_h(0, 1, c, v)
+    assert np.abs(out - want).max() / np.abs(want).max() < 1e-10
+
+
+@pytest.mark.parametrize("make", WL_SMALL)
+def test_build_vemb_matches_oracle(make):
+    wl = make()
+    sy = ofde.System(wl)
+    rhos = np.array([workloads.initial_density(wl, I) for I in range(wl.nsub)])
+    pot = sy.build_veff(rhos)
+    zero_orbitals = [[np.zeros((s.nbands, sy.basis[I][k][0].shape[0])) for k in range(s.nk)]
+                     for I, s in enumerate(sy.subs)]
+    zero_occ = [[np.zeros(s.nbands) for _ in range(s.nk)] for s in sy.subs]
+    en = sy.energies(zero_orbitals, zero_occ, rhos, pot=pot)
+    ctx = fde.context_from_workload(wl)
+    for I in range(wl.nsub):
+        ctx.set_density(I, rhos[I])
+    out = torch.zeros((wl.nsub,) + tuple(wl.grid), dtype=torch.float64, device="cuda")
+    e = ctx.build_vemb(out, energies=True)
+    got = out.cpu().numpy()
+    for I in range(wl.nsub):
+        err = np.abs(got[I] - pot["veff"][I]).max() / np.abs(pot["veff"][I]).max()
+        assert err < 1e-10, (I, err)
+    for key, okey in (("E_loc", "E_loc"), ("E_H", "E_H"), ("E_xc", "E_xc"), ("T_nad", "T_nad"),
+                      ("E_xc_nad", "E_xc_nad"), ("E_H_nad", "E_H_nad"), ("E_nn", "E_nn")):
+        assert abs(e[key] - en[okey]) < 1e-8, (key, e[key], en[okey])
+
+
+def test_build_vemb_mixed_matches_oracle():
+    wl = workloads.molecule_on_slab_small()
+    sy = ofde.System(wl)
+    rhos = np.array([workloads.initial_density(wl, I) for I in range(wl.nsub)])
+    pot = sy.build_veff(rhos)
+    ctx = fde.context_from_workload(wl, prec="mixed")
+    for I in range(wl.nsub):
+        ctx.set_density(I, rhos[I])
+    out = torch.zeros((wl.nsub,) + tuple(wl.grid), dtype=torch.float64, device="cuda")
+    ctx.build_vemb(out)
+    got = out.cpu().numpy()
+    for I in range(wl.nsub):
+        assert np.abs(got[I] - pot["veff"][I]).max() / np.abs(pot["veff"][I]).max() < 1e-5
+
+
+def test_davidson_eigenvalues_match_dense_eigh():
+    """Converged Davidson eigenvalues equal the lowest n_b eigenvalues of the dense H
+    (LAPACK eigh in the oracle), and the density of the occupied subspace matches."""
+    wl = workloads.molecule_on_slab_small()
+    sy = ofde.System(wl)
+    rhos = np.array([workloads.initial_density(wl, I) for I in range(wl.nsub)])
+    pot = sy.build_veff(rhos)
+    ctx = fde.context_from_workload(wl)
+    fde.seed_workload(ctx, wl)
+    for I in range(wl.nsub):
+        ctx.set_density(I, rhos[I])
+    ctx.build_vemb()
+    for I, s in enumerate(wl.subsystems):
+        eigs_o, vecs_o = [], []
+        for k in range(s.nk):
+            st, it = ctx.subspace_solve(I, k, 1e-9, 200)
+            assert st == fde.FDE_OK, (I, k, it)
+            w, v = oscf.eig_dense(sy, I, k, pot["veff"][I], s.nbands)
+            npw = sy.basis[I][k][0].shape[0]
+            buf = torch.zeros((s.nbands, npw), dtype=torch.complex128, device="cuda")
+            eig, _ = ctx.get_orbitals(I, k, buf, s.nbands)
+            assert np.abs(eig - w).max() < 1e-9, (I, k, eig - w)
+            eigs_o.append(w)
+            vecs_o.append(v)
+        ctx.update_density(I)
+        occ, _, _ = oscf.occupations(eigs_o, s.wk, s.nelec, s.smearing)
+        want = sy.density(I, vecs_o, occ)
+        got = torch.zeros(tuple(wl.grid), dtype=torch.float64, device="cuda")
+        ctx.get_density(I, got)
+        assert np.abs(got.cpu().numpy() - want).max() < 1e-7 * np.abs(want).max()
+
+
+def test_freeze_thaw_cycle_matches_oracle_plain_fde():
+    """One Jacobi freeze-and-thaw cycle on the 2 x 3-atom LDA + TF cell: every energy term
+    within 1e-8 Ha of the oracle's cycle from the same seeded start."""
+    wl = workloads.plain_fde_32()
+    sy = ofde.System(wl)
+    st = oscf.initial_state(sy)
+    _, want = oscf.freeze_thaw_cycle(sy, st)
+    ctx = fde.context_from_workload(wl)
+    fde.seed_workload(ctx, wl)
+    s, got = ctx.freeze_thaw_cycle(wl.tol, 100)
+    assert s == fde.FDE_OK
+    for key in ("E_fde", "E_kin", "E_loc", "E_H", "E_xc", "T_nad", "E_nn"):
+        assert abs(got[key] - want[key]) < 1e-8, (key, got[key], want[key])
