@@ -213,6 +213,14 @@ fde_status fde_scf_subsystem(fde_ctx* ctx, int sub, double tol_ha, int max_scf,
  * out (nullable) receives the energies of the refreshed state. */
 fde_status fde_freeze_thaw_cycle(fde_ctx* ctx, double tol_ha, int max_scf, fde_energies* out);
 
+/* Per-kernel timing of the library's own launches (measurement support; no counterpart in
+ * the paper).  fde_profile_enable(ctx, 1) clears the records and starts recording a CUDA
+ * event pair around every launch of the timed kernels (k_zinv, k_plane, k_zfwd) on the
+ * context stream; 0 stops.  fde_profile_get returns the number of recorded launches of
+ * `kernel` and their summed device time in ms (synchronising; 0 launches if none). */
+fde_status fde_profile_enable(fde_ctx* ctx, int enable);
+fde_status fde_profile_get(fde_ctx* ctx, const char* kernel, int* launches, double* total_ms);
+
 /* Synchronise the context stream and check the device status word. */
 fde_status fde_sync(fde_ctx* ctx);
 

@@ -17,9 +17,12 @@
 #include "fde.h"
 #include "grid_kernels.h"
 #include "kernels.h"
+#include "prof.h"
 #include "small.h"
 
 namespace fde {
+
+thread_local Profiler* tl_prof = nullptr;
 
 struct Err {
   fde_status st;
@@ -238,7 +241,7 @@ template <typename T> struct EngineT : Engine {
   // band work
   DBuf<C> scratch;
   DBuf<double2> gwork, Pm, Qm;
-  DBuf<C> V, HV, V2, HV2, R;
+  DBuf<C> V, HV, V2, HV2, R, Pb, HPb;
   DBuf<double2> S, Hs, L, Li, Ht, Y, Cc, tmp, jwork;
   DBuf<double> wv, dnorm, deps, dtb;
   DBuf<int> didx;
@@ -778,6 +781,7 @@ template <typename T> struct EngineT : Engine {
   }
 
   // ---- Rayleigh-Ritz on the n rows of V / HV; keeps the lowest nb pairs in V2 / HV2 ------------
+  // The coefficients of the kept pairs stay in Cc ([n][n], column j = pair j).
   void rayleigh_ritz(KP<T>& q, int n, int nb, std::vector<double>& eps) {
     const int K = q.npw;
     gwork.ensure(gemm_hn_work(n, n, K));
@@ -800,28 +804,50 @@ template <typename T> struct EngineT : Engine {
     eps.resize(nb);
   }
 
+  // Orthogonalise the m rows B against the nb current orbitals (rows 0..nb of V), apply the
+  // same change to their H-images HB when given, and normalise the rows (HB alike).
+  void orth_block(KP<T>& q, int nb, C* Bk, C* HBk, int m) {
+    const int K = q.npw;
+    gwork.ensure(gemm_hn_work(nb, m, K));
+    launch_gemm_hn<T>(V.p, K, Bk, K, nb, m, K, Cc.p, m, gwork.p, st);
+    launch_gemm_rot<T>(V.p, K, Cc.p, m, nb, m, K, Bk, K, -1.0, 1.0, st);
+    if (HBk) launch_gemm_rot<T>(HV.p, K, Cc.p, m, nb, m, K, HBk, K, -1.0, 1.0, st);
+    std::vector<double> sc(m);
+    launch_row_norms<T>(Bk, K, m, K, nullptr, dnorm.p, nullptr, st);
+    CK(cudaMemcpyAsync(sc.data(), dnorm.p, m * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (int a = 0; a < m; ++a) sc[a] = 1.0 / sqrt(std::max(sc[a], 1e-300));
+    CK(cudaMemcpyAsync(dtb.p, sc.data(), m * sizeof(double), cudaMemcpyHostToDevice, st));
+    launch_scale_rows<T>(Bk, K, m, K, dtb.p, st);
+    if (HBk) launch_scale_rows<T>(HBk, K, m, K, dtb.p, st);
+  }
+
+  // Block eigensolver (LOBPCG form of block Davidson): the search space of every iteration is
+  // the current orbitals X, the TPA-preconditioned residuals W of the unconverged bands and
+  // their previous update directions P; Rayleigh-Ritz in FP64 keeps the lowest nb pairs.
   fde_status subspace_solve(int i, int k, double tol, int max_iter, int* iters) override {
     Sub<T>& s = sub(i);
     KP<T>& q = kpt(i, k);
     REQ(q.have_orbitals, FDE_EINVAL, "orbitals of this (subsystem, k) are not set");
     const int nb = s.nb, K = q.npw;
     const size_t rowsz = (size_t)K * sizeof(C);
-    V.ensure((size_t)2 * nb * K);
-    HV.ensure((size_t)2 * nb * K);
-    V2.ensure((size_t)2 * nb * K);
-    HV2.ensure((size_t)2 * nb * K);
+    V.ensure((size_t)3 * nb * K);
+    HV.ensure((size_t)3 * nb * K);
+    V2.ensure((size_t)nb * K);
+    HV2.ensure((size_t)nb * K);
     R.ensure((size_t)nb * K);
-    ensure_small(2 * nb);
+    Pb.ensure((size_t)nb * K);
+    HPb.ensure((size_t)nb * K);
+    ensure_small(3 * nb);
     std::vector<double> eps;
-    // Rayleigh-Ritz on the current orbitals
     CK(cudaMemcpyAsync(V.p, q.X.p, nb * rowsz, cudaMemcpyDeviceToDevice, st));
     apply_h_dev(s, q, V.p, HV.p, nb);
     rayleigh_ritz(q, nb, nb, eps);
     CK(cudaMemcpyAsync(V.p, V2.p, nb * rowsz, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(HV.p, HV2.p, nb * rowsz, cudaMemcpyDeviceToDevice, st));
     int it = 0;
-    bool conv = false;
-    std::vector<double> rn(nb), tb(nb), sc(nb);
+    bool conv = false, havep = false;
+    std::vector<double> rn(nb), tb(nb);
     for (;;) {
       CK(cudaMemcpyAsync(deps.p, eps.data(), nb * sizeof(double), cudaMemcpyHostToDevice, st));
       launch_residual<T>(HV.p, V.p, deps.p, nb, K, K, R.p, K, st);
@@ -840,7 +866,6 @@ template <typename T> struct EngineT : Engine {
       CK(cudaMemcpyAsync(didx.p, sel.data(), m * sizeof(int), cudaMemcpyHostToDevice, st));
       C* W = V.p + (size_t)nb * K;
       launch_gather_rows<T>(R.p, K, didx.p, m, K, W, K, st);
-      // band kinetic energies of the selected bands -> TPA preconditioner
       launch_row_norms<T>(V.p, K, nb, K, q.kin_d.p, dnorm.p, nullptr, st);
       CK(cudaMemcpyAsync(tb.data(), dnorm.p, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
@@ -848,25 +873,37 @@ template <typename T> struct EngineT : Engine {
       for (int a = 0; a < m; ++a) tsel[a] = tb[sel[a]];
       CK(cudaMemcpyAsync(dtb.p, tsel.data(), m * sizeof(double), cudaMemcpyHostToDevice, st));
       launch_tpa<T>(W, K, q.kin_d.p, dtb.p, m, K, W, K, st);
-      // orthogonalise against the current orbitals and normalise
-      gwork.ensure(gemm_hn_work(nb, m, K));
-      launch_gemm_hn<T>(V.p, K, W, K, nb, m, K, Cc.p, m, gwork.p, st);
-      launch_gemm_rot<T>(V.p, K, Cc.p, m, nb, m, K, W, K, -1.0, 1.0, st);
-      launch_row_norms<T>(W, K, m, K, nullptr, dnorm.p, nullptr, st);
-      CK(cudaMemcpyAsync(sc.data(), dnorm.p, m * sizeof(double), cudaMemcpyDeviceToHost, st));
-      CK(cudaStreamSynchronize(st));
-      for (int a = 0; a < m; ++a) sc[a] = 1.0 / sqrt(std::max(sc[a], 1e-300));
-      CK(cudaMemcpyAsync(dtb.p, sc.data(), m * sizeof(double), cudaMemcpyHostToDevice, st));
-      launch_scale_rows<T>(W, K, m, K, dtb.p, st);
+      orth_block(q, nb, W, nullptr, m);
+      int np = 0;
+      if (havep) {
+        C* P = V.p + (size_t)(nb + m) * K;
+        C* HP = HV.p + (size_t)(nb + m) * K;
+        launch_gather_rows<T>(Pb.p, K, didx.p, m, K, P, K, st);
+        launch_gather_rows<T>(HPb.p, K, didx.p, m, K, HP, K, st);
+        orth_block(q, nb, P, HP, m);
+        np = m;
+      }
       apply_h_dev(s, q, W, HV.p + (size_t)nb * K, m);
+      int n = nb + m + np;
       try {
-        rayleigh_ritz(q, nb + m, nb, eps);
+        rayleigh_ritz(q, n, nb, eps);
       } catch (Err& e) {
         if (e.st != FDE_ENOCONV) throw;
-        break;  // dependent search directions: keep the current orbitals
+        if (np == 0) break;  // dependent search directions: keep the current orbitals
+        n = nb + m;          // drop the previous directions and retry once
+        try {
+          rayleigh_ritz(q, n, nb, eps);
+        } catch (Err& e2) {
+          if (e2.st != FDE_ENOCONV) throw;
+          break;
+        }
       }
+      // update directions P = [W P] C[nb:n, :nb] (and their H-images)
+      launch_gemm_rot<T>(V.p + (size_t)nb * K, K, Cc.p + (size_t)nb * n, n, n - nb, nb, K, Pb.p, K, 1.0, 0.0, st);
+      launch_gemm_rot<T>(HV.p + (size_t)nb * K, K, Cc.p + (size_t)nb * n, n, n - nb, nb, K, HPb.p, K, 1.0, 0.0, st);
       CK(cudaMemcpyAsync(V.p, V2.p, nb * rowsz, cudaMemcpyDeviceToDevice, st));
       CK(cudaMemcpyAsync(HV.p, HV2.p, nb * rowsz, cudaMemcpyDeviceToDevice, st));
+      havep = true;
     }
     CK(cudaMemcpyAsync(q.X.p, V.p, nb * rowsz, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(q.HX.p, HV.p, nb * rowsz, cudaMemcpyDeviceToDevice, st));
@@ -1093,7 +1130,12 @@ template <typename T> struct EngineT : Engine {
   }
 
   // ---- subsystem SCF and freeze-and-thaw ------------------------------------------------------
-  double davidson_tol(double tol) const { return sizeof(T) == 8 ? std::max(1e-9, std::min(1e-6, 0.1 * sqrt(tol))) : 3e-5; }
+  // Inner-iteration thresholds.  One freeze-and-thaw cycle evaluates the energy with every
+  // density refreshed, which is not stationary in the inner-SCF densities, so the density
+  // residual int|rho_out - rho_in| is converged to 10 x the energy tolerance (FP32 orbitals
+  // floor it near 1e-4 in the mixed path).
+  double davidson_tol(double tol) const { return sizeof(T) == 8 ? std::max(1e-10, std::min(1e-6, tol)) : 3e-5; }
+  double dres_tol(double tol) const { return sizeof(T) == 8 ? 10.0 * tol : std::max(10.0 * tol, 1e-4); }
 
   fde_status scf_subsystem(int I, double tol, int max_scf, fde_energies* out) override {
     Sub<T>& s = sub(I);
@@ -1146,7 +1188,7 @@ template <typename T> struct EngineT : Engine {
       const double dres = integrate_absdiff(s.rho.p, rho_in.p);
       en.dE = have_prev ? en.F_fde - Eprev : 0.0;
       REQ(std::isfinite(en.F_fde), FDE_ENONFINITE, "non-finite energy");
-      if (have_prev && fabs(en.dE) < tol && dres < sqrt(tol)) {
+      if (have_prev && fabs(en.dE) < tol && dres < dres_tol(tol)) {
         if (out) *out = en;
         return FDE_OK;
       }
@@ -1209,20 +1251,25 @@ struct fde_ctx {
   std::unique_ptr<fde::Engine> eng;
   std::string err;
   fde_prec prec;
+  fde::Profiler prof;
 };
 
 template <typename F> static fde_status guard(fde_ctx* c, F&& f) {
   if (!c) return FDE_EINVAL;
+  fde::tl_prof = &c->prof;
+  fde_status r;
   try {
     c->err.clear();
-    return f();
+    r = f();
   } catch (fde::Err& e) {
     c->err = e.msg;
-    return e.st;
+    r = e.st;
   } catch (std::exception& e) {
     c->err = e.what();
-    return FDE_ENOMEM;
+    r = FDE_ENOMEM;
   }
+  fde::tl_prof = nullptr;
+  return r;
 }
 
 extern "C" {
@@ -1309,6 +1356,21 @@ fde_status fde_freeze_thaw_cycle(fde_ctx* c, double tol, int max_scf, fde_energi
 }
 fde_status fde_sync(fde_ctx* c) {
   return guard(c, [&]() { c->eng->sync(); return FDE_OK; });
+}
+fde_status fde_profile_enable(fde_ctx* c, int enable) {
+  return guard(c, [&]() {
+    c->eng->sync();
+    c->prof.reset();
+    c->prof.on = enable != 0;
+    return FDE_OK;
+  });
+}
+fde_status fde_profile_get(fde_ctx* c, const char* kernel, int* launches, double* total_ms) {
+  return guard(c, [&]() {
+    if (!kernel || !launches || !total_ms) throw fde::Err{FDE_EINVAL, "null argument"};
+    c->prof.get(kernel, launches, total_ms);
+    return FDE_OK;
+  });
 }
 const char* fde_last_error(const fde_ctx* c) { return c ? c->err.c_str() : "null context"; }
 fde_status fde_destroy(fde_ctx* c) {

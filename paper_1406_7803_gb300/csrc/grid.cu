@@ -310,17 +310,20 @@ __global__ void k_pointwise(const double* __restrict__ rho, cplx<T>* gx, cplx<T>
                             double* partial) {
   double ax = 0, ak = 0;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < nr; idx += (long long)gridDim.x * blockDim.x) {
-    const T r = (T)rho[idx];
-    T x = 0, y = 0, z = 0;
-    if (gx) { x = gx[idx].x; y = gy[idx].x; z = gz[idx].x; }
-    T v, h;
+    // The functionals are evaluated in FP64 in both precisions: at low density the PBE
+    // correlation's intermediate A t^2 overflows FP32, and these points cost little
+    // next to the transforms.
+    const double r = rho[idx];
+    double x = 0, y = 0, z = 0;
+    if (gx) { x = (double)gx[idx].x; y = (double)gy[idx].x; z = (double)gz[idx].x; }
+    double v, h;
     double ex, ek;
-    point_functional<T>(r, x, y, z, xc_mode, xc_pot, kedf, (T)rho_cut, &v, &h, &ex, &ek);
-    if (vpart) vpart[idx] = (double)v;
+    point_functional<double>(r, x, y, z, xc_mode, xc_pot, kedf, rho_cut, &v, &h, &ex, &ek);
+    if (vpart) vpart[idx] = v;
     if (gx) {
-      gx[idx] = mk<T>(h * x, 0);
-      gy[idx] = mk<T>(h * y, 0);
-      gz[idx] = mk<T>(h * z, 0);
+      gx[idx] = mk<T>((T)(h * x), 0);
+      gy[idx] = mk<T>((T)(h * y), 0);
+      gz[idx] = mk<T>((T)(h * z), 0);
     }
     ax += ex;
     ak += ek;

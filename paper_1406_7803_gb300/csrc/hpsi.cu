@@ -19,6 +19,7 @@
 // of the 4 x N_r of a plain 3D transform pair.
 #include "fft.cuh"
 #include "kernels.h"
+#include "prof.h"
 
 namespace fde {
 
@@ -153,10 +154,19 @@ void launch_hpsi_local(const cplx<T>* psi, int ldpsi, cplx<T>* hpsi, int ldh, in
   allow_smem(k_zinv<T>, zs);
   allow_smem(k_zfwd<T>, zs);
   allow_smem(k_plane<T>, ps);
-  k_zinv<T><<<gz, kColsPerCta * 32, zs, st>>>(psi, ldpsi, scratch, sp, g.n3, fp.p3);
-  k_plane<T><<<dim3(g.n3, nb), kPlaneThreads, ps, st>>>(scratch, sp, vplane, g, fp.p1, fp.p2);
+  {
+    ProfScope p("k_zinv", st);
+    k_zinv<T><<<gz, kColsPerCta * 32, zs, st>>>(psi, ldpsi, scratch, sp, g.n3, fp.p3);
+  }
+  {
+    ProfScope p("k_plane", st);
+    k_plane<T><<<dim3(g.n3, nb), kPlaneThreads, ps, st>>>(scratch, sp, vplane, g, fp.p1, fp.p2);
+  }
   const T inv_nr = (T)(1.0 / ((double)g.n1 * g.n2 * g.n3));
-  k_zfwd<T><<<gz, kColsPerCta * 32, zs, st>>>(scratch, psi, ldpsi, hpsi, ldh, kin, sp, g.n3, inv_nr, fp.p3);
+  {
+    ProfScope p("k_zfwd", st);
+    k_zfwd<T><<<gz, kColsPerCta * 32, zs, st>>>(scratch, psi, ldpsi, hpsi, ldh, kin, sp, g.n3, inv_nr, fp.p3);
+  }
 }
 
 // ---- densities ---------------------------------------------------------------------------

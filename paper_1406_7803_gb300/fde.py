@@ -70,6 +70,8 @@ EXPORTS = {
     "fde_energy": (C.c_int, [C.c_void_p, C.POINTER(Energies)]),
     "fde_scf_subsystem": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_int, C.POINTER(Energies)]),
     "fde_freeze_thaw_cycle": (C.c_int, [C.c_void_p, C.c_double, C.c_int, C.POINTER(Energies)]),
+    "fde_profile_enable": (C.c_int, [C.c_void_p, C.c_int]),
+    "fde_profile_get": (C.c_int, [C.c_void_p, C.c_char_p, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "fde_sync": (C.c_int, [C.c_void_p]),
     "fde_last_error": (C.c_char_p, [C.c_void_p]),
     "fde_destroy": (C.c_int, [C.c_void_p]),
@@ -252,6 +254,15 @@ class Context:
 
     def sync(self):
         return self._check(self.lib.fde_sync(self.h), "fde_sync")
+
+    def profile_enable(self, on=True):
+        return self._check(self.lib.fde_profile_enable(self.h, int(on)), "fde_profile_enable")
+
+    def profile_get(self, kernel):
+        n = C.c_int()
+        ms = C.c_double()
+        self._check(self.lib.fde_profile_get(self.h, kernel.encode(), C.byref(n), C.byref(ms)), "fde_profile_get")
+        return n.value, ms.value
 
 
 def context_from_workload(wl: workloads.Workload, prec="fp64", stream=None) -> Context:
