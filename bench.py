@@ -200,6 +200,7 @@ def run_ours(args):
     ctx.sync()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     ctx.profile_enable(True)
+    launches0 = ctx.launch_count()
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -213,6 +214,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
     step_ms = [a.elapsed_time(b) for a, b in ev]
+    launches = ctx.launch_count() - launches0
     total_ms = float(np.sum(step_ms))
     prof = {n: ctx.profile_get(n) for n in ("k_zinv", "k_plane", "k_zfwd")}
     ctx.profile_enable(False)
@@ -298,7 +300,7 @@ def run_ours(args):
                            "parallelism": f"replicas x{ws}"},
                 "e2e": {"value": ws * units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
-                "gpu_launches": None, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
+                "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
                 "wall_s": wall, "step_ms": step_ms}
         print(json.dumps(line))
     if ws > 1:

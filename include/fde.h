@@ -221,6 +221,10 @@ fde_status fde_freeze_thaw_cycle(fde_ctx* ctx, double tol_ha, int max_scf, fde_e
 fde_status fde_profile_enable(fde_ctx* ctx, int enable);
 fde_status fde_profile_get(fde_ctx* ctx, const char* kernel, int* launches, double* total_ms);
 
+/* Number of CUDA kernel launches the context's calls have made since it was created
+ * (counted on the host at every launch; measurement support, no counterpart in the paper). */
+fde_status fde_launch_count(fde_ctx* ctx, long long* launches);
+
 /* Synchronise the context stream and check the device status word. */
 fde_status fde_sync(fde_ctx* ctx);
 

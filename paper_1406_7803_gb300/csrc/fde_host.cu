@@ -213,8 +213,15 @@ struct Engine {
   virtual void update_density(int sub) = 0;
   virtual void energy(fde_energies* out) = 0;
   virtual fde_status scf_subsystem(int sub, double tol, int max_scf, fde_energies* out) = 0;
-  virtual fde_status freeze_thaw(double tol, int max_scf, fde_energies* out) = 0;
+  virtual fde_status freeze_thaw(double tol, int max_scf, fde_energies* out, const double* start) = 0;
   virtual void sync() = 0;
+  virtual int nsub() const = 0;
+  virtual long long grid_points() const = 0;
+  virtual void shape(int sub, int* nb, int* nk) = 0;
+  virtual int npw(int sub, int k) = 0;
+  virtual void set_eig_occ(int sub, int k, const double* eig, const double* occ) = 0;
+  virtual void set_subsystem_entropy(int sub, double ts) = 0;
+  virtual double subsystem_entropy(int sub) = 0;
 };
 
 template <typename T> struct EngineT : Engine {
@@ -303,6 +310,22 @@ template <typename T> struct EngineT : Engine {
     REQ(i >= 0 && i < (int)subs.size(), FDE_EINVAL, "subsystem index out of range");
     return *subs[i];
   }
+  int nsub() const override { return (int)subs.size(); }
+  long long grid_points() const override { return nr; }
+  void shape(int i, int* nb, int* nk) override {
+    *nb = sub(i).nb;
+    *nk = sub(i).nk;
+  }
+  int npw(int i, int k) override { return kpt(i, k).npw; }
+  void set_eig_occ(int i, int k, const double* eig, const double* occ) override {
+    KP<T>& q = kpt(i, k);
+    const int nb = sub(i).nb;
+    q.eig.assign(eig, eig + nb);
+    q.occ.assign(occ, occ + nb);
+    q.have_eig = true;
+  }
+  void set_subsystem_entropy(int i, double ts) override { sub(i).entropy = ts; }
+  double subsystem_entropy(int i) override { return sub(i).entropy; }
   KP<T>& kpt(int i, int k) {
     Sub<T>& s = sub(i);
     REQ(k >= 0 && k < s.nk, FDE_EINVAL, "k-point index out of range");
@@ -627,7 +650,6 @@ template <typename T> struct EngineT : Engine {
   }
 
   void build_vemb(double* d_out, fde_energies* e) override {
-    locked = false;
     ensure_vloc();
     EnergyParts ep = grid_pass(true, e != nullptr, -1);
     if (d_out)
@@ -1200,7 +1222,10 @@ template <typename T> struct EngineT : Engine {
     return FDE_ENOCONV;
   }
 
-  fde_status freeze_thaw(double tol, int max_scf, fde_energies* out) override {
+  // One Jacobi cycle against the current densities (frozen at the cycle start).  start
+  // (device [nsub][N_r], nullable): densities each subsystem SCF starts from instead of
+  // its frozen one (a warm start that leaves the cycle's fixed point unchanged).
+  fde_status freeze_thaw(double tol, int max_scf, fde_energies* out, const double* start) override {
     REQ(!subs.empty(), FDE_EINVAL, "no subsystems");
     ensure_vloc();
     const size_t ns = subs.size();
@@ -1212,7 +1237,8 @@ template <typename T> struct EngineT : Engine {
     int iters = 0;
     for (size_t I = 0; I < ns; ++I) {
       for (size_t J = 0; J < ns; ++J)
-        CK(cudaMemcpyAsync(subs[J]->rho.p, frozen.p + J * nr, nr * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(subs[J]->rho.p, (start && J == I ? start : frozen.p) + J * nr, nr * sizeof(double),
+                           cudaMemcpyDeviceToDevice, st));
       fde_energies e{};
       const fde_status r = scf_subsystem((int)I, tol, max_scf, &e);
       if (r != FDE_OK) worst = r;
@@ -1248,11 +1274,90 @@ template <> void EngineT<float>::convert_out(const float2* a, double2* b, size_t
 
 // ---- C ABI ------------------------------------------------------------------------------------
 struct fde_ctx {
-  std::unique_ptr<fde::Engine> eng;
+  std::unique_ptr<fde::Engine> eng;    // working precision
+  std::unique_ptr<fde::Engine> eng64;  // FP64 refinement engine of a mixed context
+  cudaStream_t stream = nullptr;
   std::string err;
   fde_prec prec;
   fde::Profiler prof;
 };
+
+namespace fde {
+
+// Copy densities, orbitals, eigenvalues, occupations and entropies of every subsystem from
+// one engine to another (the precisions may differ; orbitals pass through FP64).
+static void transfer_state(Engine& from, Engine& to, cudaStream_t st) {
+  const int ns = from.nsub();
+  const long long nr = from.grid_points();
+  DBuf<double> rho;
+  rho.alloc(nr);
+  for (int I = 0; I < ns; ++I) {
+    from.get_density(I, rho.p);
+    to.set_density(I, rho.p, 1);
+    int nb, nk;
+    from.shape(I, &nb, &nk);
+    for (int k = 0; k < nk; ++k) {
+      DBuf<double2> psi;
+      psi.alloc((size_t)nb * from.npw(I, k));
+      std::vector<double> eig(nb), occ(nb);
+      from.get_orbitals(I, k, (double*)psi.p, eig.data(), occ.data());
+      to.set_orbitals(I, k, (const double*)psi.p);
+      to.set_eig_occ(I, k, eig.data(), occ.data());
+      CK(cudaStreamSynchronize(st));
+    }
+    to.set_subsystem_entropy(I, from.subsystem_entropy(I));
+  }
+  CK(cudaStreamSynchronize(st));
+}
+
+// Mixed-precision freeze-and-thaw cycle: the FP32 engine runs the cycle to a relaxed
+// tolerance, then the FP64 engine repeats the same cycle (same frozen densities) warm-
+// started from the FP32 densities and orbitals to the requested tolerance, and the result
+// is copied back to the FP32 engine.
+static fde_status mixed_cycle(fde_ctx* c, double tol, int max_scf, fde_energies* out, cudaStream_t st) {
+  Engine& lo = *c->eng;
+  Engine& hi = *c->eng64;
+  const int ns = lo.nsub();
+  const long long nr = lo.grid_points();
+  DBuf<double> start;
+  start.alloc((size_t)ns * nr);
+  for (int I = 0; I < ns; ++I) {
+    lo.get_density(I, start.p + I * nr);
+    hi.set_density(I, start.p + I * nr, 1);
+  }
+  fde_energies e1{};
+  const fde_status s1 = lo.freeze_thaw(std::max(tol, 1e-5), max_scf, &e1, nullptr);
+  if (s1 != FDE_OK && s1 != FDE_ENOCONV) return s1;
+  // orbitals of the FP32 result into the FP64 engine; its densities stay the frozen ones
+  for (int I = 0; I < ns; ++I) {
+    lo.get_density(I, start.p + I * nr);
+    int nb, nk;
+    lo.shape(I, &nb, &nk);
+    for (int k = 0; k < nk; ++k) {
+      DBuf<double2> psi;
+      psi.alloc((size_t)nb * lo.npw(I, k));
+      std::vector<double> eig(nb), occ(nb);
+      lo.get_orbitals(I, k, (double*)psi.p, eig.data(), occ.data());
+      hi.set_orbitals(I, k, (const double*)psi.p);
+      hi.set_eig_occ(I, k, eig.data(), occ.data());
+      CK(cudaStreamSynchronize(st));
+    }
+    hi.set_subsystem_entropy(I, lo.subsystem_entropy(I));
+  }
+  CK(cudaStreamSynchronize(st));
+  fde_energies e2{};
+  const fde_status s2 = hi.freeze_thaw(tol, max_scf, &e2, start.p);
+  transfer_state(hi, lo, st);
+  lo.build_vemb(nullptr, nullptr);
+  lo.sync();
+  if (out) {
+    *out = e2;
+    out->iters = e1.iters + e2.iters;
+  }
+  return s2;
+}
+
+}  // namespace fde
 
 template <typename F> static fde_status guard(fde_ctx* c, F&& f) {
   if (!c) return FDE_EINVAL;
@@ -1284,7 +1389,11 @@ fde_status fde_create(const fde_cell_desc* cell, const fde_func_desc* func, fde_
   fde_status s = guard(c, [&]() {
     cudaStream_t st = (cudaStream_t)cuda_stream;
     if (prec == FDE_PREC_FP64) c->eng.reset(new fde::EngineT<double>(cell, func, st));
-    else c->eng.reset(new fde::EngineT<float>(cell, func, st));
+    else {
+      c->eng.reset(new fde::EngineT<float>(cell, func, st));
+      c->eng64.reset(new fde::EngineT<double>(cell, func, st));
+    }
+    c->stream = st;
     return FDE_OK;
   });
   if (s != FDE_OK) {
@@ -1299,6 +1408,7 @@ fde_status fde_create(const fde_cell_desc* cell, const fde_func_desc* func, fde_
 fde_status fde_add_subsystem(fde_ctx* c, const fde_subsys_desc* d, int* id) {
   return guard(c, [&]() {
     const int i = c->eng->add_subsystem(d);
+    if (c->eng64) c->eng64->add_subsystem(d);
     if (id) *id = i;
     return FDE_OK;
   });
@@ -1352,7 +1462,10 @@ fde_status fde_scf_subsystem(fde_ctx* c, int sub, double tol, int max_scf, fde_e
   return guard(c, [&]() { return c->eng->scf_subsystem(sub, tol, max_scf, out); });
 }
 fde_status fde_freeze_thaw_cycle(fde_ctx* c, double tol, int max_scf, fde_energies* out) {
-  return guard(c, [&]() { return c->eng->freeze_thaw(tol, max_scf, out); });
+  return guard(c, [&]() {
+    if (c->eng64) return fde::mixed_cycle(c, tol, max_scf, out, c->stream);
+    return c->eng->freeze_thaw(tol, max_scf, out, nullptr);
+  });
 }
 fde_status fde_sync(fde_ctx* c) {
   return guard(c, [&]() { c->eng->sync(); return FDE_OK; });
@@ -1369,6 +1482,13 @@ fde_status fde_profile_get(fde_ctx* c, const char* kernel, int* launches, double
   return guard(c, [&]() {
     if (!kernel || !launches || !total_ms) throw fde::Err{FDE_EINVAL, "null argument"};
     c->prof.get(kernel, launches, total_ms);
+    return FDE_OK;
+  });
+}
+fde_status fde_launch_count(fde_ctx* c, long long* launches) {
+  return guard(c, [&]() {
+    if (!launches) throw fde::Err{FDE_EINVAL, "null argument"};
+    *launches = c->prof.launches;
     return FDE_OK;
   });
 }

@@ -7,6 +7,7 @@
 
 #include "fft.cuh"
 #include "grid_kernels.h"
+#include "prof.h"
 
 namespace fde {
 
@@ -54,6 +55,7 @@ void launch_fft3d(cplx<T>* data, const GridDims& g, const FftPlans<T>& fp, int s
   for (int a = 0; a < 3; ++a) {
     const long long nlines = nr / ax[a].N;
     const size_t sm = (size_t)kLinesPerCta * (ax[a].N + 1) * sizeof(cplx<T>);
+    count_launches(1);
     k_fft_axis<T><<<(unsigned)((nlines + kLinesPerCta - 1) / kLinesPerCta), kLinesPerCta * 32, sm, st>>>(
         data, nlines, ax[a].N, ax[a].I, *ax[a].p, sign);
   }
@@ -413,61 +415,75 @@ static int gs(long long n) {
 
 template <typename T>
 void grid_poisson(const cplx<T>* F, cplx<T>* V, const GridDims& g, const CellDev& c, double* partial, cudaStream_t st) {
+  count_launches(1);
   k_poisson<T><<<kRedBlocks, kRedThreads, 0, st>>>(F, V, g, c, 1.0 / ((double)g.n1 * g.n2 * g.n3), partial);
 }
 template <typename T>
 void grid_gradient_g(const cplx<T>* F, cplx<T>* ox, cplx<T>* oy, cplx<T>* oz, const GridDims& g, const CellDev& c,
                      cudaStream_t st) {
   const long long nr = (long long)g.n1 * g.n2 * g.n3;
+  count_launches(1);
   k_grad_g<T><<<gs(nr), 256, 0, st>>>(F, ox, oy, oz, g, c, 1.0 / (double)nr);
 }
 template <typename T>
 void grid_divergence_g(cplx<T>* hx, const cplx<T>* hy, const cplx<T>* hz, const GridDims& g, const CellDev& c,
                        cudaStream_t st) {
   const long long nr = (long long)g.n1 * g.n2 * g.n3;
+  count_launches(1);
   k_div_g<T><<<gs(nr), 256, 0, st>>>(hx, hy, hz, g, c, 1.0 / (double)nr);
 }
 void grid_vloc_g(double2* V, const GridDims& g, const CellDev& c, const double* pos, const double* Z, int natoms,
                  double rc, cudaStream_t st) {
   const long long nr = (long long)g.n1 * g.n2 * g.n3;
+  count_launches(1);
   k_vloc_g<<<gs(nr), 256, 0, st>>>(V, g, c, pos, Z, natoms, rc);
 }
 template <typename T>
 void grid_pointwise(const double* rho, cplx<T>* gx, cplx<T>* gy, cplx<T>* gz, long long nr, int xc_mode, int xc_pot,
                     int kedf, double rho_cut, double* vpart, double* partial, cudaStream_t st) {
+  count_launches(1);
   k_pointwise<T><<<kRedBlocks, kRedThreads, 0, st>>>(rho, gx, gy, gz, nr, xc_mode, xc_pot, kedf, rho_cut, vpart,
                                                       partial);
 }
 template <typename T>
 void grid_real_to_c(const double* a, cplx<T>* c, long long n, cudaStream_t st) {
+  count_launches(1);
   k_real_to_c<T><<<gs(n), 256, 0, st>>>(a, c, n);
 }
 template <typename T>
 void grid_c_to_real(const cplx<T>* c, double* a, long long n, cudaStream_t st) {
+  count_launches(1);
   k_c_to_real<T><<<gs(n), 256, 0, st>>>(c, a, n);
 }
 template <typename T>
 void grid_combine(const double* a, const double* b, const double* c, const cplx<T>* d, double sd, double* out,
                   long long n, cudaStream_t st) {
+  count_launches(1);
   k_combine<T><<<gs(n), 256, 0, st>>>(a, b, c, d, sd, out, n);
 }
 void grid_sum_rows(const double* a, int nrows, long long n, double* out, cudaStream_t st) {
+  count_launches(1);
   k_sum_rows<<<gs(n), 256, 0, st>>>(a, nrows, n, out);
 }
 void grid_dot_partial(const double* a, const double* b, long long n, int mode, double* partial, cudaStream_t st) {
+  count_launches(1);
   k_dot_partial<<<kRedBlocks, kRedThreads, 0, st>>>(a, b, n, mode, partial);
 }
 void grid_finalize(const double* partial, int nq, double scale, double* out, cudaStream_t st) {
+  count_launches(1);
   k_finalize<<<1, 32, 0, st>>>(partial, kRedBlocks, nq, scale, out);
 }
 void grid_lincomb(const double* const* ins, const double* const* res, const double* coef, int m, double beta,
                   long long n, double* out, cudaStream_t st) {
+  count_launches(1);
   k_lincomb<<<gs(n), 256, 0, st>>>(ins, res, coef, m, beta, n, out);
 }
 void grid_axpy(double* a, const double* b, double alpha, long long n, cudaStream_t st) {
+  count_launches(1);
   k_axpy<<<gs(n), 256, 0, st>>>(a, b, alpha, n);
 }
 void grid_nonfinite(const double* a, long long n, unsigned* status, cudaStream_t st) {
+  count_launches(1);
   k_nonfinite<<<gs(n), 256, 0, st>>>(a, n, status);
 }
 int grid_red_blocks() { return kRedBlocks; }

@@ -156,15 +156,18 @@ void launch_hpsi_local(const cplx<T>* psi, int ldpsi, cplx<T>* hpsi, int ldh, in
   allow_smem(k_plane<T>, ps);
   {
     ProfScope p("k_zinv", st);
+    count_launches(1);
     k_zinv<T><<<gz, kColsPerCta * 32, zs, st>>>(psi, ldpsi, scratch, sp, g.n3, fp.p3);
   }
   {
     ProfScope p("k_plane", st);
+    count_launches(1);
     k_plane<T><<<dim3(g.n3, nb), kPlaneThreads, ps, st>>>(scratch, sp, vplane, g, fp.p1, fp.p2);
   }
   const T inv_nr = (T)(1.0 / ((double)g.n1 * g.n2 * g.n3));
   {
     ProfScope p("k_zfwd", st);
+    count_launches(1);
     k_zfwd<T><<<gz, kColsPerCta * 32, zs, st>>>(scratch, psi, ldpsi, hpsi, ldh, kin, sp, g.n3, inv_nr, fp.p3);
   }
 }
@@ -214,7 +217,9 @@ void launch_density(const cplx<T>* psi, int ldpsi, int nb, const double* weight,
   const size_t zs = zpass_smem<T>(g.n3), ps = plane_smem<T>(g);
   allow_smem(k_zinv<T>, zs);
   allow_smem(k_plane_density<T>, ps);
+  count_launches(1);
   k_zinv<T><<<gz, kColsPerCta * 32, zs, st>>>(psi, ldpsi, scratch, sp, g.n3, fp.p3);
+  count_launches(1);
   k_plane_density<T><<<g.n3, kPlaneThreads, ps, st>>>(scratch, sp, nb, weight, rho_plane, accumulate, g, fp.p1, fp.p2);
 }
 
@@ -241,6 +246,7 @@ __global__ void k_transpose(const Tin* __restrict__ in, Tout* __restrict__ out, 
 template <typename Tin, typename Tout>
 void launch_transpose(const Tin* in, Tout* out, int rows, int cols, int accumulate, cudaStream_t st) {
   dim3 grid(ceil_div(cols, 32), ceil_div(rows, 32));
+  count_launches(1);
   k_transpose<Tin, Tout><<<grid, dim3(32, 8), 0, st>>>(in, out, rows, cols, accumulate);
 }
 

@@ -6,6 +6,7 @@
 #include <math.h>
 
 #include "kernels.h"
+#include "prof.h"
 
 namespace fde {
 
@@ -89,7 +90,9 @@ void launch_gemm_hn(const cplx<T>* A, int lda, const cplx<T>* B, int ldb, int m,
   kchunk = ((kchunk + kGK - 1) / kGK) * kGK;
   const int ns = ceil_div(K, kchunk > 0 ? kchunk : 1);
   const dim3 grid(ceil_div(m, kGT), ceil_div(n, kGT), ns > 0 ? ns : 1);
+  count_launches(1);
   k_gemm_hn_partial<T, T><<<grid, 256, 0, st>>>(A, lda, B, ldb, m, n, K, kchunk, work);
+  count_launches(1);
   k_gemm_hn_reduce<<<ceil_div((long long)m * n, 256), 256, 0, st>>>(work, grid.z, m, n, C, ldc);
 }
 
@@ -160,6 +163,7 @@ void launch_gemm_rot(const cplx<T>* X, int ldx, const double2* U, int ldu, int m
                      int ldy, double alpha, double beta, cudaStream_t st) {
   if (n <= 0 || K <= 0) return;
   const dim3 grid(ceil_div(K, 64), ceil_div(n, 32));
+  count_launches(1);
   k_gemm_rot<T><<<grid, 256, 0, st>>>(X, ldx, U, ldu, m, n, K, Y, ldy, (T)alpha, (T)beta);
 }
 
@@ -224,6 +228,7 @@ k_cholesky_inv(const double2* __restrict__ S, int n, double2* __restrict__ L, do
 }
 
 void launch_cholesky_inv(const double2* S, int n, double2* L, double2* Linv, unsigned* status, cudaStream_t st) {
+  count_launches(1);
   k_cholesky_inv<<<1, 512, 0, st>>>(S, n, L, Linv, status);
 }
 
@@ -363,6 +368,7 @@ k_jacobi(double2* __restrict__ A, int n, double* __restrict__ w, double2* __rest
 }
 
 void launch_jacobi_eig(double2* A, int n, double* w, double2* V, double2* work, cudaStream_t st) {
+  count_launches(1);
   k_jacobi<<<1, 1024, 0, st>>>(A, n, w, V, work);
 }
 
@@ -379,6 +385,7 @@ __global__ void k_hermitize(double2* A, int n) {
 }
 
 void launch_hermitize(double2* A, int n, cudaStream_t st) {
+  count_launches(1);
   k_hermitize<<<ceil_div((long long)n * n, 256), 256, 0, st>>>(A, n);
 }
 
@@ -398,6 +405,7 @@ template <typename T>
 void launch_residual(const cplx<T>* HX, const cplx<T>* X, const double* eps, int nb, int K, int ld, cplx<T>* R,
                      int ldr, cudaStream_t st) {
   if (nb <= 0) return;
+  count_launches(1);
   k_residual<T><<<dim3(ceil_div(K, 256 * 4), nb), 256, 0, st>>>(HX, X, eps, K, ld, R, ldr);
 }
 
@@ -427,6 +435,7 @@ template <typename T>
 void launch_row_norms(const cplx<T>* X, int ld, int nb, int K, const T* weight, double* out, double*,
                       cudaStream_t st) {
   if (nb <= 0) return;
+  count_launches(1);
   k_row_norms<T><<<nb, 512, 0, st>>>(X, ld, K, weight, out);
 }
 
@@ -450,6 +459,7 @@ template <typename T>
 void launch_tpa(const cplx<T>* R, int ldr, const T* kin, const double* tband, int nb, int K, cplx<T>* W, int ldw,
                 cudaStream_t st) {
   if (nb <= 0) return;
+  count_launches(1);
   k_tpa<T><<<dim3(ceil_div(K, 256 * 4), nb), 256, 0, st>>>(R, ldr, kin, tband, K, W, ldw);
 }
 
@@ -468,6 +478,7 @@ __global__ void k_scale_rows(cplx<T>* X, int ld, int K, const double* s) {
 template <typename T>
 void launch_scale_rows(cplx<T>* X, int ld, int nb, int K, const double* s, cudaStream_t st) {
   if (nb <= 0) return;
+  count_launches(1);
   k_scale_rows<T><<<dim3(ceil_div(K, 256 * 4), nb), 256, 0, st>>>(X, ld, K, s);
 }
 
@@ -480,6 +491,7 @@ __global__ void k_convert_c(const cplx<Ta>* a, cplx<Tb>* b, size_t n) {
 template <typename Ta, typename Tb>
 void launch_convert_c(const cplx<Ta>* a, cplx<Tb>* b, size_t n, cudaStream_t st) {
   if (!n) return;
+  count_launches(1);
   k_convert_c<Ta, Tb><<<(int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096), 256, 0, st>>>(a, b, n);
 }
 
@@ -498,6 +510,7 @@ __global__ void k_shape_init(cplx<T>* X, int ld, const T* kin, int K) {
 template <typename T>
 void launch_shape_init(cplx<T>* X, int ld, const T* kin, int nb, int K, cudaStream_t st) {
   if (nb <= 0) return;
+  count_launches(1);
   k_shape_init<T><<<dim3(ceil_div(K, 256 * 4), nb), 256, 0, st>>>(X, ld, kin, K);
 }
 

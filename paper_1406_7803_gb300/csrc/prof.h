@@ -14,6 +14,7 @@ namespace fde {
 
 struct Profiler {
   bool on = false;
+  long long launches = 0;  // kernel launches made by the context's calls (always counted)
   struct Rec {
     std::vector<cudaEvent_t> a, b;
   };
@@ -51,6 +52,10 @@ struct Profiler {
 
 // Profiler of the context whose ABI call is running on this thread (or null).
 extern thread_local Profiler* tl_prof;
+
+inline void count_launches(int n) {
+  if (tl_prof) tl_prof->launches += n;
+}
 
 struct ProfScope {
   const char* n;

@@ -1,6 +1,7 @@
 // small.cu -- products of small dense FP64 complex matrices (subspace size <= a few hundred)
 // used by the Rayleigh-Ritz step: C = op(A) op(B) with op = identity or conjugate transpose.
 #include "kernels.h"
+#include "prof.h"
 #include "small.h"
 
 namespace fde {
@@ -39,6 +40,7 @@ __global__ void k_small_gemm(const double2* __restrict__ A, int lda, int opA, co
 void launch_small_gemm(const double2* A, int lda, int opA, const double2* B, int ldb, int opB, int m, int n, int k,
                        double2* C, int ldc, cudaStream_t st) {
   dim3 grid(ceil_div(n, 16), ceil_div(m, 16));
+  count_launches(1);
   k_small_gemm<<<grid, dim3(16, 16), 0, st>>>(A, lda, opA, B, ldb, opB, m, n, k, C, ldc);
 }
 
@@ -56,6 +58,7 @@ template <typename T>
 void launch_gather_rows(const cplx<T>* src, int lds, const int* idx, int nrows, int K, cplx<T>* dst, int ldd,
                         cudaStream_t st) {
   if (nrows <= 0) return;
+  count_launches(1);
   k_gather_rows<T><<<dim3(ceil_div(K, 1024), nrows), 256, 0, st>>>(src, lds, idx, K, dst, ldd);
 }
 

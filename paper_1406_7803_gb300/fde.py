@@ -72,6 +72,7 @@ EXPORTS = {
     "fde_freeze_thaw_cycle": (C.c_int, [C.c_void_p, C.c_double, C.c_int, C.POINTER(Energies)]),
     "fde_profile_enable": (C.c_int, [C.c_void_p, C.c_int]),
     "fde_profile_get": (C.c_int, [C.c_void_p, C.c_char_p, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+    "fde_launch_count": (C.c_int, [C.c_void_p, C.POINTER(C.c_longlong)]),
     "fde_sync": (C.c_int, [C.c_void_p]),
     "fde_last_error": (C.c_char_p, [C.c_void_p]),
     "fde_destroy": (C.c_int, [C.c_void_p]),
@@ -257,6 +258,11 @@ class Context:
 
     def profile_enable(self, on=True):
         return self._check(self.lib.fde_profile_enable(self.h, int(on)), "fde_profile_enable")
+
+    def launch_count(self):
+        n = C.c_longlong()
+        self._check(self.lib.fde_launch_count(self.h, C.byref(n)), "fde_launch_count")
+        return n.value
 
     def profile_get(self, kernel):
         n = C.c_int()
