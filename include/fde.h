@@ -225,6 +225,30 @@ fde_status fde_profile_get(fde_ctx* ctx, const char* kernel, int* launches, doub
  * (counted on the host at every launch; measurement support, no counterpart in the paper). */
 fde_status fde_launch_count(fde_ctx* ctx, long long* launches);
 
+/* Local part of H psi without any device allocation, for callers that cannot call
+ * cudaMalloc (code running under another framework's memory pool or allocator hooks, a
+ * host application that owns every device allocation, or a call path that must not grow
+ * the device footprint).  The paper has no counterpart: this is a deployment variant of
+ * the local part of fde_apply_h, (H psi)(G) = |k+G|^2/2 psi(G) + P_sphere FFT[v . IFFT psi],
+ * without the nonlocal projectors and without a context.
+ *   cell:     orthorhombic cell and grid (ecut_ha unused); kfrac: host k-point [3], crystal.
+ *   d_miller: device int [npw][3], the sphere in the library's order (fde_get_basis).
+ *   d_veff:   device double [n1][n2][n3]; d_psi, d_hpsi: device complex double [nb][npw],
+ *             not overlapping.  cuda_stream: cudaStream_t (NULL: legacy default stream).
+ * Working memory is a set of fixed device arrays inside the library (about 26 MB, held by
+ * every GPU that loads the library until the process exits); limits: npw <= 65536,
+ * <= 8192 (m1, m2) columns, n1, n2 <= 160, n3 <= 320, n1 n2 n3 <= 1048576; larger inputs
+ * return FDE_EUNSUPPORTED.  Bands are processed in chunks that fit the arrays.  The first
+ * call on a device resolves the arrays' device addresses (cudaGetSymbolAddress) and must
+ * come before any stream capture.  Calls share the arrays: calls that overlap on the GPU
+ * (other streams, other host threads) race and must be serialised by the caller.  The call
+ * synchronises the stream once (to read the column count).  Errors: FDE_EINVAL (null or
+ * non-positive arguments), FDE_EUNSUPPORTED (sizes above the limits, non-orthorhombic cell,
+ * grid sizes not of the form 2^a 3^b 5^c), FDE_ECUDA. */
+fde_status fde_apply_h_local_static(const fde_cell_desc* cell, const double* kfrac, int npw, const int* d_miller,
+                                    const double* d_veff, const double* d_psi, double* d_hpsi, int nb,
+                                    void* cuda_stream);
+
 /* Synchronise the context stream and check the device status word. */
 fde_status fde_sync(fde_ctx* ctx);
 

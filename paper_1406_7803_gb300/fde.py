@@ -73,6 +73,8 @@ EXPORTS = {
     "fde_profile_enable": (C.c_int, [C.c_void_p, C.c_int]),
     "fde_profile_get": (C.c_int, [C.c_void_p, C.c_char_p, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "fde_launch_count": (C.c_int, [C.c_void_p, C.POINTER(C.c_longlong)]),
+    "fde_apply_h_local_static": (C.c_int, [C.POINTER(CellDesc), C.POINTER(C.c_double), C.c_int, C.c_void_p,
+                                           C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "fde_sync": (C.c_int, [C.c_void_p]),
     "fde_last_error": (C.c_char_p, [C.c_void_p]),
     "fde_destroy": (C.c_int, [C.c_void_p]),
@@ -269,6 +271,25 @@ class Context:
         ms = C.c_double()
         self._check(self.lib.fde_profile_get(self.h, kernel.encode(), C.byref(n), C.byref(ms)), "fde_profile_get")
         return n.value, ms.value
+
+
+def apply_h_local_static(lattice, grid, kfrac, miller, veff, psi, hpsi, nb, stream=None):
+    """fde_apply_h_local_static: local H psi with no device allocation (no context).
+    miller, veff, psi, hpsi are torch CUDA tensors (int32 [npw][3], float64 grid, complex128
+    [nb][npw])."""
+    lib = load()
+    cell = CellDesc()
+    for i in range(3):
+        for j in range(3):
+            cell.lattice[i][j] = float(lattice[i][j])
+        cell.grid[i] = int(grid[i])
+    cell.ecut_ha = 0.0
+    k = (C.c_double * 3)(*[float(x) for x in kfrac])
+    s = lib.fde_apply_h_local_static(C.byref(cell), k, int(miller.shape[0]), _dptr(miller), _dptr(veff),
+                                     _dptr(psi), _dptr(hpsi), int(nb), C.c_void_p(stream) if stream else None)
+    if s != FDE_OK:
+        raise FDEError(s, "fde_apply_h_local_static failed")
+    return s
 
 
 def context_from_workload(wl: workloads.Workload, prec="fp64", stream=None) -> Context:
