@@ -59,7 +59,8 @@ typedef enum {
 
 enum { FDE_XC_LDA = 0, FDE_XC_PBE = 1 };                         /* exchange-correlation */
 enum { FDE_KEDF_TF = 0, FDE_KEDF_REVAPBEK = 1, FDE_KEDF_LC94 = 2 };  /* kinetic functional */
-enum { FDE_PRECOND_TPA = 0 };                                    /* Davidson preconditioner */
+enum { FDE_PRECOND_TPA = 0, FDE_PRECOND_LEARNED = 1 };          /* eigensolver preconditioner */
+enum { FDE_PRECOND_PARAMS = 8641 };  /* learned-preconditioner parameter count (floats) */
 
 /* Cell, shared real-space grid and wavefunction cutoff (Sec. 2: one shared grid holds rho
  * and every potential, Eq. meth:1).  lattice rows are a_1, a_2, a_3 (bohr); the cell must
@@ -197,6 +198,43 @@ fde_status fde_subspace_solve(fde_ctx* ctx, int sub, int k, double tol, int max_
  * |u_jk|^2 (Sec. 2) from the stored orbitals.  The new density replaces rho_I. */
 fde_status fde_update_density(fde_ctx* ctx, int sub);
 
+/* ---- learned preconditioner of the block eigensolver (no counterpart in the paper, which
+ * leaves the eigensolver to its host code; Eq. KS is what the solver solves).
+ * The preconditioned residual is W_jG = K(y) exp(o_jG) R_jG with K the Teter-Payne-Allan
+ * factor, y = (|k+G|^2/2) / T_j (T_j the band's kinetic energy) and o the output of a per-G
+ * network: three tanh layers of width 64 and a linear output on the features
+ * (log(1 + y), log T_j, |R_jG| / rms_G |R_j|).  Parameters: FDE_PRECOND_PARAMS floats,
+ * W1[64][3] b1[64] W2[64][64] b2[64] W3[64][64] b3[64] W4[64] b4.  Inference uses the
+ * weights rounded to bfloat16 with FP32 accumulation; training keeps FP32 master weights.
+ * Training pairs (R, D): D the ideal correction of residual R.  The loss is
+ * sum_j sum_G |m_jG R_jG - D_jG|^2 / |D_j|^2; training takes full-batch Adam steps. */
+fde_status fde_set_precond(fde_ctx* ctx, int precond); /* preconditioner of fde_scf_subsystem /
+                                                          fde_freeze_thaw_cycle solves */
+fde_status fde_precond_set_weights(fde_ctx* ctx, const float* h_params);      /* resets Adam */
+fde_status fde_precond_get_weights(fde_ctx* ctx, float* h_params, float* h_bf16_rounded);
+/* Pairs from the converged orbitals of (sub, k): h_raw [n][npw][2] seeded raw draws, shaped by
+ * 1/(1 + |k+G|^2/2), orthogonalised to the converged block and normalised into D; then
+ * R = (H - eps_j) D_j for the first n bands.  Needs a converged fde_subspace_solve. */
+fde_status fde_precond_harvest(fde_ctx* ctx, int sub, int k, const double* h_raw, int n);
+/* Caller pairs: h_r, h_d complex double [n][npw] (host), h_tband [n] band kinetic energies. */
+fde_status fde_precond_add_pairs(fde_ctx* ctx, int sub, int k, int n, const double* h_r, const double* h_d,
+                                 const double* h_tband);
+/* Pairs from the eigensolver's own iterations: while iterations > 0, every fde_subspace_solve
+ * (and every solve inside an SCF) keeps (R, X) of its first `iterations` iterates and, once
+ * it converges to the block Psi, stores the pairs (R, (1 - Psi Psi^H) X): the error of each
+ * iterate is the correction its residual asks for.  0 stops recording. */
+fde_status fde_precond_record(fde_ctx* ctx, int iterations);
+fde_status fde_precond_clear(fde_ctx* ctx);
+/* Loss and gradient (FP32 master weights) over every stored pair; h_grad [FDE_PRECOND_PARAMS]. */
+fde_status fde_precond_loss_grad(fde_ctx* ctx, double* h_grad, double* loss);
+fde_status fde_precond_train(fde_ctx* ctx, int steps, double lr, double* loss_first, double* loss_last);
+/* W = preconditioned R for nb rows of (sub, k) (device, working-precision complex [nb][npw]),
+ * h_tband [nb] band kinetic energies. */
+fde_status fde_precond_apply(fde_ctx* ctx, int sub, int k, const void* d_r, void* d_w, int nb,
+                             const double* h_tband);
+/* Cumulative eigensolver iterations and band-applies of H made by the context. */
+fde_status fde_get_stats(fde_ctx* ctx, long long* davidson_iters, long long* hpsi_bands);
+
 /* Every energy term of the current state (synchronising). */
 fde_status fde_energy(fde_ctx* ctx, fde_energies* out);
 
@@ -248,6 +286,12 @@ fde_status fde_launch_count(fde_ctx* ctx, long long* launches);
 fde_status fde_apply_h_local_static(const fde_cell_desc* cell, const double* kfrac, int npw, const int* d_miller,
                                     const double* d_veff, const double* d_psi, double* d_hpsi, int nb,
                                     void* cuda_stream);
+
+/* The library's full-grid 3D transform applied in place to a caller grid (complex, [n1][n2][n3],
+ * double2 in FP64 contexts and float2 in mixed ones): sign -1 forward, scaled by 1/N_r
+ * (f(G) = (1/N_r) sum_r f(r) e^{-iG.r}); sign +1 inverse, unscaled.  Exposed so the
+ * transforms can be checked on their own. */
+fde_status fde_fft3d(fde_ctx* ctx, void* d_data, int sign);
 
 /* Synchronise the context stream and check the device status word. */
 fde_status fde_sync(fde_ctx* ctx);

@@ -18,6 +18,7 @@
 #include "grid_kernels.h"
 #include "kernels.h"
 #include "prof.h"
+#include "precond.h"
 #include "small.h"
 
 namespace fde {
@@ -209,12 +210,24 @@ struct Engine {
   virtual void init_orbitals(int sub, int k, const double* raw) = 0;
   virtual void set_orbitals(int sub, int k, const double* d_psi) = 0;
   virtual void get_orbitals(int sub, int k, double* d_psi, double* eig, double* occ) = 0;
-  virtual fde_status subspace_solve(int sub, int k, double tol, int max_iter, int* iters) = 0;
+  virtual fde_status subspace_solve(int sub, int k, double tol, int max_iter, int* iters, int precond) = 0;
   virtual void update_density(int sub) = 0;
   virtual void energy(fde_energies* out) = 0;
   virtual fde_status scf_subsystem(int sub, double tol, int max_scf, fde_energies* out) = 0;
   virtual fde_status freeze_thaw(double tol, int max_scf, fde_energies* out, const double* start) = 0;
   virtual void sync() = 0;
+  virtual void fft3d(void* data, int sign) = 0;
+  virtual void precond_set_weights(const float* h) = 0;
+  virtual void precond_get_weights(float* h, float* hb) = 0;
+  virtual void precond_harvest(int sub, int k, const double* raw, int n) = 0;
+  virtual void precond_add_pairs(int sub, int k, int n, const double* r, const double* d, const double* tb) = 0;
+  virtual void precond_clear() = 0;
+  virtual void precond_loss_grad(double* grad, double* loss) = 0;
+  virtual void precond_train(int steps, double lr, double* l0, double* l1) = 0;
+  virtual void precond_apply(int sub, int k, const void* r, void* w, int nb, const double* tband) = 0;
+  virtual void set_precond_mode(int mode) = 0;
+  virtual void stats(long long* dav, long long* hpsi) = 0;
+  virtual void set_precond_record(int n) = 0;
   virtual int nsub() const = 0;
   virtual long long grid_points() const = 0;
   virtual void shape(int sub, int* nb, int* nk) = 0;
@@ -241,7 +254,10 @@ template <typename T> struct EngineT : Engine {
   DBuf<double> vloc;
   double enn = 0;
   // grid work
-  DBuf<C> cb[5];
+  // Work grids of the embedding-potential build.  Its transforms run in FP64 in both
+  // precisions: FP32 gradients of the density are noise where the density is small (the
+  // vacuum above the slab), and the GGA potentials amplify that noise by rho^{-4/3}.
+  DBuf<double2> cb[5];
   DBuf<double2> cvl;
   DBuf<double> rho_tot, vcommon, vpart, vtmp, partial, scal;
   DBuf<unsigned> status;
@@ -330,6 +346,12 @@ template <typename T> struct EngineT : Engine {
     Sub<T>& s = sub(i);
     REQ(k >= 0 && k < s.nk, FDE_EINVAL, "k-point index out of range");
     return s.kp[k];
+  }
+  void fft3d(void* data, int sign) override {
+    REQ(data && (sign == 1 || sign == -1), FDE_EINVAL, "bad transform arguments");
+    C* d = (C*)data;
+    launch_fft3d<T>(d, g, plans.fp, sign, st);
+    if (sign < 0) grid_scale_c<T>(d, 1.0 / (double)nr, nr, st);
   }
   void sync() override {
     CK(cudaStreamSynchronize(st));
@@ -542,7 +564,7 @@ template <typename T> struct EngineT : Engine {
   void sum_densities() {
     CK(cudaMemcpyAsync(rho_tot.p, subs[0]->rho.p, nr * sizeof(double), cudaMemcpyDeviceToDevice, st));
     for (size_t I = 1; I < subs.size(); ++I)
-      grid_combine<T>(rho_tot.p, subs[I]->rho.p, nullptr, nullptr, 0.0, rho_tot.p, nr, st);
+      grid_combine<double>(rho_tot.p, subs[I]->rho.p, nullptr, nullptr, 0.0, rho_tot.p, nr, st);
   }
   void get_density(int i, double* d_rho) override {
     REQ(d_rho, FDE_EINVAL, "null output");
@@ -561,14 +583,14 @@ template <typename T> struct EngineT : Engine {
 
   // Gradient of the density held (forward-transformed, unscaled) in cb[0] into cb[2..4] (real).
   void gradient_from_cb0() {
-    grid_gradient_g<T>(cb[0].p, cb[2].p, cb[3].p, cb[4].p, g, cell, st);
-    for (int c = 2; c < 5; ++c) launch_fft3d<T>(cb[c].p, g, plans.fp, +1, st);
+    grid_gradient_g<double>(cb[0].p, cb[2].p, cb[3].p, cb[4].p, g, cell, st);
+    for (int c = 2; c < 5; ++c) launch_fft3d<double>(cb[c].p, g, plans64.fp, +1, st);
   }
   // Divergence of h held (real) in cb[2..4]; result (real part) in cb[2].
   void divergence_cb234() {
-    for (int c = 2; c < 5; ++c) launch_fft3d<T>(cb[c].p, g, plans.fp, -1, st);
-    grid_divergence_g<T>(cb[2].p, cb[3].p, cb[4].p, g, cell, st);
-    launch_fft3d<T>(cb[2].p, g, plans.fp, +1, st);
+    for (int c = 2; c < 5; ++c) launch_fft3d<double>(cb[c].p, g, plans64.fp, -1, st);
+    grid_divergence_g<double>(cb[2].p, cb[3].p, cb[4].p, g, cell, st);
+    launch_fft3d<double>(cb[2].p, g, plans64.fp, +1, st);
   }
 
   // Builds the potentials (want_pot) of the subsystems in `which` (-1 all) and/or the grid
@@ -580,38 +602,38 @@ template <typename T> struct EngineT : Engine {
     const int nrb = grid_red_blocks();
     const double dv = omega / (double)nr;
     sum_densities();
-    grid_real_to_c<T>(rho_tot.p, cb[0].p, nr, st);
-    launch_fft3d<T>(cb[0].p, g, plans.fp, -1, st);
-    grid_poisson<T>(cb[0].p, want_pot ? cb[1].p : nullptr, g, cell, partial.p, st);
+    grid_real_to_c<double>(rho_tot.p, cb[0].p, nr, st);
+    launch_fft3d<double>(cb[0].p, g, plans64.fp, -1, st);
+    grid_poisson<double>(cb[0].p, want_pot ? cb[1].p : nullptr, g, cell, partial.p, st);
     grid_finalize(partial.p, 1, 0.5 * omega, scal.p + 0, st);
-    if (want_pot) launch_fft3d<T>(cb[1].p, g, plans.fp, +1, st);
+    if (want_pot) launch_fft3d<double>(cb[1].p, g, plans64.fp, +1, st);
     const bool grad = gga_xc() || gga_kin();
     if (grad) gradient_from_cb0();
-    grid_pointwise<T>(rho_tot.p, grad ? cb[2].p : nullptr, grad ? cb[3].p : nullptr, grad ? cb[4].p : nullptr, nr,
+    grid_pointwise<double>(rho_tot.p, grad ? cb[2].p : nullptr, grad ? cb[3].p : nullptr, grad ? cb[4].p : nullptr, nr,
                       func.xc, 1, func.kedf, func.rho_cut, want_pot ? vpart.p : nullptr, partial.p, st);
     grid_finalize(partial.p, 2, dv, scal.p + 1, st);
     grid_dot_partial(vloc.p, rho_tot.p, nr, 0, partial.p, st);
     grid_finalize(partial.p, 1, dv, scal.p + 3, st);
     if (want_pot) {
-      grid_combine<T>(vloc.p, vpart.p, nullptr, cb[1].p, 1.0, vcommon.p, nr, st);
+      grid_combine<double>(vloc.p, vpart.p, nullptr, cb[1].p, 1.0, vcommon.p, nr, st);
       if (grad) {
         divergence_cb234();
-        grid_combine<T>(vcommon.p, nullptr, nullptr, cb[2].p, -1.0, vcommon.p, nr, st);
+        grid_combine<double>(vcommon.p, nullptr, nullptr, cb[2].p, -1.0, vcommon.p, nr, st);
       }
     }
     for (size_t I = 0; I < subs.size(); ++I) {
       const bool pot_I = want_pot && (which < 0 || which == (int)I);
       if (!pot_I && !want_e) continue;
       Sub<T>& s = *subs[I];
-      grid_real_to_c<T>(s.rho.p, cb[0].p, nr, st);
-      launch_fft3d<T>(cb[0].p, g, plans.fp, -1, st);
+      grid_real_to_c<double>(s.rho.p, cb[0].p, nr, st);
+      launch_fft3d<double>(cb[0].p, g, plans64.fp, -1, st);
       if (want_e) {
-        grid_poisson<T>(cb[0].p, nullptr, g, cell, partial.p, st);
+        grid_poisson<double>(cb[0].p, nullptr, g, cell, partial.p, st);
         grid_finalize(partial.p, 1, 0.5 * omega, scal.p + 4 + 3 * I, st);
       }
       const bool gI = gga_kin() || (want_e && gga_xc());
       if (gI) gradient_from_cb0();
-      grid_pointwise<T>(s.rho.p, gI ? cb[2].p : nullptr, gI ? cb[3].p : nullptr, gI ? cb[4].p : nullptr, nr,
+      grid_pointwise<double>(s.rho.p, gI ? cb[2].p : nullptr, gI ? cb[3].p : nullptr, gI ? cb[4].p : nullptr, nr,
                         want_e ? func.xc : -1, 0, func.kedf, func.rho_cut, pot_I ? vpart.p : nullptr, partial.p, st);
       grid_finalize(partial.p, 2, dv, scal.p + 5 + 3 * I, st);
       if (pot_I) {
@@ -620,7 +642,7 @@ template <typename T> struct EngineT : Engine {
         grid_axpy(s.veff.p, vpart.p, -1.0, nr, st);
         if (gga_kin()) {
           divergence_cb234();
-          grid_combine<T>(s.veff.p, nullptr, nullptr, cb[2].p, 1.0, s.veff.p, nr, st);
+          grid_combine<double>(s.veff.p, nullptr, nullptr, cb[2].p, 1.0, s.veff.p, nr, st);
         }
         grid_nonfinite(s.veff.p, nr, status.p, st);
         to_plane(s);
@@ -675,7 +697,9 @@ template <typename T> struct EngineT : Engine {
   }
 
   // ---- H psi ----------------------------------------------------------------------------------
+  long long davidson_iters = 0, hpsi_bands = 0;
   void apply_h_dev(Sub<T>& s, KP<T>& q, const C* psi, C* hpsi, int nb) {
+    hpsi_bands += nb;
     scratch.ensure((size_t)nb * g.n3 * q.sp.ncol);
     launch_hpsi_local<T>(psi, q.npw, hpsi, q.npw, nb, q.kin_d.p, s.vplane.p, scratch.p, q.sp, g, plans.fp, st);
     if (s.nproj) {
@@ -847,7 +871,12 @@ template <typename T> struct EngineT : Engine {
   // Block eigensolver (LOBPCG form of block Davidson): the search space of every iteration is
   // the current orbitals X, the TPA-preconditioned residuals W of the unconverged bands and
   // their previous update directions P; Rayleigh-Ritz in FP64 keeps the lowest nb pairs.
-  fde_status subspace_solve(int i, int k, double tol, int max_iter, int* iters) override {
+  fde_status subspace_solve(int i, int k, double tol, int max_iter, int* iters, int precond) override {
+    const bool learned = precond == FDE_PRECOND_LEARNED;
+    if (learned) REQ(have_pw, FDE_EINVAL, "learned preconditioner has no weights");
+    bool fallback = false;  // TPA takes over when the residual stalls
+    double best = 1e300;
+    int stalls = 0;
     Sub<T>& s = sub(i);
     KP<T>& q = kpt(i, k);
     REQ(q.have_orbitals, FDE_EINVAL, "orbitals of this (subsystem, k) are not set");
@@ -883,6 +912,21 @@ template <typename T> struct EngineT : Engine {
       }
       if (sel.empty()) { conv = true; break; }
       if (it >= max_iter) break;
+      if (it < precond_record) {
+        // keep (R, X) of this iterate; the correction target (1 - P) X is formed once the
+        // converged block P is known
+        auto p = std::make_unique<Pairs>();
+        p->sub = i;
+        p->k = k;
+        p->n = nb;
+        p->R.alloc((size_t)nb * K);
+        p->D.alloc((size_t)nb * K);
+        p->tb.alloc(nb);
+        CK(cudaMemcpyAsync(p->R.p, R.p, nb * rowsz, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(p->D.p, V.p, nb * rowsz, cudaMemcpyDeviceToDevice, st));
+        launch_row_norms<T>(V.p, K, nb, K, q.kin_d.p, p->tb.p, nullptr, st);
+        recorded.push_back(std::move(p));
+      }
       ++it;
       const int m = (int)sel.size();
       CK(cudaMemcpyAsync(didx.p, sel.data(), m * sizeof(int), cudaMemcpyHostToDevice, st));
@@ -894,7 +938,27 @@ template <typename T> struct EngineT : Engine {
       std::vector<double> tsel(m);
       for (int a = 0; a < m; ++a) tsel[a] = tb[sel[a]];
       CK(cudaMemcpyAsync(dtb.p, tsel.data(), m * sizeof(double), cudaMemcpyHostToDevice, st));
-      launch_tpa<T>(W, K, q.kin_d.p, dtb.p, m, K, W, K, st);
+      if (learned && !fallback) {
+        double worst = 0;
+        std::vector<double> ss(m);
+        for (int a = 0; a < m; ++a) {
+          ss[a] = rn[sel[a]];
+          worst = std::max(worst, rn[sel[a]]);
+        }
+        // stall test: three iterations without a 1% drop of the largest residual
+        if (worst > 0.99 * best) {
+          if (++stalls >= 3) fallback = true;
+        } else {
+          stalls = 0;
+        }
+        best = std::min(best, worst);
+        dss.ensure(m);
+        CK(cudaMemcpyAsync(dss.p, ss.data(), m * sizeof(double), cudaMemcpyHostToDevice, st));
+      }
+      if (learned && !fallback)
+        launch_precond_apply<T>(W, K, q.kin_d.p, dtb.p, dss.p, m, K, pwb.p, W, K, st);
+      else
+        launch_tpa<T>(W, K, q.kin_d.p, dtb.p, m, K, W, K, st);
       orth_block(q, nb, W, nullptr, m);
       int np = 0;
       if (havep) {
@@ -927,6 +991,18 @@ template <typename T> struct EngineT : Engine {
       CK(cudaMemcpyAsync(HV.p, HV2.p, nb * rowsz, cudaMemcpyDeviceToDevice, st));
       havep = true;
     }
+    if (conv) {
+      // recorded iterates: D = (1 - P) X with P the projector on the converged block (rows of V)
+      for (auto& p : recorded) {
+        gwork.ensure(gemm_hn_work(nb, nb, K));
+        launch_gemm_hn<T>(V.p, K, p->D.p, K, nb, nb, K, Cc.p, nb, gwork.p, st);
+        launch_gemm_rot<T>(V.p, K, Cc.p, nb, nb, nb, K, p->D.p, K, -1.0, 1.0, st);
+        pair_stats(*p, q);
+        CK(cudaStreamSynchronize(st));
+        pairs.push_back(std::move(p));
+      }
+    }
+    recorded.clear();
     CK(cudaMemcpyAsync(q.X.p, V.p, nb * rowsz, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(q.HX.p, HV.p, nb * rowsz, cudaMemcpyDeviceToDevice, st));
     q.eig = eps;
@@ -1088,6 +1164,174 @@ template <typename T> struct EngineT : Engine {
     out->E_band_form = band + deband + ep.Eloc + ep.EH + ep.Exc + out->T_nad + enn;
   }
 
+  // ---- learned preconditioner ----------------------------------------------------------------
+  DBuf<float> pw, pm1, pm2, pround, gpart;
+  DBuf<unsigned short> pwb;
+  DBuf<double> gsum, dss;
+  bool have_pw = false;
+  int adam_step = 0;
+  int precond_mode = FDE_PRECOND_TPA;
+  struct Pairs {
+    int sub = 0, k = 0, n = 0;
+    DBuf<cplx<T>> R, D;
+    DBuf<double> tb, ss, dn;
+  };
+  std::vector<std::unique_ptr<Pairs>> pairs;
+
+  void ensure_pw() {
+    if (pw.n) return;
+    pw.alloc(kPrecondParams);
+    pm1.alloc(kPrecondParams);
+    pm2.alloc(kPrecondParams);
+    pround.alloc(kPrecondParams);
+    pwb.alloc(kPrecondParams);
+    gsum.alloc(kPrecondParams + 1);
+  }
+  void set_precond_mode(int mode) override {
+    REQ(mode == FDE_PRECOND_TPA || mode == FDE_PRECOND_LEARNED, FDE_EINVAL, "unknown preconditioner");
+    if (mode == FDE_PRECOND_LEARNED) REQ(have_pw, FDE_EINVAL, "learned preconditioner has no weights");
+    precond_mode = mode;
+  }
+  void precond_set_weights(const float* h) override {
+    REQ(h, FDE_EINVAL, "null weights");
+    ensure_pw();
+    CK(cudaMemcpyAsync(pw.p, h, kPrecondParams * sizeof(float), cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(pm1.p, 0, kPrecondParams * sizeof(float), st));
+    CK(cudaMemsetAsync(pm2.p, 0, kPrecondParams * sizeof(float), st));
+    launch_precond_to_bf16(pw.p, pwb.p, pround.p, st);
+    CK(cudaStreamSynchronize(st));
+    adam_step = 0;
+    have_pw = true;
+  }
+  void precond_get_weights(float* h, float* hb) override {
+    REQ(have_pw, FDE_EINVAL, "no weights");
+    if (h) CK(cudaMemcpyAsync(h, pw.p, kPrecondParams * sizeof(float), cudaMemcpyDeviceToHost, st));
+    if (hb) {
+      launch_precond_to_bf16(pw.p, pwb.p, pround.p, st);
+      CK(cudaMemcpyAsync(hb, pround.p, kPrecondParams * sizeof(float), cudaMemcpyDeviceToHost, st));
+    }
+    CK(cudaStreamSynchronize(st));
+  }
+  void precond_clear() override { pairs.clear(); }
+  int precond_record = 0;  // record (residual, iterate) pairs of the first iterations of each solve
+  std::vector<std::unique_ptr<Pairs>> recorded;
+  void set_precond_record(int n) override { precond_record = std::max(0, n); }
+  void stats(long long* dav, long long* hpsi) override {
+    if (dav) *dav = davidson_iters;
+    if (hpsi) *hpsi = hpsi_bands;
+  }
+  // Row statistics of a pair set: band kinetic energies come with it; |R_j|^2, |D_j|^2 here.
+  void pair_stats(Pairs& p, KP<T>& q) {
+    p.ss.alloc(p.n);
+    p.dn.alloc(p.n);
+    launch_row_norms<T>(p.R.p, q.npw, p.n, q.npw, nullptr, p.ss.p, nullptr, st);
+    launch_row_norms<T>(p.D.p, q.npw, p.n, q.npw, nullptr, p.dn.p, nullptr, st);
+  }
+  void precond_add_pairs(int i, int k, int n, const double* r, const double* d, const double* tb) override {
+    REQ(r && d && tb && n > 0, FDE_EINVAL, "bad pair arguments");
+    KP<T>& q = kpt(i, k);
+    auto p = std::make_unique<Pairs>();
+    p->sub = i;
+    p->k = k;
+    p->n = n;
+    const size_t cnt = (size_t)n * q.npw;
+    p->R.alloc(cnt);
+    p->D.alloc(cnt);
+    p->tb.alloc(n);
+    DBuf<double2> tmpd;
+    tmpd.alloc(cnt);
+    CK(cudaMemcpyAsync(tmpd.p, r, cnt * sizeof(double2), cudaMemcpyHostToDevice, st));
+    convert_in(tmpd.p, p->R.p, cnt);
+    CK(cudaStreamSynchronize(st));
+    CK(cudaMemcpyAsync(tmpd.p, d, cnt * sizeof(double2), cudaMemcpyHostToDevice, st));
+    convert_in(tmpd.p, p->D.p, cnt);
+    CK(cudaMemcpyAsync(p->tb.p, tb, n * sizeof(double), cudaMemcpyHostToDevice, st));
+    pair_stats(*p, q);
+    CK(cudaStreamSynchronize(st));
+    pairs.push_back(std::move(p));
+  }
+  // Training pairs from the converged orbitals of (sub, k): seeded smooth perturbations D
+  // orthogonal to the converged block, R = (H - eps_j) D_j; the ideal correction of R is D.
+  void precond_harvest(int i, int k, const double* raw, int n) override {
+    REQ(raw && n > 0, FDE_EINVAL, "bad harvest arguments");
+    Sub<T>& s = sub(i);
+    KP<T>& q = kpt(i, k);
+    REQ(q.have_eig, FDE_EINVAL, "harvest needs converged orbitals (run fde_subspace_solve first)");
+    n = std::min(n, s.nb);
+    const int K = q.npw;
+    auto p = std::make_unique<Pairs>();
+    p->sub = i;
+    p->k = k;
+    p->n = n;
+    p->R.alloc((size_t)n * K);
+    p->D.alloc((size_t)n * K);
+    p->tb.alloc(n);
+    DBuf<double2> tmpd;
+    tmpd.alloc((size_t)n * K);
+    CK(cudaMemcpyAsync(tmpd.p, raw, (size_t)n * K * sizeof(double2), cudaMemcpyHostToDevice, st));
+    convert_in(tmpd.p, p->D.p, (size_t)n * K);
+    launch_shape_init<T>(p->D.p, K, q.kin_d.p, n, K, st);
+    ensure_small(std::max(3 * s.nb, n));
+    gwork.ensure(gemm_hn_work(s.nb, n, K));
+    launch_gemm_hn<T>(q.X.p, K, p->D.p, K, s.nb, n, K, Cc.p, n, gwork.p, st);
+    launch_gemm_rot<T>(q.X.p, K, Cc.p, n, s.nb, n, K, p->D.p, K, -1.0, 1.0, st);
+    std::vector<double> sc(n);
+    launch_row_norms<T>(p->D.p, K, n, K, nullptr, dnorm.p, nullptr, st);
+    CK(cudaMemcpyAsync(sc.data(), dnorm.p, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (int a = 0; a < n; ++a) sc[a] = 1.0 / sqrt(std::max(sc[a], 1e-300));
+    CK(cudaMemcpyAsync(dtb.p, sc.data(), n * sizeof(double), cudaMemcpyHostToDevice, st));
+    launch_scale_rows<T>(p->D.p, K, n, K, dtb.p, st);
+    apply_h_dev(s, q, p->D.p, p->R.p, n);
+    CK(cudaMemcpyAsync(deps.p, q.eig.data(), n * sizeof(double), cudaMemcpyHostToDevice, st));
+    launch_residual<T>(p->R.p, p->D.p, deps.p, n, K, K, p->R.p, K, st);
+    launch_row_norms<T>(q.X.p, K, n, K, q.kin_d.p, p->tb.p, nullptr, st);
+    pair_stats(*p, q);
+    CK(cudaStreamSynchronize(st));
+    pairs.push_back(std::move(p));
+  }
+  void precond_loss_grad(double* grad, double* loss) override {
+    REQ(have_pw, FDE_EINVAL, "no weights");
+    REQ(!pairs.empty(), FDE_EINVAL, "no training pairs");
+    std::vector<double> acc(kPrecondParams + 1, 0.0), h(kPrecondParams + 1);
+    for (auto& pp : pairs) {
+      Pairs& p = *pp;
+      KP<T>& q = kpt(p.sub, p.k);
+      gpart.ensure((size_t)precond_grad_blocks(p.n, q.npw) * (kPrecondParams + 1));
+      launch_precond_grad<T>(p.R.p, p.D.p, p.n, q.npw, q.kin_d.p, p.tb.p, p.ss.p, p.dn.p, pw.p, gpart.p, gsum.p, st);
+      CK(cudaMemcpyAsync(h.data(), gsum.p, (kPrecondParams + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      for (int a = 0; a <= kPrecondParams; ++a) acc[a] += h[a];
+    }
+    if (grad) memcpy(grad, acc.data(), kPrecondParams * sizeof(double));
+    if (loss) *loss = acc[kPrecondParams];
+    CK(cudaMemcpyAsync(gsum.p, acc.data(), (kPrecondParams + 1) * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+  }
+  void precond_train(int steps, double lr, double* l0, double* l1) override {
+    REQ(steps > 0 && lr > 0, FDE_EINVAL, "bad training arguments");
+    double loss = 0;
+    for (int s = 0; s < steps; ++s) {
+      precond_loss_grad(nullptr, &loss);
+      if (s == 0 && l0) *l0 = loss;
+      launch_precond_adam(pw.p, pwb.p, gsum.p, pm1.p, pm2.p, (float)lr, ++adam_step, st);
+    }
+    precond_loss_grad(nullptr, &loss);
+    if (l1) *l1 = loss;
+  }
+  void precond_apply(int i, int k, const void* r, void* w, int nb, const double* tband) override {
+    REQ(r && w && tband && nb > 0, FDE_EINVAL, "bad arguments");
+    REQ(have_pw, FDE_EINVAL, "no weights");
+    KP<T>& q = kpt(i, k);
+    DBuf<double> tb, ss;
+    tb.alloc(nb);
+    ss.alloc(nb);
+    CK(cudaMemcpyAsync(tb.p, tband, nb * sizeof(double), cudaMemcpyHostToDevice, st));
+    launch_row_norms<T>((const C*)r, q.npw, nb, q.npw, nullptr, ss.p, nullptr, st);
+    launch_precond_apply<T>((const C*)r, q.npw, q.kin_d.p, tb.p, ss.p, nb, q.npw, pwb.p, (C*)w, q.npw, st);
+    CK(cudaStreamSynchronize(st));
+  }
+
   // ---- Pulay mixing -----------------------------------------------------------------------------
   int hist_len = 0, hist_head = 0;
   void pulay_reset() { hist_len = 0; hist_head = 0; }
@@ -1185,7 +1429,8 @@ template <typename T> struct EngineT : Engine {
       grid_pass(true, false, I);
       for (int k = 0; k < s.nk; ++k) {
         int its = 0;
-        subspace_solve(I, k, dtol, 60, &its);
+        subspace_solve(I, k, dtol, 60, &its, precond_mode);
+        davidson_iters += its;
       }
       occupations(s);
       density_from_orbitals(s, s.rho.p);
@@ -1448,8 +1693,9 @@ fde_status fde_get_orbitals(fde_ctx* c, int sub, int k, double* d_psi, double* e
 }
 fde_status fde_subspace_solve(fde_ctx* c, int sub, int k, double tol, int max_iter, int precond, int* iters) {
   return guard(c, [&]() {
-    if (precond != FDE_PRECOND_TPA) throw fde::Err{FDE_EUNSUPPORTED, "unknown preconditioner"};
-    return c->eng->subspace_solve(sub, k, tol, max_iter, iters);
+    if (precond != FDE_PRECOND_TPA && precond != FDE_PRECOND_LEARNED)
+      throw fde::Err{FDE_EUNSUPPORTED, "unknown preconditioner"};
+    return c->eng->subspace_solve(sub, k, tol, max_iter, iters, precond);
   });
 }
 fde_status fde_update_density(fde_ctx* c, int sub) {
@@ -1466,6 +1712,43 @@ fde_status fde_freeze_thaw_cycle(fde_ctx* c, double tol, int max_scf, fde_energi
     if (c->eng64) return fde::mixed_cycle(c, tol, max_scf, out, c->stream);
     return c->eng->freeze_thaw(tol, max_scf, out, nullptr);
   });
+}
+fde_status fde_set_precond(fde_ctx* c, int precond) {
+  return guard(c, [&]() { c->eng->set_precond_mode(precond); return FDE_OK; });
+}
+fde_status fde_precond_set_weights(fde_ctx* c, const float* h) {
+  return guard(c, [&]() { c->eng->precond_set_weights(h); return FDE_OK; });
+}
+fde_status fde_precond_get_weights(fde_ctx* c, float* h, float* hb) {
+  return guard(c, [&]() { c->eng->precond_get_weights(h, hb); return FDE_OK; });
+}
+fde_status fde_precond_harvest(fde_ctx* c, int sub, int k, const double* raw, int n) {
+  return guard(c, [&]() { c->eng->precond_harvest(sub, k, raw, n); return FDE_OK; });
+}
+fde_status fde_precond_add_pairs(fde_ctx* c, int sub, int k, int n, const double* r, const double* d,
+                                 const double* tband) {
+  return guard(c, [&]() { c->eng->precond_add_pairs(sub, k, n, r, d, tband); return FDE_OK; });
+}
+fde_status fde_precond_record(fde_ctx* c, int iterations) {
+  return guard(c, [&]() { c->eng->set_precond_record(iterations); return FDE_OK; });
+}
+fde_status fde_precond_clear(fde_ctx* c) {
+  return guard(c, [&]() { c->eng->precond_clear(); return FDE_OK; });
+}
+fde_status fde_precond_loss_grad(fde_ctx* c, double* grad, double* loss) {
+  return guard(c, [&]() { c->eng->precond_loss_grad(grad, loss); return FDE_OK; });
+}
+fde_status fde_precond_train(fde_ctx* c, int steps, double lr, double* loss_first, double* loss_last) {
+  return guard(c, [&]() { c->eng->precond_train(steps, lr, loss_first, loss_last); return FDE_OK; });
+}
+fde_status fde_precond_apply(fde_ctx* c, int sub, int k, const void* d_r, void* d_w, int nb, const double* tband) {
+  return guard(c, [&]() { c->eng->precond_apply(sub, k, d_r, d_w, nb, tband); return FDE_OK; });
+}
+fde_status fde_get_stats(fde_ctx* c, long long* davidson_iters, long long* hpsi_bands) {
+  return guard(c, [&]() { c->eng->stats(davidson_iters, hpsi_bands); return FDE_OK; });
+}
+fde_status fde_fft3d(fde_ctx* c, void* d_data, int sign) {
+  return guard(c, [&]() { c->eng->fft3d(d_data, sign); return FDE_OK; });
 }
 fde_status fde_sync(fde_ctx* c) {
   return guard(c, [&]() { c->eng->sync(); return FDE_OK; });

@@ -1,0 +1,213 @@
+// fftct.cuh -- compile-time specialised mixed-radix Stockham transforms of many lines held
+// in shared memory, executed by a whole CTA.
+//
+// The length N of a line and its radix sequence (8, 9, 4, 3, 5, 2, largest first) are
+// template constants, so every index division and twiddle stride folds at compile time.
+// A stage works on the flattened set of (line, butterfly) items of a batch of lines: each
+// thread loads up to IPT butterflies into registers, the CTA synchronises, the permuted
+// outputs are written back, and the CTA synchronises again (in place, one buffer).
+// Stage s (radix R, Ns = product of the earlier radices): butterfly j of a line reads
+// x_r = a[j + r N/R], multiplies x_r by W_N^{r (j mod Ns) N/(Ns R)}, takes the R-point
+// DFT y_q = sum_r x_r W_R^{rq} and writes a'[(j div Ns) Ns R + (j mod Ns) + q Ns] = y_q,
+// with W_m = exp(sign 2 pi i / m).
+#pragma once
+
+#include "fft.cuh"
+
+namespace fde {
+
+struct CtPlan {
+  int n, ns;
+  int r[8];
+};
+
+__host__ __device__ constexpr CtPlan ct_factor(int n) {
+  CtPlan p{n, 0, {0, 0, 0, 0, 0, 0, 0, 0}};
+  int m = n;
+  while (m % 8 == 0 && p.ns < 8) { p.r[p.ns++] = 8; m /= 8; }
+  while (m % 9 == 0 && p.ns < 8) { p.r[p.ns++] = 9; m /= 9; }
+  while (m % 4 == 0 && p.ns < 8) { p.r[p.ns++] = 4; m /= 4; }
+  while (m % 3 == 0 && p.ns < 8) { p.r[p.ns++] = 3; m /= 3; }
+  while (m % 5 == 0 && p.ns < 8) { p.r[p.ns++] = 5; m /= 5; }
+  while (m % 2 == 0 && p.ns < 8) { p.r[p.ns++] = 2; m /= 2; }
+  if (m != 1) p.ns = -1;
+  return p;
+}
+
+// 8- and 9-point DFTs as 2 x 4 and 3 x 3 Cooley-Tukey in registers.
+template <typename C> __device__ __forceinline__ void dft8(C* v, int sign) {
+  using T = decltype(v[0].x);
+  const T h = (T)0.70710678118654752440;  // cos(pi/4)
+  C e[4] = {v[0], v[2], v[4], v[6]}, o[4] = {v[1], v[3], v[5], v[7]};
+  dft4(e, sign);
+  dft4(o, sign);
+  // o_k *= W_8^k
+  C t1 = o[1], t3 = o[3];
+  o[1] = cscale(cadd(t1, cmuli(t1, sign)), h);           // (1 + sign i)/sqrt2
+  o[2] = cmuli(o[2], sign);                              // sign i
+  o[3] = cscale(csub(cmuli(t3, sign), t3), h);           // (-1 + sign i)/sqrt2
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    v[k] = cadd(e[k], o[k]);
+    v[k + 4] = csub(e[k], o[k]);
+  }
+}
+
+template <typename C> __device__ __forceinline__ void dft9(C* v, int sign) {
+  using T = decltype(v[0].x);
+  // W_9^1, W_9^2, W_9^4 for sign = -1 (conjugated for sign = +1)
+  const T c1 = (T)0.76604444311897803520, s1 = (T)0.64278760968653932632;   // 2 pi / 9
+  const T c2 = (T)0.17364817766693034885, s2 = (T)0.98480775301220805936;   // 4 pi / 9
+  const T c4 = (T)-0.93969262078590838405, s4 = (T)0.34202014332566873304;  // 8 pi / 9
+  C a[3][3];
+#pragma unroll
+  for (int n2 = 0; n2 < 3; ++n2) {
+    a[n2][0] = v[n2];
+    a[n2][1] = v[n2 + 3];
+    a[n2][2] = v[n2 + 6];
+    dft3(a[n2], sign);
+  }
+  const T sg = (T)sign;
+  // a[1][1] *= W^1, a[1][2] *= W^2, a[2][1] *= W^2, a[2][2] *= W^4 with W = exp(sign 2 pi i/9)
+  a[1][1] = cmul(a[1][1], mk<T>(c1, sg * s1));
+  a[1][2] = cmul(a[1][2], mk<T>(c2, sg * s2));
+  a[2][1] = cmul(a[2][1], mk<T>(c2, sg * s2));
+  a[2][2] = cmul(a[2][2], mk<T>(c4, sg * s4));
+#pragma unroll
+  for (int k1 = 0; k1 < 3; ++k1) {
+    C b[3] = {a[0][k1], a[1][k1], a[2][k1]};
+    dft3(b, sign);
+    v[k1] = b[0];
+    v[k1 + 3] = b[1];
+    v[k1 + 6] = b[2];
+  }
+}
+
+template <int R, typename C> __device__ __forceinline__ void dft_ct(C* v, int sign) {
+  if constexpr (R == 2) dft2(v, sign);
+  else if constexpr (R == 3) dft3(v, sign);
+  else if constexpr (R == 4) dft4(v, sign);
+  else if constexpr (R == 5) dft5(v, sign);
+  else if constexpr (R == 8) dft8(v, sign);
+  else dft9(v, sign);
+}
+
+// Register budget (complex values per thread) of one stage.
+template <typename T> __host__ __device__ constexpr int ct_budget() { return sizeof(T) == 4 ? 16 : 9; }
+template <typename T, int R> __host__ __device__ constexpr int ct_ipt() {
+  return ct_budget<T>() / R > 0 ? ct_budget<T>() / R : 1;
+}
+
+template <typename T, int N, int NT, int S = 0>
+__host__ __device__ constexpr int ct_lines_per_batch() {
+  constexpr CtPlan P = ct_factor(N);
+  if constexpr (S >= P.ns) {
+    return 1 << 20;
+  } else {
+    constexpr int R = P.r[S];
+    constexpr int here = NT * ct_ipt<T, R>() / (N / R);
+    constexpr int rest = ct_lines_per_batch<T, N, NT, S + 1>();
+    return here < rest ? here : rest;
+  }
+}
+
+// Line addressing: line l of the batch starts at base(l); elements are es apart.
+struct LinesContig {  // line l at l * pitch, unit element stride
+  int pitch;
+  __device__ __forceinline__ int base(int l) const { return l * pitch; }
+  static constexpr bool kUnit = true;
+};
+struct LinesRows {  // line l at rows[l] * pitch, unit element stride
+  const int* rows;
+  int pitch;
+  __device__ __forceinline__ int base(int l) const { return rows[l] * pitch; }
+  static constexpr bool kUnit = true;
+};
+struct LinesCols {  // line l at l, element stride pitch (columns of a plane)
+  int pitch;
+  __device__ __forceinline__ int base(int l) const { return l; }
+  static constexpr bool kUnit = false;
+};
+
+template <typename T, int N, int R, int NS, int NT, int NL, typename A>
+__device__ __forceinline__ void ct_stage(cplx<T>* buf, const A& addr, int l0, int nl,
+                                         const cplx<T>* __restrict__ tw, int sign) {
+  using C = cplx<T>;
+  constexpr int NB = N / R;
+  constexpr int TWS = N / (NS * R);
+  constexpr int IPT = ct_ipt<T, R>();
+  const int es = A::kUnit ? 1 : addr.pitch;
+  const int items = nl * NB;
+  C v[IPT][R];
+#pragma unroll
+  for (int it = 0; it < IPT; ++it) {
+    const int w = threadIdx.x + it * NT;
+    if (w < items) {
+      // unit-stride lines: consecutive threads walk one line; strided lines (plane
+      // columns): consecutive threads walk neighbouring lines for conflict-free banks
+      int l, j;
+      if (A::kUnit) { l = w / NB; j = w - l * NB; } else { j = w / NL; l = w - j * NL; }
+      const int k = j % NS;
+      const C* a = buf + addr.base(l0 + l);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        C x = a[(j + r * NB) * es];
+        if (r > 0 && NS > 1) {
+          C t = tw[r * k * TWS];
+          if (sign > 0) t.y = -t.y;
+          x = cmul(x, t);
+        }
+        v[it][r] = x;
+      }
+      dft_ct<R>(v[it], sign);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int it = 0; it < IPT; ++it) {
+    const int w = threadIdx.x + it * NT;
+    if (w < items) {
+      int l, j;
+      if (A::kUnit) { l = w / NB; j = w - l * NB; } else { j = w / NL; l = w - j * NL; }
+      const int k = j % NS;
+      const int d = (j / NS) * NS * R + k;
+      C* a = buf + addr.base(l0 + l);
+#pragma unroll
+      for (int q = 0; q < R; ++q) a[(d + q * NS) * es] = v[it][q];
+    }
+  }
+  __syncthreads();
+}
+
+template <typename T, int N, int NT, int NL, int S, int NS, typename A>
+__device__ __forceinline__ void ct_stages(cplx<T>* buf, const A& addr, int l0, int nl, const cplx<T>* tw, int sign) {
+  constexpr CtPlan P = ct_factor(N);
+  if constexpr (S < P.ns) {
+    constexpr int R = P.r[S];
+    ct_stage<T, N, R, NS, NT, NL>(buf, addr, l0, nl, tw, sign);
+    ct_stages<T, N, NT, NL, S + 1, NS * R>(buf, addr, l0, nl, tw, sign);
+  }
+}
+
+// Largest divisor of N not above LB (batch size of strided lines, so every batch is full).
+template <int N, int LB> __host__ __device__ constexpr int ct_full_batch() {
+  int b = LB < N ? LB : N;
+  while (N % b) --b;
+  return b;
+}
+
+// Transform nlines lines of length N with the whole CTA (NT threads; all must call).
+// Strided (column) lines must come N at a time: nlines == N.
+template <typename T, int N, int NT, typename A>
+__device__ __forceinline__ void ct_lines(cplx<T>* buf, const A& addr, int nlines, const cplx<T>* tw, int sign) {
+  static_assert(ct_factor(N).ns > 0, "length must factor into 2, 3, 5");
+  constexpr int LB0 = ct_lines_per_batch<T, N, NT>();
+  static_assert(LB0 >= 1, "register budget too small for this length");
+  constexpr int LB = A::kUnit ? LB0 : ct_full_batch<N, LB0>();
+  for (int l0 = 0; l0 < nlines; l0 += LB) {
+    const int nl = nlines - l0 < LB ? nlines - l0 : LB;
+    ct_stages<T, N, NT, LB, 0, 1>(buf, addr, l0, nl, tw, sign);
+  }
+}
+
+}  // namespace fde

@@ -49,6 +49,7 @@ k_fft_axis(cplx<T>* __restrict__ data, long long nlines, int N, long long I, Lin
 
 template <typename T>
 void launch_fft3d(cplx<T>* data, const GridDims& g, const FftPlans<T>& fp, int sign, cudaStream_t st) {
+  if (launch_fft3d_ct<T>(data, g, fp, sign, st)) return;
   const long long nr = (long long)g.n1 * g.n2 * g.n3;
   struct Ax { int N; long long I; const LinePlan<T>* p; } ax[3] = {
       {g.n3, 1, &fp.p3}, {g.n2, g.n3, &fp.p2}, {g.n1, (long long)g.n2 * g.n3, &fp.p1}};
@@ -360,6 +361,14 @@ __global__ void k_combine(const double* a, const double* b, const double* c, con
   }
 }
 
+template <typename T>
+__global__ void k_scale_c(cplx<T>* __restrict__ a, double s, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    a[i].x = (T)(a[i].x * s);
+    a[i].y = (T)(a[i].y * s);
+  }
+}
+
 __global__ void k_sum_rows(const double* __restrict__ a, int nrows, long long n, double* __restrict__ out) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     double v = 0;
@@ -461,6 +470,13 @@ void grid_combine(const double* a, const double* b, const double* c, const cplx<
   count_launches(1);
   k_combine<T><<<gs(n), 256, 0, st>>>(a, b, c, d, sd, out, n);
 }
+template <typename T>
+void grid_scale_c(cplx<T>* a, double s, long long n, cudaStream_t st) {
+  count_launches(1);
+  k_scale_c<T><<<gs(n), 256, 0, st>>>(a, s, n);
+}
+template void grid_scale_c<float>(float2*, double, long long, cudaStream_t);
+template void grid_scale_c<double>(double2*, double, long long, cudaStream_t);
 void grid_sum_rows(const double* a, int nrows, long long n, double* out, cudaStream_t st) {
   count_launches(1);
   k_sum_rows<<<gs(n), 256, 0, st>>>(a, nrows, n, out);

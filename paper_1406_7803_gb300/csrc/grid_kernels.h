@@ -26,6 +26,8 @@ void grid_c_to_real(const cplx<T>* c, double* a, long long n, cudaStream_t st);
 template <typename T>
 void grid_combine(const double* a, const double* b, const double* c, const cplx<T>* d, double sd, double* out,
                   long long n, cudaStream_t st);
+template <typename T>
+void grid_scale_c(cplx<T>* a, double s, long long n, cudaStream_t st);
 void grid_sum_rows(const double* a, int nrows, long long n, double* out, cudaStream_t st);
 void grid_dot_partial(const double* a, const double* b, long long n, int mode, double* partial, cudaStream_t st);
 void grid_finalize(const double* partial, int nq, double scale, double* out, cudaStream_t st);

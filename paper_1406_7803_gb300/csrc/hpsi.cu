@@ -149,6 +149,7 @@ void launch_hpsi_local(const cplx<T>* psi, int ldpsi, cplx<T>* hpsi, int ldh, in
                        const T* kin, const T* vplane, cplx<T>* scratch, const SphereDev& sp,
                        const GridDims& g, const FftPlans<T>& fp, cudaStream_t st) {
   if (nb <= 0) return;
+  if (launch_hpsi_local_ct<T>(psi, ldpsi, hpsi, ldh, nb, kin, vplane, scratch, sp, g, fp, st)) return;
   const dim3 gz(ceil_div(sp.ncol, kColsPerCta), nb);
   const size_t zs = zpass_smem<T>(g.n3), ps = plane_smem<T>(g);
   allow_smem(k_zinv<T>, zs);
@@ -213,6 +214,7 @@ void launch_density(const cplx<T>* psi, int ldpsi, int nb, const double* weight,
                     double* rho_plane, int accumulate, const SphereDev& sp, const GridDims& g,
                     const FftPlans<T>& fp, cudaStream_t st) {
   if (nb <= 0) return;
+  if (launch_density_ct<T>(psi, ldpsi, nb, weight, scratch, rho_plane, accumulate, sp, g, fp, st)) return;
   const dim3 gz(ceil_div(sp.ncol, kColsPerCta), nb);
   const size_t zs = zpass_smem<T>(g.n3), ps = plane_smem<T>(g);
   allow_smem(k_zinv<T>, zs);

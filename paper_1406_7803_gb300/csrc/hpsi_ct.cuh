@@ -1,0 +1,327 @@
+// hpsi_ct.cuh -- H psi, band-density and full-grid transform kernels with compile-time
+// transform lengths (fftct.cuh).  Same data flow as hpsi.cu / grid.cu; included by one
+// translation unit per precision, which instantiates the supported lengths.
+#pragma once
+
+#include "fftct.cuh"
+#include "kernels.h"
+#include "prof.h"
+
+namespace fde {
+
+constexpr int kCtThreads = 256;
+constexpr int kCtCols = 8;  // z-lines per CTA in the z passes and axis transforms
+
+template <typename T, int N3>
+__global__ void __launch_bounds__(kCtThreads)
+k_zinv_ct(const cplx<T>* __restrict__ psi, int ldpsi, cplx<T>* __restrict__ scratch, SphereDev sp,
+          const cplx<T>* __restrict__ tw) {
+  using C = cplx<T>;
+  constexpr int LP = N3 + 1;
+  __shared__ __align__(16) C lines[kCtCols * LP];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c0 = blockIdx.x * kCtCols, b = blockIdx.y;
+  for (int i = threadIdx.x; i < kCtCols * LP; i += kCtThreads) lines[i] = mk<T>(0, 0);
+  __syncthreads();
+  const int c = c0 + w;
+  if (c < sp.ncol) {
+    const int s = sp.col_start[c], e = sp.col_start[c + 1], m3 = sp.col_m3lo[c];
+    const C* src = psi + (size_t)b * ldpsi + s;
+    C* L = lines + w * LP;
+    for (int t = lane; t < e - s; t += 32) {
+      int i3 = m3 + t;
+      i3 += (i3 < 0) ? N3 : 0;
+      L[i3] = src[t];
+    }
+  }
+  __syncthreads();
+  ct_lines<T, N3, kCtThreads>(lines, LinesContig{LP}, kCtCols, tw, +1);
+  const int nc = min(kCtCols, sp.ncol - c0);
+  C* dst = scratch + (size_t)b * N3 * sp.ncol + c0;
+  for (int idx = threadIdx.x; idx < N3 * kCtCols; idx += kCtThreads) {
+    const int i3 = idx / kCtCols, ww = idx % kCtCols;
+    if (ww < nc) dst[(size_t)i3 * sp.ncol + ww] = lines[ww * LP + i3];
+  }
+}
+
+template <typename T, int N3>
+__global__ void __launch_bounds__(kCtThreads)
+k_zfwd_ct(const cplx<T>* __restrict__ scratch, const cplx<T>* __restrict__ psi, int ldpsi, cplx<T>* __restrict__ hpsi,
+          int ldh, const T* __restrict__ kin, SphereDev sp, T inv_nr, const cplx<T>* __restrict__ tw) {
+  using C = cplx<T>;
+  constexpr int LP = N3 + 1;
+  __shared__ __align__(16) C lines[kCtCols * LP];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c0 = blockIdx.x * kCtCols, b = blockIdx.y;
+  const int nc = min(kCtCols, sp.ncol - c0);
+  const C* src = scratch + (size_t)b * N3 * sp.ncol + c0;
+  for (int idx = threadIdx.x; idx < N3 * kCtCols; idx += kCtThreads) {
+    const int i3 = idx / kCtCols, ww = idx % kCtCols;
+    lines[ww * LP + i3] = (ww < nc) ? src[(size_t)i3 * sp.ncol + ww] : mk<T>(0, 0);
+  }
+  __syncthreads();
+  ct_lines<T, N3, kCtThreads>(lines, LinesContig{LP}, kCtCols, tw, -1);
+  const int c = c0 + w;
+  if (c >= sp.ncol) return;
+  const C* L = lines + w * LP;
+  const int s = sp.col_start[c], e = sp.col_start[c + 1], m3 = sp.col_m3lo[c];
+  const C* ps = psi + (size_t)b * ldpsi;
+  C* hs = hpsi + (size_t)b * ldh;
+  for (int t = lane; t < e - s; t += 32) {
+    int i3 = m3 + t;
+    i3 += (i3 < 0) ? N3 : 0;
+    const int gidx = s + t;
+    const C x = ps[gidx];
+    const T kk = kin[gidx];
+    C o = L[i3];
+    o.x = o.x * inv_nr + kk * x.x;
+    o.y = o.y * inv_nr + kk * x.y;
+    hs[gidx] = o;
+  }
+}
+
+// One CTA per (band, z-plane): columns in, 2D inverse FFT (y on the rows holding columns,
+// then x), potential multiply, 2D forward FFT, columns out.  n1 = n2 = N.
+template <typename T, int N>
+__global__ void __launch_bounds__(kCtThreads)
+k_plane_ct(cplx<T>* __restrict__ scratch, SphereDev sp, const T* __restrict__ vplane, int n3,
+           const cplx<T>* __restrict__ tw1, const cplx<T>* __restrict__ tw2) {
+  using C = cplx<T>;
+  constexpr int PITCH = N + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* P = reinterpret_cast<C*>(smem_raw);
+  __shared__ int rows[N];
+  const int i3 = blockIdx.x, b = blockIdx.y;
+  C* S = scratch + ((size_t)b * n3 + i3) * sp.ncol;
+  for (int idx = threadIdx.x; idx < N * PITCH; idx += kCtThreads) P[idx] = mk<T>(0, 0);
+  for (int r = threadIdx.x; r < sp.nrow; r += kCtThreads) rows[r] = sp.row_i1[r];
+  __syncthreads();
+  for (int c = threadIdx.x; c < sp.ncol; c += kCtThreads) P[sp.col_i1[c] * PITCH + sp.col_i2[c]] = S[c];
+  __syncthreads();
+  ct_lines<T, N, kCtThreads>(P, LinesRows{rows, PITCH}, sp.nrow, tw2, +1);
+  ct_lines<T, N, kCtThreads>(P, LinesCols{PITCH}, N, tw1, +1);
+  const T* V = vplane + (size_t)i3 * N * N;
+  for (int idx = threadIdx.x; idx < N * N; idx += kCtThreads) {
+    const int i1 = idx / N, i2 = idx - i1 * N;
+    C& z = P[i1 * PITCH + i2];
+    const T v = V[idx];
+    z.x *= v;
+    z.y *= v;
+  }
+  __syncthreads();
+  ct_lines<T, N, kCtThreads>(P, LinesCols{PITCH}, N, tw1, -1);
+  ct_lines<T, N, kCtThreads>(P, LinesRows{rows, PITCH}, sp.nrow, tw2, -1);
+  for (int c = threadIdx.x; c < sp.ncol; c += kCtThreads) S[c] = P[sp.col_i1[c] * PITCH + sp.col_i2[c]];
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(kCtThreads)
+k_plane_density_ct(const cplx<T>* __restrict__ scratch, SphereDev sp, int nb, const double* __restrict__ weight,
+                   double* __restrict__ rho_plane, int accumulate, int n3, const cplx<T>* __restrict__ tw1,
+                   const cplx<T>* __restrict__ tw2) {
+  using C = cplx<T>;
+  constexpr int PITCH = N + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* P = reinterpret_cast<C*>(smem_raw);
+  __shared__ int rows[N];
+  const int i3 = blockIdx.x;
+  for (int r = threadIdx.x; r < sp.nrow; r += kCtThreads) rows[r] = sp.row_i1[r];
+  double* R = rho_plane + (size_t)i3 * N * N;
+  for (int b = 0; b < nb; ++b) {
+    const C* S = scratch + ((size_t)b * n3 + i3) * sp.ncol;
+    for (int idx = threadIdx.x; idx < N * PITCH; idx += kCtThreads) P[idx] = mk<T>(0, 0);
+    __syncthreads();
+    for (int c = threadIdx.x; c < sp.ncol; c += kCtThreads) P[sp.col_i1[c] * PITCH + sp.col_i2[c]] = S[c];
+    __syncthreads();
+    ct_lines<T, N, kCtThreads>(P, LinesRows{rows, PITCH}, sp.nrow, tw2, +1);
+    ct_lines<T, N, kCtThreads>(P, LinesCols{PITCH}, N, tw1, +1);
+    const double wb = weight[b];
+    const bool first = (b == 0) && !accumulate;
+    for (int idx = threadIdx.x; idx < N * N; idx += kCtThreads) {
+      const int i1 = idx / N, i2 = idx - i1 * N;
+      const C z = P[i1 * PITCH + i2];
+      const double d = wb * ((double)z.x * (double)z.x + (double)z.y * (double)z.y);
+      R[idx] = first ? d : R[idx] + d;
+    }
+    __syncthreads();
+  }
+}
+
+// One axis of a full 3D transform: element (o, e, t) at (o * N + e) * I + t; 8 lines per CTA.
+template <typename T, int N>
+__global__ void __launch_bounds__(kCtThreads)
+k_fft_axis_ct(cplx<T>* __restrict__ data, long long nlines, long long I, const cplx<T>* __restrict__ tw, int sign) {
+  using C = cplx<T>;
+  constexpr int LP = N + 1;
+  __shared__ __align__(16) C lines[kCtCols * LP];
+  const long long l0 = (long long)blockIdx.x * kCtCols;
+  const int nl = (int)min((long long)kCtCols, nlines - l0);
+  for (int idx = threadIdx.x; idx < kCtCols * N; idx += kCtThreads) {
+    int tl, e;
+    if (I == 1) { tl = idx / N; e = idx - tl * N; } else { e = idx / kCtCols; tl = idx - e * kCtCols; }
+    if (tl < nl) {
+      const long long l = l0 + tl, o = l / I, t = l - o * I;
+      lines[tl * LP + e] = data[(o * N + e) * I + t];
+    } else {
+      lines[tl * LP + e] = mk<T>(0, 0);
+    }
+  }
+  __syncthreads();
+  ct_lines<T, N, kCtThreads>(lines, LinesContig{LP}, kCtCols, tw, sign);
+  for (int idx = threadIdx.x; idx < kCtCols * N; idx += kCtThreads) {
+    int tl, e;
+    if (I == 1) { tl = idx / N; e = idx - tl * N; } else { e = idx / kCtCols; tl = idx - e * kCtCols; }
+    if (tl < nl) {
+      const long long l = l0 + tl, o = l / I, t = l - o * I;
+      data[(o * N + e) * I + t] = lines[tl * LP + e];
+    }
+  }
+}
+
+template <typename K> static inline void ct_allow_smem(K kernel, size_t bytes) {
+  if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+#define FDE_CT_LINES(X) X(24) X(32) X(60) X(72) X(96) X(144) X(180) X(288)
+#define FDE_CT_PLANES(X) X(24) X(32) X(72) X(96) X(144)
+
+template <typename T> bool ct_line_ok(int n) {
+  switch (n) {
+#define FDE_CASE(N) case N:
+    FDE_CT_LINES(FDE_CASE)
+#undef FDE_CASE
+    return true;
+    default: return false;
+  }
+}
+template <typename T> bool ct_plane_ok(int n1, int n2) {
+  if (n1 != n2) return false;
+  if ((size_t)n1 * (n1 + 1) * sizeof(cplx<T>) > 200 * 1024) return false;
+  switch (n1) {
+#define FDE_CASE(N) case N:
+    FDE_CT_PLANES(FDE_CASE)
+#undef FDE_CASE
+    return true;
+    default: return false;
+  }
+}
+
+template <typename T>
+static void ct_zinv(int n3, dim3 grid, cudaStream_t st, const cplx<T>* psi, int ld, cplx<T>* scr, const SphereDev& sp,
+                    const cplx<T>* tw) {
+  switch (n3) {
+#define FDE_CASE(N)                                                              \
+  case N:                                                                        \
+    count_launches(1);                                                           \
+    k_zinv_ct<T, N><<<grid, kCtThreads, 0, st>>>(psi, ld, scr, sp, tw);         \
+    break;
+    FDE_CT_LINES(FDE_CASE)
+#undef FDE_CASE
+  }
+}
+
+template <typename T>
+static void ct_zfwd(int n3, dim3 grid, cudaStream_t st, const cplx<T>* scr, const cplx<T>* psi, int ld, cplx<T>* h,
+                    int ldh, const T* kin, const SphereDev& sp, T inv_nr, const cplx<T>* tw) {
+  switch (n3) {
+#define FDE_CASE(N)                                                                          \
+  case N:                                                                                    \
+    count_launches(1);                                                                       \
+    k_zfwd_ct<T, N><<<grid, kCtThreads, 0, st>>>(scr, psi, ld, h, ldh, kin, sp, inv_nr, tw); \
+    break;
+    FDE_CT_LINES(FDE_CASE)
+#undef FDE_CASE
+  }
+}
+
+template <typename T>
+static void ct_plane(int n, dim3 grid, cudaStream_t st, cplx<T>* scr, const SphereDev& sp, const T* vplane, int n3,
+                     const cplx<T>* tw1, const cplx<T>* tw2) {
+  const size_t sm = (size_t)n * (n + 1) * sizeof(cplx<T>);
+  switch (n) {
+#define FDE_CASE(N)                                                                   \
+  case N:                                                                             \
+    ct_allow_smem(k_plane_ct<T, N>, sm);                                              \
+    count_launches(1);                                                                \
+    k_plane_ct<T, N><<<grid, kCtThreads, sm, st>>>(scr, sp, vplane, n3, tw1, tw2);    \
+    break;
+    FDE_CT_PLANES(FDE_CASE)
+#undef FDE_CASE
+  }
+}
+
+template <typename T>
+static void ct_plane_density(int n, int n3, cudaStream_t st, const cplx<T>* scr, const SphereDev& sp, int nb,
+                             const double* weight, double* rho_plane, int acc, const cplx<T>* tw1,
+                             const cplx<T>* tw2) {
+  const size_t sm = (size_t)n * (n + 1) * sizeof(cplx<T>);
+  switch (n) {
+#define FDE_CASE(N)                                                                                      \
+  case N:                                                                                                \
+    ct_allow_smem(k_plane_density_ct<T, N>, sm);                                                         \
+    count_launches(1);                                                                                   \
+    k_plane_density_ct<T, N><<<n3, kCtThreads, sm, st>>>(scr, sp, nb, weight, rho_plane, acc, n3, tw1, tw2); \
+    break;
+    FDE_CT_PLANES(FDE_CASE)
+#undef FDE_CASE
+  }
+}
+
+template <typename T>
+static void ct_axis(int n, long long nlines, long long I, cudaStream_t st, cplx<T>* data, const cplx<T>* tw, int sign) {
+  const unsigned blocks = (unsigned)((nlines + kCtCols - 1) / kCtCols);
+  switch (n) {
+#define FDE_CASE(N)                                                                     \
+  case N:                                                                               \
+    count_launches(1);                                                                  \
+    k_fft_axis_ct<T, N><<<blocks, kCtThreads, 0, st>>>(data, nlines, I, tw, sign);      \
+    break;
+    FDE_CT_LINES(FDE_CASE)
+#undef FDE_CASE
+  }
+}
+
+template <typename T>
+bool launch_hpsi_local_ct(const cplx<T>* psi, int ldpsi, cplx<T>* hpsi, int ldh, int nb, const T* kin,
+                          const T* vplane, cplx<T>* scratch, const SphereDev& sp, const GridDims& g,
+                          const FftPlans<T>& fp, cudaStream_t st) {
+  if (!ct_plane_ok<T>(g.n1, g.n2) || !ct_line_ok<T>(g.n3)) return false;
+  const dim3 gz(ceil_div(sp.ncol, kCtCols), nb);
+  {
+    ProfScope p("k_zinv", st);
+    ct_zinv<T>(g.n3, gz, st, psi, ldpsi, scratch, sp, fp.p3.tw);
+  }
+  {
+    ProfScope p("k_plane", st);
+    ct_plane<T>(g.n1, dim3(g.n3, nb), st, scratch, sp, vplane, g.n3, fp.p1.tw, fp.p2.tw);
+  }
+  const T inv_nr = (T)(1.0 / ((double)g.n1 * g.n2 * g.n3));
+  {
+    ProfScope p("k_zfwd", st);
+    ct_zfwd<T>(g.n3, gz, st, scratch, psi, ldpsi, hpsi, ldh, kin, sp, inv_nr, fp.p3.tw);
+  }
+  return true;
+}
+
+template <typename T>
+bool launch_density_ct(const cplx<T>* psi, int ldpsi, int nb, const double* weight, cplx<T>* scratch,
+                       double* rho_plane, int accumulate, const SphereDev& sp, const GridDims& g,
+                       const FftPlans<T>& fp, cudaStream_t st) {
+  if (!ct_plane_ok<T>(g.n1, g.n2) || !ct_line_ok<T>(g.n3)) return false;
+  const dim3 gz(ceil_div(sp.ncol, kCtCols), nb);
+  ct_zinv<T>(g.n3, gz, st, psi, ldpsi, scratch, sp, fp.p3.tw);
+  ct_plane_density<T>(g.n1, g.n3, st, scratch, sp, nb, weight, rho_plane, accumulate, fp.p1.tw, fp.p2.tw);
+  return true;
+}
+
+template <typename T>
+bool launch_fft3d_ct(cplx<T>* data, const GridDims& g, const FftPlans<T>& fp, int sign, cudaStream_t st) {
+  if (!ct_line_ok<T>(g.n1) || !ct_line_ok<T>(g.n2) || !ct_line_ok<T>(g.n3)) return false;
+  const long long nr = (long long)g.n1 * g.n2 * g.n3;
+  ct_axis<T>(g.n3, nr / g.n3, 1, st, data, fp.p3.tw, sign);
+  ct_axis<T>(g.n2, nr / g.n2, g.n3, st, data, fp.p2.tw, sign);
+  ct_axis<T>(g.n1, nr / g.n1, (long long)g.n2 * g.n3, st, data, fp.p1.tw, sign);
+  return true;
+}
+
+}  // namespace fde

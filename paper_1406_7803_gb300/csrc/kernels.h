@@ -40,6 +40,19 @@ void launch_density(const cplx<T>* psi, int ldpsi, int nb, const double* weight,
                     cplx<T>* scratch, double* rho_plane, int accumulate, const SphereDev& sp,
                     const GridDims& g, const FftPlans<T>& fp, cudaStream_t st);
 
+// Compile-time-length variants (hpsi_ct.cuh); return false when the grid sizes are not
+// among the instantiated ones, and the runtime-length kernels run instead.
+template <typename T>
+bool launch_hpsi_local_ct(const cplx<T>* psi, int ldpsi, cplx<T>* hpsi, int ldh, int nb, const T* kin,
+                          const T* vplane, cplx<T>* scratch, const SphereDev& sp, const GridDims& g,
+                          const FftPlans<T>& fp, cudaStream_t st);
+template <typename T>
+bool launch_density_ct(const cplx<T>* psi, int ldpsi, int nb, const double* weight, cplx<T>* scratch,
+                       double* rho_plane, int accumulate, const SphereDev& sp, const GridDims& g,
+                       const FftPlans<T>& fp, cudaStream_t st);
+template <typename T>
+bool launch_fft3d_ct(cplx<T>* data, const GridDims& g, const FftPlans<T>& fp, int sign, cudaStream_t st);
+
 // out[j][i] = (Tout) in[i][j], in is [rows][cols]; with optional accumulate.
 template <typename Tin, typename Tout>
 void launch_transpose(const Tin* in, Tout* out, int rows, int cols, int accumulate, cudaStream_t st);

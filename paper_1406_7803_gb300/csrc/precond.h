@@ -1,0 +1,29 @@
+// precond.h -- launch wrappers of the learned preconditioner (precond.cu).
+#pragma once
+
+#include "kernels.h"
+
+namespace fde {
+
+constexpr int kPrecondWidth = 64;
+constexpr int kPrecondParams = kPrecondWidth * 3 + kPrecondWidth + 2 * (kPrecondWidth * kPrecondWidth + kPrecondWidth) +
+                               kPrecondWidth + 1;
+
+// W[j][g] = K(y) exp(MLP(f)) R[j][g] for nb rows (in place allowed); wb: bf16 weights.
+template <typename T>
+void launch_precond_apply(const cplx<T>* R, int ldr, const T* kin, const double* tband, const double* sumsq, int nb,
+                          int K, const void* wb, cplx<T>* W, int ldw, cudaStream_t st);
+
+// Loss and gradient over nb x K pairs; part: precond_grad_blocks(nb, K) x (kPrecondParams + 1)
+// floats; out[kPrecondParams + 1] (gradient, then the loss) is overwritten.
+int precond_grad_blocks(int nb, int K);
+template <typename T>
+void launch_precond_grad(const cplx<T>* R, const cplx<T>* D, int nb, int K, const T* kin, const double* tband,
+                         const double* sumsq, const double* dnorm2, const float* wf, float* part, double* out,
+                         cudaStream_t st);
+
+void launch_precond_adam(float* wf, void* wb, const double* grad, float* m1, float* m2, float lr, int step,
+                         cudaStream_t st);
+void launch_precond_to_bf16(const float* wf, void* wb, float* rounded, cudaStream_t st);
+
+}  // namespace fde

@@ -20,7 +20,8 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libfde.so")
 FDE_OK, FDE_EINVAL, FDE_ENOMEM, FDE_ECUDA, FDE_ENOCONV, FDE_ENONFINITE, FDE_ETIMEOUT, FDE_EUNSUPPORTED = \
     0, -1, -2, -3, -4, -5, -6, -7
 FDE_PREC_FP64, FDE_PREC_MIXED = 0, 1
-FDE_PRECOND_TPA = 0
+FDE_PRECOND_TPA, FDE_PRECOND_LEARNED = 0, 1
+FDE_PRECOND_PARAMS = 8641
 STATUS_NAMES = {0: "FDE_OK", -1: "FDE_EINVAL", -2: "FDE_ENOMEM", -3: "FDE_ECUDA", -4: "FDE_ENOCONV",
                 -5: "FDE_ENONFINITE", -6: "FDE_ETIMEOUT", -7: "FDE_EUNSUPPORTED"}
 
@@ -75,6 +76,20 @@ EXPORTS = {
     "fde_launch_count": (C.c_int, [C.c_void_p, C.POINTER(C.c_longlong)]),
     "fde_apply_h_local_static": (C.c_int, [C.POINTER(CellDesc), C.POINTER(C.c_double), C.c_int, C.c_void_p,
                                            C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "fde_fft3d": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "fde_set_precond": (C.c_int, [C.c_void_p, C.c_int]),
+    "fde_precond_set_weights": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "fde_precond_get_weights": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "fde_precond_harvest": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int]),
+    "fde_precond_add_pairs": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                                        C.c_void_p]),
+    "fde_precond_clear": (C.c_int, [C.c_void_p]),
+    "fde_precond_record": (C.c_int, [C.c_void_p, C.c_int]),
+    "fde_precond_loss_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]),
+    "fde_precond_train": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.POINTER(C.c_double),
+                                    C.POINTER(C.c_double)]),
+    "fde_precond_apply": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "fde_get_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
     "fde_sync": (C.c_int, [C.c_void_p]),
     "fde_last_error": (C.c_char_p, [C.c_void_p]),
     "fde_destroy": (C.c_int, [C.c_void_p]),
@@ -260,6 +275,64 @@ class Context:
 
     def profile_enable(self, on=True):
         return self._check(self.lib.fde_profile_enable(self.h, int(on)), "fde_profile_enable")
+
+    # ---- learned preconditioner ----------------------------------------------------------
+    def set_precond(self, mode):
+        return self._check(self.lib.fde_set_precond(self.h, int(mode)), "fde_set_precond")
+
+    def precond_set_weights(self, w):
+        a = np.ascontiguousarray(w, dtype=np.float32)
+        assert a.size == FDE_PRECOND_PARAMS
+        return self._check(self.lib.fde_precond_set_weights(self.h, _hptr(a)), "fde_precond_set_weights")
+
+    def precond_get_weights(self):
+        w = np.zeros(FDE_PRECOND_PARAMS, dtype=np.float32)
+        wb = np.zeros(FDE_PRECOND_PARAMS, dtype=np.float32)
+        self._check(self.lib.fde_precond_get_weights(self.h, _hptr(w), _hptr(wb)), "fde_precond_get_weights")
+        return w, wb
+
+    def precond_harvest(self, sub, k, raw):
+        a = np.ascontiguousarray(raw, dtype=np.complex128)
+        return self._check(self.lib.fde_precond_harvest(self.h, sub, k, _hptr(a), int(a.shape[0])),
+                           "fde_precond_harvest")
+
+    def precond_add_pairs(self, sub, k, r, d, tband):
+        r = np.ascontiguousarray(r, dtype=np.complex128)
+        d = np.ascontiguousarray(d, dtype=np.complex128)
+        tb = np.ascontiguousarray(tband, dtype=np.float64)
+        return self._check(self.lib.fde_precond_add_pairs(self.h, sub, k, int(r.shape[0]), _hptr(r), _hptr(d),
+                                                          _hptr(tb)), "fde_precond_add_pairs")
+
+    def precond_record(self, iterations):
+        return self._check(self.lib.fde_precond_record(self.h, int(iterations)), "fde_precond_record")
+
+    def precond_clear(self):
+        return self._check(self.lib.fde_precond_clear(self.h), "fde_precond_clear")
+
+    def precond_loss_grad(self):
+        g = np.zeros(FDE_PRECOND_PARAMS)
+        loss = C.c_double()
+        self._check(self.lib.fde_precond_loss_grad(self.h, _hptr(g), C.byref(loss)), "fde_precond_loss_grad")
+        return loss.value, g
+
+    def precond_train(self, steps, lr):
+        l0, l1 = C.c_double(), C.c_double()
+        self._check(self.lib.fde_precond_train(self.h, int(steps), float(lr), C.byref(l0), C.byref(l1)),
+                    "fde_precond_train")
+        return l0.value, l1.value
+
+    def precond_apply(self, sub, k, r, w, nb, tband):
+        tb = np.ascontiguousarray(tband, dtype=np.float64)
+        return self._check(self.lib.fde_precond_apply(self.h, sub, k, _dptr(r), _dptr(w), int(nb), _hptr(tb)),
+                           "fde_precond_apply")
+
+    def stats(self):
+        a, b = C.c_longlong(), C.c_longlong()
+        self._check(self.lib.fde_get_stats(self.h, C.byref(a), C.byref(b)), "fde_get_stats")
+        return a.value, b.value
+
+    def fft3d(self, data, sign):
+        return self._check(self.lib.fde_fft3d(self.h, _dptr(data), int(sign)), "fde_fft3d")
 
     def launch_count(self):
         n = C.c_longlong()

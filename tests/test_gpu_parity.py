@@ -82,6 +82,40 @@ def test_apply_h_matches_oracle(make, prec, tol):
             assert err < tol, (I, k, err)
 
 
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("mixed", 1e-5)])
+def test_full_size_molecule_on_slab_sampled(prec, tol):
+    """At the benchmark's full size (72 x 72 x 180 grid, 43.7k plane waves) in the launch
+    configuration bench.py times: the embedding-potential build element by element, and
+    H psi on sampled bands of a slab k-point (whole 64-band block, first bands checked)
+    and of the molecule, against the oracle."""
+    wl = workloads.molecule_on_slab()
+    sy = ofde.System(wl)
+    rhos = np.array([workloads.initial_density(wl, I) for I in range(wl.nsub)])
+    pot = sy.build_veff(rhos)
+    ctx = fde.context_from_workload(wl, prec=prec)
+    for I in range(wl.nsub):
+        ctx.set_density(I, rhos[I])
+    out = torch.zeros((wl.nsub,) + tuple(wl.grid), dtype=torch.float64, device="cuda")
+    ctx.build_vemb(out)
+    got = out.cpu().numpy()
+    vtol = 1e-10 if prec == "fp64" else 1e-5
+    for I in range(wl.nsub):
+        assert np.abs(got[I] - pot["veff"][I]).max() / np.abs(pot["veff"][I]).max() < vtol
+    ctdt = torch.complex128 if prec == "fp64" else torch.complex64
+    for I, k, nsample in ((0, 2, 3), (1, 0, 2)):
+        ctx.set_veff(I, _dev(pot["veff"][I], torch.float64))
+        s = wl.subsystems[I]
+        npw = sy.basis[I][k][0].shape[0]
+        c = workloads.raw_orbitals(13, I, k, s.nbands, npw)
+        psi = _dev(c, ctdt)
+        hpsi = torch.zeros_like(psi)
+        ctx.apply_h(I, k, psi, hpsi, s.nbands)
+        torch.cuda.synchronize()
+        want = sy.apply_h(I, k, c[:nsample], pot["veff"][I])
+        g = hpsi[:nsample].to(torch.complex128).cpu().numpy()
+        assert np.abs(g - want).max() / np.abs(want).max() < tol
+
+
 def test_apply_h_host_path_matches_device_path():
     wl = workloads.molecule_on_slab_small()
     sy = ofde.System(wl)
