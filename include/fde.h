@@ -176,6 +176,13 @@ fde_status fde_apply_h_host(fde_ctx* ctx, int sub, int k, const double* h_psi, d
  * into the context's H psi buffers: one batched pass of the hot path.  Asynchronous. */
 fde_status fde_apply_h_all(fde_ctx* ctx);
 
+/* One pass of the hot path over the whole cell: fde_build_vemb (no energies) followed by
+ * fde_apply_h_all.  use_graph = 1 replays the pass from a CUDA graph captured on the
+ * context stream (captured on the first call, and again whenever the context has
+ * reallocated device memory since); the context stream must then not be the legacy default
+ * stream (FDE_EINVAL).  Asynchronous. */
+fde_status fde_hot_step(fde_ctx* ctx, int use_graph);
+
 /* Initial orbitals of (sub, k) from raw complex draws h_raw [nbands][npw][2] (host):
  * c_G = raw_G / (1 + |k+G|^2/2), then orthonormalised on the device. */
 fde_status fde_init_orbitals(fde_ctx* ctx, int sub, int k, const double* h_raw);
@@ -292,6 +299,13 @@ fde_status fde_apply_h_local_static(const fde_cell_desc* cell, const double* kfr
  * (f(G) = (1/N_r) sum_r f(r) e^{-iG.r}); sign +1 inverse, unscaled.  Exposed so the
  * transforms can be checked on their own. */
 fde_status fde_fft3d(fde_ctx* ctx, void* d_data, int sign);
+
+/* The FP64 Hermitian eigensolver of the Rayleigh-Ritz step applied to a caller matrix:
+ * d_A device complex double [n][n] (Hermitian, row-major, not modified), d_w device [n]
+ * receives every eigenvalue in ascending order, d_V device complex double [n][n] receives
+ * in column j (V[r*n + j]) the unit eigenvector of w[j] for j < nvec and zeros beyond.
+ * Householder tridiagonalisation, bisection and inverse iteration; n <= 1024. */
+fde_status fde_dense_eigh(fde_ctx* ctx, int n, const double* d_A, int nvec, double* d_w, double* d_V);
 
 /* Synchronise the context stream and check the device status word. */
 fde_status fde_sync(fde_ctx* ctx);

@@ -40,6 +40,10 @@ struct Err {
     if (!(c)) throw Err{(s), (m)}; \
   } while (0)
 
+// Every device (re)allocation or release bumps this counter; a captured CUDA graph whose
+// counter value is stale may reference freed buffers and is captured again.
+static unsigned long long g_alloc_generation = 0;
+
 template <typename X> struct DBuf {
   X* p = nullptr;
   size_t n = 0;
@@ -53,12 +57,16 @@ template <typename X> struct DBuf {
   }
   ~DBuf() { release(); }
   void release() {
-    if (p) cudaFree(p);
+    if (p) {
+      cudaFree(p);
+      ++g_alloc_generation;
+    }
     p = nullptr;
     n = 0;
   }
   void alloc(size_t count) {
     release();
+    ++g_alloc_generation;
     if (count) {
       cudaError_t e = cudaMalloc(&p, count * sizeof(X));
       if (e != cudaSuccess) { p = nullptr; throw Err{FDE_ENOMEM, "cudaMalloc failed"}; }
@@ -228,6 +236,7 @@ struct Engine {
   virtual void set_precond_mode(int mode) = 0;
   virtual void stats(long long* dav, long long* hpsi) = 0;
   virtual void set_precond_record(int n) = 0;
+  virtual void hot_step(bool use_graph) = 0;
   virtual int nsub() const = 0;
   virtual long long grid_points() const = 0;
   virtual void shape(int sub, int* nb, int* nk) = 0;
@@ -266,7 +275,7 @@ template <typename T> struct EngineT : Engine {
   DBuf<double2> gwork, Pm, Qm;
   DBuf<C> V, HV, V2, HV2, R, Pb, HPb;
   DBuf<double2> S, Hs, L, Li, Ht, Y, Cc, tmp, jwork;
-  DBuf<double> wv, dnorm, deps, dtb;
+  DBuf<double> wv, dnorm, deps, dtb, hwork;
   DBuf<int> didx;
   DBuf<double> rho_plane, occw;
   // Pulay history and freeze-and-thaw copies
@@ -320,6 +329,7 @@ template <typename T> struct EngineT : Engine {
   }
   ~EngineT() override {
     if (pin) cudaFreeHost(pin);
+    if (step_exec) cudaGraphExecDestroy(step_exec);
   }
 
   Sub<T>& sub(int i) {
@@ -750,6 +760,49 @@ template <typename T> struct EngineT : Engine {
       for (auto& q : sp->kp) apply_h_dev(*sp, q, q.X.p, q.HX.p, sp->nb);
   }
 
+  // One pass of the hot path over the whole cell (potential build + every band's H psi),
+  // optionally replayed from a captured CUDA graph.
+  cudaGraphExec_t step_exec = nullptr;
+  unsigned long long step_gen = ~0ull;
+  long long step_kernels = 0;
+  void hot_step(bool use_graph) override {
+    ensure_vloc();
+    if (!use_graph) {
+      grid_pass(true, false, -1);
+      apply_h_all();
+      return;
+    }
+    if (!step_exec || step_gen != g_alloc_generation) {
+      grid_pass(true, false, -1);  // an eager pass sizes every buffer first
+      apply_h_all();
+      CK(cudaStreamSynchronize(st));
+      if (step_exec) {
+        cudaGraphExecDestroy(step_exec);
+        step_exec = nullptr;
+      }
+      Profiler* pr = tl_prof;
+      const long long before = pr ? pr->launches : 0;
+      const bool was_on = pr && pr->on;
+      if (pr) pr->on = false;
+      cudaGraph_t gph;
+      CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+      grid_pass(true, false, -1);
+      apply_h_all();
+      CK(cudaStreamEndCapture(st, &gph));
+      const cudaError_t ie = cudaGraphInstantiate(&step_exec, gph, 0);
+      cudaGraphDestroy(gph);
+      CK(ie);
+      step_kernels = pr ? pr->launches - before : 0;
+      if (pr) {
+        pr->on = was_on;
+        pr->launches = before;
+      }
+      step_gen = g_alloc_generation;
+    }
+    CK(cudaGraphLaunch(step_exec, st));
+    if (tl_prof) tl_prof->launches += step_kernels;
+  }
+
   // ---- orbitals -------------------------------------------------------------------------------
   void init_orbitals(int i, int k, const double* raw) override {
     REQ(raw, FDE_EINVAL, "null raw draws");
@@ -840,7 +893,8 @@ template <typename T> struct EngineT : Engine {
     launch_small_gemm(Li.p, n, 0, Hs.p, n, 0, n, n, n, tmp.p, n, st);
     launch_small_gemm(tmp.p, n, 0, Li.p, n, 1, n, n, n, Ht.p, n, st);
     launch_hermitize(Ht.p, n, st);
-    launch_jacobi_eig(Ht.p, n, wv.p, Y.p, jwork.p, st);
+    hwork.ensure(heev_work_doubles(n, nb));
+    launch_heev(Ht.p, n, nb, wv.p, Y.p, hwork.p, st);
     launch_small_gemm(Li.p, n, 1, Y.p, n, 0, n, n, n, Cc.p, n, st);
     launch_gemm_rot<T>(V.p, K, Cc.p, n, n, nb, K, V2.p, K, 1.0, 0.0, st);
     launch_gemm_rot<T>(HV.p, K, Cc.p, n, n, nb, K, HV2.p, K, 1.0, 0.0, st);
@@ -1423,13 +1477,16 @@ template <typename T> struct EngineT : Engine {
     double Eprev = 0;
     bool have_prev = false;
     const double dtol = davidson_tol(tol);
+    // Early SCF iterations need only rough eigenvectors: the eigensolver tolerance follows
+    // the density residual of the previous iteration down to dtol.
+    double dres_prev = 1.0;
     fde_energies en{};
     for (int it = 1; it <= max_scf; ++it) {
       CK(cudaMemcpyAsync(s.rho.p, rho_in.p, nr * sizeof(double), cudaMemcpyDeviceToDevice, st));
       grid_pass(true, false, I);
       for (int k = 0; k < s.nk; ++k) {
         int its = 0;
-        subspace_solve(I, k, dtol, 60, &its, precond_mode);
+        subspace_solve(I, k, std::max(dtol, std::min(1e-3, 1e-2 * dres_prev)), 60, &its, precond_mode);
         davidson_iters += its;
       }
       occupations(s);
@@ -1453,6 +1510,7 @@ template <typename T> struct EngineT : Engine {
       en.F_fde = en.E_fde - en.TS;
       en.iters = it;
       const double dres = integrate_absdiff(s.rho.p, rho_in.p);
+      dres_prev = dres;
       en.dE = have_prev ? en.F_fde - Eprev : 0.0;
       REQ(std::isfinite(en.F_fde), FDE_ENONFINITE, "non-finite energy");
       if (have_prev && fabs(en.dE) < tol && dres < dres_tol(tol)) {
@@ -1729,6 +1787,14 @@ fde_status fde_precond_add_pairs(fde_ctx* c, int sub, int k, int n, const double
                                  const double* tband) {
   return guard(c, [&]() { c->eng->precond_add_pairs(sub, k, n, r, d, tband); return FDE_OK; });
 }
+fde_status fde_hot_step(fde_ctx* c, int use_graph) {
+  return guard(c, [&]() {
+    if (use_graph && c->stream == nullptr)
+      throw fde::Err{FDE_EINVAL, "graph replay needs a non-default context stream"};
+    c->eng->hot_step(use_graph != 0);
+    return FDE_OK;
+  });
+}
 fde_status fde_precond_record(fde_ctx* c, int iterations) {
   return guard(c, [&]() { c->eng->set_precond_record(iterations); return FDE_OK; });
 }
@@ -1746,6 +1812,21 @@ fde_status fde_precond_apply(fde_ctx* c, int sub, int k, const void* d_r, void* 
 }
 fde_status fde_get_stats(fde_ctx* c, long long* davidson_iters, long long* hpsi_bands) {
   return guard(c, [&]() { c->eng->stats(davidson_iters, hpsi_bands); return FDE_OK; });
+}
+fde_status fde_dense_eigh(fde_ctx* c, int n, const double* d_A, int nvec, double* d_w, double* d_V) {
+  return guard(c, [&]() {
+    using fde::Err;
+    if (n <= 0 || n > 1024 || nvec < 0 || nvec > n || !d_A || !d_w || !d_V)
+      throw fde::Err{FDE_EINVAL, "bad eigensolver arguments"};
+    fde::DBuf<double2> a;
+    fde::DBuf<double> wk;
+    a.alloc((size_t)n * n);
+    wk.alloc(fde::heev_work_doubles(n, nvec));
+    CK(cudaMemcpyAsync(a.p, d_A, (size_t)n * n * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
+    fde::launch_heev(a.p, n, nvec, d_w, (double2*)d_V, wk.p, c->stream);
+    CK(cudaStreamSynchronize(c->stream));
+    return FDE_OK;
+  });
 }
 fde_status fde_fft3d(fde_ctx* c, void* d_data, int sign) {
   return guard(c, [&]() { c->eng->fft3d(d_data, sign); return FDE_OK; });

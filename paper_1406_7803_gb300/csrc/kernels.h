@@ -79,6 +79,10 @@ void launch_cholesky_inv(const double2* S, int n, double2* L, double2* Linv, uns
 // Hermitian eigenproblem by cyclic Jacobi: A (n x n, destroyed) -> eigenvalues w[n]
 // ascending and eigenvectors V (column j = vector j), FP64.
 void launch_jacobi_eig(double2* A, int n, double* w, double2* V, double2* work, cudaStream_t st);
+// Same result by tridiagonalisation, bisection and inverse iteration (heev.cu); only the
+// eigenvectors of the lowest nvec eigenvalues are formed (other columns of V are zero).
+size_t heev_work_doubles(int n, int nvec);
+void launch_heev(double2* A, int n, int nvec, double* w, double2* V, double* work, cudaStream_t st);
 
 // Row-wise helpers on [nb][K] blocks.
 template <typename T>

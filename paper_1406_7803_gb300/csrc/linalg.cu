@@ -211,18 +211,29 @@ k_cholesky_inv(const double2* __restrict__ S, int n, double2* __restrict__ L, do
   }
   __syncthreads();
   if (fail) return;
-  // Li = L^{-1}: column c by forward substitution, one thread per column.
-  for (int c = threadIdx.x; c < n; c += blockDim.x) {
-    for (int i = 0; i < c; ++i) Li[(size_t)i * n + c] = make_double2(0, 0);
+  // Li = L^{-1}: column c by forward substitution, one warp per column (lanes share the
+  // inner products).
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int c = threadIdx.x >> 5; c < n; c += nw) {
+    for (int i = lane; i < c; i += 32) Li[(size_t)i * n + c] = make_double2(0, 0);
     for (int i = c; i < n; ++i) {
-      double re = (i == c) ? 1.0 : 0.0, im = 0.0;
-      for (int k = c; k < i; ++k) {
+      double re = 0.0, im = 0.0;
+      for (int k = c + lane; k < i; k += 32) {
         const double2 l = L[(size_t)i * n + k], x = Li[(size_t)k * n + c];
-        re -= l.x * x.x - l.y * x.y;
-        im -= l.x * x.y + l.y * x.x;
+        re += l.x * x.x - l.y * x.y;
+        im += l.x * x.y + l.y * x.x;
       }
-      const double dd = L[(size_t)i * n + i].x;
-      Li[(size_t)i * n + c] = make_double2(re / dd, im / dd);
+      for (int o = 16; o > 0; o >>= 1) {
+        re += __shfl_xor_sync(0xffffffffu, re, o);
+        im += __shfl_xor_sync(0xffffffffu, im, o);
+      }
+      if (lane == 0) {
+        const double dd = L[(size_t)i * n + i].x;
+        Li[(size_t)i * n + c] = make_double2(((i == c) ? 1.0 : 0.0) - re, -im);
+        Li[(size_t)i * n + c].x /= dd;
+        Li[(size_t)i * n + c].y /= dd;
+      }
+      __syncwarp();
     }
   }
 }

@@ -77,6 +77,8 @@ EXPORTS = {
     "fde_apply_h_local_static": (C.c_int, [C.POINTER(CellDesc), C.POINTER(C.c_double), C.c_int, C.c_void_p,
                                            C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "fde_fft3d": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "fde_hot_step": (C.c_int, [C.c_void_p, C.c_int]),
+    "fde_dense_eigh": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "fde_set_precond": (C.c_int, [C.c_void_p, C.c_int]),
     "fde_precond_set_weights": (C.c_int, [C.c_void_p, C.c_void_p]),
     "fde_precond_get_weights": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -275,6 +277,13 @@ class Context:
 
     def profile_enable(self, on=True):
         return self._check(self.lib.fde_profile_enable(self.h, int(on)), "fde_profile_enable")
+
+    def dense_eigh(self, A, nvec, w, V):
+        return self._check(self.lib.fde_dense_eigh(self.h, int(A.shape[0]), _dptr(A), int(nvec), _dptr(w), _dptr(V)),
+                           "fde_dense_eigh")
+
+    def hot_step(self, use_graph=False):
+        return self._check(self.lib.fde_hot_step(self.h, int(bool(use_graph))), "fde_hot_step")
 
     # ---- learned preconditioner ----------------------------------------------------------
     def set_precond(self, mode):
