@@ -85,7 +85,8 @@ typedef struct {
  * Appendix: subsystem-specific projectors).  pos [natoms][3] bohr, Z [natoms]; every atom
  * carries the local potential -Z erf(|r-R|/rc)/|r-R| and nproj_per_atom Gaussian s-type
  * Kleinman-Bylander projectors of widths proj_sigma [nproj_per_atom] (bohr) coupled by
- * proj_D [nproj_per_atom][nproj_per_atom] (Ha, symmetric).  kpts [nk][3] in crystal
+ * proj_D [nproj_per_atom][nproj_per_atom] (Ha, symmetric; nproj_per_atom <= 8, else
+ * FDE_EUNSUPPORTED).  kpts [nk][3] in crystal
  * coordinates with weights wk [nk] summing to 1.  smearing_ha > 0: Fermi-Dirac occupations;
  * 0: integer occupations (then nk must be 1 and nelec/2 an integer <= nbands).
  * All arrays are host memory and are copied. */
@@ -182,6 +183,10 @@ fde_status fde_apply_h_all(fde_ctx* ctx);
  * reallocated device memory since); the context stream must then not be the legacy default
  * stream (FDE_EINVAL).  Asynchronous. */
 fde_status fde_hot_step(fde_ctx* ctx, int use_graph);
+
+/* Copy the stored H psi of (sub, k) (written by fde_apply_h_all / fde_hot_step and by the
+ * eigensolver) to a caller device buffer, complex double [nbands][npw]. */
+fde_status fde_get_hpsi(fde_ctx* ctx, int sub, int k, double* d_hpsi);
 
 /* Initial orbitals of (sub, k) from raw complex draws h_raw [nbands][npw][2] (host):
  * c_G = raw_G / (1 + |k+G|^2/2), then orthonormalised on the device. */

@@ -7,6 +7,7 @@
 // Only scalars (eigenvalues, norms, energies, DIIS coefficients) travel to the host.
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -43,6 +44,16 @@ struct Err {
 // Every device (re)allocation or release bumps this counter; a captured CUDA graph whose
 // counter value is stale may reference freed buffers and is captured again.
 static unsigned long long g_alloc_generation = 0;
+
+// FDE_TRACE=1 in the environment prints one line per SCF iteration to stderr.
+static int trace_level() {
+  static int lv = -1;
+  if (lv < 0) {
+    const char* e = getenv("FDE_TRACE");
+    lv = e ? atoi(e) : 0;
+  }
+  return lv;
+}
 
 template <typename X> struct DBuf {
   X* p = nullptr;
@@ -193,7 +204,7 @@ template <typename T> struct Sub {
   double rc = 0, nelec = 0, smearing = 0;
   std::vector<double> pos, Z, sigma, D, kpts, wk;
   std::vector<KP<T>> kp;
-  DBuf<double2> Dfull;
+  KbBlock Dblk{};  // per-atom projector coupling
   DBuf<double> rho, veff;
   DBuf<T> vplane;
   double entropy = 0, mu = 0;
@@ -237,6 +248,7 @@ struct Engine {
   virtual void stats(long long* dav, long long* hpsi) = 0;
   virtual void set_precond_record(int n) = 0;
   virtual void hot_step(bool use_graph) = 0;
+  virtual void get_hpsi(int sub, int k, double* d_hpsi) = 0;
   virtual int nsub() const = 0;
   virtual long long grid_points() const = 0;
   virtual void shape(int sub, int* nb, int* nk) = 0;
@@ -266,9 +278,10 @@ template <typename T> struct EngineT : Engine {
   // Work grids of the embedding-potential build.  Its transforms run in FP64 in both
   // precisions: FP32 gradients of the density are noise where the density is small (the
   // vacuum above the slab), and the GGA potentials amplify that noise by rho^{-4/3}.
-  DBuf<double2> cb[5];
+  DBuf<double2> cb[2];                // packed transform / potential; rho_tot(G)
+  std::vector<DBuf<double2>> packs;   // per subsystem pair: packed gradient grids
   DBuf<double2> cvl;
-  DBuf<double> rho_tot, vcommon, vpart, vtmp, partial, scal;
+  DBuf<double> rho_tot, vpart, htot[3], partial, scal;
   DBuf<unsigned> status;
   // band work
   DBuf<C> scratch;
@@ -318,9 +331,8 @@ template <typename T> struct EngineT : Engine {
     make_plans(plans64, grid, st);
     for (auto& b : cb) b.alloc(nr);
     rho_tot.alloc(nr);
-    vcommon.alloc(nr);
     vpart.alloc(nr);
-    vtmp.alloc(nr);
+    for (auto& b : htot) b.alloc(nr);
     partial.alloc(64 * (size_t)grid_red_blocks());
     scal.alloc(128);
     status.alloc(1);
@@ -475,6 +487,7 @@ template <typename T> struct EngineT : Engine {
     REQ(d->kpts && d->wk, FDE_EINVAL, "null k-point arrays");
     REQ(d->nproj_per_atom >= 0 && (d->nproj_per_atom == 0 || (d->proj_sigma && d->proj_D)), FDE_EINVAL,
         "null projector arrays");
+    REQ(d->nproj_per_atom <= 8, FDE_EUNSUPPORTED, "at most 8 projectors per atom");
     if (d->smearing_ha <= 0) {
       const double no = d->nelec / 2.0;
       REQ(d->nk == 1 && fabs(no - round(no)) < 1e-12 && round(no) <= d->nbands && no >= 0, FDE_EINVAL,
@@ -510,14 +523,8 @@ template <typename T> struct EngineT : Engine {
       q.occ.assign(s->nb, 0.0);
     }
     if (s->nproj) {
-      std::vector<double2> Df((size_t)s->nproj * s->nproj, make_double2(0, 0));
-      for (int a = 0; a < s->natoms; ++a)
-        for (int i = 0; i < s->nproj_atom; ++i)
-          for (int j = 0; j < s->nproj_atom; ++j)
-            Df[(size_t)(a * s->nproj_atom + i) * s->nproj + a * s->nproj_atom + j] =
-                make_double2(s->D[i * s->nproj_atom + j], 0.0);
-      s->Dfull.alloc(Df.size());
-      CK(cudaMemcpy(s->Dfull.p, Df.data(), Df.size() * sizeof(double2), cudaMemcpyHostToDevice));
+      s->Dblk.np = s->nproj_atom;
+      for (int i = 0; i < s->nproj_atom * s->nproj_atom; ++i) s->Dblk.d[i] = s->D[i];
     }
     s->rho.alloc(nr);
     s->veff.alloc(nr);
@@ -591,74 +598,112 @@ template <typename T> struct EngineT : Engine {
   bool gga_xc() const { return func.xc == FDE_XC_PBE; }
   bool gga_kin() const { return func.kedf != FDE_KEDF_TF; }
 
-  // Gradient of the density held (forward-transformed, unscaled) in cb[0] into cb[2..4] (real).
-  void gradient_from_cb0() {
-    grid_gradient_g<double>(cb[0].p, cb[2].p, cb[3].p, cb[4].p, g, cell, st);
-    for (int c = 2; c < 5; ++c) launch_fft3d<double>(cb[c].p, g, plans64.fp, +1, st);
-  }
-  // Divergence of h held (real) in cb[2..4]; result (real part) in cb[2].
-  void divergence_cb234() {
-    for (int c = 2; c < 5; ++c) launch_fft3d<double>(cb[c].p, g, plans64.fp, -1, st);
-    grid_divergence_g<double>(cb[2].p, cb[3].p, cb[4].p, g, cell, st);
-    launch_fft3d<double>(cb[2].p, g, plans64.fp, +1, st);
+  // Packed gradient grids of subsystem pair q (three complex grids).
+  double2* pack(int q, int c) {
+    const size_t need = (size_t)3 * (q + 1);
+    if (packs.size() < need) packs.resize(need);
+    DBuf<double2>& b = packs[(size_t)3 * q + c];
+    if (!b.p) b.alloc(nr);
+    return b.p;
   }
 
   // Builds the potentials (want_pot) of the subsystems in `which` (-1 all) and/or the grid
   // energy terms (want_e); slots of scal: 0 E_H, 1/2 E_xc/T_tot, 3 E_loc, then per
   // subsystem 4+3I: E_H[rho_I], 5+3I: E_xc[rho_I], 6+3I: T[rho_I].
+  //
+  // v_eff^I = v_loc + v_H[rho] + v_xc[rho] + v~_kin[rho] - v~_kin[rho_I] (Eq. 4 with the
+  // kinetic potential of Eq. 7): with f the pointwise energy densities, a functional's
+  // potential is df/drho - div(df/dgrad rho), so
+  //   v_eff^I = v_loc + v_H + (w_tot - w_I) - div(h_tot - h_I)
+  // where w and h are the two derivatives at rho (xc + kinetic) and at rho_I (kinetic).
+  // Subsystems are taken in pairs (a, b), each pair's real fields packed into one complex
+  // transform: rho_a + i rho_b forward, the gradients as (x + i y of a), (x + i y of b),
+  // (z of a + i z of b) backward, the divergence arguments the same way forward, and
+  // (v_a + i v_b) backward: 8 transforms per pair.
   EnergyParts grid_pass(bool want_pot, bool want_e, int which) {
     ensure_vloc();
     REQ(4 + 3 * subs.size() <= 120, FDE_EUNSUPPORTED, "too many subsystems for one energy pass");
-    const int nrb = grid_red_blocks();
+    const int nsb = (int)subs.size();
+    const int npairs = (nsb + 1) / 2;
+    REQ(npairs <= kMaxPairs, FDE_EUNSUPPORTED, "at most 16 subsystems");
+    const size_t nrb = (size_t)grid_red_blocks();
     const double dv = omega / (double)nr;
-    sum_densities();
-    grid_real_to_c<double>(rho_tot.p, cb[0].p, nr, st);
-    launch_fft3d<double>(cb[0].p, g, plans64.fp, -1, st);
-    grid_poisson<double>(cb[0].p, want_pot ? cb[1].p : nullptr, g, cell, partial.p, st);
-    grid_finalize(partial.p, 1, 0.5 * omega, scal.p + 0, st);
-    if (want_pot) launch_fft3d<double>(cb[1].p, g, plans64.fp, +1, st);
     const bool grad = gga_xc() || gga_kin();
-    if (grad) gradient_from_cb0();
-    grid_pointwise<double>(rho_tot.p, grad ? cb[2].p : nullptr, grad ? cb[3].p : nullptr, grad ? cb[4].p : nullptr, nr,
-                      func.xc, 1, func.kedf, func.rho_cut, want_pot ? vpart.p : nullptr, partial.p, st);
+    double2* C = cb[0].p;
+    double2* RT = cb[1].p;
+    sum_densities();
+    // 1. densities to reciprocal space, total density, Hartree sums and gradients
+    GradPacks gp{};
+    gp.npairs = grad ? npairs : 0;
+    for (int q = 0; q < npairs; ++q) {
+      const int ia = 2 * q, ib = 2 * q + 1;
+      const bool hb = ib < nsb;
+      grid_pack2(subs[ia]->rho.p, hb ? subs[ib]->rho.p : nullptr, C, nr, st);
+      launch_fft3d<double>(C, g, plans64.fp, -1, st);
+      double2* Pa = grad ? pack(q, 0) : nullptr;
+      double2* Pb = (grad && hb) ? pack(q, 1) : nullptr;
+      double2* Pz = grad ? pack(q, 2) : nullptr;
+      grid_unpack_density(C, hb ? 1 : 0, RT, q > 0 ? 1 : 0, Pa, Pb, Pz, g, cell, want_e ? partial.p : nullptr, st);
+      if (want_e) {
+        grid_finalize(partial.p, 1, 0.5 * omega, scal.p + 4 + 3 * ia, st);
+        if (hb) grid_finalize(partial.p + nrb, 1, 0.5 * omega, scal.p + 4 + 3 * ib, st);
+      }
+      if (grad) {
+        launch_fft3d<double>(Pa, g, plans64.fp, +1, st);
+        if (hb) launch_fft3d<double>(Pb, g, plans64.fp, +1, st);
+        launch_fft3d<double>(Pz, g, plans64.fp, +1, st);
+        gp.a[q] = Pa;
+        gp.b[q] = Pb;
+        gp.z[q] = Pz;
+        gp.has_b[q] = hb ? 1 : 0;
+      }
+    }
+    // 2. functionals of the total density
+    grid_pw_total(rho_tot.p, gp, func.xc, func.kedf, func.rho_cut, want_pot ? vpart.p : nullptr,
+                  (want_pot && grad) ? htot[0].p : nullptr, htot[1].p, htot[2].p, nr, partial.p, st);
     grid_finalize(partial.p, 2, dv, scal.p + 1, st);
     grid_dot_partial(vloc.p, rho_tot.p, nr, 0, partial.p, st);
     grid_finalize(partial.p, 1, dv, scal.p + 3, st);
-    if (want_pot) {
-      grid_combine<double>(vloc.p, vpart.p, nullptr, cb[1].p, 1.0, vcommon.p, nr, st);
+    if (want_e) {
+      grid_assemble_pair(RT, nullptr, nullptr, nullptr, 0, nullptr, g, cell, partial.p, st);
+      grid_finalize(partial.p, 1, 0.5 * omega, scal.p + 0, st);
+    }
+    // 3. per pair: subsystem functionals, divergences, reciprocal-space part, potentials
+    for (int q = 0; q < npairs; ++q) {
+      const int ia = 2 * q, ib = 2 * q + 1;
+      const bool hb = ib < nsb;
+      const bool pa = want_pot && (which < 0 || which == ia);
+      const bool pb = hb && want_pot && (which < 0 || which == ib);
+      if (!pa && !pb && !want_e) continue;
+      Sub<T>& A = *subs[ia];
+      Sub<T>* B = hb ? subs[ib].get() : nullptr;
+      double2* Pa = grad ? pack(q, 0) : nullptr;
+      double2* Pb = (grad && hb) ? pack(q, 1) : nullptr;
+      double2* Pz = grad ? pack(q, 2) : nullptr;
+      const bool pot = pa || pb;
+      grid_pw_pair(A.rho.p, B ? B->rho.p : nullptr, Pa, Pb, Pz, htot[0].p, htot[1].p, htot[2].p,
+                   want_pot ? vpart.p : nullptr, want_e ? func.xc : -1, func.kedf, func.rho_cut, pa ? A.veff.p : nullptr,
+                   pb ? B->veff.p : nullptr, (pot && grad) ? 1 : 0, nr, partial.p, st);
+      grid_finalize(partial.p, 2, dv, scal.p + 5 + 3 * ia, st);
+      if (hb) grid_finalize(partial.p + 2 * nrb, 2, dv, scal.p + 5 + 3 * ib, st);
+      if (!pot) continue;
       if (grad) {
-        divergence_cb234();
-        grid_combine<double>(vcommon.p, nullptr, nullptr, cb[2].p, -1.0, vcommon.p, nr, st);
+        launch_fft3d<double>(Pa, g, plans64.fp, -1, st);
+        if (hb) launch_fft3d<double>(Pb, g, plans64.fp, -1, st);
+        launch_fft3d<double>(Pz, g, plans64.fp, -1, st);
+      }
+      grid_assemble_pair(RT, Pa, Pb, Pz, hb ? 1 : 0, C, g, cell, nullptr, st);
+      launch_fft3d<double>(C, g, plans64.fp, +1, st);
+      grid_finish_pair(C, vloc.p, pa ? A.veff.p : nullptr, pb ? B->veff.p : nullptr, nr, st);
+      if (pa) {
+        grid_nonfinite(A.veff.p, nr, status.p, st);
+        to_plane(A);
+      }
+      if (pb) {
+        grid_nonfinite(B->veff.p, nr, status.p, st);
+        to_plane(*B);
       }
     }
-    for (size_t I = 0; I < subs.size(); ++I) {
-      const bool pot_I = want_pot && (which < 0 || which == (int)I);
-      if (!pot_I && !want_e) continue;
-      Sub<T>& s = *subs[I];
-      grid_real_to_c<double>(s.rho.p, cb[0].p, nr, st);
-      launch_fft3d<double>(cb[0].p, g, plans64.fp, -1, st);
-      if (want_e) {
-        grid_poisson<double>(cb[0].p, nullptr, g, cell, partial.p, st);
-        grid_finalize(partial.p, 1, 0.5 * omega, scal.p + 4 + 3 * I, st);
-      }
-      const bool gI = gga_kin() || (want_e && gga_xc());
-      if (gI) gradient_from_cb0();
-      grid_pointwise<double>(s.rho.p, gI ? cb[2].p : nullptr, gI ? cb[3].p : nullptr, gI ? cb[4].p : nullptr, nr,
-                        want_e ? func.xc : -1, 0, func.kedf, func.rho_cut, pot_I ? vpart.p : nullptr, partial.p, st);
-      grid_finalize(partial.p, 2, dv, scal.p + 5 + 3 * I, st);
-      if (pot_I) {
-        // v_eff^I = v_common - v~_kin[rho_I] = v_common - vpart_I + div h_I
-        CK(cudaMemcpyAsync(s.veff.p, vcommon.p, nr * sizeof(double), cudaMemcpyDeviceToDevice, st));
-        grid_axpy(s.veff.p, vpart.p, -1.0, nr, st);
-        if (gga_kin()) {
-          divergence_cb234();
-          grid_combine<double>(s.veff.p, nullptr, nullptr, cb[2].p, 1.0, s.veff.p, nr, st);
-        }
-        grid_nonfinite(s.veff.p, nr, status.p, st);
-        to_plane(s);
-      }
-    }
-    (void)nrb;
     EnergyParts ep;
     if (want_e) {
       std::vector<double> h(4 + 3 * subs.size());
@@ -712,12 +757,16 @@ template <typename T> struct EngineT : Engine {
     hpsi_bands += nb;
     scratch.ensure((size_t)nb * g.n3 * q.sp.ncol);
     launch_hpsi_local<T>(psi, q.npw, hpsi, q.npw, nb, q.kin_d.p, s.vplane.p, scratch.p, q.sp, g, plans.fp, st);
+    apply_nl(s, q, psi, hpsi, nb);
+  }
+  // hpsi += sum_{a in I} beta D <beta|psi> (projectors of the subsystem's own atoms)
+  void apply_nl(Sub<T>& s, KP<T>& q, const C* psi, C* hpsi, int nb) {
     if (s.nproj) {
       gwork.ensure(gemm_hn_work(s.nproj, nb, q.npw));
       Pm.ensure((size_t)s.nproj * nb);
       Qm.ensure((size_t)s.nproj * nb);
       launch_gemm_hn<T>(q.beta.p, q.npw, psi, q.npw, s.nproj, nb, q.npw, Pm.p, nb, gwork.p, st);
-      launch_gemm_rot<double>(Pm.p, nb, s.Dfull.p, s.nproj, s.nproj, s.nproj, nb, Qm.p, nb, 1.0, 0.0, st);
+      launch_kb_couple(Pm.p, s.Dblk, s.natoms, nb, Qm.p, st);
       launch_gemm_rot<T>(q.beta.p, q.npw, Qm.p, nb, s.nproj, nb, q.npw, hpsi, q.npw, 1.0, 1.0, st);
     }
   }
@@ -755,9 +804,30 @@ template <typename T> struct EngineT : Engine {
   void convert_in(const double2* a, C* b, size_t n);
   void convert_out(const C* a, double2* b, size_t n);
 
+  // H psi of every band of every (subsystem, k): the local part of all of them in one
+  // batched launch per phase, then each subsystem's own projectors.
   void apply_h_all() override {
+    size_t total = 0;
     for (auto& sp : subs)
-      for (auto& q : sp->kp) apply_h_dev(*sp, q, q.X.p, q.HX.p, sp->nb);
+      for (auto& q : sp->kp) total += (size_t)sp->nb * g.n3 * q.sp.ncol;
+    scratch.ensure(total);
+    std::vector<HpsiItemDesc<T>> items;
+    size_t off = 0;
+    for (auto& sp : subs)
+      for (auto& q : sp->kp) {
+        items.push_back(HpsiItemDesc<T>{q.sp, q.X.p, q.HX.p, q.kin_d.p, sp->vplane.p, scratch.p + off, q.npw, sp->nb});
+        off += (size_t)sp->nb * g.n3 * q.sp.ncol;
+      }
+    if (!launch_hpsi_batch_ct<T>(items.data(), (int)items.size(), g, plans.fp, st)) {
+      for (auto& sp : subs)
+        for (auto& q : sp->kp) apply_h_dev(*sp, q, q.X.p, q.HX.p, sp->nb);
+      return;
+    }
+    for (auto& sp : subs)
+      for (auto& q : sp->kp) {
+        hpsi_bands += sp->nb;
+        apply_nl(*sp, q, q.X.p, q.HX.p, sp->nb);
+      }
   }
 
   // One pass of the hot path over the whole cell (potential build + every band's H psi),
@@ -869,6 +939,13 @@ template <typename T> struct EngineT : Engine {
     convert_in((const double2*)d_psi, q.X.p, (size_t)s.nb * q.npw);
     q.have_orbitals = true;
     q.have_eig = false;
+  }
+  void get_hpsi(int i, int k, double* d_hpsi) override {
+    REQ(d_hpsi, FDE_EINVAL, "null output");
+    Sub<T>& s = sub(i);
+    KP<T>& q = kpt(i, k);
+    convert_out(q.HX.p, (double2*)d_hpsi, (size_t)s.nb * q.npw);
+    CK(cudaStreamSynchronize(st));
   }
   void get_orbitals(int i, int k, double* d_psi, double* eig, double* occ) override {
     Sub<T>& s = sub(i);
@@ -1513,6 +1590,9 @@ template <typename T> struct EngineT : Engine {
       dres_prev = dres;
       en.dE = have_prev ? en.F_fde - Eprev : 0.0;
       REQ(std::isfinite(en.F_fde), FDE_ENONFINITE, "non-finite energy");
+      if (trace_level() > 0)
+        fprintf(stderr, "[fde] scf sub %d it %d F %.12f dE %.3e drho %.3e eig_iters %lld\n", I, it, en.F_fde, en.dE,
+                dres, davidson_iters);
       if (have_prev && fabs(en.dE) < tol && dres < dres_tol(tol)) {
         if (out) *out = en;
         return FDE_OK;
@@ -1786,6 +1866,9 @@ fde_status fde_precond_harvest(fde_ctx* c, int sub, int k, const double* raw, in
 fde_status fde_precond_add_pairs(fde_ctx* c, int sub, int k, int n, const double* r, const double* d,
                                  const double* tband) {
   return guard(c, [&]() { c->eng->precond_add_pairs(sub, k, n, r, d, tband); return FDE_OK; });
+}
+fde_status fde_get_hpsi(fde_ctx* c, int sub, int k, double* d_hpsi) {
+  return guard(c, [&]() { c->eng->get_hpsi(sub, k, d_hpsi); return FDE_OK; });
 }
 fde_status fde_hot_step(fde_ctx* c, int use_graph) {
   return guard(c, [&]() {

@@ -416,6 +416,213 @@ __global__ void k_nonfinite(const double* __restrict__ a, long long n, unsigned*
     if (!isfinite(a[i])) { atomicOr(status, ST_NONFINITE); return; }
 }
 
+// ---- packed pairs of real fields ------------------------------------------------------------
+// One complex transform carries two real fields a and b: with C = FFT(a + i b),
+// a(G) = (C(G) + conj C(-G)) / 2 and b(G) = (C(G) - conj C(-G)) / (2 i).  The potential build
+// packs the subsystem densities, gradient components and divergence arguments in pairs, so
+// that it needs half the FP64 transforms while computing the same quantities.
+__device__ __forceinline__ long long neg_index(long long idx, const GridDims& g) {
+  const int i3 = (int)(idx % g.n3);
+  const long long r = idx / g.n3;
+  const int i2 = (int)(r % g.n2), i1 = (int)(r / g.n2);
+  const int j1 = i1 ? g.n1 - i1 : 0, j2 = i2 ? g.n2 - i2 : 0, j3 = i3 ? g.n3 - i3 : 0;
+  return ((long long)j1 * g.n2 + j2) * g.n3 + j3;
+}
+__device__ __forceinline__ void unpack2(double2 c, double2 cn, double2* a, double2* b) {
+  *a = make_double2(0.5 * (c.x + cn.x), 0.5 * (c.y - cn.y));
+  *b = make_double2(0.5 * (c.y + cn.y), -0.5 * (c.x - cn.x));
+}
+// u + i v for complex u, v
+__device__ __forceinline__ double2 pack2(double2 u, double2 v) { return make_double2(u.x - v.y, u.y + v.x); }
+// i g f
+__device__ __forceinline__ double2 ig_mul(double gc, double2 f) { return make_double2(-gc * f.y, gc * f.x); }
+
+__global__ void k_pack2(const double* __restrict__ a, const double* __restrict__ b, double2* __restrict__ c,
+                        long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    c[i] = make_double2(a[i], b ? b[i] : 0.0);
+}
+
+// From C = FFT(rho_a + i rho_b) (unscaled): RT (+)= rho_a(G) + rho_b(G); Hartree sums
+// sum 4 pi |rho_x(G)|^2 / G^2 of both into partial rows 0 and 1; packed gradient transforms
+// Pa = iGx a + i iGy a, Pb = iGx b + i iGy b, Pz = iGz a + i iGz b (Nyquist planes zero).
+// Without b, C is rho_a's transform itself, Pb is not written and Pz carries iGz a alone.
+__global__ void k_unpack_density(const double2* __restrict__ C, int has_b, double2* __restrict__ RT, int accumulate,
+                                 double2* __restrict__ Pa, double2* __restrict__ Pb, double2* __restrict__ Pz,
+                                 GridDims g, CellDev c, double inv_nr, double* partial) {
+  const long long nr = (long long)g.n1 * g.n2 * g.n3;
+  double ea = 0, eb = 0;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < nr; idx += (long long)gridDim.x * blockDim.x) {
+    const Gpt p = gvec(idx, g, c);
+    const double2 cv = C[idx];
+    double2 a, b;
+    if (has_b) {
+      unpack2(cv, C[neg_index(idx, g)], &a, &b);
+    } else {
+      a = cv;
+      b = make_double2(0, 0);
+    }
+    a.x *= inv_nr; a.y *= inv_nr;
+    b.x *= inv_nr; b.y *= inv_nr;
+    double2 t = make_double2(a.x + b.x, a.y + b.y);
+    if (accumulate) t = make_double2(RT[idx].x + t.x, RT[idx].y + t.y);
+    RT[idx] = t;
+    if (p.g2 > 0 && !p.nyq) {
+      const double f = 4.0 * M_PI / p.g2;
+      ea += f * (a.x * a.x + a.y * a.y);
+      eb += f * (b.x * b.x + b.y * b.y);
+    }
+    if (Pa) {
+      if (p.nyq) {
+        Pa[idx] = Pz[idx] = make_double2(0, 0);
+        if (has_b) Pb[idx] = make_double2(0, 0);
+      } else {
+        Pa[idx] = pack2(ig_mul(p.gx, a), ig_mul(p.gy, a));
+        if (has_b) Pb[idx] = pack2(ig_mul(p.gx, b), ig_mul(p.gy, b));
+        Pz[idx] = pack2(ig_mul(p.gz, a), ig_mul(p.gz, b));
+      }
+    }
+  }
+  if (partial) {
+    block_sum_store(ea, partial + blockIdx.x);
+    block_sum_store(eb, partial + kRedBlocks + blockIdx.x);
+  }
+}
+
+// Functional of the total density rho_tot = sum_I rho_I whose gradient is the sum of the
+// subsystem gradients held in the packed grids of each pair.  Writes vpart (d f / d rho) and
+// h = (d f / d grad rho) in hx, hy, hz (real; when there are gradients); energy partial rows
+// 0 (xc) and 1 (kinetic).
+__global__ void k_pw_total(const double* __restrict__ rho, GradPacks gp, int xc_mode, int kedf, double rho_cut,
+                           double* __restrict__ vpart, double* __restrict__ hx, double* __restrict__ hy,
+                           double* __restrict__ hz, long long nr, double* partial) {
+  double ax = 0, ak = 0;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < nr; idx += (long long)gridDim.x * blockDim.x) {
+    double x = 0, y = 0, z = 0;
+    for (int q = 0; q < gp.npairs; ++q) {
+      const double2 pa = gp.a[q][idx], pz = gp.z[q][idx];
+      x += pa.x;
+      y += pa.y;
+      z += pz.x;
+      if (gp.has_b[q]) {
+        const double2 pb = gp.b[q][idx];
+        x += pb.x;
+        y += pb.y;
+        z += pz.y;
+      }
+    }
+    double v, h, ex, ek;
+    point_functional<double>(rho[idx], x, y, z, xc_mode, 1, kedf, rho_cut, &v, &h, &ex, &ek);
+    if (vpart) vpart[idx] = v;
+    if (hx) {
+      hx[idx] = h * x;
+      hy[idx] = h * y;
+      hz[idx] = h * z;
+    }
+    ax += ex;
+    ak += ek;
+  }
+  block_sum_store(ax, partial + blockIdx.x);
+  block_sum_store(ak, partial + kRedBlocks + blockIdx.x);
+}
+
+// The kinetic functional (and, for energies, the xc functional) of the two densities of a
+// pair: w_x = vpart_tot - d f_kin / d rho_x (the pointwise part of v~_kin[rho] - v~_kin[rho_x]
+// with the xc part of the total), and, in place of the packed gradients, the packed
+// divergence arguments d_x = h_tot - h_x.  Energy partial rows 0/1 (xc/kin of a), 2/3 (b).
+__global__ void k_pw_pair(const double* __restrict__ ra, const double* __restrict__ rb, double2* Pa, double2* Pb,
+                          double2* Pz, const double* __restrict__ hx, const double* __restrict__ hy,
+                          const double* __restrict__ hz, const double* __restrict__ vtot, int xc_mode, int kedf,
+                          double rho_cut, double* __restrict__ wa, double* __restrict__ wb, int write_d, long long nr,
+                          double* partial) {
+  double xa = 0, ka = 0, xb = 0, kb = 0;
+  const bool has_b = rb != nullptr;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < nr; idx += (long long)gridDim.x * blockDim.x) {
+    double2 pa = make_double2(0, 0), pb = make_double2(0, 0), pz = make_double2(0, 0);
+    if (Pa) {
+      pa = Pa[idx];
+      pz = Pz[idx];
+      if (has_b) pb = Pb[idx];
+    }
+    double va, ha, ex, ek;
+    point_functional<double>(ra[idx], pa.x, pa.y, pz.x, xc_mode, 0, kedf, rho_cut, &va, &ha, &ex, &ek);
+    xa += ex;
+    ka += ek;
+    double vb = 0, hb = 0;
+    if (has_b) {
+      point_functional<double>(rb[idx], pb.x, pb.y, pz.y, xc_mode, 0, kedf, rho_cut, &vb, &hb, &ex, &ek);
+      xb += ex;
+      kb += ek;
+    }
+    const double vt = vtot ? vtot[idx] : 0.0;
+    if (wa) wa[idx] = vt - va;
+    if (wb) wb[idx] = vt - vb;
+    if (write_d) {
+      const double tx = hx[idx], ty = hy[idx], tz = hz[idx];
+      Pa[idx] = make_double2(tx - ha * pa.x, ty - ha * pa.y);
+      if (has_b) Pb[idx] = make_double2(tx - hb * pb.x, ty - hb * pb.y);
+      Pz[idx] = make_double2(tz - ha * pz.x, has_b ? tz - hb * pz.y : 0.0);
+    }
+  }
+  block_sum_store(xa, partial + blockIdx.x);
+  block_sum_store(ka, partial + kRedBlocks + blockIdx.x);
+  block_sum_store(xb, partial + 2 * kRedBlocks + blockIdx.x);
+  block_sum_store(kb, partial + 3 * kRedBlocks + blockIdx.x);
+}
+
+// Reciprocal-space part of the potentials of a pair: F = Va + i Vb with
+// Vx(G) = v_H(G) - i G . d_x(G), v_H = 4 pi RT / G^2 (RT = rho_tot(G), scaled), the d_x
+// unpacked from the forward transforms Da (x, y of a), Db (x, y of b), Dz (z of a and b),
+// unscaled; without gradients Va = Vb = v_H.  Hartree sum of rho_tot into partial row 0.
+__global__ void k_assemble_pair(const double2* __restrict__ RT, const double2* __restrict__ Da,
+                                const double2* __restrict__ Db, const double2* __restrict__ Dz, int has_b,
+                                double2* __restrict__ F, GridDims g, CellDev c, double inv_nr, double* partial) {
+  const long long nr = (long long)g.n1 * g.n2 * g.n3;
+  double eh = 0;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < nr; idx += (long long)gridDim.x * blockDim.x) {
+    const Gpt p = gvec(idx, g, c);
+    double2 vh = make_double2(0, 0);
+    if (p.g2 > 0 && !p.nyq) {
+      const double f = 4.0 * M_PI / p.g2;
+      const double2 r = RT[idx];
+      vh = make_double2(f * r.x, f * r.y);
+      eh += f * (r.x * r.x + r.y * r.y);
+    }
+    double2 va = vh, vb = vh;
+    if (Da && !p.nyq) {
+      const long long jn = neg_index(idx, g);
+      double2 ax, ay, az, bx = make_double2(0, 0), by = make_double2(0, 0), bz = make_double2(0, 0);
+      unpack2(Da[idx], Da[jn], &ax, &ay);
+      if (has_b) {
+        unpack2(Db[idx], Db[jn], &bx, &by);
+        unpack2(Dz[idx], Dz[jn], &az, &bz);
+      } else {
+        const double2 t = Dz[idx], tn = Dz[jn];
+        az = make_double2(0.5 * (t.x + tn.x), 0.5 * (t.y - tn.y));
+      }
+      // i G . d / N_r
+      const double dar = p.gx * ax.x + p.gy * ay.x + p.gz * az.x, dai = p.gx * ax.y + p.gy * ay.y + p.gz * az.y;
+      const double dbr = p.gx * bx.x + p.gy * by.x + p.gz * bz.x, dbi = p.gx * bx.y + p.gy * by.y + p.gz * bz.y;
+      va = make_double2(vh.x + dai * inv_nr, vh.y - dar * inv_nr);
+      vb = make_double2(vh.x + dbi * inv_nr, vh.y - dbr * inv_nr);
+    }
+    if (F) F[idx] = has_b ? pack2(va, vb) : va;
+  }
+  if (partial) block_sum_store(eh, partial + blockIdx.x);
+}
+
+// veff_x = vloc + Re/Im F (inverse-transformed reciprocal part) + w_x for the pair's
+// subsystems (either output may be NULL).
+__global__ void k_finish_pair(const double2* __restrict__ F, const double* __restrict__ vloc, double* va,
+                              double* vb, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double2 f = F[i];
+    const double vl = vloc[i];
+    if (va) va[i] = vl + f.x + va[i];
+    if (vb) vb[i] = vl + f.y + vb[i];
+  }
+}
+
 // ---- launch wrappers ------------------------------------------------------------------------
 static int gs(long long n) {
   long long b = (n + 255) / 256;
@@ -501,6 +708,38 @@ void grid_axpy(double* a, const double* b, double alpha, long long n, cudaStream
 void grid_nonfinite(const double* a, long long n, unsigned* status, cudaStream_t st) {
   count_launches(1);
   k_nonfinite<<<gs(n), 256, 0, st>>>(a, n, status);
+}
+void grid_pack2(const double* a, const double* b, double2* c, long long n, cudaStream_t st) {
+  count_launches(1);
+  k_pack2<<<gs(n), 256, 0, st>>>(a, b, c, n);
+}
+void grid_unpack_density(const double2* C, int has_b, double2* RT, int accumulate, double2* Pa, double2* Pb,
+                         double2* Pz, const GridDims& g, const CellDev& c, double* partial, cudaStream_t st) {
+  count_launches(1);
+  k_unpack_density<<<kRedBlocks, kRedThreads, 0, st>>>(C, has_b, RT, accumulate, Pa, Pb, Pz, g, c,
+                                                       1.0 / ((double)g.n1 * g.n2 * g.n3), partial);
+}
+void grid_pw_total(const double* rho, const GradPacks& gp, int xc_mode, int kedf, double rho_cut, double* vpart,
+                   double* hx, double* hy, double* hz, long long nr, double* partial, cudaStream_t st) {
+  count_launches(1);
+  k_pw_total<<<kRedBlocks, kRedThreads, 0, st>>>(rho, gp, xc_mode, kedf, rho_cut, vpart, hx, hy, hz, nr, partial);
+}
+void grid_pw_pair(const double* ra, const double* rb, double2* Pa, double2* Pb, double2* Pz, const double* hx,
+                  const double* hy, const double* hz, const double* vtot, int xc_mode, int kedf, double rho_cut,
+                  double* wa, double* wb, int write_d, long long nr, double* partial, cudaStream_t st) {
+  count_launches(1);
+  k_pw_pair<<<kRedBlocks, kRedThreads, 0, st>>>(ra, rb, Pa, Pb, Pz, hx, hy, hz, vtot, xc_mode, kedf, rho_cut, wa, wb,
+                                                write_d, nr, partial);
+}
+void grid_assemble_pair(const double2* RT, const double2* Da, const double2* Db, const double2* Dz, int has_b,
+                        double2* F, const GridDims& g, const CellDev& c, double* partial, cudaStream_t st) {
+  count_launches(1);
+  k_assemble_pair<<<kRedBlocks, kRedThreads, 0, st>>>(RT, Da, Db, Dz, has_b, F, g, c,
+                                                      1.0 / ((double)g.n1 * g.n2 * g.n3), partial);
+}
+void grid_finish_pair(const double2* F, const double* vloc, double* va, double* vb, long long n, cudaStream_t st) {
+  count_launches(1);
+  k_finish_pair<<<gs(n), 256, 0, st>>>(F, vloc, va, vb, n);
 }
 int grid_red_blocks() { return kRedBlocks; }
 

@@ -36,4 +36,25 @@ void grid_lincomb(const double* const* ins, const double* const* res, const doub
 void grid_axpy(double* a, const double* b, double alpha, long long n, cudaStream_t st);
 void grid_nonfinite(const double* a, long long n, unsigned* status, cudaStream_t st);
 
+// ---- packed pairs of real fields (two real grids in one complex transform) ----
+constexpr int kMaxPairs = 8;
+struct GradPacks {  // real-space gradients of the subsystem densities, pairwise packed
+  const double2* a[kMaxPairs];  // d/dx + i d/dy of the first density of pair q
+  const double2* b[kMaxPairs];  // the same for the second density (when has_b)
+  const double2* z[kMaxPairs];  // d/dz of the first + i d/dz of the second
+  int has_b[kMaxPairs];
+  int npairs;
+};
+void grid_pack2(const double* a, const double* b, double2* c, long long n, cudaStream_t st);
+void grid_unpack_density(const double2* C, int has_b, double2* RT, int accumulate, double2* Pa, double2* Pb,
+                         double2* Pz, const GridDims& g, const CellDev& c, double* partial, cudaStream_t st);
+void grid_pw_total(const double* rho, const GradPacks& gp, int xc_mode, int kedf, double rho_cut, double* vpart,
+                   double* hx, double* hy, double* hz, long long nr, double* partial, cudaStream_t st);
+void grid_pw_pair(const double* ra, const double* rb, double2* Pa, double2* Pb, double2* Pz, const double* hx,
+                  const double* hy, const double* hz, const double* vtot, int xc_mode, int kedf, double rho_cut,
+                  double* wa, double* wb, int write_d, long long nr, double* partial, cudaStream_t st);
+void grid_assemble_pair(const double2* RT, const double2* Da, const double2* Db, const double2* Dz, int has_b,
+                        double2* F, const GridDims& g, const CellDev& c, double* partial, cudaStream_t st);
+void grid_finish_pair(const double2* F, const double* vloc, double* va, double* vb, long long n, cudaStream_t st);
+
 }  // namespace fde

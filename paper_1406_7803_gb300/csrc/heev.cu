@@ -1,4 +1,5 @@
-// heev.cu -- FP64 Hermitian eigenproblem of the Rayleigh-Ritz step (Eq. KS, block solver).
+// heev.cu -- FP64 Hermitian eigenproblem of the Rayleigh-Ritz step (Eq. KS, block solver):
+// the one-CTA solver for sizes beyond the cluster-distributed one of dense.cu.
 //
 // One CTA of 1024 threads:
 //   1. Householder reduction of the Hermitian A (n x n) to a real symmetric tridiagonal
@@ -12,6 +13,9 @@
 //   4. Back-transformation v = Q z (one warp per vector).
 #include <math.h>
 
+#include <algorithm>
+
+#include "dense.h"
 #include "kernels.h"
 #include "prof.h"
 
@@ -319,10 +323,13 @@ k_heev(double2* __restrict__ A, int n, int nvec, double* __restrict__ w, double2
 }
 
 size_t heev_work_doubles(int n, int nvec) {
-  return (size_t)n * (2 + 4) + (size_t)nvec * n + (size_t)kHeevWarps * 6 * n + 64;
+  const size_t one_cta = (size_t)n * (2 + 4) + (size_t)nvec * n + (size_t)kHeevWarps * 6 * n + 64;
+  return std::max(one_cta, heev_cluster_work_doubles(n, nvec));
 }
 
+// The cluster-distributed solver (dense.cu) when n fits it, else this one-CTA kernel.
 void launch_heev(double2* A, int n, int nvec, double* w, double2* V, double* work, cudaStream_t st) {
+  if (launch_heev_cluster(A, n, nvec, w, V, work, st)) return;
   count_launches(1);
   k_heev<<<1, kHeevThreads, 0, st>>>(A, n, nvec, w, V, work);
 }

@@ -7,26 +7,58 @@
 #include "kernels.h"
 #include "prof.h"
 
+#include <algorithm>
+
 namespace fde {
 
 constexpr int kCtThreads = 256;
 constexpr int kCtCols = 8;  // z-lines per CTA in the z passes and axis transforms
 
+// Every (subsystem, k) block of bands is an item; the kernels below run a batch of items in
+// one launch (the batch travels as a kernel parameter), so subsystems of uneven size share
+// the GPU instead of taking one small launch each.  The first z-block and the first plane
+// block of each item are prefix offsets; a CTA finds its item by scanning the table.
+template <typename T> struct HpsiItem {
+  SphereDev sp;
+  const cplx<T>* psi;
+  cplx<T>* hpsi;
+  const T* kin;
+  const T* vplane;
+  cplx<T>* scratch;  // [nb][n3][ncol]
+  int ld, nb, zstart, pstart;
+};
+constexpr int kBatchMax = 24;
+template <typename T> struct HpsiBatch {
+  int n;
+  HpsiItem<T> it[kBatchMax];
+};
+
+template <typename T>
+__device__ __forceinline__ int batch_item(const HpsiBatch<T>& B, int blk, bool plane) {
+  int i = 0;
+  for (int j = 1; j < B.n; ++j)
+    if ((plane ? B.it[j].pstart : B.it[j].zstart) <= blk) i = j;
+  return i;
+}
+
 template <typename T, int N3>
 __global__ void __launch_bounds__(kCtThreads)
-k_zinv_ct(const cplx<T>* __restrict__ psi, int ldpsi, cplx<T>* __restrict__ scratch, SphereDev sp,
-          const cplx<T>* __restrict__ tw) {
+k_zinv_ct(const __grid_constant__ HpsiBatch<T> B, const cplx<T>* __restrict__ tw) {
   using C = cplx<T>;
   constexpr int LP = N3 + 1;
   __shared__ __align__(16) C lines[kCtCols * LP];
+  const HpsiItem<T>& I = B.it[batch_item(B, blockIdx.x, false)];
+  const SphereDev& sp = I.sp;
+  const int ntile = (sp.ncol + kCtCols - 1) / kCtCols;
+  const int local = blockIdx.x - I.zstart;
+  const int b = local / ntile, c0 = (local - b * ntile) * kCtCols;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int c0 = blockIdx.x * kCtCols, b = blockIdx.y;
   for (int i = threadIdx.x; i < kCtCols * LP; i += kCtThreads) lines[i] = mk<T>(0, 0);
   __syncthreads();
   const int c = c0 + w;
   if (c < sp.ncol) {
     const int s = sp.col_start[c], e = sp.col_start[c + 1], m3 = sp.col_m3lo[c];
-    const C* src = psi + (size_t)b * ldpsi + s;
+    const C* src = I.psi + (size_t)b * I.ld + s;
     C* L = lines + w * LP;
     for (int t = lane; t < e - s; t += 32) {
       int i3 = m3 + t;
@@ -37,7 +69,7 @@ k_zinv_ct(const cplx<T>* __restrict__ psi, int ldpsi, cplx<T>* __restrict__ scra
   __syncthreads();
   ct_lines<T, N3, kCtThreads>(lines, LinesContig{LP}, kCtCols, tw, +1);
   const int nc = min(kCtCols, sp.ncol - c0);
-  C* dst = scratch + (size_t)b * N3 * sp.ncol + c0;
+  C* dst = I.scratch + (size_t)b * N3 * sp.ncol + c0;
   for (int idx = threadIdx.x; idx < N3 * kCtCols; idx += kCtThreads) {
     const int i3 = idx / kCtCols, ww = idx % kCtCols;
     if (ww < nc) dst[(size_t)i3 * sp.ncol + ww] = lines[ww * LP + i3];
@@ -46,15 +78,18 @@ k_zinv_ct(const cplx<T>* __restrict__ psi, int ldpsi, cplx<T>* __restrict__ scra
 
 template <typename T, int N3>
 __global__ void __launch_bounds__(kCtThreads)
-k_zfwd_ct(const cplx<T>* __restrict__ scratch, const cplx<T>* __restrict__ psi, int ldpsi, cplx<T>* __restrict__ hpsi,
-          int ldh, const T* __restrict__ kin, SphereDev sp, T inv_nr, const cplx<T>* __restrict__ tw) {
+k_zfwd_ct(const __grid_constant__ HpsiBatch<T> B, T inv_nr, const cplx<T>* __restrict__ tw) {
   using C = cplx<T>;
   constexpr int LP = N3 + 1;
   __shared__ __align__(16) C lines[kCtCols * LP];
+  const HpsiItem<T>& I = B.it[batch_item(B, blockIdx.x, false)];
+  const SphereDev& sp = I.sp;
+  const int ntile = (sp.ncol + kCtCols - 1) / kCtCols;
+  const int local = blockIdx.x - I.zstart;
+  const int b = local / ntile, c0 = (local - b * ntile) * kCtCols;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int c0 = blockIdx.x * kCtCols, b = blockIdx.y;
   const int nc = min(kCtCols, sp.ncol - c0);
-  const C* src = scratch + (size_t)b * N3 * sp.ncol + c0;
+  const C* src = I.scratch + (size_t)b * N3 * sp.ncol + c0;
   for (int idx = threadIdx.x; idx < N3 * kCtCols; idx += kCtThreads) {
     const int i3 = idx / kCtCols, ww = idx % kCtCols;
     lines[ww * LP + i3] = (ww < nc) ? src[(size_t)i3 * sp.ncol + ww] : mk<T>(0, 0);
@@ -65,14 +100,14 @@ k_zfwd_ct(const cplx<T>* __restrict__ scratch, const cplx<T>* __restrict__ psi, 
   if (c >= sp.ncol) return;
   const C* L = lines + w * LP;
   const int s = sp.col_start[c], e = sp.col_start[c + 1], m3 = sp.col_m3lo[c];
-  const C* ps = psi + (size_t)b * ldpsi;
-  C* hs = hpsi + (size_t)b * ldh;
+  const C* ps = I.psi + (size_t)b * I.ld;
+  C* hs = I.hpsi + (size_t)b * I.ld;
   for (int t = lane; t < e - s; t += 32) {
     int i3 = m3 + t;
     i3 += (i3 < 0) ? N3 : 0;
     const int gidx = s + t;
     const C x = ps[gidx];
-    const T kk = kin[gidx];
+    const T kk = I.kin[gidx];
     C o = L[i3];
     o.x = o.x * inv_nr + kk * x.x;
     o.y = o.y * inv_nr + kk * x.y;
@@ -80,19 +115,22 @@ k_zfwd_ct(const cplx<T>* __restrict__ scratch, const cplx<T>* __restrict__ psi, 
   }
 }
 
-// One CTA per (band, z-plane): columns in, 2D inverse FFT (y on the rows holding columns,
-// then x), potential multiply, 2D forward FFT, columns out.  n1 = n2 = N.
+// One CTA per (item, band, z-plane): columns in, 2D inverse FFT (y on the rows holding
+// columns, then x), potential multiply, 2D forward FFT, columns out.  n1 = n2 = N.
 template <typename T, int N>
 __global__ void __launch_bounds__(kCtThreads)
-k_plane_ct(cplx<T>* __restrict__ scratch, SphereDev sp, const T* __restrict__ vplane, int n3,
-           const cplx<T>* __restrict__ tw1, const cplx<T>* __restrict__ tw2) {
+k_plane_ct(const __grid_constant__ HpsiBatch<T> B, int n3, const cplx<T>* __restrict__ tw1,
+           const cplx<T>* __restrict__ tw2) {
   using C = cplx<T>;
   constexpr int PITCH = N + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* P = reinterpret_cast<C*>(smem_raw);
   __shared__ int rows[N];
-  const int i3 = blockIdx.x, b = blockIdx.y;
-  C* S = scratch + ((size_t)b * n3 + i3) * sp.ncol;
+  const HpsiItem<T>& I = B.it[batch_item(B, blockIdx.x, true)];
+  const SphereDev& sp = I.sp;
+  const int local = blockIdx.x - I.pstart;
+  const int b = local / n3, i3 = local - b * n3;
+  C* S = I.scratch + ((size_t)b * n3 + i3) * sp.ncol;
   for (int idx = threadIdx.x; idx < N * PITCH; idx += kCtThreads) P[idx] = mk<T>(0, 0);
   for (int r = threadIdx.x; r < sp.nrow; r += kCtThreads) rows[r] = sp.row_i1[r];
   __syncthreads();
@@ -100,7 +138,7 @@ k_plane_ct(cplx<T>* __restrict__ scratch, SphereDev sp, const T* __restrict__ vp
   __syncthreads();
   ct_lines<T, N, kCtThreads>(P, LinesRows{rows, PITCH}, sp.nrow, tw2, +1);
   ct_lines<T, N, kCtThreads>(P, LinesCols{PITCH}, N, tw1, +1);
-  const T* V = vplane + (size_t)i3 * N * N;
+  const T* V = I.vplane + (size_t)i3 * N * N;
   for (int idx = threadIdx.x; idx < N * N; idx += kCtThreads) {
     const int i1 = idx / N, i2 = idx - i1 * N;
     C& z = P[i1 * PITCH + i2];
@@ -207,13 +245,12 @@ template <typename T> bool ct_plane_ok(int n1, int n2) {
 }
 
 template <typename T>
-static void ct_zinv(int n3, dim3 grid, cudaStream_t st, const cplx<T>* psi, int ld, cplx<T>* scr, const SphereDev& sp,
-                    const cplx<T>* tw) {
+static void ct_zinv(int n3, unsigned blocks, cudaStream_t st, const HpsiBatch<T>& B, const cplx<T>* tw) {
   switch (n3) {
-#define FDE_CASE(N)                                                              \
-  case N:                                                                        \
-    count_launches(1);                                                           \
-    k_zinv_ct<T, N><<<grid, kCtThreads, 0, st>>>(psi, ld, scr, sp, tw);         \
+#define FDE_CASE(N)                                                    \
+  case N:                                                              \
+    count_launches(1);                                                 \
+    k_zinv_ct<T, N><<<blocks, kCtThreads, 0, st>>>(B, tw);            \
     break;
     FDE_CT_LINES(FDE_CASE)
 #undef FDE_CASE
@@ -221,13 +258,12 @@ static void ct_zinv(int n3, dim3 grid, cudaStream_t st, const cplx<T>* psi, int 
 }
 
 template <typename T>
-static void ct_zfwd(int n3, dim3 grid, cudaStream_t st, const cplx<T>* scr, const cplx<T>* psi, int ld, cplx<T>* h,
-                    int ldh, const T* kin, const SphereDev& sp, T inv_nr, const cplx<T>* tw) {
+static void ct_zfwd(int n3, unsigned blocks, cudaStream_t st, const HpsiBatch<T>& B, T inv_nr, const cplx<T>* tw) {
   switch (n3) {
-#define FDE_CASE(N)                                                                          \
-  case N:                                                                                    \
-    count_launches(1);                                                                       \
-    k_zfwd_ct<T, N><<<grid, kCtThreads, 0, st>>>(scr, psi, ld, h, ldh, kin, sp, inv_nr, tw); \
+#define FDE_CASE(N)                                                    \
+  case N:                                                              \
+    count_launches(1);                                                 \
+    k_zfwd_ct<T, N><<<blocks, kCtThreads, 0, st>>>(B, inv_nr, tw);    \
     break;
     FDE_CT_LINES(FDE_CASE)
 #undef FDE_CASE
@@ -235,15 +271,15 @@ static void ct_zfwd(int n3, dim3 grid, cudaStream_t st, const cplx<T>* scr, cons
 }
 
 template <typename T>
-static void ct_plane(int n, dim3 grid, cudaStream_t st, cplx<T>* scr, const SphereDev& sp, const T* vplane, int n3,
-                     const cplx<T>* tw1, const cplx<T>* tw2) {
+static void ct_plane(int n, unsigned blocks, cudaStream_t st, const HpsiBatch<T>& B, int n3, const cplx<T>* tw1,
+                     const cplx<T>* tw2) {
   const size_t sm = (size_t)n * (n + 1) * sizeof(cplx<T>);
   switch (n) {
-#define FDE_CASE(N)                                                                   \
-  case N:                                                                             \
-    ct_allow_smem(k_plane_ct<T, N>, sm);                                              \
-    count_launches(1);                                                                \
-    k_plane_ct<T, N><<<grid, kCtThreads, sm, st>>>(scr, sp, vplane, n3, tw1, tw2);    \
+#define FDE_CASE(N)                                                          \
+  case N:                                                                    \
+    ct_allow_smem(k_plane_ct<T, N>, sm);                                     \
+    count_launches(1);                                                       \
+    k_plane_ct<T, N><<<blocks, kCtThreads, sm, st>>>(B, n3, tw1, tw2);       \
     break;
     FDE_CT_PLANES(FDE_CASE)
 #undef FDE_CASE
@@ -281,26 +317,56 @@ static void ct_axis(int n, long long nlines, long long I, cudaStream_t st, cplx<
   }
 }
 
+// Run up to kBatchMax items per launch; items[i].zstart / pstart are filled here.
+template <typename T>
+bool launch_hpsi_batch_ct(const HpsiItemDesc<T>* items, int nitems, const GridDims& g, const FftPlans<T>& fp,
+                          cudaStream_t st) {
+  if (!ct_plane_ok<T>(g.n1, g.n2) || !ct_line_ok<T>(g.n3)) return false;
+  const T inv_nr = (T)(1.0 / ((double)g.n1 * g.n2 * g.n3));
+  for (int i0 = 0; i0 < nitems; i0 += kBatchMax) {
+    HpsiBatch<T> B;
+    B.n = std::min(kBatchMax, nitems - i0);
+    int zb = 0, pb = 0;
+    for (int j = 0; j < B.n; ++j) {
+      const HpsiItemDesc<T>& d = items[i0 + j];
+      HpsiItem<T>& it = B.it[j];
+      it.sp = d.sp;
+      it.psi = d.psi;
+      it.hpsi = d.hpsi;
+      it.kin = d.kin;
+      it.vplane = d.vplane;
+      it.scratch = d.scratch;
+      it.ld = d.ld;
+      it.nb = d.nb;
+      it.zstart = zb;
+      it.pstart = pb;
+      zb += ceil_div(d.sp.ncol, kCtCols) * d.nb;
+      pb += g.n3 * d.nb;
+    }
+    if (zb == 0) continue;
+    {
+      ProfScope p("k_zinv", st);
+      ct_zinv<T>(g.n3, (unsigned)zb, st, B, fp.p3.tw);
+    }
+    {
+      ProfScope p("k_plane", st);
+      ct_plane<T>(g.n1, (unsigned)pb, st, B, g.n3, fp.p1.tw, fp.p2.tw);
+    }
+    {
+      ProfScope p("k_zfwd", st);
+      ct_zfwd<T>(g.n3, (unsigned)zb, st, B, inv_nr, fp.p3.tw);
+    }
+  }
+  return true;
+}
+
 template <typename T>
 bool launch_hpsi_local_ct(const cplx<T>* psi, int ldpsi, cplx<T>* hpsi, int ldh, int nb, const T* kin,
                           const T* vplane, cplx<T>* scratch, const SphereDev& sp, const GridDims& g,
                           const FftPlans<T>& fp, cudaStream_t st) {
-  if (!ct_plane_ok<T>(g.n1, g.n2) || !ct_line_ok<T>(g.n3)) return false;
-  const dim3 gz(ceil_div(sp.ncol, kCtCols), nb);
-  {
-    ProfScope p("k_zinv", st);
-    ct_zinv<T>(g.n3, gz, st, psi, ldpsi, scratch, sp, fp.p3.tw);
-  }
-  {
-    ProfScope p("k_plane", st);
-    ct_plane<T>(g.n1, dim3(g.n3, nb), st, scratch, sp, vplane, g.n3, fp.p1.tw, fp.p2.tw);
-  }
-  const T inv_nr = (T)(1.0 / ((double)g.n1 * g.n2 * g.n3));
-  {
-    ProfScope p("k_zfwd", st);
-    ct_zfwd<T>(g.n3, gz, st, scratch, psi, ldpsi, hpsi, ldh, kin, sp, inv_nr, fp.p3.tw);
-  }
-  return true;
+  if (ldpsi != ldh) return false;
+  HpsiItemDesc<T> d{sp, psi, hpsi, kin, vplane, scratch, ldpsi, nb};
+  return launch_hpsi_batch_ct<T>(&d, 1, g, fp, st);
 }
 
 template <typename T>
@@ -308,8 +374,10 @@ bool launch_density_ct(const cplx<T>* psi, int ldpsi, int nb, const double* weig
                        double* rho_plane, int accumulate, const SphereDev& sp, const GridDims& g,
                        const FftPlans<T>& fp, cudaStream_t st) {
   if (!ct_plane_ok<T>(g.n1, g.n2) || !ct_line_ok<T>(g.n3)) return false;
-  const dim3 gz(ceil_div(sp.ncol, kCtCols), nb);
-  ct_zinv<T>(g.n3, gz, st, psi, ldpsi, scratch, sp, fp.p3.tw);
+  HpsiBatch<T> B;
+  B.n = 1;
+  B.it[0] = HpsiItem<T>{sp, psi, nullptr, nullptr, nullptr, scratch, ldpsi, nb, 0, 0};
+  ct_zinv<T>(g.n3, (unsigned)(ceil_div(sp.ncol, kCtCols) * nb), st, B, fp.p3.tw);
   ct_plane_density<T>(g.n1, g.n3, st, scratch, sp, nb, weight, rho_plane, accumulate, fp.p1.tw, fp.p2.tw);
   return true;
 }

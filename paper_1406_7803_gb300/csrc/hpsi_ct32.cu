@@ -8,6 +8,8 @@ template bool launch_hpsi_local_ct<float>(const cplx<float>*, int, cplx<float>*,
                                        cudaStream_t);
 template bool launch_density_ct<float>(const cplx<float>*, int, int, const double*, cplx<float>*, double*, int,
                                     const SphereDev&, const GridDims&, const FftPlans<float>&, cudaStream_t);
+template bool launch_hpsi_batch_ct<float>(const HpsiItemDesc<float>*, int, const GridDims&, const FftPlans<float>&,
+                                       cudaStream_t);
 template bool launch_fft3d_ct<float>(cplx<float>*, const GridDims&, const FftPlans<float>&, int, cudaStream_t);
 
 }  // namespace fde

@@ -40,6 +40,21 @@ void launch_density(const cplx<T>* psi, int ldpsi, int nb, const double* weight,
                     cplx<T>* scratch, double* rho_plane, int accumulate, const SphereDev& sp,
                     const GridDims& g, const FftPlans<T>& fp, cudaStream_t st);
 
+// One (subsystem, k) block of bands of a batched H psi launch.
+template <typename T> struct HpsiItemDesc {
+  SphereDev sp;
+  const cplx<T>* psi;
+  cplx<T>* hpsi;
+  const T* kin;
+  const T* vplane;
+  cplx<T>* scratch;  // [nb][n3][ncol] of this item
+  int ld, nb;
+};
+// Local H psi of many items in three launches (batches of up to 24 items each).
+template <typename T>
+bool launch_hpsi_batch_ct(const HpsiItemDesc<T>* items, int nitems, const GridDims& g, const FftPlans<T>& fp,
+                          cudaStream_t st);
+
 // Compile-time-length variants (hpsi_ct.cuh); return false when the grid sizes are not
 // among the instantiated ones, and the runtime-length kernels run instead.
 template <typename T>
@@ -70,6 +85,15 @@ void launch_gemm_hn(const cplx<T>* A, int lda, const cplx<T>* B, int ldb, int m,
 template <typename T>
 void launch_gemm_rot(const cplx<T>* X, int ldx, const double2* U, int ldu, int m, int n, int K,
                      cplx<T>* Y, int ldy, double alpha, double beta, cudaStream_t st);
+
+// Per-atom block of the projector coupling (np x np, row-major, np <= 8).
+struct KbBlock {
+  double d[64];
+  int np;
+};
+// Q[a np + i][b] = sum_j D[i][j] P[a np + j][b] for natoms atoms and nb columns (FP64 complex,
+// leading dimension nb).
+void launch_kb_couple(const double2* P, const KbBlock& D, int natoms, int nb, double2* Q, cudaStream_t st);
 
 // Cholesky S = L L^H (n x n, FP64 complex, lower, in place into L) and Linv = L^{-1};
 // sets status bit ST_CHOLESKY on a non-positive pivot.

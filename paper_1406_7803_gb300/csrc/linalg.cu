@@ -5,6 +5,9 @@
 // helpers.
 #include <math.h>
 
+#include <algorithm>
+
+#include "dense.h"
 #include "kernels.h"
 #include "prof.h"
 
@@ -238,9 +241,40 @@ k_cholesky_inv(const double2* __restrict__ S, int n, double2* __restrict__ L, do
   }
 }
 
+// The cluster-distributed factorisation (dense.cu) when n fits it, else one CTA.
 void launch_cholesky_inv(const double2* S, int n, double2* L, double2* Linv, unsigned* status, cudaStream_t st) {
+  if (launch_cholesky_cluster(S, n, L, Linv, status, st)) return;
   count_launches(1);
   k_cholesky_inv<<<1, 512, 0, st>>>(S, n, L, Linv, status);
+}
+
+// ---- per-atom projector coupling ------------------------------------------------------------
+// Q[a np + i][b] = sum_j D[i][j] P[a np + j][b]: D is the same small block for every atom, so
+// the coupling of Eq. KB (nonlocal part) is block diagonal and needs no dense product.
+__global__ void k_kb_couple(const double2* __restrict__ P, KbBlock D, int natoms, int nb, double2* __restrict__ Q) {
+  const long long n = (long long)natoms * D.np * nb;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n; idx += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(idx % nb);
+    const long long r = idx / nb;
+    const int i = (int)(r % D.np);
+    const long long base = (r - i) * nb + b;
+    double re = 0, im = 0;
+    for (int j = 0; j < D.np; ++j) {
+      const double d = D.d[i * D.np + j];
+      const double2 p = P[base + (long long)j * nb];
+      re += d * p.x;
+      im += d * p.y;
+    }
+    Q[idx] = make_double2(re, im);
+  }
+}
+
+void launch_kb_couple(const double2* P, const KbBlock& D, int natoms, int nb, double2* Q, cudaStream_t st) {
+  const long long n = (long long)natoms * D.np * nb;
+  if (n <= 0) return;
+  count_launches(1);
+  const int blocks = (int)std::min<long long>((n + 255) / 256, 1024);
+  k_kb_couple<<<blocks, 256, 0, st>>>(P, D, natoms, nb, Q);
 }
 
 // ---- Hermitian cyclic Jacobi (one CTA, round-robin parallel ordering) ----------------------

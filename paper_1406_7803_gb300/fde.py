@@ -78,6 +78,7 @@ EXPORTS = {
                                            C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "fde_fft3d": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "fde_hot_step": (C.c_int, [C.c_void_p, C.c_int]),
+    "fde_get_hpsi": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p]),
     "fde_dense_eigh": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "fde_set_precond": (C.c_int, [C.c_void_p, C.c_int]),
     "fde_precond_set_weights": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -281,6 +282,9 @@ class Context:
     def dense_eigh(self, A, nvec, w, V):
         return self._check(self.lib.fde_dense_eigh(self.h, int(A.shape[0]), _dptr(A), int(nvec), _dptr(w), _dptr(V)),
                            "fde_dense_eigh")
+
+    def get_hpsi(self, sub, k, out):
+        return self._check(self.lib.fde_get_hpsi(self.h, sub, k, _dptr(out)), "fde_get_hpsi")
 
     def hot_step(self, use_graph=False):
         return self._check(self.lib.fde_hot_step(self.h, int(bool(use_graph))), "fde_hot_step")
