@@ -252,7 +252,8 @@ fde_status fde_energy(fde_ctx* ctx, fde_energies* out);
 
 /* Self-consistent field of one subsystem with every other density frozen: repeat
  * {build V_eff^I, Davidson on every k, occupations and density, Pulay mixing} until the
- * FDE free energy changes by less than tol_ha and int|rho_out - rho_in| < sqrt(tol_ha).
+ * FDE free energy changes by less than tol_ha and int|rho_out - rho_in| < 10 tol_ha
+ * (mixed-precision contexts: max(10 tol_ha, 1e-4)).
  * out (nullable) gets the energies. FDE_ENOCONV after max_scf iterations. */
 fde_status fde_scf_subsystem(fde_ctx* ctx, int sub, double tol_ha, int max_scf,
                              fde_energies* out);
@@ -311,6 +312,22 @@ fde_status fde_fft3d(fde_ctx* ctx, void* d_data, int sign);
  * in column j (V[r*n + j]) the unit eigenvector of w[j] for j < nvec and zeros beyond.
  * Householder tridiagonalisation, bisection and inverse iteration; n <= 1024. */
 fde_status fde_dense_eigh(fde_ctx* ctx, int n, const double* d_A, int nvec, double* d_w, double* d_V);
+
+/* The band-block inner product C = A^H B of the eigensolver's Gram and subspace-Hamiltonian
+ * matrices and of the projector contraction <beta|psi> (Eq. KS; Appendix, projectors),
+ * applied to caller data: d_A device complex float [m][lda], d_B [n][ldb] (rows of length
+ * K <= lda, ldb), d_C device complex double [m][ldc] receives the m x n result (FP32
+ * products, summed over K-chunks in FP64 in a fixed order).  path: 0 CUDA cores (FP32
+ * fused multiply-add); 1 tensor cores (tcgen05, TF32 operands, FP32 accumulation);
+ * 3 tensor cores with each operand split into TF32 hi + lo parts (hi*hi + hi*lo + lo*hi,
+ * FP32 accuracy).  Synchronising; FDE_ETIMEOUT if a tensor-core wait ran out. */
+fde_status fde_gemm_hn_f32(fde_ctx* ctx, const void* d_A, int lda, const void* d_B, int ldb, int m, int n,
+                           int K, double* d_C, int ldc, int path);
+
+/* Path (0, 1 or 3, as for fde_gemm_hn_f32) of every FP32 band-block inner product the
+ * library makes (mixed-precision contexts; FP64 products always use the CUDA cores).
+ * Process-wide; the default is 0. */
+fde_status fde_set_gemm_path(int path);
 
 /* Synchronise the context stream and check the device status word. */
 fde_status fde_sync(fde_ctx* ctx);

@@ -1,0 +1,318 @@
+// gemm_tc.cu -- C = A^H B over a long K on the 5th-generation tensor cores (tcgen05, TF32
+// inputs, FP32 accumulation in tensor memory): the subspace Gram / subspace-Hamiltonian
+// products of the block eigensolver and the projector contraction <beta|psi> of the
+// Kleinman-Bylander term (Eq. KS; Appendix, subsystem-specific projectors).
+//
+// Complex to real.  With a = (Re a_0, Im a_0, Re a_1, ...) the interleaved row of A and
+// b~ = (Im b_0, -Re b_0, Im b_1, ...) the "rotated" row of B,
+//   Re (A^H B)_ij = a_i . b_j,   Im (A^H B)_ij = a_i . b~_j,
+// so one real GEMM with the B tile stacked as [b_0..b_63 ; b~_0..b~_63] (N = 128) yields
+// both parts: D[i][j] = Re, D[i][64 + j] = Im.
+//
+// Precision.  TF32 keeps 10 mantissa bits.  Each operand is split x = hi + lo with hi = x
+// truncated to TF32 (exact) and lo = x - hi (exact in FP32); D += Ahi Bhi + Ahi Blo + Alo Bhi
+// (three MMAs per k-step) carries ~21 bits, the accuracy of the FP32 CUDA-core product.
+// passes = 1 keeps only Ahi Bhi.
+//
+// Data flow per CTA (256 threads, one 128 x 64 complex output tile, one K-chunk):
+//   registers <- global (8-byte loads, one k-tile of 16 complex ahead) ; split, rotate and
+//   store into the 128-byte-swizzled K-major shared-memory layout the MMA descriptors
+//   describe ; fence.proxy.async ; one elected thread issues 4 k-steps x passes MMAs of
+//   M = 128, N = 128, K = 8 and commits them to the stage's mbarrier ; two stages.
+//   Epilogue: tcgen05.ld of the 128 x 128 FP32 accumulator, FP64 partial tile to global;
+//   k_gemm_hn_reduce (linalg.cu) sums the K-splits in a fixed order.
+// Every wait is bounded; on timeout the kernel sets ST_TIMEOUT, waits (bounded) for its
+// issued MMAs, frees its tensor memory and returns.
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "kernels.h"
+#include "prof.h"
+
+namespace fde {
+
+namespace {
+
+constexpr int kTcThreads = 256;
+constexpr int kTcM = 128;      // output rows (A rows) per CTA
+constexpr int kTcN = 64;       // complex output columns (B rows) per CTA
+constexpr int kTcKc = 16;      // complex K per k-tile (32 floats = one 128-byte row)
+constexpr int kTile = 16384;   // bytes of one 128-row x 128-byte operand tile
+constexpr int kStage = 4 * kTile;  // A hi, A lo, B hi, B lo
+constexpr int kStages = 2;
+constexpr int kTmemCols = 128;
+constexpr long long kSpin = 1ll << 22;  // bounded mbarrier polls (with back-off: ~1 s)
+
+__device__ unsigned g_tc_status;
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint32_t bar, unsigned parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, unsigned parity) {
+  for (long long i = 0; i < kSpin; ++i) {
+    if (mbar_test(bar, parity)) return true;
+    if (i > 32) __nanosleep(128);
+  }
+  return false;
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row groups 1024 B
+// apart (stride byte offset), leading byte offset unused for this layout (1), descriptor
+// version 1, base offset 0 (tiles are 1024-byte aligned).
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// Instruction descriptor, kind::tf32: D f32 (bits 4-5 = 1), A and B tf32 (bits 7-9, 10-12
+// = 2), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(2 * kTcN / 8) << 17) |
+                            ((uint32_t)(kTcM / 16) << 24);
+
+__device__ __forceinline__ void mma_tf32(uint32_t dt, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dt),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+
+// Byte offset of floats (c, c + 1) of row r in a 128-byte-swizzled tile (c even).
+__device__ __forceinline__ uint32_t swz(int r, int c) {
+  return (uint32_t)(r * 128 + ((((c >> 2) ^ (r & 7)) << 4) | ((c & 3) << 2)));
+}
+__device__ __forceinline__ void st2(uint32_t addr, float a, float b) {
+  asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(a), "f"(b) : "memory");
+}
+
+constexpr int kAld = kTcM * kTcKc / kTcThreads;  // A elements per thread per k-tile (8)
+constexpr int kBld = kTcN * kTcKc / kTcThreads;  // B elements per thread per k-tile (4)
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+k_gemm_hn_tc(const float2* __restrict__ A, int lda, const float2* __restrict__ B, int ldb, int m, int n, int K,
+             int kchunk, int passes, double2* __restrict__ part) {
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bars[kStages];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t base = (su32(smem_raw) + 1023u) & ~1023u;
+  const int i0 = blockIdx.x * kTcM, j0 = blockIdx.y * kTcN;
+  const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
+  const int nt = ke > kb ? (ke - kb + kTcKc - 1) / kTcKc : 0;
+
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) mbar_init(su32(&bars[s]), 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  float2 ra[kAld], rb[kBld];
+  auto load = [&](int t) {
+    const int k0 = kb + t * kTcKc;
+#pragma unroll
+    for (int q = 0; q < kAld; ++q) {
+      const int idx = tid + kTcThreads * q, r = idx >> 4, kc = idx & 15;
+      const int i = i0 + r, k = k0 + kc;
+      ra[q] = (i < m && k < ke) ? __ldg(A + (size_t)i * lda + k) : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int q = 0; q < kBld; ++q) {
+      const int idx = tid + kTcThreads * q, r = idx >> 4, kc = idx & 15;
+      const int j = j0 + r, k = k0 + kc;
+      rb[q] = (j < n && k < ke) ? __ldg(B + (size_t)j * ldb + k) : make_float2(0.f, 0.f);
+    }
+  };
+  auto store = [&](uint32_t st) {
+#pragma unroll
+    for (int q = 0; q < kAld; ++q) {
+      const int idx = tid + kTcThreads * q, r = idx >> 4, c = 2 * (idx & 15);
+      const float hx = tf32_hi(ra[q].x), hy = tf32_hi(ra[q].y);
+      st2(st + swz(r, c), hx, hy);
+      if (passes > 1) st2(st + kTile + swz(r, c), ra[q].x - hx, ra[q].y - hy);
+    }
+#pragma unroll
+    for (int q = 0; q < kBld; ++q) {
+      const int idx = tid + kTcThreads * q, r = idx >> 4, c = 2 * (idx & 15);
+      const float hx = tf32_hi(rb[q].x), hy = tf32_hi(rb[q].y);
+      st2(st + 2 * kTile + swz(r, c), hx, hy);                // b
+      st2(st + 2 * kTile + swz(r + kTcN, c), hy, -hx);        // b~ = (Im b, -Re b)
+      if (passes > 1) {
+        const float lx = rb[q].x - hx, ly = rb[q].y - hy;
+        st2(st + 3 * kTile + swz(r, c), lx, ly);
+        st2(st + 3 * kTile + swz(r + kTcN, c), ly, -lx);
+      }
+    }
+  };
+
+  int issued = 0;  // k-tiles whose MMAs were committed (meaningful in thread 0)
+  if (nt > 0) load(0);
+  for (int t = 0; t < nt; ++t) {
+    const int s = t & 1;
+    const uint32_t st = base + (uint32_t)s * kStage;
+    if (t >= kStages) {
+      // stage s is free once the MMAs of tile t - 2 have completed
+      if (tid == 0 && !mbar_wait(su32(&bars[s]), (unsigned)(((t - kStages) >> 1) & 1))) abort_flag = 1;
+      __syncthreads();
+      if (abort_flag) break;
+    }
+    store(st);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+#pragma unroll
+      for (int kk = 0; kk < kTcKc * 2 / 8; ++kk) {
+        const uint32_t off = (uint32_t)kk * 32u;
+        const uint64_t ah = sdesc(st + off), bh = sdesc(st + 2 * kTile + off);
+        mma_tf32(tmem, ah, bh, (t > 0 || kk > 0) ? 1u : 0u);
+        if (passes > 1) {
+          const uint64_t al = sdesc(st + kTile + off), bl = sdesc(st + 3 * kTile + off);
+          mma_tf32(tmem, ah, bl, 1u);
+          mma_tf32(tmem, al, bh, 1u);
+        }
+      }
+      mma_commit(su32(&bars[s]));
+      ++issued;
+    }
+    if (t + 1 < nt) load(t + 1);
+  }
+
+  // wait for the last commit of each stage: every issued MMA has completed
+  if (tid == 0) {
+    for (int s = 0; s < kStages && s < issued; ++s) {
+      const int uses = (issued - s + kStages - 1) / kStages;
+      if (!mbar_wait(su32(&bars[s]), (unsigned)((uses - 1) & 1))) abort_flag = 1;
+    }
+  }
+  __syncthreads();
+  const bool ok = !abort_flag;
+  if (!ok && tid == 0) atomicOr(&g_tc_status, ST_TIMEOUT);
+  tc_fence_after();
+  if (ok) {
+    // warp w reads accumulator lanes 32 (w % 4) .. + 31 (its rows); warps 0-3 take the
+    // complex columns 0..31, warps 4-7 the columns 32..63
+    const int q = warp & 3, h = warp >> 2;
+    const int r = 32 * q + lane, i = i0 + r;
+    const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16);
+    double2* P = part + ((size_t)blockIdx.z * m + (size_t)(i < m ? i : 0)) * n;
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      const int jc = 32 * h + 16 * half;
+      float re[16], im[16];
+      if (nt > 0) {
+        tmem_ld16(trow + (uint32_t)jc, re);
+        tmem_ld16(trow + (uint32_t)(kTcN + jc), im);
+      } else {
+#pragma unroll
+        for (int x = 0; x < 16; ++x) re[x] = im[x] = 0.f;
+      }
+      if (i < m) {
+#pragma unroll
+        for (int x = 0; x < 16; ++x) {
+          const int j = j0 + jc + x;
+          if (j < n) P[j] = make_double2((double)re[x], (double)im[x]);
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
+}
+
+}  // namespace
+
+// K-splits of the tensor-core product: about two CTAs per SM over the grid, at least eight
+// k-tiles per split.
+int gemm_hn_tc_splits(int m, int n, int K) {
+  const int tiles = ceil_div(m, kTcM) * ceil_div(n, kTcN);
+  int s = ceil_div(2 * 152, tiles);
+  const int smax = std::max(1, ceil_div(K, 8 * kTcKc));
+  return std::max(1, std::min(s, smax));
+}
+
+size_t gemm_hn_tc_smem() { return (size_t)kStages * kStage + 1024; }
+
+// Partial tiles of C = A^H B into part[nsplit][m][n]; returns the number of splits (0 if the
+// kernel could not be configured; nothing is launched then).
+int launch_gemm_hn_tc(const float2* A, int lda, const float2* B, int ldb, int m, int n, int K, int passes,
+                      double2* part, cudaStream_t st) {
+  static int attr = 0;  // 1 configured, -1 failed
+  if (attr == 0)
+    attr = cudaFuncSetAttribute(k_gemm_hn_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)gemm_hn_tc_smem()) == cudaSuccess ? 1 : -1;
+  if (attr < 0) return 0;
+  const int s = gemm_hn_tc_splits(m, n, K);
+  int kchunk = ceil_div(K, s);
+  kchunk = ((kchunk + kTcKc - 1) / kTcKc) * kTcKc;
+  const int ns = std::max(1, ceil_div(K, std::max(kchunk, 1)));
+  const dim3 grid(ceil_div(m, kTcM), ceil_div(n, kTcN), ns);
+  count_launches(1);
+  ProfScope p("k_gemm_hn_tc", st);
+  k_gemm_hn_tc<<<grid, kTcThreads, gemm_hn_tc_smem(), st>>>(A, lda, B, ldb, m, n, K, kchunk, passes, part);
+  return ns;
+}
+
+// Status bits raised by the tensor-core kernels since the last call (read and cleared;
+// synchronises the stream).
+unsigned gemm_tc_take_status(cudaStream_t st) {
+  unsigned h = 0, z = 0;
+  if (cudaMemcpyFromSymbolAsync(&h, g_tc_status, sizeof(unsigned), 0, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return 0;  // the stream's own error surfaces at the caller's next check
+  if (h) cudaMemcpyToSymbolAsync(g_tc_status, &z, sizeof(unsigned), 0, cudaMemcpyHostToDevice, st);
+  return h;
+}
+
+}  // namespace fde

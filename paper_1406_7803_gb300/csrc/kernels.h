@@ -76,6 +76,19 @@ void launch_transpose(const Tin* in, Tout* out, int rows, int cols, int accumula
 // C[i][j] = sum_g conj(A[i][g]) B[j][g], A [m][K] (lda), B [n][K] (ldb); C [m][n] FP64
 // complex (ldc).  work: at least gemm_hn_work(m, n, K) double2 elements.
 size_t gemm_hn_work(int m, int n, int K);
+// Path of the FP32 products C = A^H B: 0 CUDA cores (FP32 FMA), 1 tensor cores with TF32
+// operands, 3 tensor cores with split-TF32 operands (hi*hi + hi*lo + lo*hi, FP32 accuracy).
+// Process-wide; the default is 0.
+void set_gemm_hn_path(int path);
+int gemm_hn_path();
+// The tensor-core kernel itself (gemm_tc.cu): partial tiles into part[nsplit][m][n];
+// returns nsplit, or 0 when the kernel could not be configured (nothing launched).
+int gemm_hn_tc_splits(int m, int n, int K);
+int launch_gemm_hn_tc(const float2* A, int lda, const float2* B, int ldb, int m, int n, int K, int passes,
+                      double2* part, cudaStream_t st);
+// ST_* bits raised by the tensor-core kernels since the last call (read, cleared; syncs).
+unsigned gemm_tc_take_status(cudaStream_t st);
+void launch_gemm_hn_reduce(const double2* part, int nsplit, int m, int n, double2* C, int ldc, cudaStream_t st);
 template <typename T>
 void launch_gemm_hn(const cplx<T>* A, int lda, const cplx<T>* B, int ldb, int m, int n, int K,
                     double2* C, int ldc, double2* work, cudaStream_t st);

@@ -82,12 +82,39 @@ static int gemm_hn_splits(int m, int n, int K) {
   return s;
 }
 
-size_t gemm_hn_work(int m, int n, int K) { return (size_t)gemm_hn_splits(m, n, K) * m * n; }
+size_t gemm_hn_work(int m, int n, int K) {
+  return (size_t)std::max(gemm_hn_splits(m, n, K), gemm_hn_tc_splits(m, n, K)) * m * n;
+}
+
+static int g_gemm_path = 0;
+void set_gemm_hn_path(int path) { g_gemm_path = (path == 0 || path == 1) ? path : 3; }
+int gemm_hn_path() { return g_gemm_path; }
+
+void launch_gemm_hn_reduce(const double2* part, int nsplit, int m, int n, double2* C, int ldc, cudaStream_t st) {
+  count_launches(1);
+  k_gemm_hn_reduce<<<ceil_div((long long)m * n, 256), 256, 0, st>>>(part, nsplit, m, n, C, ldc);
+}
+
+template <typename T>
+static bool gemm_hn_tensor(const cplx<T>*, int, const cplx<T>*, int, int, int, int, double2*, int, double2*,
+                           cudaStream_t) {
+  return false;  // FP64 products stay on the CUDA cores (the part's FP64 tensor rate is no faster)
+}
+template <>
+bool gemm_hn_tensor<float>(const float2* A, int lda, const float2* B, int ldb, int m, int n, int K, double2* C,
+                           int ldc, double2* work, cudaStream_t st) {
+  if (g_gemm_path == 0 || K <= 0) return false;
+  const int ns = launch_gemm_hn_tc(A, lda, B, ldb, m, n, K, g_gemm_path, work, st);
+  if (ns == 0) return false;
+  launch_gemm_hn_reduce(work, ns, m, n, C, ldc, st);
+  return true;
+}
 
 template <typename T>
 void launch_gemm_hn(const cplx<T>* A, int lda, const cplx<T>* B, int ldb, int m, int n, int K, double2* C,
                     int ldc, double2* work, cudaStream_t st) {
   if (m <= 0 || n <= 0) return;
+  if (gemm_hn_tensor<T>(A, lda, B, ldb, m, n, K, C, ldc, work, st)) return;
   const int s = gemm_hn_splits(m, n, K);
   int kchunk = ceil_div(K, s);
   kchunk = ((kchunk + kGK - 1) / kGK) * kGK;

@@ -79,6 +79,9 @@ EXPORTS = {
     "fde_fft3d": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "fde_hot_step": (C.c_int, [C.c_void_p, C.c_int]),
     "fde_get_hpsi": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p]),
+    "fde_gemm_hn_f32": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int,
+                                  C.c_void_p, C.c_int, C.c_int]),
+    "fde_set_gemm_path": (C.c_int, [C.c_int]),
     "fde_dense_eigh": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "fde_set_precond": (C.c_int, [C.c_void_p, C.c_int]),
     "fde_precond_set_weights": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -115,6 +118,14 @@ def load(path: str = LIB_PATH):
         fn.argtypes = args
     _lib = lib
     return lib
+
+
+def set_gemm_path(path: int) -> None:
+    """Path of the library's FP32 band-block products: 0 CUDA cores, 1 tensor cores (TF32),
+    3 tensor cores with split-TF32 operands.  Process-wide (default 0)."""
+    s = load().fde_set_gemm_path(int(path))
+    if s != FDE_OK:
+        raise FDEError(s, "fde_set_gemm_path: path must be 0, 1 or 3")
 
 
 class FDEError(RuntimeError):
@@ -282,6 +293,13 @@ class Context:
     def dense_eigh(self, A, nvec, w, V):
         return self._check(self.lib.fde_dense_eigh(self.h, int(A.shape[0]), _dptr(A), int(nvec), _dptr(w), _dptr(V)),
                            "fde_dense_eigh")
+
+    def gemm_hn_f32(self, A, B, K, C, path):
+        """C = A^H B over the first K columns of the rows of A (m x lda) and B (n x ldb),
+        complex64 device tensors; C complex128 (m x ldc)."""
+        return self._check(self.lib.fde_gemm_hn_f32(self.h, _dptr(A), int(A.shape[1]), _dptr(B), int(B.shape[1]),
+                                                    int(A.shape[0]), int(B.shape[0]), int(K), _dptr(C),
+                                                    int(C.shape[1]), int(path)), "fde_gemm_hn_f32")
 
     def get_hpsi(self, sub, k, out):
         return self._check(self.lib.fde_get_hpsi(self.h, sub, k, _dptr(out)), "fde_get_hpsi")
