@@ -326,7 +326,7 @@ fde_status fde_gemm_hn_f32(fde_ctx* ctx, const void* d_A, int lda, const void* d
 
 /* Path (0, 1 or 3, as for fde_gemm_hn_f32) of every FP32 band-block inner product the
  * library makes (mixed-precision contexts; FP64 products always use the CUDA cores).
- * Process-wide; the default is 0. */
+ * Process-wide; the default is 3 (FDE_GEMM_PATH in the environment sets the initial path). */
 fde_status fde_set_gemm_path(int path);
 
 /* Synchronise the context stream and check the device status word. */

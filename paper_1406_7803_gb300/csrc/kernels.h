@@ -78,7 +78,7 @@ void launch_transpose(const Tin* in, Tout* out, int rows, int cols, int accumula
 size_t gemm_hn_work(int m, int n, int K);
 // Path of the FP32 products C = A^H B: 0 CUDA cores (FP32 FMA), 1 tensor cores with TF32
 // operands, 3 tensor cores with split-TF32 operands (hi*hi + hi*lo + lo*hi, FP32 accuracy).
-// Process-wide; the default is 0.
+// Process-wide; the default is 3.
 void set_gemm_hn_path(int path);
 int gemm_hn_path();
 // The tensor-core kernel itself (gemm_tc.cu): partial tiles into part[nsplit][m][n];

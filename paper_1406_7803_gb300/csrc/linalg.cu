@@ -4,6 +4,7 @@
 // Jacobi for the small Hermitian eigenproblem, and the row-wise residual / preconditioner
 // helpers.
 #include <math.h>
+#include <stdlib.h>
 
 #include <algorithm>
 
@@ -86,7 +87,13 @@ size_t gemm_hn_work(int m, int n, int K) {
   return (size_t)std::max(gemm_hn_splits(m, n, K), gemm_hn_tc_splits(m, n, K)) * m * n;
 }
 
-static int g_gemm_path = 0;
+// FDE_GEMM_PATH (0, 1 or 3) in the environment sets the initial path.
+static int initial_gemm_path() {
+  const char* e = getenv("FDE_GEMM_PATH");
+  const int p = e ? atoi(e) : 3;
+  return (p == 0 || p == 1) ? p : 3;
+}
+static int g_gemm_path = initial_gemm_path();
 void set_gemm_hn_path(int path) { g_gemm_path = (path == 0 || path == 1) ? path : 3; }
 int gemm_hn_path() { return g_gemm_path; }
 

@@ -122,7 +122,7 @@ def load(path: str = LIB_PATH):
 
 def set_gemm_path(path: int) -> None:
     """Path of the library's FP32 band-block products: 0 CUDA cores, 1 tensor cores (TF32),
-    3 tensor cores with split-TF32 operands.  Process-wide (default 0)."""
+    3 tensor cores with split-TF32 operands.  Process-wide (default 3)."""
     s = load().fde_set_gemm_path(int(path))
     if s != FDE_OK:
         raise FDEError(s, "fde_set_gemm_path: path must be 0, 1 or 3")
