@@ -96,6 +96,28 @@ class Clocks:
         return out
 
 
+def _profile_traffic(name, files):
+    """DRAM bytes per launch of a kernel from its committed ncu summary (profiles/<name>.md),
+    or None when the kernel's sources have changed since the counters were taken."""
+    import hashlib
+    try:
+        text = open(os.path.join(ROOT, "profiles", name + ".md")).read()
+    except OSError:
+        return None
+    fields = dict(l.split(":", 1) for l in text.splitlines() if l.startswith(("traffic_bytes_per_launch:", "source_sha256:")))
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(f.encode() + b"\0" + fh.read())
+    if fields.get("source_sha256", "").split()[0:1] != [h.hexdigest()[:16]]:
+        return None
+    return float(fields["traffic_bytes_per_launch"])
+
+
+PLANE_SOURCES = ["paper_1406_7803_gb300/csrc/hpsi_ct.cuh", "paper_1406_7803_gb300/csrc/fftct.cuh",
+                 "paper_1406_7803_gb300/csrc/fft.cuh", "paper_1406_7803_gb300/csrc/common.cuh"]
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -295,8 +317,9 @@ def run_ours(args):
         if args.prec == "fp64":
             fp_peak = 1.25  # nominal FP64 rate of the part (TFLOP/s)
         achieved = flops_per_launch / sec / 1e12
+        traffic = _profile_traffic("k_plane_ct_molecule_on_slab", PLANE_SOURCES) if args.prec == "mixed" else None
         roof = {"bound": "alu", "achieved": achieved, "peak": fp_peak, "unit": "TFLOP/s", "frac": achieved / fp_peak,
-                "traffic": None, "kernel": "k_plane", "launches": n_plane,
+                "traffic": traffic, "kernel": "k_plane", "launches": n_plane,
                 "avg_launch_us": 1e6 * sec, "peak_source": f"{'FP32' if args.prec != 'fp64' else 'FP64'} lanes x "
                 f"clock ({'152 SMs x 128 lanes x 2 x sm_max' if args.prec != 'fp64' else 'nominal'}); "
                 f"HBM peak {peaks.get('hbm_gbs')} GB/s {src}",
@@ -326,7 +349,7 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
