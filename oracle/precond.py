@@ -14,7 +14,11 @@ follow beyond Eq. KS itself.  What it computes is fixed here:
   kinetic preconditioner exactly.
 * Training pairs come from converged eigensolves: for converged (psi_j, eps_j), a seeded
   smooth perturbation d_j orthogonal to the converged block gives r_j = (H - eps_j) d_j, and
-  the ideal correction of r_j is d_j.  Loss L = sum_j sum_G |m_jG r_jG - d_jG|^2 / |d_j|^2.
+  the ideal correction of r_j is d_j.  The block eigensolver's Rayleigh-Ritz step picks the
+  complex coefficient of every preconditioned residual itself, so only its direction
+  matters: L = sum_j min_a |a m_j r_j - d_j|^2 / |d_j|^2, minimised by
+  a_j = <m_j r_j, d_j> / |m_j r_j|^2 (L_j = 1 - cos^2 of the angle between m_j r_j and d_j).
+  By the envelope theorem dL/dm = 2 Re(conj(e) a r) / |d_j|^2 with e = a m r - d at that a.
 * Inference and training use weights rounded to bfloat16 (round to nearest even) with
   FP32 accumulation; the oracle evaluates the same rounded weights in FP64.
 
@@ -91,9 +95,18 @@ def apply(params, kin, tband, r):
     return multiplier(params, kin, tband, r) * r
 
 
+def best_scale(m, r, d):
+    """a_j = <m r_j, d_j> / |m r_j|^2 per band (0 where m r_j vanishes)."""
+    u = m * r
+    num = np.sum(np.conj(u) * d, axis=1)
+    den = np.sum(np.abs(u) ** 2, axis=1)
+    return np.where(den > 0, num / np.where(den > 0, den, 1.0), 0.0)
+
+
 def loss(params, kin, tband, r, d):
     m = multiplier(params, kin, tband, r)
-    e = m * r - d
+    a = best_scale(m, r, d)[:, None]
+    e = a * m * r - d
     return float(np.sum(np.sum(np.abs(e) ** 2, axis=1) / np.sum(np.abs(d) ** 2, axis=1)))
 
 
@@ -103,11 +116,12 @@ def backward(params, kin, tband, r, d):
     o, acts = forward(params, f)
     K = tpa(y)
     m = K * np.exp(o)
-    e = m * r - d
+    ar = best_scale(m, r, d)[:, None] * r
+    e = m * ar - d
     nd = np.sum(np.abs(d) ** 2, axis=1, keepdims=True)
     L = float(np.sum(np.sum(np.abs(e) ** 2, axis=1, keepdims=True) / nd))
-    # dL/dm = 2 Re(conj(e) r) / |d_j|^2 ; dm/do = m
-    g = (2.0 * np.real(np.conj(e) * r) / nd * m).reshape(-1, 1)
+    # dL/dm = 2 Re(conj(e) a r) / |d_j|^2 at the optimal a (envelope theorem); dm/do = m
+    g = (2.0 * np.real(np.conj(e) * ar) / nd * m).reshape(-1, 1)
     grads = [None] * len(params)
     for i in range(len(params) - 1, -1, -1):
         W, b = params[i]

@@ -1300,7 +1300,7 @@ template <typename T> struct EngineT : Engine {
   // ---- learned preconditioner ----------------------------------------------------------------
   DBuf<float> pw, pm1, pm2, pround, gpart;
   DBuf<unsigned short> pwb;
-  DBuf<double> gsum, dss;
+  DBuf<double> gsum, dss, awork;
   bool have_pw = false;
   int adam_step = 0;
   int precond_mode = FDE_PRECOND_TPA;
@@ -1431,7 +1431,9 @@ template <typename T> struct EngineT : Engine {
       Pairs& p = *pp;
       KP<T>& q = kpt(p.sub, p.k);
       gpart.ensure((size_t)precond_grad_blocks(p.n, q.npw) * (kPrecondParams + 1));
-      launch_precond_grad<T>(p.R.p, p.D.p, p.n, q.npw, q.kin_d.p, p.tb.p, p.ss.p, p.dn.p, pw.p, gpart.p, gsum.p, st);
+      awork.ensure(precond_alpha_work(p.n));
+      launch_precond_grad<T>(p.R.p, p.D.p, p.n, q.npw, q.kin_d.p, p.tb.p, p.ss.p, p.dn.p, pw.p, gpart.p, awork.p,
+                             gsum.p, st);
       CK(cudaMemcpyAsync(h.data(), gsum.p, (kPrecondParams + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
       for (int a = 0; a <= kPrecondParams; ++a) acc[a] += h[a];

@@ -1,7 +1,7 @@
 // fftct.cuh -- compile-time specialised mixed-radix Stockham transforms of many lines held
 // in shared memory, executed by a whole CTA.
 //
-// The length N of a line and its radix sequence (8, 9, 4, 3, 5, 2, largest first) are
+// The length N of a line and its radix sequence (9, 3, 5, then 8, 4, 2) are
 // template constants, so every index division and twiddle stride folds at compile time.
 // A stage works on the flattened set of (line, butterfly) items of a batch of lines: each
 // thread loads up to IPT butterflies into registers, the CTA synchronises, the permuted
@@ -21,14 +21,18 @@ struct CtPlan {
   int r[8];
 };
 
+// Radix order: the odd radices (9, 3, 5) first, then 8, 4, 2.  The first stage writes its
+// outputs R complex values apart; an odd R spreads a warp's stores over every shared-memory
+// bank, where R = 8 put them on 2 (float2) or 4 (double2) banks.  Later stages write runs of
+// Ns contiguous values.
 __host__ __device__ constexpr CtPlan ct_factor(int n) {
   CtPlan p{n, 0, {0, 0, 0, 0, 0, 0, 0, 0}};
   int m = n;
-  while (m % 8 == 0 && p.ns < 8) { p.r[p.ns++] = 8; m /= 8; }
   while (m % 9 == 0 && p.ns < 8) { p.r[p.ns++] = 9; m /= 9; }
-  while (m % 4 == 0 && p.ns < 8) { p.r[p.ns++] = 4; m /= 4; }
   while (m % 3 == 0 && p.ns < 8) { p.r[p.ns++] = 3; m /= 3; }
   while (m % 5 == 0 && p.ns < 8) { p.r[p.ns++] = 5; m /= 5; }
+  while (m % 8 == 0 && p.ns < 8) { p.r[p.ns++] = 8; m /= 8; }
+  while (m % 4 == 0 && p.ns < 8) { p.r[p.ns++] = 4; m /= 4; }
   while (m % 2 == 0 && p.ns < 8) { p.r[p.ns++] = 2; m /= 2; }
   if (m != 1) p.ns = -1;
   return p;

@@ -184,122 +184,147 @@ __global__ void k_vloc_g(double2* __restrict__ V, GridDims g, CellDev c, const d
 }
 
 // ---- pointwise functionals ------------------------------------------------------------------
-// Values with their derivatives along rho and sigma = |grad rho|^2 (forward-mode dual
-// numbers), so the potentials follow from the energy densities exactly.
-template <typename T> struct Dual {
-  T v, r, s;
+// Energy densities with their partial derivatives along rho and sigma = |grad rho|^2, in
+// closed form.  Every rho power comes from one cube root (rho^{1/3}, 1/rho^{1/3} = rho^{2/3}
+// / rho), and each chain-rule factor is written next to the quantity it differentiates, so
+// the potentials are the exact derivatives of the coded energy densities.
+struct Pt {
+  double rho, ir, r13, ir13;  // rho, 1/rho, rho^{1/3}, rho^{-1/3}
 };
-template <typename T> __device__ __forceinline__ Dual<T> dc(T v) { return {v, 0, 0}; }
-template <typename T> __device__ __forceinline__ Dual<T> operator+(Dual<T> a, Dual<T> b) { return {a.v + b.v, a.r + b.r, a.s + b.s}; }
-template <typename T> __device__ __forceinline__ Dual<T> operator-(Dual<T> a, Dual<T> b) { return {a.v - b.v, a.r - b.r, a.s - b.s}; }
-template <typename T> __device__ __forceinline__ Dual<T> operator*(Dual<T> a, Dual<T> b) {
-  return {a.v * b.v, a.r * b.v + a.v * b.r, a.s * b.v + a.v * b.s};
-}
-template <typename T> __device__ __forceinline__ Dual<T> operator/(Dual<T> a, Dual<T> b) {
-  const T iv = (T)1 / b.v, q = a.v * iv;
-  return {q, (a.r - q * b.r) * iv, (a.s - q * b.s) * iv};
-}
-template <typename T> __device__ __forceinline__ Dual<T> operator*(T k, Dual<T> a) { return {k * a.v, k * a.r, k * a.s}; }
-template <typename T> __device__ __forceinline__ Dual<T> operator+(T k, Dual<T> a) { return {k + a.v, a.r, a.s}; }
-template <typename T> __device__ __forceinline__ Dual<T> dlog(Dual<T> a) { const T iv = (T)1 / a.v; return {log(a.v), a.r * iv, a.s * iv}; }
-template <typename T> __device__ __forceinline__ Dual<T> dexp(Dual<T> a) { const T e = exp(a.v); return {e, a.r * e, a.s * e}; }
-template <typename T> __device__ __forceinline__ Dual<T> dsqrt(Dual<T> a) {
-  const T q = sqrt(a.v), h = (T)0.5 / q;
-  return {q, a.r * h, a.s * h};
-}
-template <typename T> __device__ __forceinline__ Dual<T> dpow(Dual<T> a, T p) {
-  const T q = pow(a.v, p), d = p * q / a.v;
-  return {q, a.r * d, a.s * d};
+__device__ __forceinline__ Pt make_pt(double rho) {
+  Pt p;
+  p.rho = rho;
+  p.ir = 1.0 / rho;
+  p.r13 = cbrt(rho);
+  p.ir13 = p.r13 * p.r13 * p.ir;
+  return p;
 }
 
-// Slater exchange + PW92 correlation energy per volume of the uniform gas at rho.
-template <typename T> __device__ __forceinline__ Dual<T> lda_xc(Dual<T> rho, Dual<T>* eps_c_out) {
-  const T third = (T)(1.0 / 3.0);
-  const Dual<T> ex = (T)(-0.75 * 0.98474502184269654) * dpow(rho, (T)(4.0 / 3.0));  // (3/pi)^{1/3}
-  // rs = (3 / (4 pi rho))^{1/3} with derivative through rho
-  const Dual<T> rsd = dpow(dc<T>((T)(3.0 / (4.0 * M_PI))) / rho, third);
-  const T A = (T)0.031091, a1 = (T)0.21370;
-  const T b1 = (T)7.5957, b2 = (T)3.5876, b3 = (T)1.6382, b4 = (T)0.49294;
-  const Dual<T> srs = dsqrt(rsd);
-  const Dual<T> den = ((T)2 * A) * (b1 * srs + b2 * rsd + b3 * (rsd * srs) + b4 * (rsd * rsd));
-  const Dual<T> ec = ((T)-2 * A) * (((T)1 + a1 * rsd) * dlog((T)1 + dc<T>(1) / den));
-  *eps_c_out = ec;
-  return ex + rho * ec;
+// Slater exchange of the uniform gas per volume, e_x = C_x rho^{4/3}, and its rho derivative.
+constexpr double kCx = -0.75 * 0.98474502184269654;  // -(3/4)(3/pi)^{1/3}
+__device__ __forceinline__ void slater(const Pt& p, double* e, double* de) {
+  *e = kCx * p.rho * p.r13;
+  *de = (4.0 / 3.0) * kCx * p.r13;
 }
 
-template <typename T> __device__ __forceinline__ Dual<T> pbe_xc(Dual<T> rho, Dual<T> sig) {
-  const T kappa = (T)0.804, mu = (T)0.2195149727645171;
-  const T beta = (T)0.06672455060314922, gamma = (T)((1.0 - 0.69314718055994530942) / (M_PI * M_PI));
-  Dual<T> ec;
-  const Dual<T> ex_unif = (T)(-0.75 * 0.98474502184269654) * dpow(rho, (T)(4.0 / 3.0));
-  (void)lda_xc(rho, &ec);
-  const Dual<T> kf = dpow((T)(3.0 * M_PI * M_PI) * rho, (T)(1.0 / 3.0));
-  const Dual<T> s2 = sig / ((T)4 * (kf * kf * rho * rho));
-  const Dual<T> fx = ((T)1 + kappa) + dc<T>(0) - kappa * (dc<T>(1) / ((T)1 + (mu / kappa) * s2));
-  const Dual<T> ks = dsqrt((T)(4.0 / M_PI) * kf);
-  const Dual<T> t2 = sig / ((T)4 * (ks * ks * rho * rho));
-  const T bg = beta / gamma;
-  const Dual<T> Aa = bg * (dc<T>(1) / (dexp(((T)-1 / gamma) * ec) - dc<T>(1)));
-  const Dual<T> At2 = Aa * t2;
-  const Dual<T> H = gamma * dlog((T)1 + bg * (t2 * (((T)1 + At2) / ((T)1 + At2 + At2 * At2))));
-  return ex_unif * fx + rho * (ec + H);
+// PW92 correlation energy per particle of the unpolarised gas, eps_c(r_s), and d eps_c / d rho.
+// r_s = (3 / (4 pi rho))^{1/3};  eps_c = -2A (1 + a1 r_s) ln(1 + 1/D),
+// D = 2A (b1 r_s^{1/2} + b2 r_s + b3 r_s^{3/2} + b4 r_s^2).
+__device__ __forceinline__ void pw92(const Pt& p, double* ec, double* dec) {
+  const double A = 0.031091, a1 = 0.21370, b1 = 7.5957, b2 = 3.5876, b3 = 1.6382, b4 = 0.49294;
+  const double rs = 0.62035049089940001667 * p.ir13;  // (3/(4 pi))^{1/3}
+  const double srs = sqrt(rs);
+  const double D = 2.0 * A * (b1 * srs + b2 * rs + b3 * rs * srs + b4 * rs * rs);
+  const double dD = 2.0 * A * (0.5 * b1 / srs + b2 + 1.5 * b3 * srs + 2.0 * b4 * rs);  // dD/dr_s
+  const double iD = 1.0 / D;
+  const double L = log1p(iD);
+  const double dL = -iD * iD / (1.0 + iD);  // d ln(1 + 1/D) / dD
+  *ec = -2.0 * A * (1.0 + a1 * rs) * L;
+  const double dec_drs = -2.0 * A * (a1 * L + (1.0 + a1 * rs) * dL * dD);
+  *dec = dec_drs * (-rs * p.ir / 3.0);  // d r_s / d rho = -r_s / (3 rho)
+}
+
+// PBE exchange-correlation energy per volume e(rho, sigma) with e_rho, e_sigma:
+//   e = e_x^unif F_x(s) + rho (eps_c + H),  F_x = 1 + kappa - kappa / (1 + mu s^2 / kappa),
+//   s^2 = sigma / (4 k_F^2 rho^2),  k_F = (3 pi^2 rho)^{1/3},
+//   H = gamma ln(1 + (beta/gamma) t^2 (1 + A t^2) / (1 + A t^2 + A^2 t^4)),
+//   t^2 = sigma / (4 k_s^2 rho^2),  k_s^2 = 4 k_F / pi,  A = (beta/gamma) / (exp(-eps_c/gamma) - 1).
+__device__ __forceinline__ void pbe(const Pt& p, double sig, double* e, double* er, double* es) {
+  const double kappa = 0.804, mu = 0.2195149727645171;
+  const double beta = 0.06672455060314922, gamma = (1.0 - 0.69314718055994530942) / (M_PI * M_PI);
+  const double bg = beta / gamma;
+  const double ckf = 3.0936677262801359310;  // (3 pi^2)^{1/3}
+  double ex, dex, ec, dec;
+  slater(p, &ex, &dex);
+  pw92(p, &ec, &dec);
+  const double ir2 = p.ir * p.ir;
+  // s^2 = sigma / (4 ckf^2) rho^{-8/3}
+  const double s2_s = ir2 * p.ir13 * p.ir13 / (4.0 * ckf * ckf);  // d s^2 / d sigma
+  const double s2 = sig * s2_s;
+  const double u = 1.0 + mu * s2 / kappa, iu = 1.0 / u;
+  const double Fx = 1.0 + kappa - kappa * iu;
+  const double dFx = mu * iu * iu;  // dF_x / d s^2
+  // t^2 = sigma pi / (16 ckf) rho^{-7/3}
+  const double t2_s = ir2 * p.ir13 * (M_PI / (16.0 * ckf));  // d t^2 / d sigma
+  const double t2 = sig * t2_s;
+  const double em1 = expm1(-ec / gamma);
+  const double Aa = bg / em1;
+  const double dA = Aa * Aa * (em1 + 1.0) / (bg * gamma);  // dA / d eps_c
+  const double x = Aa * t2;
+  const double Dn = 1.0 + x + x * x, iDn = 1.0 / Dn;
+  const double P = (1.0 + x) * iDn;
+  const double dP = -x * (2.0 + x) * iDn * iDn;  // dP / dx
+  const double Q = bg * t2 * P;
+  const double H = gamma * log1p(Q);
+  const double dHdQ = gamma / (1.0 + Q);
+  const double dQ_t2 = bg * (P + t2 * Aa * dP);  // dQ / dt^2 at fixed A
+  const double dQ_A = bg * t2 * t2 * dP;         // dQ / dA at fixed t^2
+  *e = ex * Fx + p.rho * (ec + H);
+  // rho derivatives: d s^2/d rho = -(8/3) s^2 / rho, d t^2/d rho = -(7/3) t^2 / rho
+  const double dH_r = dHdQ * (dQ_t2 * (-7.0 / 3.0) * t2 * p.ir + dQ_A * dA * dec);
+  *er = dex * Fx + ex * dFx * (-8.0 / 3.0) * s2 * p.ir + ec + H + p.rho * (dec + dH_r);
+  *es = ex * dFx * s2_s + p.rho * dHdQ * dQ_t2 * t2_s;
 }
 
 // Kinetic enhancement factors F(s) and F'(s).
-template <typename T> __device__ __forceinline__ void kedf_F(int kind, T s, T* F, T* dF) {
+__device__ __forceinline__ void kedf_F(int kind, double s, double* F, double* dF) {
   if (kind == 0) { *F = 1; *dF = 0; return; }
   if (kind == 1) {  // revAPBEK
-    const T k = (T)1.245, mu = (T)0.23889;
-    const T d = (T)1 + mu * s * s / k;
-    *F = (T)1 + k - k / d;
-    *dF = (T)2 * mu * s / (d * d);
+    const double k = 1.245, mu = 0.23889;
+    const double id = 1.0 / (1.0 + mu * s * s / k);
+    *F = 1.0 + k - k * id;
+    *dF = 2.0 * mu * s * id * id;
     return;
   }
   // LC94 (PW91 form)
-  const T a = (T)0.093907, b = (T)76.32, c = (T)0.26608, dd = (T)-0.0809615, al = (T)100, f = (T)0.000057767;
-  const T ash = asinh(b * s), ex = exp(-al * s * s);
-  const T num = (T)1 + a * s * ash + (c + dd * ex) * s * s;
-  const T den = (T)1 + a * s * ash + f * s * s * s * s;
-  const T dash = a * ash + a * s * b / sqrt((T)1 + b * b * s * s);
-  const T dnum = dash + (T)2 * s * (c + dd * ex) - (T)2 * al * dd * s * s * s * ex;
-  const T dden = dash + (T)4 * f * s * s * s;
-  *F = num / den;
-  *dF = (dnum * den - num * dden) / (den * den);
+  const double a = 0.093907, b = 76.32, c = 0.26608, dd = -0.0809615, al = 100, f = 0.000057767;
+  const double ash = asinh(b * s), ex = exp(-al * s * s);
+  const double num = 1.0 + a * s * ash + (c + dd * ex) * s * s;
+  const double den = 1.0 + a * s * ash + f * s * s * s * s;
+  const double dash = a * ash + a * s * b / sqrt(1.0 + b * b * s * s);
+  const double dnum = dash + 2.0 * s * (c + dd * ex) - 2.0 * al * dd * s * s * s * ex;
+  const double dden = dash + 4.0 * f * s * s * s;
+  const double iden = 1.0 / den;
+  *F = num * iden;
+  *dF = (dnum - num * iden * dden) * iden;
 }
 
 // One point of a functional evaluation.  xc_mode: -1 none, 0 LDA, 1 PBE.  kedf: -1 none,
 // 0 TF, 1 revAPBEK, 2 LC94.  Returns the local potential part (d e/d rho of both), the
 // coefficient multiplying grad rho in the divergence term, and the two energy densities.
-template <typename T>
-__device__ __forceinline__ void point_functional(T rho, T gx, T gy, T gz, int xc_mode, int xc_pot, int kedf,
-                                                 T rho_cut, T* vloc, T* hcoef, double* exc, double* ekin) {
+__device__ __forceinline__ void point_functional(double rho, double gx, double gy, double gz, int xc_mode,
+                                                 int xc_pot, int kedf, double rho_cut, double* vloc, double* hcoef,
+                                                 double* exc, double* ekin) {
   *vloc = 0; *hcoef = 0; *exc = 0; *ekin = 0;
   if (!(rho >= rho_cut)) return;
-  const T sig = gx * gx + gy * gy + gz * gz;
+  const double sig = gx * gx + gy * gy + gz * gz;
+  const Pt p = make_pt(rho);
   if (xc_mode == 0) {
-    Dual<T> ec;
-    const Dual<T> e = lda_xc(Dual<T>{rho, 1, 0}, &ec);
-    if (xc_pot) *vloc += e.r;
-    *exc = e.v;
+    double ex, dex, ec, dec;
+    slater(p, &ex, &dex);
+    pw92(p, &ec, &dec);
+    if (xc_pot) *vloc += dex + ec + rho * dec;
+    *exc = ex + rho * ec;
   } else if (xc_mode == 1) {
-    const Dual<T> e = pbe_xc(Dual<T>{rho, 1, 0}, Dual<T>{sig, 0, 1});
+    double e, er, es;
+    pbe(p, sig, &e, &er, &es);
     if (xc_pot) {
-      *vloc += e.r;
-      *hcoef += (T)2 * e.s;
+      *vloc += er;
+      *hcoef += 2.0 * es;
     }
-    *exc = e.v;
+    *exc = e;
   }
   if (kedf >= 0) {
-    const T ctf = (T)2.8712340001881918;   // (3/10)(3 pi^2)^{2/3}
-    const T cs = (T)0.16162045967399548;   // 1 / (2 (3 pi^2)^{1/3})
-    const T r13 = cbrt(rho), r23 = r13 * r13, r43 = rho * r13;
-    const T gn = sqrt(sig);
-    const T s = cs * gn / r43;
-    T F, dF;
-    kedf_F<T>(kedf, s, &F, &dF);
-    *ekin = (double)(ctf * rho * r23 * F);
-    *vloc += ctf * r23 * ((T)(5.0 / 3.0) * F - (T)(4.0 / 3.0) * s * dF);
-    if (kedf > 0) *hcoef += ctf * cs * r13 * dF / (gn > (T)1e-30 ? gn : (T)1e-30);
+    const double ctf = 2.8712340001881918;   // (3/10)(3 pi^2)^{2/3}
+    const double cs = 0.16162045967399548;   // 1 / (2 (3 pi^2)^{1/3})
+    const double r23 = p.r13 * p.r13;
+    const double gn = sqrt(sig);
+    const double s = cs * gn * p.ir * p.ir13;  // cs |grad rho| / rho^{4/3}
+    double F, dF;
+    kedf_F(kedf, s, &F, &dF);
+    *ekin = ctf * rho * r23 * F;
+    *vloc += ctf * r23 * ((5.0 / 3.0) * F - (4.0 / 3.0) * s * dF);
+    if (kedf > 0) *hcoef += ctf * cs * p.r13 * dF / (gn > 1e-30 ? gn : 1e-30);
   }
 }
 
@@ -321,7 +346,7 @@ __global__ void k_pointwise(const double* __restrict__ rho, cplx<T>* gx, cplx<T>
     if (gx) { x = (double)gx[idx].x; y = (double)gy[idx].x; z = (double)gz[idx].x; }
     double v, h;
     double ex, ek;
-    point_functional<double>(r, x, y, z, xc_mode, xc_pot, kedf, rho_cut, &v, &h, &ex, &ek);
+    point_functional(r, x, y, z, xc_mode, xc_pot, kedf, rho_cut, &v, &h, &ex, &ek);
     if (vpart) vpart[idx] = v;
     if (gx) {
       gx[idx] = mk<T>((T)(h * x), 0);
@@ -512,7 +537,7 @@ __global__ void k_pw_total(const double* __restrict__ rho, GradPacks gp, int xc_
       }
     }
     double v, h, ex, ek;
-    point_functional<double>(rho[idx], x, y, z, xc_mode, 1, kedf, rho_cut, &v, &h, &ex, &ek);
+    point_functional(rho[idx], x, y, z, xc_mode, 1, kedf, rho_cut, &v, &h, &ex, &ek);
     if (vpart) vpart[idx] = v;
     if (hx) {
       hx[idx] = h * x;
@@ -545,12 +570,12 @@ __global__ void k_pw_pair(const double* __restrict__ ra, const double* __restric
       if (has_b) pb = Pb[idx];
     }
     double va, ha, ex, ek;
-    point_functional<double>(ra[idx], pa.x, pa.y, pz.x, xc_mode, 0, kedf, rho_cut, &va, &ha, &ex, &ek);
+    point_functional(ra[idx], pa.x, pa.y, pz.x, xc_mode, 0, kedf, rho_cut, &va, &ha, &ex, &ek);
     xa += ex;
     ka += ek;
     double vb = 0, hb = 0;
     if (has_b) {
-      point_functional<double>(rb[idx], pb.x, pb.y, pz.y, xc_mode, 0, kedf, rho_cut, &vb, &hb, &ex, &ek);
+      point_functional(rb[idx], pb.x, pb.y, pz.y, xc_mode, 0, kedf, rho_cut, &vb, &hb, &ex, &ek);
       xb += ex;
       kb += ek;
     }

@@ -117,8 +117,10 @@ k_zfwd_ct(const __grid_constant__ HpsiBatch<T> B, T inv_nr, const cplx<T>* __res
 
 // One CTA per (item, band, z-plane): columns in, 2D inverse FFT (y on the rows holding
 // columns, then x), potential multiply, 2D forward FFT, columns out.  n1 = n2 = N.
+// Four FP32 CTAs per SM (42 KB of shared memory each for a 72 x 72 plane) need <= 64
+// registers per thread; FP64 planes (84 KB) fit two.
 template <typename T, int N>
-__global__ void __launch_bounds__(kCtThreads)
+__global__ void __launch_bounds__(kCtThreads, sizeof(T) == 4 ? 4 : 2)
 k_plane_ct(const __grid_constant__ HpsiBatch<T> B, int n3, const cplx<T>* __restrict__ tw1,
            const cplx<T>* __restrict__ tw2) {
   using C = cplx<T>;

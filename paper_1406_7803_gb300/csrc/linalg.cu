@@ -61,17 +61,35 @@ k_gemm_hn_partial(const cplx<T>* __restrict__ A, int lda, const cplx<T>* __restr
     }
 }
 
-__global__ void k_gemm_hn_reduce(const double2* __restrict__ part, int nsplit, int m, int n, double2* C, int ldc) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= m * n) return;
+// Sum of the K-split partial tiles: a CTA owns 32 consecutive outputs (one per lane, so
+// every split's row segment is one coalesced 512-byte read); warp w sums the splits
+// s = w, w + 8, ..., and the eight warp sums are added in warp order (fixed order: the
+// result does not depend on scheduling).
+__global__ void __launch_bounds__(256)
+k_gemm_hn_reduce(const double2* __restrict__ part, int nsplit, int m, int n, double2* C, int ldc) {
+  __shared__ double2 acc[8][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long long mn = (long long)m * n;
+  const long long idx = (long long)blockIdx.x * 32 + lane;
   double re = 0, im = 0;
-  for (int s = 0; s < nsplit; ++s) {
-    const double2 v = part[(size_t)s * m * n + idx];
-    re += v.x;
-    im += v.y;
+  if (idx < mn)
+    for (int s = w; s < nsplit; s += 8) {
+      const double2 v = part[(size_t)s * mn + idx];
+      re += v.x;
+      im += v.y;
+    }
+  acc[w][lane] = make_double2(re, im);
+  __syncthreads();
+  if (w == 0 && idx < mn) {
+    double2 t = acc[0][lane];
+#pragma unroll
+    for (int q = 1; q < 8; ++q) {
+      t.x += acc[q][lane].x;
+      t.y += acc[q][lane].y;
+    }
+    const int i = (int)(idx / n), j = (int)(idx % n);
+    C[(size_t)i * ldc + j] = t;
   }
-  const int i = idx / n, j = idx % n;
-  C[(size_t)i * ldc + j] = make_double2(re, im);
 }
 
 static int gemm_hn_splits(int m, int n, int K) {
@@ -99,7 +117,7 @@ int gemm_hn_path() { return g_gemm_path; }
 
 void launch_gemm_hn_reduce(const double2* part, int nsplit, int m, int n, double2* C, int ldc, cudaStream_t st) {
   count_launches(1);
-  k_gemm_hn_reduce<<<ceil_div((long long)m * n, 256), 256, 0, st>>>(part, nsplit, m, n, C, ldc);
+  k_gemm_hn_reduce<<<ceil_div((long long)m * n, 32), 256, 0, st>>>(part, nsplit, m, n, C, ldc);
 }
 
 template <typename T>
@@ -130,7 +148,7 @@ void launch_gemm_hn(const cplx<T>* A, int lda, const cplx<T>* B, int ldb, int m,
   count_launches(1);
   k_gemm_hn_partial<T, T><<<grid, 256, 0, st>>>(A, lda, B, ldb, m, n, K, kchunk, work);
   count_launches(1);
-  k_gemm_hn_reduce<<<ceil_div((long long)m * n, 256), 256, 0, st>>>(work, grid.z, m, n, C, ldc);
+  k_gemm_hn_reduce<<<ceil_div((long long)m * n, 32), 256, 0, st>>>(work, grid.z, m, n, C, ldc);
 }
 
 // ---- Y = alpha * U^T-combination of rows of X + beta * Y -----------------------------------

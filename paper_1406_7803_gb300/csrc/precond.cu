@@ -4,8 +4,11 @@
 // y = |k+G|^2/2 / T_j, and o = MLP(f) a per-G network of three tanh layers of width 64 and
 // a linear output on f = (log(1 + y), log T_j, |R_jG| / rms_G |R_j|).  Inference reads
 // bfloat16 weights and accumulates in FP32; training keeps FP32 master weights, evaluates
-// the loss sum_j sum_G |m R - D|^2 / |D_j|^2 and its gradient with per-block partial sums
-// reduced in a fixed order, and takes Adam steps.
+// the loss sum_j min_a |a m R_j - D_j|^2 / |D_j|^2 (a complex: the eigensolver's Rayleigh-Ritz
+// step rescales each preconditioned residual, so only its direction counts) and its gradient
+// with per-block partial sums reduced in a fixed order, and takes Adam steps.  The optimal
+// a_j = <m R_j, D_j> / |m R_j|^2 comes from a first pass; by the envelope theorem the
+// gradient of the minimised loss is that of |a m R - D|^2 at fixed a.
 #include <cuda_bf16.h>
 #include <math.h>
 
@@ -96,6 +99,60 @@ k_precond_apply(const cplx<T>* __restrict__ R, int ldr, const T* __restrict__ ki
   }
 }
 
+// Per-band sums for the optimal scale a_j: <m R_j, D_j> (re, im) and |m R_j|^2 with the FP32
+// master weights; CTA (b, j) strides over G, block sums in a fixed order into
+// part[(j * kAlphaBlocks + b) * 3 + {0, 1, 2}].
+constexpr int kAlphaBlocks = 32;
+constexpr int kAlphaThreads = 128;
+template <typename T>
+__global__ void __launch_bounds__(kAlphaThreads)
+k_precond_alpha(const cplx<T>* __restrict__ R, const cplx<T>* __restrict__ D, int K, const T* __restrict__ kin,
+                const double* __restrict__ tband, const double* __restrict__ sumsq, const float* __restrict__ wf,
+                double* __restrict__ part) {
+  __shared__ __align__(16) float w[kPrecondParams + 3];
+  __shared__ double red[3][kAlphaThreads];
+  load_weights(w, nullptr, wf);
+  const int j = blockIdx.y;
+  const float tb = (float)tband[j];
+  const float rms = (float)sqrt(sumsq[j] / (double)K);
+  double cr = 0, ci = 0, nn = 0;
+  for (int g = blockIdx.x * kAlphaThreads + threadIdx.x; g < K; g += kAlphaBlocks * kAlphaThreads) {
+    const cplx<T> r = R[(size_t)j * K + g], d = D[(size_t)j * K + g];
+    const float rx = (float)r.x, ry = (float)r.y;
+    float f[3], y;
+    features((float)kin[g], tb, sqrtf(rx * rx + ry * ry), rms, f, &y);
+    float ha[kH], hb[kH];
+    const float m = tpa_f(y) * expf(mlp_forward(w, f, ha, hb, ha));
+    cr += (double)(m * (rx * (float)d.x + ry * (float)d.y));
+    ci += (double)(m * (rx * (float)d.y - ry * (float)d.x));
+    nn += (double)(m * m * (rx * rx + ry * ry));
+  }
+  red[0][threadIdx.x] = cr;
+  red[1][threadIdx.x] = ci;
+  red[2][threadIdx.x] = nn;
+  __syncthreads();
+  for (int h = kAlphaThreads / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h)
+      for (int c = 0; c < 3; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x < 3) part[((size_t)j * kAlphaBlocks + blockIdx.x) * 3 + threadIdx.x] = red[threadIdx.x][0];
+}
+// a_j = <m R_j, D_j> / |m R_j|^2 (0 when m R_j vanishes); alpha[2 j], alpha[2 j + 1].
+__global__ void k_precond_alpha_fin(const double* __restrict__ part, int nb, double* __restrict__ alpha) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nb) return;
+  double cr = 0, ci = 0, nn = 0;
+  for (int b = 0; b < kAlphaBlocks; ++b) {
+    const double* q = part + ((size_t)j * kAlphaBlocks + b) * 3;
+    cr += q[0];
+    ci += q[1];
+    nn += q[2];
+  }
+  alpha[2 * j] = nn > 0 ? cr / nn : 0.0;
+  alpha[2 * j + 1] = nn > 0 ? ci / nn : 0.0;
+}
+
 // Loss and gradient: one CTA of kGradBlock threads handles kGradBlock elements (rows of
 // (band j, G)); per-block partial gradients go to part[blk][0..kPrecondParams), the partial
 // loss to part[blk][kPrecondParams].  Activations and back-propagated errors live in
@@ -109,7 +166,8 @@ template <typename T>
 __global__ void __launch_bounds__(kGradBlock)
 k_precond_grad(const cplx<T>* __restrict__ R, const cplx<T>* __restrict__ D, int K, int nb,
                const T* __restrict__ kin, const double* __restrict__ tband, const double* __restrict__ sumsq,
-               const double* __restrict__ dnorm2, const float* __restrict__ wf, float* __restrict__ part) {
+               const double* __restrict__ dnorm2, const double* __restrict__ alpha, const float* __restrict__ wf,
+               float* __restrict__ part) {
   extern __shared__ __align__(16) float smem[];
   float* w = smem;
   float* base = smem + ((kPrecondParams + 3 + 3) / 4) * 4;
@@ -153,10 +211,13 @@ k_precond_grad(const cplx<T>* __restrict__ R, const cplx<T>* __restrict__ D, int
     float o = w[ob4];
     for (int k = 0; k < kH; ++k) o += w[oW4 + k] * h3[k];
     const float m = tpa_f(y) * expf(o);
-    const float ex = m * rx - (float)d.x, ey = m * ry - (float)d.y;
+    // a r (complex product), e = m a r - d; dL/dm = 2 Re(conj(e) a r) / |d_j|^2
+    const float ax = (float)alpha[2 * j], ay = (float)alpha[2 * j + 1];
+    const float qx = ax * rx - ay * ry, qy = ax * ry + ay * rx;
+    const float ex = m * qx - (float)d.x, ey = m * qy - (float)d.y;
     const float nd = (float)dnorm2[j];
     lo = (ex * ex + ey * ey) / nd;
-    go = 2.f * (ex * rx + ey * ry) / nd * m;
+    go = 2.f * (ex * qx + ey * qy) / nd * m;
   } else {
     for (int i = 0; i < kH; ++i) h1[i] = h2[i] = h3[i] = 0.f;
   }
@@ -254,14 +315,18 @@ void launch_precond_apply(const cplx<T>* R, int ldr, const T* kin, const double*
 
 int precond_grad_blocks(int nb, int K) { return ceil_div((long long)nb * K, kGradBlock); }
 
+size_t precond_alpha_work(int nb) { return (size_t)nb * kAlphaBlocks * 3 + 2 * (size_t)nb; }
 template <typename T>
 void launch_precond_grad(const cplx<T>* R, const cplx<T>* D, int nb, int K, const T* kin, const double* tband,
-                         const double* sumsq, const double* dnorm2, const float* wf, float* part, double* out,
-                         cudaStream_t st) {
+                         const double* sumsq, const double* dnorm2, const float* wf, float* part, double* awork,
+                         double* out, cudaStream_t st) {
   const int nblk = precond_grad_blocks(nb, K);
+  double* alpha = awork + (size_t)nb * kAlphaBlocks * 3;
   cudaFuncSetAttribute(k_precond_grad<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGradSmem);
-  count_launches(2);
-  k_precond_grad<T><<<nblk, kGradBlock, kGradSmem, st>>>(R, D, K, nb, kin, tband, sumsq, dnorm2, wf, part);
+  count_launches(4);
+  k_precond_alpha<T><<<dim3(kAlphaBlocks, nb), kAlphaThreads, 0, st>>>(R, D, K, kin, tband, sumsq, wf, awork);
+  k_precond_alpha_fin<<<ceil_div(nb, 128), 128, 0, st>>>(awork, nb, alpha);
+  k_precond_grad<T><<<nblk, kGradBlock, kGradSmem, st>>>(R, D, K, nb, kin, tband, sumsq, dnorm2, alpha, wf, part);
   k_precond_reduce<<<ceil_div(kPrecondParams + 1, 256), 256, 0, st>>>(part, nblk, out);
 }
 
@@ -284,8 +349,10 @@ template void launch_precond_apply<float>(const float2*, int, const float*, cons
 template void launch_precond_apply<double>(const double2*, int, const double*, const double*, const double*, int, int,
                                            const void*, double2*, int, cudaStream_t);
 template void launch_precond_grad<float>(const float2*, const float2*, int, int, const float*, const double*,
-                                         const double*, const double*, const float*, float*, double*, cudaStream_t);
+                                         const double*, const double*, const float*, float*, double*, double*,
+                                         cudaStream_t);
 template void launch_precond_grad<double>(const double2*, const double2*, int, int, const double*, const double*,
-                                          const double*, const double*, const float*, float*, double*, cudaStream_t);
+                                          const double*, const double*, const float*, float*, double*, double*,
+                                          cudaStream_t);
 
 }  // namespace fde

@@ -24,11 +24,15 @@ OUT = os.path.join(HERE, "ft_cycle_molecule_on_slab_small.json")
 KEYS = ("F_fde", "E_fde", "E_kin", "E_nl", "E_loc", "E_H", "E_xc", "T_nad", "TS")
 
 
+# The oracle modules the freeze-and-thaw cycle runs (the learned-preconditioner oracle is not
+# among them).
+CYCLE_MODULES = ("__init__.py", "basis.py", "fde.py", "functionals.py", "potentials.py", "scf.py")
+
+
 def oracle_digest() -> str:
-    """SHA-256 over the oracle's Python sources and the workload generator, in name order."""
+    """SHA-256 over the oracle sources of the cycle and the workload generator, in name order."""
     h = hashlib.sha256()
-    files = sorted(f for f in os.listdir(os.path.join(ROOT, "oracle")) if f.endswith(".py"))
-    for f in files:
+    for f in CYCLE_MODULES:
         with open(os.path.join(ROOT, "oracle", f), "rb") as fh:
             h.update(f.encode() + b"\0" + fh.read())
     with open(os.path.join(ROOT, "paper_1406_7803_gb300", "workloads.py"), "rb") as fh:

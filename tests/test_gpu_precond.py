@@ -112,14 +112,17 @@ def _solve_all(ctx, wl, precond, tol):
 
 
 def test_trained_network_gain_over_kinetic_preconditioner():
-    """Train on pairs harvested from converged solves of the molecule-on-slab cell, then
-    solve the same eigenproblems from the same seeded start with both preconditioners:
-    identical eigenvalues (the answer does not change); the iteration counts are the gain."""
+    """Train on (residual, error) pairs recorded over whole eigensolves of the molecule-on-slab
+    cell, then solve the same eigenproblems from the same seeded start with both
+    preconditioners: identical eigenvalues (the answer does not change); the iteration counts
+    are the gain.  Pairs from the first iterates only (8 per solve) teach the network the
+    early error spectrum and it then slows the late iterations; pairs over the whole
+    trajectory do not."""
     wl = workloads.molecule_on_slab_small()
     ctx = fde.context_from_workload(wl)
     fde.seed_workload(ctx, wl)
     ctx.build_vemb()
-    ctx.precond_record(8)  # (residual, error) pairs of the first iterations of every solve
+    ctx.precond_record(60)  # (residual, error) pairs of every iteration of every solve
     it_tpa, e_tpa = _solve_all(ctx, wl, fde.FDE_PRECOND_TPA, 1e-8)
     ctx.precond_record(0)
     ctx.precond_set_weights(_flat(opre.init_params(0)))

@@ -67,3 +67,25 @@ def test_training_pairs_are_residuals_of_the_ideal_correction():
     H = sy.dense_h(1, 0, pot["veff"][1])
     want = (H @ d.T).T - w[:3, None] * d
     assert np.abs(r - want).max() < 1e-11
+
+
+def test_loss_is_the_squared_sine_of_the_angle_and_scale_free():
+    """L_j = 1 - |<m r_j, d_j>|^2 / (|m r_j|^2 |d_j|^2): zero when m r_j is parallel to d_j
+    (whatever the complex factor), unchanged when r_j is multiplied by a complex scalar."""
+    rng = np.random.default_rng(4)
+    kin = rng.uniform(0, 10, 30)
+    r = rng.standard_normal((3, 30)) + 1j * rng.standard_normal((3, 30))
+    d = rng.standard_normal((3, 30)) + 1j * rng.standard_normal((3, 30))
+    tb = np.array([0.9, 1.7, 3.2])
+    p = precond.init_params(6)
+    p[-1][0] = 0.2 * rng.standard_normal(p[-1][0].shape)
+    m = precond.multiplier(p, kin, tb, r)
+    u = m * r
+    cos2 = np.abs(np.sum(np.conj(u) * d, axis=1)) ** 2 / (np.sum(np.abs(u) ** 2, axis=1) * np.sum(np.abs(d) ** 2, axis=1))
+    assert np.isclose(precond.loss(p, kin, tb, r, d), float(np.sum(1.0 - cos2)), rtol=1e-12)
+    # d parallel to m r (complex factor 2 - 3i): zero loss
+    assert precond.loss(p, kin, tb, r, (2 - 3j) * u) < 1e-24
+    # the multiplier depends on |r| / rms|r| only, so a complex rescaling of a band's residual
+    # leaves m and hence the loss unchanged
+    s = np.array([[0.5 + 2j], [-3.0], [1j]])
+    assert np.isclose(precond.loss(p, kin, tb, s * r, d), precond.loss(p, kin, tb, r, d), rtol=1e-12)
