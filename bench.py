@@ -10,8 +10,12 @@ One step = one pass of the hot path over the whole cell: the embedding-potential
 divergence, assembly of V_eff^I) followed by H_I psi for every band of every (subsystem,
 k-point): 4 x 64 + 12 = 268 band-applies.  value = band-applies per second over all ranks.
 
+Second part of the metric (N = 1, skipped with --no-ft): seconds per freeze-and-thaw cycle
+at 1e-6 Ha on the same cell, mixed precision (with and without the learned preconditioner)
+against the plain FP64 GPU path ("ft_cycle" in the JSON line).
+
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--prec mixed|fp64]
-                       [--impl ours|reference]
+                       [--impl ours|reference] [--no-cpu] [--no-ft]
 """
 from __future__ import annotations
 
@@ -155,6 +159,57 @@ def cpu_baseline(wl, max_seconds=15.0):
             "sample": f"one FP64 v_eff build ({t_veff:.2f} s) + {done} slab band-applies "
                       f"({t_band * 1e3:.1f} ms each, scipy.fft workers={cores}), extrapolated to "
                       f"{units} band-applies per step; setup {t1 - t0:.1f} s excluded"}
+
+
+def ft_cycles(tol=1e-6):
+    """Seconds per freeze-and-thaw cycle on the molecule-on-slab cell at tol Ha: the mixed path
+    (FP32 cycle, FP64 refinement), the plain FP64 GPU path, and the mixed path with the
+    learned preconditioner in its FP32 stage (network trained on the GPU on (residual, error)
+    pairs recorded over the eigensolves of the 8x8x20 bohr slab + molecule cell).  Every run
+    starts from the same seeded orbitals and densities; wall time of the synchronising call."""
+    import torch
+    from paper_1406_7803_gb300 import fde
+    out = {"tol_ha": tol}
+    # learned weights from the small cell
+    small = workloads.molecule_on_slab_small()
+    cs = fde.context_from_workload(small, prec="mixed")
+    fde.seed_workload(cs, small)
+    cs.build_vemb()
+    cs.precond_record(60)
+    t0 = time.perf_counter()
+    for I, s in enumerate(small.subsystems):
+        for k in range(s.nk):
+            cs.subspace_solve(I, k, 3e-5, 300, fde.FDE_PRECOND_TPA)  # the FP32 solves' residual floor
+    cs.precond_record(0)
+    cs.precond_set_weights(fde.precond_initial_weights(0))
+    l0, l1 = cs.precond_train(400, 3e-3)
+    w, _ = cs.precond_get_weights()
+    out["learned_training"] = {"cell": small.name, "steps": 400, "loss_first": l0, "loss_last": l1,
+                               "seconds": time.perf_counter() - t0}
+    del cs
+    wl = workloads.molecule_on_slab()
+    for name, prec, learned in (("mixed", "mixed", False), ("fp64", "fp64", False), ("mixed_learned", "mixed", True)):
+        ctx = fde.context_from_workload(wl, prec=prec)
+        fde.seed_workload(ctx, wl)
+        if learned:
+            ctx.precond_set_weights(w)
+            ctx.set_precond(fde.FDE_PRECOND_LEARNED)
+        ctx.sync()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        st, e = ctx.freeze_thaw_cycle(tol, 100)
+        ctx.sync()
+        dt = time.perf_counter() - t
+        dav, hb = ctx.stats()
+        out[name] = {"seconds": dt, "status": int(st), "F_fde": e["F_fde"], "E_fde": e["E_fde"],
+                     "scf_iterations": e.get("iters"), "eigensolver_iterations": dav, "band_applies": hb}
+        del ctx
+        torch.cuda.empty_cache()
+    out["speedup_mixed_vs_fp64"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
+    out["speedup_mixed_learned_vs_fp64"] = out["fp64"]["seconds"] / out["mixed_learned"]["seconds"]
+    out["dF_mixed_vs_fp64_ha"] = out["mixed"]["F_fde"] - out["fp64"]["F_fde"]
+    out["dF_mixed_learned_vs_fp64_ha"] = out["mixed_learned"]["F_fde"] - out["fp64"]["F_fde"]
+    return out
 
 
 def run_reference(args):
@@ -326,6 +381,7 @@ def run_ours(args):
                 "share_of_step": (ms_plane / args.steps) / ms}
         del sm_mhz
     cpu = cpu_baseline(wl) if (rank == 0 and not args.no_cpu) else None
+    ft = ft_cycles() if (ws == 1 and not args.no_ft) else None
     clocks = clk.summary()
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -336,7 +392,7 @@ def run_ours(args):
                            "parallelism": f"replicas x{ws}"},
                 "e2e": {"value": ws * units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
-                "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
+                "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks, "ft_cycle": ft,
                 "wall_s": wall, "step_ms": step_ms,
                 "graph": {"ms_per_step": graph_ms, "value": ws * units / (graph_ms / 1e3),
                           "note": "the same step replayed from a captured CUDA graph"}}
@@ -354,6 +410,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-ft", action="store_true", help="skip the freeze-and-thaw cycle timings (~4 min)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -324,8 +324,17 @@ fde_status fde_dense_eigh(fde_ctx* ctx, int n, const double* d_A, int nvec, doub
 fde_status fde_gemm_hn_f32(fde_ctx* ctx, const void* d_A, int lda, const void* d_B, int ldb, int m, int n,
                            int K, double* d_C, int ldc, int path);
 
-/* Path (0, 1 or 3, as for fde_gemm_hn_f32) of every FP32 band-block inner product the
- * library makes (mixed-precision contexts; FP64 products always use the CUDA cores).
+/* The band-block combination Y = alpha sum_i U[i][j] X_i + beta Y of the eigensolver's
+ * rotations and of the projector expansion sum_a beta_a (D <beta|psi>)_a (Eq. KS; Appendix,
+ * projectors), applied to caller data: d_X device complex float [m][ldx] (rows of length K),
+ * d_U device complex double [m][ldu] (n columns used), d_Y device complex float [n][ldy],
+ * updated in place (read only when beta != 0).  path as for fde_gemm_hn_f32.  X and Y must
+ * not overlap.  Synchronising; FDE_ETIMEOUT if a tensor-core wait ran out. */
+fde_status fde_gemm_rot_f32(fde_ctx* ctx, const void* d_X, int ldx, const double* d_U, int ldu, int m, int n, int K,
+                            void* d_Y, int ldy, double alpha, double beta, int path);
+
+/* Path (0, 1 or 3, as for fde_gemm_hn_f32) of every FP32 band-block inner product and
+ * combination the library makes (mixed-precision contexts; FP64 products always use the CUDA cores).
  * Process-wide; the default is 3 (FDE_GEMM_PATH in the environment sets the initial path). */
 fde_status fde_set_gemm_path(int path);
 

@@ -58,7 +58,7 @@ __device__ __forceinline__ ClusterLayout cluster_layout(int n) {
 // ---- Cholesky --------------------------------------------------------------------------------
 // Shared memory: rows [nloc][n] double2, col [n] double2, red.
 __global__ void __launch_bounds__(kClThreads)
-k_cl_cholesky(const double2* __restrict__ S, int n, double2* __restrict__ L, unsigned* status) {
+k_cl_cholesky(const double2* __restrict__ S, int n, double2* __restrict__ L, unsigned* status, double rel_pivot) {
   cg::cluster_group cl = cg::this_cluster();
   extern __shared__ __align__(16) unsigned char smem[];
   const ClusterLayout c = cluster_layout(n);
@@ -80,7 +80,7 @@ k_cl_cholesky(const double2* __restrict__ S, int n, double2* __restrict__ L, uns
     }
     __syncthreads();
     const double d = s_diag;
-    if (!(d > 0.0)) {  // identical value in every CTA: a uniform exit
+    if (!(d > rel_pivot * S[(size_t)j * n + j].x)) {  // identical values in every CTA: a uniform exit
       failed = true;
       break;
     }
@@ -629,13 +629,14 @@ static cudaLaunchConfig_t cluster_cfg(int P, size_t smem, cudaStream_t st, cudaL
   return cfg;
 }
 
-bool launch_cholesky_cluster(const double2* S, int n, double2* L, double2* Li, unsigned* status, cudaStream_t st) {
+bool launch_cholesky_cluster(const double2* S, int n, double2* L, double2* Li, unsigned* status, double rel_pivot,
+                             cudaStream_t st) {
   if (n < 1 || n > dense_cluster_max_n()) return false;
   const int P = cluster_size();
   cudaLaunchAttribute at[1];
   cudaLaunchConfig_t cfg = cluster_cfg(P, chol_smem(n, P), st, at);
   count_launches(2);
-  if (cudaLaunchKernelEx(&cfg, k_cl_cholesky, S, n, L, status) != cudaSuccess) return false;
+  if (cudaLaunchKernelEx(&cfg, k_cl_cholesky, S, n, L, status, rel_pivot) != cudaSuccess) return false;
   const int wpb = 4;
   k_tri_inverse<<<(n + wpb - 1) / wpb, 32 * wpb, 0, st>>>(L, n, Li, status);
   return true;

@@ -9,8 +9,10 @@ namespace fde {
 int dense_cluster_max_n();
 
 // S = L L^H and Li = L^{-1} (n x n FP64 complex, row-major, lower); ST_CHOLESKY in *status on
-// a non-positive pivot.  Returns false (nothing launched) when n is out of range.
-bool launch_cholesky_cluster(const double2* S, int n, double2* L, double2* Li, unsigned* status, cudaStream_t st);
+// a pivot not above rel_pivot times the input diagonal entry.  Returns false (nothing
+// launched) when n is out of range.
+bool launch_cholesky_cluster(const double2* S, int n, double2* L, double2* Li, unsigned* status, double rel_pivot,
+                             cudaStream_t st);
 
 // Eigenvalues w[n] ascending and eigenvectors of the lowest nvec (column j of the row-major V)
 // of the Hermitian A (not modified); columns nvec.. of V are zero.  work: at least

@@ -898,7 +898,7 @@ template <typename T> struct EngineT : Engine {
     gwork.ensure(gemm_hn_work(nb, nb, q.npw));
     launch_gemm_hn<T>(q.X.p, q.npw, q.X.p, q.npw, nb, nb, q.npw, S.p, nb, gwork.p, st);
     launch_hermitize(S.p, nb, st);
-    launch_cholesky_inv(S.p, nb, L.p, Li.p, status.p, st);
+    launch_cholesky_inv(S.p, nb, L.p, Li.p, status.p, rel_pivot(), st);
     check_cholesky();
     // U[i][j] = conj(Li[j][i])
     launch_small_gemm(Li.p, nb, 1, identity(nb), nb, 0, nb, nb, nb, Cc.p, nb, st);
@@ -918,6 +918,9 @@ template <typename T> struct EngineT : Engine {
     REQ(eye_n == n, FDE_EINVAL, "identity size");
     return eye.p;
   }
+  // Smallest accepted Cholesky pivot of a Gram matrix relative to its diagonal: the vectors'
+  // rounding level (squared) with a margin -- FP32 vectors ~(1e-7)^2 x 1e3, FP64 ~(1e-16)^2 x 1e3.
+  static constexpr double rel_pivot() { return sizeof(T) == 4 ? 1e-11 : 1e-29; }
   void check_cholesky() {
     unsigned h = 0;
     CK(cudaMemcpyAsync(&h, status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
@@ -967,7 +970,7 @@ template <typename T> struct EngineT : Engine {
     launch_gemm_hn<T>(V.p, K, HV.p, K, n, n, K, Hs.p, n, gwork.p, st);
     launch_hermitize(S.p, n, st);
     launch_hermitize(Hs.p, n, st);
-    launch_cholesky_inv(S.p, n, L.p, Li.p, status.p, st);
+    launch_cholesky_inv(S.p, n, L.p, Li.p, status.p, rel_pivot(), st);
     check_cholesky();
     launch_small_gemm(Li.p, n, 0, Hs.p, n, 0, n, n, n, tmp.p, n, st);
     launch_small_gemm(tmp.p, n, 0, Li.p, n, 1, n, n, n, Ht.p, n, st);
@@ -1921,6 +1924,25 @@ fde_status fde_gemm_hn_f32(fde_ctx* c, const void* d_A, int lda, const void* d_B
     CK(cudaStreamSynchronize(c->stream));
     if (fde::gemm_tc_take_status(c->stream) & fde::ST_TIMEOUT)
       throw fde::Err{FDE_ETIMEOUT, "a tensor-core product timed out waiting for its MMAs"};
+    return FDE_OK;
+  });
+}
+
+fde_status fde_gemm_rot_f32(fde_ctx* c, const void* d_X, int ldx, const double* d_U, int ldu, int m, int n, int K,
+                            void* d_Y, int ldy, double alpha, double beta, int path) {
+  return guard(c, [&]() {
+    using fde::Err;
+    if (!d_X || !d_U || !d_Y || m <= 0 || n <= 0 || K <= 0 || ldx < K || ldy < K || ldu < n ||
+        (path != 0 && path != 1 && path != 3))
+      throw fde::Err{FDE_EINVAL, "bad combination arguments"};
+    const int saved = fde::gemm_hn_path();
+    fde::set_gemm_hn_path(path);
+    fde::launch_gemm_rot<float>((const float2*)d_X, ldx, (const double2*)d_U, ldu, m, n, K, (float2*)d_Y, ldy,
+                                alpha, beta, c->stream);
+    fde::set_gemm_hn_path(saved);
+    CK(cudaStreamSynchronize(c->stream));
+    if (fde::gemm_tc_take_status(c->stream) & fde::ST_TIMEOUT)
+      throw fde::Err{FDE_ETIMEOUT, "a tensor-core combination timed out waiting for its MMAs"};
     return FDE_OK;
   });
 }

@@ -271,6 +271,193 @@ k_gemm_hn_tc(const float2* __restrict__ A, int lda, const float2* __restrict__ B
   }
 }
 
+
+// ---- Y = alpha sum_i U[i][j] X_i + beta Y (band-block rotation, projector expansion) ------------
+// One real GEMM per CTA: D[j][p] = sum_(i, c) A[j][(i, c)] B[p][(i, c)] over the interleaved
+// K index (i, c), c in {re, im}, with A[j][(i, 0)] = Re U_ij, A[j][(i, 1)] = Im U_ij and, for
+// the 128 plane waves g of the tile, rows p = g (real part of Y) and p = 128 + g (imaginary
+// part):  B[g][(i, 0)] = Re X_ig, B[g][(i, 1)] = -Im X_ig;  B[128 + g][(i, 0)] = Im X_ig,
+// B[128 + g][(i, 1)] = Re X_ig.  M = 128 output rows j, N = 256, K = 8 per MMA; the same
+// split-TF32 passes as the inner product; 128 x 256 FP32 accumulator in tensor memory.
+constexpr int kRotJ = 128;             // output rows per CTA
+constexpr int kRotG = 128;             // complex plane waves per CTA
+constexpr int kRotKi = 16;             // input rows i per k-tile (32 floats)
+constexpr int kRotA = kRotJ * 128;     // bytes of one A tile (16 KB)
+constexpr int kRotB = 2 * kRotG * 128; // bytes of one B tile (32 KB)
+constexpr int kRotStage = 2 * kRotA + 2 * kRotB;
+constexpr int kRotTmemCols = 256;
+constexpr uint32_t kIdescRot = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(2 * kRotG / 8) << 17) |
+                               ((uint32_t)(kRotJ / 16) << 24);
+
+__device__ __forceinline__ void mma_tf32_rot(uint32_t dt, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dt),
+      "l"(a), "l"(b), "r"(kIdescRot), "r"(acc)
+      : "memory");
+}
+
+constexpr int kRotXld = kRotKi * kRotG / kTcThreads;  // X elements per thread per k-tile (8)
+constexpr int kRotUld = kRotKi * kRotJ / kTcThreads;  // U elements per thread per k-tile (8)
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+k_gemm_rot_tc(const float2* __restrict__ X, int ldx, const double2* __restrict__ U, int ldu, int m, int n, int K,
+              float2* __restrict__ Y, int ldy, float alpha, float beta, int passes) {
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bars[kStages];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t base = (su32(smem_raw) + 1023u) & ~1023u;
+  const int g0 = blockIdx.x * kRotG, j0 = blockIdx.y * kRotJ;
+  const int nt = (m + kRotKi - 1) / kRotKi;
+
+  if (tid == 0) {
+    for (int q = 0; q < kStages; ++q) mbar_init(su32(&bars[q]), 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_slot)),
+                 "r"(kRotTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  // element q of a thread: input row ii = 2 (q) + (tid & 1), plane wave (or output row) tid >> 1,
+  // so pairs of threads read two rows at the same column (coalesced 8-byte runs) and a warp's
+  // shared-memory stores cover 16 swizzled rows without conflicts beyond the 2 wavefronts
+  float2 rx[kRotXld];
+  double2 ru[kRotUld];
+  auto load = [&](int t) {
+    const int i0 = t * kRotKi;
+#pragma unroll
+    for (int q = 0; q < kRotXld; ++q) {
+      const int ii = 2 * q + (tid & 1), gg = tid >> 1;
+      const int i = i0 + ii, g = g0 + gg;
+      rx[q] = (i < m && g < K) ? __ldg(X + (size_t)i * ldx + g) : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int q = 0; q < kRotUld; ++q) {
+      const int ii = 2 * q + (tid & 1), jj = tid >> 1;
+      const int i = i0 + ii, j = j0 + jj;
+      ru[q] = (i < m && j < n) ? __ldg(U + (size_t)i * ldu + j) : make_double2(0.0, 0.0);
+    }
+  };
+  auto store = [&](uint32_t st) {
+#pragma unroll
+    for (int q = 0; q < kRotUld; ++q) {
+      const int ii = 2 * q + (tid & 1), jj = tid >> 1, c = 2 * ii;
+      const float ur = (float)ru[q].x, ui = (float)ru[q].y;
+      const float hr = tf32_hi(ur), hi = tf32_hi(ui);
+      st2(st + swz(jj, c), hr, hi);
+      if (passes > 1) st2(st + kRotA + swz(jj, c), ur - hr, ui - hi);
+    }
+#pragma unroll
+    for (int q = 0; q < kRotXld; ++q) {
+      const int ii = 2 * q + (tid & 1), gg = tid >> 1, c = 2 * ii;
+      const float xr = rx[q].x, xi = rx[q].y;
+      const float hr = tf32_hi(xr), hi = tf32_hi(xi);
+      const uint32_t b = st + 2 * kRotA;
+      st2(b + swz(gg, c), hr, -hi);
+      st2(b + swz(kRotG + gg, c), hi, hr);
+      if (passes > 1) {
+        const float lr = xr - hr, li = xi - hi;
+        st2(b + kRotB + swz(gg, c), lr, -li);
+        st2(b + kRotB + swz(kRotG + gg, c), li, lr);
+      }
+    }
+  };
+
+  int issued = 0;
+  if (nt > 0) load(0);
+  for (int t = 0; t < nt; ++t) {
+    const int s = t & 1;
+    const uint32_t st = base + (uint32_t)s * kRotStage;
+    if (t >= kStages) {
+      if (tid == 0 && !mbar_wait(su32(&bars[s]), (unsigned)(((t - kStages) >> 1) & 1))) abort_flag = 1;
+      __syncthreads();
+      if (abort_flag) break;
+    }
+    store(st);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+#pragma unroll
+      for (int kk = 0; kk < kRotKi * 2 / 8; ++kk) {
+        const uint32_t off = (uint32_t)kk * 32u;
+        const uint64_t ah = sdesc(st + off), bh = sdesc(st + 2 * kRotA + off);
+        mma_tf32_rot(tmem, ah, bh, (t > 0 || kk > 0) ? 1u : 0u);
+        if (passes > 1) {
+          const uint64_t al = sdesc(st + kRotA + off), bl = sdesc(st + 2 * kRotA + kRotB + off);
+          mma_tf32_rot(tmem, ah, bl, 1u);
+          mma_tf32_rot(tmem, al, bh, 1u);
+        }
+      }
+      mma_commit(su32(&bars[s]));
+      ++issued;
+    }
+    if (t + 1 < nt) load(t + 1);
+  }
+  if (tid == 0) {
+    for (int s = 0; s < kStages && s < issued; ++s) {
+      const int uses = (issued - s + kStages - 1) / kStages;
+      if (!mbar_wait(su32(&bars[s]), (unsigned)((uses - 1) & 1))) abort_flag = 1;
+    }
+  }
+  __syncthreads();
+  const bool ok = !abort_flag;
+  if (!ok && tid == 0) atomicOr(&g_tc_status, ST_TIMEOUT);
+  tc_fence_after();
+  if (ok) {
+    // warp w: accumulator lanes 32 (w % 4) .. + 31 (output rows j), plane waves 64 (w / 4) .. + 63
+    const int q = warp & 3, h = warp >> 2;
+    const int j = j0 + 32 * q + lane;
+    const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16);
+    float2* y = Y + (size_t)(j < n ? j : 0) * ldy;
+#pragma unroll 1
+    for (int c16 = 0; c16 < 4; ++c16) {
+      const int gc = 64 * h + 16 * c16;
+      float re[16], im[16];
+      if (nt > 0) {
+        tmem_ld16(trow + (uint32_t)gc, re);
+        tmem_ld16(trow + (uint32_t)(kRotG + gc), im);
+      } else {
+#pragma unroll
+        for (int x = 0; x < 16; ++x) re[x] = im[x] = 0.f;
+      }
+      if (j < n) {
+#pragma unroll
+        for (int x = 0; x < 16; ++x) {
+          const int g = g0 + gc + x;
+          if (g < K) {
+            float2 o = make_float2(alpha * re[x], alpha * im[x]);
+            if (beta != 0.f) {
+              const float2 old = y[g];
+              o.x += beta * old.x;
+              o.y += beta * old.y;
+            }
+            y[g] = o;
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kRotTmemCols) : "memory");
+  }
+}
+
 }  // namespace
 
 // K-splits of the tensor-core product: about two CTAs per SM over the grid, at least eight
@@ -313,6 +500,29 @@ unsigned gemm_tc_take_status(cudaStream_t st) {
     return 0;  // the stream's own error surfaces at the caller's next check
   if (h) cudaMemcpyToSymbolAsync(g_tc_status, &z, sizeof(unsigned), 0, cudaMemcpyHostToDevice, st);
   return h;
+}
+
+}  // namespace fde
+
+namespace fde {
+
+size_t gemm_rot_tc_smem() { return (size_t)kStages * kRotStage + 1024; }
+
+// Y = alpha U^T-combination of the rows of X + beta Y on the tensor cores; returns false if the
+// kernel could not be configured (nothing launched).
+bool launch_gemm_rot_tc(const float2* X, int ldx, const double2* U, int ldu, int m, int n, int K, float2* Y,
+                        int ldy, double alpha, double beta, int passes, cudaStream_t st) {
+  static int attr = 0;
+  if (attr == 0)
+    attr = cudaFuncSetAttribute(k_gemm_rot_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)gemm_rot_tc_smem()) == cudaSuccess ? 1 : -1;
+  if (attr < 0) return false;
+  const dim3 grid(ceil_div(K, kRotG), ceil_div(n, kRotJ));
+  count_launches(1);
+  ProfScope p("k_gemm_rot_tc", st);
+  k_gemm_rot_tc<<<grid, kTcThreads, gemm_rot_tc_smem(), st>>>(X, ldx, U, ldu, m, n, K, Y, ldy, (float)alpha,
+                                                               (float)beta, passes);
+  return true;
 }
 
 }  // namespace fde

@@ -187,34 +187,39 @@ k_plane_density_ct(const cplx<T>* __restrict__ scratch, SphereDev sp, int nb, co
   }
 }
 
-// One axis of a full 3D transform: element (o, e, t) at (o * N + e) * I + t; 8 lines per CTA.
+// One axis of a full 3D transform: element (o, e, t) at (o * N + e) * I + t.  A CTA holds as
+// many lines as one batch of the staged transform keeps every thread busy with
+// (ct_lines_per_batch), so all stages run in a single pass over the CTA's lines; each line's
+// base offset is computed once (32-bit: the grid has fewer than 2^31 points).
+template <typename T, int N> __host__ __device__ constexpr int ct_axis_lines() {
+  return ct_lines_per_batch<T, N, kCtThreads>();
+}
 template <typename T, int N>
 __global__ void __launch_bounds__(kCtThreads)
-k_fft_axis_ct(cplx<T>* __restrict__ data, long long nlines, long long I, const cplx<T>* __restrict__ tw, int sign) {
+k_fft_axis_ct(cplx<T>* __restrict__ data, int nlines, int I, const cplx<T>* __restrict__ tw, int sign) {
   using C = cplx<T>;
   constexpr int LP = N + 1;
-  __shared__ __align__(16) C lines[kCtCols * LP];
-  const long long l0 = (long long)blockIdx.x * kCtCols;
-  const int nl = (int)min((long long)kCtCols, nlines - l0);
-  for (int idx = threadIdx.x; idx < kCtCols * N; idx += kCtThreads) {
-    int tl, e;
-    if (I == 1) { tl = idx / N; e = idx - tl * N; } else { e = idx / kCtCols; tl = idx - e * kCtCols; }
-    if (tl < nl) {
-      const long long l = l0 + tl, o = l / I, t = l - o * I;
-      lines[tl * LP + e] = data[(o * N + e) * I + t];
-    } else {
-      lines[tl * LP + e] = mk<T>(0, 0);
-    }
+  constexpr int LPC = ct_axis_lines<T, N>();
+  __shared__ __align__(16) C lines[LPC * LP];
+  __shared__ int base[LPC];
+  const int l0 = blockIdx.x * LPC;
+  const int nl = min(LPC, nlines - l0);
+  if ((int)threadIdx.x < LPC) {
+    const int l = l0 + (int)threadIdx.x, o = l / I, t = l - o * I;
+    base[threadIdx.x] = o * N * I + t;
   }
   __syncthreads();
-  ct_lines<T, N, kCtThreads>(lines, LinesContig{LP}, kCtCols, tw, sign);
-  for (int idx = threadIdx.x; idx < kCtCols * N; idx += kCtThreads) {
+  for (int idx = threadIdx.x; idx < LPC * N; idx += kCtThreads) {
     int tl, e;
-    if (I == 1) { tl = idx / N; e = idx - tl * N; } else { e = idx / kCtCols; tl = idx - e * kCtCols; }
-    if (tl < nl) {
-      const long long l = l0 + tl, o = l / I, t = l - o * I;
-      data[(o * N + e) * I + t] = lines[tl * LP + e];
-    }
+    if (I == 1) { tl = idx / N; e = idx - tl * N; } else { e = idx / LPC; tl = idx - e * LPC; }
+    lines[tl * LP + e] = (tl < nl) ? data[base[tl] + e * I] : mk<T>(0, 0);
+  }
+  __syncthreads();
+  ct_lines<T, N, kCtThreads>(lines, LinesContig{LP}, LPC, tw, sign);
+  for (int idx = threadIdx.x; idx < LPC * N; idx += kCtThreads) {
+    int tl, e;
+    if (I == 1) { tl = idx / N; e = idx - tl * N; } else { e = idx / LPC; tl = idx - e * LPC; }
+    if (tl < nl) data[base[tl] + e * I] = lines[tl * LP + e];
   }
 }
 
@@ -307,12 +312,12 @@ static void ct_plane_density(int n, int n3, cudaStream_t st, const cplx<T>* scr,
 
 template <typename T>
 static void ct_axis(int n, long long nlines, long long I, cudaStream_t st, cplx<T>* data, const cplx<T>* tw, int sign) {
-  const unsigned blocks = (unsigned)((nlines + kCtCols - 1) / kCtCols);
   switch (n) {
-#define FDE_CASE(N)                                                                     \
-  case N:                                                                               \
-    count_launches(1);                                                                  \
-    k_fft_axis_ct<T, N><<<blocks, kCtThreads, 0, st>>>(data, nlines, I, tw, sign);      \
+#define FDE_CASE(N)                                                                                    \
+  case N:                                                                                              \
+    count_launches(1);                                                                                 \
+    k_fft_axis_ct<T, N><<<(unsigned)ceil_div(nlines, ct_axis_lines<T, N>()), kCtThreads, 0, st>>>(   \
+        data, (int)nlines, (int)I, tw, sign);                                                          \
     break;
     FDE_CT_LINES(FDE_CASE)
 #undef FDE_CASE
@@ -388,6 +393,7 @@ template <typename T>
 bool launch_fft3d_ct(cplx<T>* data, const GridDims& g, const FftPlans<T>& fp, int sign, cudaStream_t st) {
   if (!ct_line_ok<T>(g.n1) || !ct_line_ok<T>(g.n2) || !ct_line_ok<T>(g.n3)) return false;
   const long long nr = (long long)g.n1 * g.n2 * g.n3;
+  if (nr >= (1ll << 31)) return false;  // the compile-time kernels index in 32 bits
   ct_axis<T>(g.n3, nr / g.n3, 1, st, data, fp.p3.tw, sign);
   ct_axis<T>(g.n2, nr / g.n2, g.n3, st, data, fp.p2.tw, sign);
   ct_axis<T>(g.n1, nr / g.n1, (long long)g.n2 * g.n3, st, data, fp.p1.tw, sign);

@@ -86,6 +86,10 @@ int gemm_hn_path();
 int gemm_hn_tc_splits(int m, int n, int K);
 int launch_gemm_hn_tc(const float2* A, int lda, const float2* B, int ldb, int m, int n, int K, int passes,
                       double2* part, cudaStream_t st);
+// Y = alpha U^T-combination of the rows of X + beta Y on the tensor cores (gemm_tc.cu), with
+// the same passes as launch_gemm_hn_tc; false when the kernel could not be configured.
+bool launch_gemm_rot_tc(const float2* X, int ldx, const double2* U, int ldu, int m, int n, int K, float2* Y,
+                        int ldy, double alpha, double beta, int passes, cudaStream_t st);
 // ST_* bits raised by the tensor-core kernels since the last call (read, cleared; syncs).
 unsigned gemm_tc_take_status(cudaStream_t st);
 void launch_gemm_hn_reduce(const double2* part, int nsplit, int m, int n, double2* C, int ldc, cudaStream_t st);
@@ -109,8 +113,10 @@ struct KbBlock {
 void launch_kb_couple(const double2* P, const KbBlock& D, int natoms, int nb, double2* Q, cudaStream_t st);
 
 // Cholesky S = L L^H (n x n, FP64 complex, lower, in place into L) and Linv = L^{-1};
-// sets status bit ST_CHOLESKY on a non-positive pivot.
-void launch_cholesky_inv(const double2* S, int n, double2* L, double2* Linv, unsigned* status,
+// sets status bit ST_CHOLESKY on a pivot not above rel_pivot S_jj (the squared norm of a
+// vector's part orthogonal to the earlier ones, relative to its own squared norm: below the
+// rounding level of the vectors' precision they are numerically dependent).
+void launch_cholesky_inv(const double2* S, int n, double2* L, double2* Linv, unsigned* status, double rel_pivot,
                          cudaStream_t st);
 
 // Hermitian eigenproblem by cyclic Jacobi: A (n x n, destroyed) -> eigenvalues w[n]

@@ -214,9 +214,22 @@ k_gemm_rot(const cplx<T>* __restrict__ X, int ldx, const double2* __restrict__ U
 }
 
 template <typename T>
+static bool gemm_rot_tensor(const cplx<T>*, int, const double2*, int, int, int, int, cplx<T>*, int, double, double,
+                            cudaStream_t) {
+  return false;
+}
+template <>
+bool gemm_rot_tensor<float>(const float2* X, int ldx, const double2* U, int ldu, int m, int n, int K, float2* Y,
+                            int ldy, double alpha, double beta, cudaStream_t st) {
+  if (g_gemm_path == 0 || m <= 0) return false;
+  return launch_gemm_rot_tc(X, ldx, U, ldu, m, n, K, Y, ldy, alpha, beta, g_gemm_path, st);
+}
+
+template <typename T>
 void launch_gemm_rot(const cplx<T>* X, int ldx, const double2* U, int ldu, int m, int n, int K, cplx<T>* Y,
                      int ldy, double alpha, double beta, cudaStream_t st) {
   if (n <= 0 || K <= 0) return;
+  if (gemm_rot_tensor<T>(X, ldx, U, ldu, m, n, K, Y, ldy, alpha, beta, st)) return;
   const dim3 grid(ceil_div(K, 64), ceil_div(n, 32));
   count_launches(1);
   k_gemm_rot<T><<<grid, 256, 0, st>>>(X, ldx, U, ldu, m, n, K, Y, ldy, (T)alpha, (T)beta);
@@ -225,7 +238,7 @@ void launch_gemm_rot(const cplx<T>* X, int ldx, const double2* U, int ldu, int m
 // ---- Cholesky and triangular inverse (one CTA) -------------------------------------------
 __global__ void __launch_bounds__(512)
 k_cholesky_inv(const double2* __restrict__ S, int n, double2* __restrict__ L, double2* __restrict__ Li,
-               unsigned* status) {
+               unsigned* status, double rel_pivot) {
   __shared__ int fail;
   if (threadIdx.x == 0) fail = 0;
   for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
@@ -235,7 +248,7 @@ k_cholesky_inv(const double2* __restrict__ S, int n, double2* __restrict__ L, do
   __syncthreads();
   for (int j = 0; j < n; ++j) {
     const double d = L[(size_t)j * n + j].x;
-    if (!(d > 0.0)) {
+    if (!(d > rel_pivot * S[(size_t)j * n + j].x)) {
       if (threadIdx.x == 0) { fail = 1; atomicOr(status, ST_CHOLESKY); }
       break;
     }
@@ -294,10 +307,11 @@ k_cholesky_inv(const double2* __restrict__ S, int n, double2* __restrict__ L, do
 }
 
 // The cluster-distributed factorisation (dense.cu) when n fits it, else one CTA.
-void launch_cholesky_inv(const double2* S, int n, double2* L, double2* Linv, unsigned* status, cudaStream_t st) {
-  if (launch_cholesky_cluster(S, n, L, Linv, status, st)) return;
+void launch_cholesky_inv(const double2* S, int n, double2* L, double2* Linv, unsigned* status, double rel_pivot,
+                         cudaStream_t st) {
+  if (launch_cholesky_cluster(S, n, L, Linv, status, rel_pivot, st)) return;
   count_launches(1);
-  k_cholesky_inv<<<1, 512, 0, st>>>(S, n, L, Linv, status);
+  k_cholesky_inv<<<1, 512, 0, st>>>(S, n, L, Linv, status, rel_pivot);
 }
 
 // ---- per-atom projector coupling ------------------------------------------------------------

@@ -82,6 +82,8 @@ EXPORTS = {
     "fde_gemm_hn_f32": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int,
                                   C.c_void_p, C.c_int, C.c_int]),
     "fde_set_gemm_path": (C.c_int, [C.c_int]),
+    "fde_gemm_rot_f32": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int,
+                                   C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_int]),
     "fde_dense_eigh": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "fde_set_precond": (C.c_int, [C.c_void_p, C.c_int]),
     "fde_precond_set_weights": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -118,6 +120,19 @@ def load(path: str = LIB_PATH):
         fn.argtypes = args
     _lib = lib
     return lib
+
+
+def precond_initial_weights(seed: int = 0) -> np.ndarray:
+    """Starting parameters of the learned preconditioner in the library's flat layout
+    (W1 b1 W2 b2 W3 b3 W4 b4): hidden weights N(0, 1/fan_in) from a seeded generator, zero
+    biases and a zero output layer, so that training starts from the kinetic preconditioner."""
+    rng = np.random.default_rng([seed, 4099])
+    width, layers, out = 64, ((3, 64), (64, 64), (64, 64), (64, 1)), []
+    for i, (fi, fo) in enumerate(layers):
+        W = np.zeros((fo, fi)) if i == len(layers) - 1 else rng.standard_normal((fo, fi)) / np.sqrt(fi)
+        out += [W.ravel(), np.zeros(fo)]
+    del width
+    return np.concatenate(out).astype(np.float32)
 
 
 def set_gemm_path(path: int) -> None:
@@ -300,6 +315,14 @@ class Context:
         return self._check(self.lib.fde_gemm_hn_f32(self.h, _dptr(A), int(A.shape[1]), _dptr(B), int(B.shape[1]),
                                                     int(A.shape[0]), int(B.shape[0]), int(K), _dptr(C),
                                                     int(C.shape[1]), int(path)), "fde_gemm_hn_f32")
+
+    def gemm_rot_f32(self, X, U, K, Y, alpha, beta, path):
+        """Y = alpha sum_i U[i][j] X_i + beta Y over the first K columns: X complex64 (m x ldx),
+        U complex128 (m x ldu, n = Y rows used), Y complex64 (n x ldy), device tensors."""
+        return self._check(self.lib.fde_gemm_rot_f32(self.h, _dptr(X), int(X.shape[1]), _dptr(U), int(U.shape[1]),
+                                                     int(X.shape[0]), int(Y.shape[0]), int(K), _dptr(Y),
+                                                     int(Y.shape[1]), float(alpha), float(beta), int(path)),
+                           "fde_gemm_rot_f32")
 
     def get_hpsi(self, sub, k, out):
         return self._check(self.lib.fde_get_hpsi(self.h, sub, k, _dptr(out)), "fde_get_hpsi")

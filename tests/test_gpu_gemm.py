@@ -78,3 +78,38 @@ def test_gram_is_hermitian_and_repeatable(ctx):
     scale = np.linalg.norm(a, axis=1).max() ** 2
     assert np.abs(g - g.conj().T).max() / scale < 1e-5
     assert np.all(np.diag(g).real > 0)
+
+
+ROT_SHAPES = [
+    # m (input rows), n (output rows), K, ldx, ldy, alpha, beta
+    (72, 64, 2777, 2777, 2777, 1.0, 1.0),      # projector expansion added to H psi
+    (192, 64, 5003, 5003, 5003, 1.0, 0.0),     # rotation of a 3 x 64 search space onto 64 bands
+    (64, 130, 1000, 1001, 1003, -1.0, 1.0),    # two output-row tiles, ragged G tile, padded rows
+    (1, 1, 1, 1, 1, 0.5, 0.0),                 # degenerate
+    (17, 3, 129, 130, 129, 1.0, -2.0),         # partial k-tile, one G past a tile
+]
+
+
+@pytest.mark.parametrize("m,n,K,ldx,ldy,alpha,beta", ROT_SHAPES)
+def test_combinations_match_fp64(ctx, m, n, K, ldx, ldy, alpha, beta):
+    """Y = alpha sum_i U_ij X_i + beta Y.  Error measure: max |Y - Y_ref| over
+    (|alpha| max_j |U_:j| max_g |X_:g| + |beta| max |Y|)."""
+    rng = np.random.default_rng([m, n, K, 3])
+    x = _draw(rng, m, ldx, K)
+    u = (rng.standard_normal((m, n)) + 1j * rng.standard_normal((m, n))) / np.sqrt(m)
+    y0 = _draw(rng, n, ldy, K)
+    ref = y0.astype(np.complex128).copy()
+    ref[:, :K] = alpha * (u.T @ x[:, :K].astype(np.complex128)) + beta * y0[:, :K]
+    scale = abs(alpha) * np.linalg.norm(u, axis=0).max() * np.linalg.norm(x, axis=0).max() + abs(beta) * np.abs(y0).max()
+    dX, dU = torch.from_numpy(x).cuda(), torch.from_numpy(u).cuda()
+    err = {}
+    for path in (0, 1, 3):
+        dY = torch.from_numpy(y0.copy()).cuda()
+        ctx.gemm_rot_f32(dX, dU, K, dY, alpha, beta, path)
+        got = dY.cpu().numpy()
+        assert np.array_equal(got[:, K:], y0[:, K:]), "columns beyond K must be untouched"
+        err[path] = float(np.abs(got - ref).max() / scale)
+    assert err[0] < 1e-5 and err[3] < 1e-5, err
+    assert err[1] < 4e-3, err
+    if m >= 16:
+        assert err[3] < err[1] / 20, err
