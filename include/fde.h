@@ -333,9 +333,12 @@ fde_status fde_gemm_hn_f32(fde_ctx* ctx, const void* d_A, int lda, const void* d
 fde_status fde_gemm_rot_f32(fde_ctx* ctx, const void* d_X, int ldx, const double* d_U, int ldu, int m, int n, int K,
                             void* d_Y, int ldy, double alpha, double beta, int path);
 
-/* Path (0, 1 or 3, as for fde_gemm_hn_f32) of every FP32 band-block inner product and
- * combination the library makes (mixed-precision contexts; FP64 products always use the CUDA cores).
- * Process-wide; the default is 3 (FDE_GEMM_PATH in the environment sets the initial path). */
+/* Path (0, 1 or 3, as for fde_gemm_hn_f32) of the FP32 band-block products the library makes
+ * in mixed-precision contexts: every inner product (Gram, subspace Hamiltonian, <beta|psi>)
+ * and the projector expansion of H psi.  The eigensolver's orbital rotations always use FP32
+ * fused multiply-adds (their rounding accumulates in the orbitals), and FP64 products always
+ * use the CUDA cores.  Process-wide; the default is 3 (FDE_GEMM_PATH in the environment sets
+ * the initial path). */
 fde_status fde_set_gemm_path(int path);
 
 /* Synchronise the context stream and check the device status word. */

@@ -1938,7 +1938,7 @@ fde_status fde_gemm_rot_f32(fde_ctx* c, const void* d_X, int ldx, const double* 
     const int saved = fde::gemm_hn_path();
     fde::set_gemm_hn_path(path);
     fde::launch_gemm_rot<float>((const float2*)d_X, ldx, (const double2*)d_U, ldu, m, n, K, (float2*)d_Y, ldy,
-                                alpha, beta, c->stream);
+                                alpha, beta, c->stream, path != 0);
     fde::set_gemm_hn_path(saved);
     CK(cudaStreamSynchronize(c->stream));
     if (fde::gemm_tc_take_status(c->stream) & fde::ST_TIMEOUT)

@@ -286,6 +286,9 @@ constexpr int kRotA = kRotJ * 128;     // bytes of one A tile (16 KB)
 constexpr int kRotB = 2 * kRotG * 128; // bytes of one B tile (32 KB)
 constexpr int kRotStage = 2 * kRotA + 2 * kRotB;
 constexpr int kRotTmemCols = 256;
+constexpr int kRotPitch = 2 * kRotG + 4;  // floats per row of the staged accumulator
+static_assert((size_t)kRotJ * kRotPitch * 4 <= (size_t)kStages * (2 * kRotJ * 128 + 4 * kRotG * 128),
+              "staged accumulator fits the stage buffers");
 constexpr uint32_t kIdescRot = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(2 * kRotG / 8) << 17) |
                                ((uint32_t)(kRotJ / 16) << 24);
 
@@ -417,36 +420,46 @@ k_gemm_rot_tc(const float2* __restrict__ X, int ldx, const double2* __restrict__
   if (!ok && tid == 0) atomicOr(&g_tc_status, ST_TIMEOUT);
   tc_fence_after();
   if (ok) {
-    // warp w: accumulator lanes 32 (w % 4) .. + 31 (output rows j), plane waves 64 (w / 4) .. + 63
-    const int q = warp & 3, h = warp >> 2;
-    const int j = j0 + 32 * q + lane;
-    const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16);
-    float2* y = Y + (size_t)(j < n ? j : 0) * ldy;
+    // Accumulator -> shared memory (the stage buffers are free: every MMA has completed), then a
+    // read-modify-write of Y with consecutive threads on consecutive plane waves.
+    // Ds[j][p], row pitch kRotPitch floats (a pitch of 4 mod 32 words keeps the 16-byte stores
+    // of eight consecutive rows on distinct banks).
+    float* Ds = reinterpret_cast<float*>(smem_raw + (base - su32(smem_raw)));
+    {
+      const int q = warp & 3, h = warp >> 2;
+      const int r = 32 * q + lane;
+      const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16);
 #pragma unroll 1
-    for (int c16 = 0; c16 < 4; ++c16) {
-      const int gc = 64 * h + 16 * c16;
-      float re[16], im[16];
-      if (nt > 0) {
-        tmem_ld16(trow + (uint32_t)gc, re);
-        tmem_ld16(trow + (uint32_t)(kRotG + gc), im);
-      } else {
+      for (int c16 = 0; c16 < 8; ++c16) {
+        const int pc = 128 * h + 16 * c16;
+        float v[16];
+        if (nt > 0) {
+          tmem_ld16(trow + (uint32_t)pc, v);
+        } else {
 #pragma unroll
-        for (int x = 0; x < 16; ++x) re[x] = im[x] = 0.f;
-      }
-      if (j < n) {
-#pragma unroll
-        for (int x = 0; x < 16; ++x) {
-          const int g = g0 + gc + x;
-          if (g < K) {
-            float2 o = make_float2(alpha * re[x], alpha * im[x]);
-            if (beta != 0.f) {
-              const float2 old = y[g];
-              o.x += beta * old.x;
-              o.y += beta * old.y;
-            }
-            y[g] = o;
-          }
+          for (int x = 0; x < 16; ++x) v[x] = 0.f;
         }
+        float4* dst = reinterpret_cast<float4*>(Ds + (size_t)r * kRotPitch + pc);
+#pragma unroll
+        for (int x = 0; x < 4; ++x) dst[x] = make_float4(v[4 * x], v[4 * x + 1], v[4 * x + 2], v[4 * x + 3]);
+      }
+    }
+    __syncthreads();
+    const int gg = tid & (kRotG - 1), jr = tid >> 7;  // 128 plane waves x 2 rows per pass
+    const int g = g0 + gg;
+    if (g < K) {
+#pragma unroll 4
+      for (int jj = jr; jj < kRotJ; jj += kTcThreads / kRotG) {
+        const int j = j0 + jj;
+        if (j >= n) break;
+        float2 o = make_float2(alpha * Ds[(size_t)jj * kRotPitch + gg], alpha * Ds[(size_t)jj * kRotPitch + kRotG + gg]);
+        float2* y = Y + (size_t)j * ldy + g;
+        if (beta != 0.f) {
+          const float2 old = *y;
+          o.x += beta * old.x;
+          o.y += beta * old.y;
+        }
+        *y = o;
       }
     }
   }

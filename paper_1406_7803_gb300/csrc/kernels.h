@@ -98,10 +98,13 @@ void launch_gemm_hn(const cplx<T>* A, int lda, const cplx<T>* B, int ldb, int m,
                     double2* C, int ldc, double2* work, cudaStream_t st);
 
 // Y[j][g] = alpha * sum_i U[i][j] X[i][g] + beta * Y[j][g]; X [m][K] (ldx), U [m][n] FP64
-// complex (ldu), Y [n][K] (ldy).  alpha/beta real.
+// complex (ldu), Y [n][K] (ldy).  alpha/beta real.  tensor: FP32 data may take the tensor-core
+// kernel (the gemm_hn path's split TF32, ~2^-20 relative per product) -- used for the projector
+// expansion of H psi; the eigensolver's rotations, whose errors accumulate in the orbitals
+// from one iteration to the next, keep FP32 fused multiply-adds (2^-24).
 template <typename T>
 void launch_gemm_rot(const cplx<T>* X, int ldx, const double2* U, int ldu, int m, int n, int K,
-                     cplx<T>* Y, int ldy, double alpha, double beta, cudaStream_t st);
+                     cplx<T>* Y, int ldy, double alpha, double beta, cudaStream_t st, bool tensor = false);
 
 // Per-atom block of the projector coupling (np x np, row-major, np <= 8).
 struct KbBlock {

@@ -227,9 +227,9 @@ bool gemm_rot_tensor<float>(const float2* X, int ldx, const double2* U, int ldu,
 
 template <typename T>
 void launch_gemm_rot(const cplx<T>* X, int ldx, const double2* U, int ldu, int m, int n, int K, cplx<T>* Y,
-                     int ldy, double alpha, double beta, cudaStream_t st) {
+                     int ldy, double alpha, double beta, cudaStream_t st, bool tensor) {
   if (n <= 0 || K <= 0) return;
-  if (gemm_rot_tensor<T>(X, ldx, U, ldu, m, n, K, Y, ldy, alpha, beta, st)) return;
+  if (tensor && gemm_rot_tensor<T>(X, ldx, U, ldu, m, n, K, Y, ldy, alpha, beta, st)) return;
   const dim3 grid(ceil_div(K, 64), ceil_div(n, 32));
   count_launches(1);
   k_gemm_rot<T><<<grid, 256, 0, st>>>(X, ldx, U, ldu, m, n, K, Y, ldy, (T)alpha, (T)beta);
@@ -629,7 +629,7 @@ void launch_shape_init(cplx<T>* X, int ld, const T* kin, int nb, int K, cudaStre
   template void launch_gemm_hn<T>(const cplx<T>*, int, const cplx<T>*, int, int, int, int, double2*, int,        \
                                   double2*, cudaStream_t);                                                       \
   template void launch_gemm_rot<T>(const cplx<T>*, int, const double2*, int, int, int, int, cplx<T>*, int,       \
-                                   double, double, cudaStream_t);                                                \
+                                   double, double, cudaStream_t, bool);                                          \
   template void launch_residual<T>(const cplx<T>*, const cplx<T>*, const double*, int, int, int, cplx<T>*, int,  \
                                    cudaStream_t);                                                                \
   template void launch_row_norms<T>(const cplx<T>*, int, int, int, const T*, double*, double*, cudaStream_t);    \
