@@ -388,6 +388,7 @@ def run_ours(args):
                 "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32" if args.prec == "mixed" else "f64", "data": "synthetic",
                 "config": {"workload": wl.name, "band_applies_per_step": units, "precision": args.prec,
+                           "plane_variant": fde.tuned_plane_variant(wl.grid[0], wl.grid[2]),
                            "l2": "flushed between steps (256 MB write)", "seed": wl.seed,
                            "parallelism": f"replicas x{ws}"},
                 "e2e": {"value": ws * units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,

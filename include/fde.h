@@ -341,6 +341,17 @@ fde_status fde_gemm_rot_f32(fde_ctx* ctx, const void* d_X, int ldx, const double
  * the initial path). */
 fde_status fde_set_gemm_path(int path);
 
+/* The FP32 plane pass of H psi (the (x, y) transforms, potential multiply and back) comes in
+ * several compiled variants (register budget per thread, CTAs per SM, radix order of the
+ * 72-point transforms).  The first large batch of a grid shape times each once on the batch
+ * itself and keeps the fastest (measurement support; no counterpart in the paper).  Returns the
+ * variant chosen for plane side n1 and z length n3, or -1 if none was tuned yet; the
+ * environment variable FDE_PLANE_VARIANT pins one. */
+int fde_tuned_plane_variant(int n1, int n3);
+/* Pin the plane-pass variant used from now on in this process (0 .. 3), or return to tuning
+ * (-1).  FDE_EINVAL for other values. */
+fde_status fde_pin_plane_variant(int variant);
+
 /* Synchronise the context stream and check the device status word. */
 fde_status fde_sync(fde_ctx* ctx);
 

@@ -1947,6 +1947,9 @@ fde_status fde_gemm_rot_f32(fde_ctx* c, const void* d_X, int ldx, const double* 
   });
 }
 
+int fde_tuned_plane_variant(int n1, int n3) { return fde::query_plane_variant(n1, n3); }
+fde_status fde_pin_plane_variant(int variant) { return fde::pin_plane_variant(variant) ? FDE_OK : FDE_EINVAL; }
+
 fde_status fde_set_gemm_path(int path) {
   if (path != 0 && path != 1 && path != 3) return FDE_EINVAL;
   fde::set_gemm_hn_path(path);

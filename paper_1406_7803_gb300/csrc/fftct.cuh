@@ -1,8 +1,9 @@
 // fftct.cuh -- compile-time specialised mixed-radix Stockham transforms of many lines held
 // in shared memory, executed by a whole CTA.
 //
-// The length N of a line and its radix sequence (9, 3, 5, then 8, 4, 2) are
-// template constants, so every index division and twiddle stride folds at compile time.
+// The length N of a line, its radix sequence (9, 3, 5, then 8, 4, 2 by default) and the
+// register budget of a stage are template constants, so every index division and twiddle
+// stride folds at compile time.
 // A stage works on the flattened set of (line, butterfly) items of a batch of lines: each
 // thread loads up to IPT butterflies into registers, the CTA synchronises, the permuted
 // outputs are written back, and the CTA synchronises again (in place, one buffer).
@@ -21,14 +22,20 @@ struct CtPlan {
   int r[8];
 };
 
-// Radix order: the odd radices (9, 3, 5) first, then 8, 4, 2.  The first stage writes its
+// Radix order 0: the odd radices (9, 3, 5) first, then 8, 4, 2.  The first stage writes its
 // outputs R complex values apart; an odd R spreads a warp's stores over every shared-memory
 // bank, where R = 8 put them on 2 (float2) or 4 (double2) banks.  Later stages write runs of
-// Ns contiguous values.
-__host__ __device__ constexpr CtPlan ct_factor(int n) {
+// Ns contiguous values.  Order 1: largest radix first (8, 9, 4, 3, 5, 2).
+__host__ __device__ constexpr CtPlan ct_factor(int n, int order = 0) {
   CtPlan p{n, 0, {0, 0, 0, 0, 0, 0, 0, 0}};
   int m = n;
+  if (order == 1) {
+    while (m % 8 == 0 && p.ns < 8) { p.r[p.ns++] = 8; m /= 8; }
+  }
   while (m % 9 == 0 && p.ns < 8) { p.r[p.ns++] = 9; m /= 9; }
+  if (order == 1) {
+    while (m % 4 == 0 && p.ns < 8) { p.r[p.ns++] = 4; m /= 4; }
+  }
   while (m % 3 == 0 && p.ns < 8) { p.r[p.ns++] = 3; m /= 3; }
   while (m % 5 == 0 && p.ns < 8) { p.r[p.ns++] = 5; m /= 5; }
   while (m % 8 == 0 && p.ns < 8) { p.r[p.ns++] = 8; m /= 8; }
@@ -37,6 +44,10 @@ __host__ __device__ constexpr CtPlan ct_factor(int n) {
   if (m != 1) p.ns = -1;
   return p;
 }
+
+// Variant V of the staged transform: bits 0-3 the register budget (0: 16 complex values per
+// thread for FP32 data, 9 for FP64; 1: 18 / 9), bit 4 the radix order of ct_factor.
+__host__ __device__ constexpr int ct_order(int V) { return (V >> 4) & 1; }
 
 // 8- and 9-point DFTs as 2 x 4 and 3 x 3 Cooley-Tukey in registers.
 template <typename C> __device__ __forceinline__ void dft8(C* v, int sign) {
@@ -97,20 +108,22 @@ template <int R, typename C> __device__ __forceinline__ void dft_ct(C* v, int si
 }
 
 // Register budget (complex values per thread) of one stage.
-template <typename T> __host__ __device__ constexpr int ct_budget() { return sizeof(T) == 4 ? 16 : 9; }
-template <typename T, int R> __host__ __device__ constexpr int ct_ipt() {
-  return ct_budget<T>() / R > 0 ? ct_budget<T>() / R : 1;
+template <typename T, int V = 0> __host__ __device__ constexpr int ct_budget() {
+  return sizeof(T) == 4 ? ((V & 15) == 1 ? 18 : 16) : 9;
+}
+template <typename T, int R, int V = 0> __host__ __device__ constexpr int ct_ipt() {
+  return ct_budget<T, V>() / R > 0 ? ct_budget<T, V>() / R : 1;
 }
 
-template <typename T, int N, int NT, int S = 0>
+template <typename T, int N, int NT, int V = 0, int S = 0>
 __host__ __device__ constexpr int ct_lines_per_batch() {
-  constexpr CtPlan P = ct_factor(N);
+  constexpr CtPlan P = ct_factor(N, ct_order(V));
   if constexpr (S >= P.ns) {
     return 1 << 20;
   } else {
     constexpr int R = P.r[S];
-    constexpr int here = NT * ct_ipt<T, R>() / (N / R);
-    constexpr int rest = ct_lines_per_batch<T, N, NT, S + 1>();
+    constexpr int here = NT * ct_ipt<T, R, V>() / (N / R);
+    constexpr int rest = ct_lines_per_batch<T, N, NT, V, S + 1>();
     return here < rest ? here : rest;
   }
 }
@@ -133,13 +146,13 @@ struct LinesCols {  // line l at l, element stride pitch (columns of a plane)
   static constexpr bool kUnit = false;
 };
 
-template <typename T, int N, int R, int NS, int NT, int NL, typename A>
+template <typename T, int N, int R, int NS, int NT, int NL, int V, typename A>
 __device__ __forceinline__ void ct_stage(cplx<T>* buf, const A& addr, int l0, int nl,
                                          const cplx<T>* __restrict__ tw, int sign) {
   using C = cplx<T>;
   constexpr int NB = N / R;
   constexpr int TWS = N / (NS * R);
-  constexpr int IPT = ct_ipt<T, R>();
+  constexpr int IPT = ct_ipt<T, R, V>();
   const int es = A::kUnit ? 1 : addr.pitch;
   const int items = nl * NB;
   C v[IPT][R];
@@ -183,13 +196,13 @@ __device__ __forceinline__ void ct_stage(cplx<T>* buf, const A& addr, int l0, in
   __syncthreads();
 }
 
-template <typename T, int N, int NT, int NL, int S, int NS, typename A>
+template <typename T, int N, int NT, int NL, int S, int NS, int V, typename A>
 __device__ __forceinline__ void ct_stages(cplx<T>* buf, const A& addr, int l0, int nl, const cplx<T>* tw, int sign) {
-  constexpr CtPlan P = ct_factor(N);
+  constexpr CtPlan P = ct_factor(N, ct_order(V));
   if constexpr (S < P.ns) {
     constexpr int R = P.r[S];
-    ct_stage<T, N, R, NS, NT, NL>(buf, addr, l0, nl, tw, sign);
-    ct_stages<T, N, NT, NL, S + 1, NS * R>(buf, addr, l0, nl, tw, sign);
+    ct_stage<T, N, R, NS, NT, NL, V>(buf, addr, l0, nl, tw, sign);
+    ct_stages<T, N, NT, NL, S + 1, NS * R, V>(buf, addr, l0, nl, tw, sign);
   }
 }
 
@@ -202,15 +215,15 @@ template <int N, int LB> __host__ __device__ constexpr int ct_full_batch() {
 
 // Transform nlines lines of length N with the whole CTA (NT threads; all must call).
 // Strided (column) lines must come N at a time: nlines == N.
-template <typename T, int N, int NT, typename A>
+template <typename T, int N, int NT, typename A, int V = 0>
 __device__ __forceinline__ void ct_lines(cplx<T>* buf, const A& addr, int nlines, const cplx<T>* tw, int sign) {
-  static_assert(ct_factor(N).ns > 0, "length must factor into 2, 3, 5");
-  constexpr int LB0 = ct_lines_per_batch<T, N, NT>();
+  static_assert(ct_factor(N, ct_order(V)).ns > 0, "length must factor into 2, 3, 5");
+  constexpr int LB0 = ct_lines_per_batch<T, N, NT, V>();
   static_assert(LB0 >= 1, "register budget too small for this length");
   constexpr int LB = A::kUnit ? LB0 : ct_full_batch<N, LB0>();
   for (int l0 = 0; l0 < nlines; l0 += LB) {
     const int nl = nlines - l0 < LB ? nlines - l0 : LB;
-    ct_stages<T, N, NT, LB, 0, 1>(buf, addr, l0, nl, tw, sign);
+    ct_stages<T, N, NT, LB, 0, 1, V>(buf, addr, l0, nl, tw, sign);
   }
 }
 

@@ -8,6 +8,11 @@
 #include "prof.h"
 
 #include <algorithm>
+#include <atomic>
+#include <cstdlib>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 namespace fde {
 
@@ -117,10 +122,11 @@ k_zfwd_ct(const __grid_constant__ HpsiBatch<T> B, T inv_nr, const cplx<T>* __res
 
 // One CTA per (item, band, z-plane): columns in, 2D inverse FFT (y on the rows holding
 // columns, then x), potential multiply, 2D forward FFT, columns out.  n1 = n2 = N.
-// Four FP32 CTAs per SM (42 KB of shared memory each for a 72 x 72 plane) need <= 64
-// registers per thread; FP64 planes (84 KB) fit two.
-template <typename T, int N>
-__global__ void __launch_bounds__(kCtThreads, sizeof(T) == 4 ? 4 : 2)
+// Variants of the plane pass (FP32): V selects the staged transform's register budget and
+// radix order (fftct.cuh), MINB the CTAs per SM the registers are bounded for (four FP32 CTAs
+// of 42 KB for a 72 x 72 plane need <= 64 registers).  FP64 planes (84 KB) fit two CTAs.
+template <typename T, int N, int V = 0, int MINB = (sizeof(T) == 4 ? 4 : 2)>
+__global__ void __launch_bounds__(kCtThreads, MINB)
 k_plane_ct(const __grid_constant__ HpsiBatch<T> B, int n3, const cplx<T>* __restrict__ tw1,
            const cplx<T>* __restrict__ tw2) {
   using C = cplx<T>;
@@ -138,19 +144,19 @@ k_plane_ct(const __grid_constant__ HpsiBatch<T> B, int n3, const cplx<T>* __rest
   __syncthreads();
   for (int c = threadIdx.x; c < sp.ncol; c += kCtThreads) P[sp.col_i1[c] * PITCH + sp.col_i2[c]] = S[c];
   __syncthreads();
-  ct_lines<T, N, kCtThreads>(P, LinesRows{rows, PITCH}, sp.nrow, tw2, +1);
-  ct_lines<T, N, kCtThreads>(P, LinesCols{PITCH}, N, tw1, +1);
-  const T* V = I.vplane + (size_t)i3 * N * N;
+  ct_lines<T, N, kCtThreads, LinesRows, V>(P, LinesRows{rows, PITCH}, sp.nrow, tw2, +1);
+  ct_lines<T, N, kCtThreads, LinesCols, V>(P, LinesCols{PITCH}, N, tw1, +1);
+  const T* vp = I.vplane + (size_t)i3 * N * N;
   for (int idx = threadIdx.x; idx < N * N; idx += kCtThreads) {
     const int i1 = idx / N, i2 = idx - i1 * N;
     C& z = P[i1 * PITCH + i2];
-    const T v = V[idx];
+    const T v = vp[idx];
     z.x *= v;
     z.y *= v;
   }
   __syncthreads();
-  ct_lines<T, N, kCtThreads>(P, LinesCols{PITCH}, N, tw1, -1);
-  ct_lines<T, N, kCtThreads>(P, LinesRows{rows, PITCH}, sp.nrow, tw2, -1);
+  ct_lines<T, N, kCtThreads, LinesCols, V>(P, LinesCols{PITCH}, N, tw1, -1);
+  ct_lines<T, N, kCtThreads, LinesRows, V>(P, LinesRows{rows, PITCH}, sp.nrow, tw2, -1);
   for (int c = threadIdx.x; c < sp.ncol; c += kCtThreads) S[c] = P[sp.col_i1[c] * PITCH + sp.col_i2[c]];
 }
 
@@ -277,20 +283,111 @@ static void ct_zfwd(int n3, unsigned blocks, cudaStream_t st, const HpsiBatch<T>
   }
 }
 
+// Plane-pass variants tried by the tuner (FP32 only; FP64 runs variant 0):
+//   0: budget 16, odd radices first, 4 CTAs/SM    1: budget 18, odd first, 2 CTAs/SM
+//   2: budget 16, largest radix first, 4 CTAs/SM  3: budget 18, odd first, 3 CTAs/SM
+constexpr int kPlaneVariants = 4;
+
+template <typename T, int N, int V, int MINB>
+static void ct_plane_launch(unsigned blocks, cudaStream_t st, const HpsiBatch<T>& B, int n3, const cplx<T>* tw1,
+                            const cplx<T>* tw2) {
+  const size_t sm = (size_t)N * (N + 1) * sizeof(cplx<T>);
+  ct_allow_smem(k_plane_ct<T, N, V, MINB>, sm);
+  count_launches(1);
+  k_plane_ct<T, N, V, MINB><<<blocks, kCtThreads, sm, st>>>(B, n3, tw1, tw2);
+}
+
+template <typename T, int N>
+static void ct_plane_variant(int variant, unsigned blocks, cudaStream_t st, const HpsiBatch<T>& B, int n3,
+                             const cplx<T>* tw1, const cplx<T>* tw2) {
+  if constexpr (sizeof(T) == 4) {
+    if (variant == 1) return ct_plane_launch<T, N, 1, 2>(blocks, st, B, n3, tw1, tw2);
+    if (variant == 2) return ct_plane_launch<T, N, 16, 4>(blocks, st, B, n3, tw1, tw2);
+    if (variant == 3) return ct_plane_launch<T, N, 1, 3>(blocks, st, B, n3, tw1, tw2);
+  }
+  ct_plane_launch<T, N, 0, (sizeof(T) == 4 ? 4 : 2)>(blocks, st, B, n3, tw1, tw2);
+}
+
 template <typename T>
 static void ct_plane(int n, unsigned blocks, cudaStream_t st, const HpsiBatch<T>& B, int n3, const cplx<T>* tw1,
-                     const cplx<T>* tw2) {
-  const size_t sm = (size_t)n * (n + 1) * sizeof(cplx<T>);
+                     const cplx<T>* tw2, int variant) {
   switch (n) {
 #define FDE_CASE(N)                                                          \
   case N:                                                                    \
-    ct_allow_smem(k_plane_ct<T, N>, sm);                                     \
-    count_launches(1);                                                       \
-    k_plane_ct<T, N><<<blocks, kCtThreads, sm, st>>>(B, n3, tw1, tw2);       \
+    ct_plane_variant<T, N>(variant, blocks, st, B, n3, tw1, tw2);            \
     break;
     FDE_CT_PLANES(FDE_CASE)
 #undef FDE_CASE
   }
+}
+
+// Plane-pass tuner: the first large batch (>= kTuneMinPlanes planes) of a grid shape (plane
+// side, z length) times every variant once on the batch itself -- the z pass is rerun before
+// each trial, so the scratch it transforms in place is regenerated -- and keeps the fastest
+// for that shape.  Smaller batches (the eigensolver's residual blocks) use the tuned choice
+// when there is one, else variant 0.  Never runs while the stream is being captured.
+// FDE_PLANE_VARIANT=<v> in the environment pins the variant (reproducible rounding across
+// machines).
+constexpr unsigned kTuneMinPlanes = 4096;
+struct PlaneTuner {
+  std::mutex mu;
+  std::map<std::tuple<int, int, int>, int> best;
+};
+inline PlaneTuner& plane_tuner() {
+  static PlaneTuner t;
+  return t;
+}
+// Pinned variant (-1: tune); FDE_PLANE_VARIANT in the environment sets the initial value.
+inline std::atomic<int>& plane_pin() {
+  static std::atomic<int> pin([] {
+    const char* e = getenv("FDE_PLANE_VARIANT");
+    const int v = e ? atoi(e) : -1;
+    return (v >= 0 && v < kPlaneVariants) ? v : -1;
+  }());
+  return pin;
+}
+// Tuned variant of the FP32 plane pass for a grid shape, or -1 if none was tuned yet.
+inline int tuned_plane_variant(int n, int n3) {
+  PlaneTuner& tuner = plane_tuner();
+  std::lock_guard<std::mutex> lock(tuner.mu);
+  auto it = tuner.best.find(std::make_tuple(n, n3, 4));
+  return it == tuner.best.end() ? -1 : it->second;
+}
+template <typename T>
+static int plane_variant(int n, int n3, unsigned zb, unsigned pb, cudaStream_t st, const HpsiBatch<T>& B,
+                         const FftPlans<T>& fp) {
+  if (sizeof(T) != 4) return 0;
+  const int pinned = plane_pin().load();
+  if (pinned >= 0) return pinned;
+  const auto key = std::make_tuple(n, n3, (int)sizeof(T));
+  PlaneTuner& tuner = plane_tuner();
+  std::lock_guard<std::mutex> lock(tuner.mu);
+  auto& tab = tuner.best;
+  auto it = tab.find(key);
+  if (it != tab.end()) return it->second;
+  if (pb < kTuneMinPlanes) return 0;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return 0;
+  cudaEvent_t a, b;
+  if (cudaEventCreate(&a) != cudaSuccess) return 0;
+  if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return 0; }
+  int bestv = 0;
+  float bestt = 1e30f;
+  for (int v = 0; v < kPlaneVariants; ++v) {
+    ct_zinv<T>(n3, zb, st, B, fp.p3.tw);
+    cudaEventRecord(a, st);
+    ct_plane<T>(n, pb, st, B, n3, fp.p1.tw, fp.p2.tw, v);
+    cudaEventRecord(b, st);
+    float ms = 1e30f;
+    if (cudaEventSynchronize(b) == cudaSuccess && cudaEventElapsedTime(&ms, a, b) == cudaSuccess && ms < bestt) {
+      bestt = ms;
+      bestv = v;
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  tab[key] = bestv;
+  return bestv;
 }
 
 template <typename T>
@@ -351,13 +448,14 @@ bool launch_hpsi_batch_ct(const HpsiItemDesc<T>* items, int nitems, const GridDi
       pb += g.n3 * d.nb;
     }
     if (zb == 0) continue;
+    const int variant = plane_variant<T>(g.n1, g.n3, (unsigned)zb, (unsigned)pb, st, B, fp);
     {
       ProfScope p("k_zinv", st);
       ct_zinv<T>(g.n3, (unsigned)zb, st, B, fp.p3.tw);
     }
     {
       ProfScope p("k_plane", st);
-      ct_plane<T>(g.n1, (unsigned)pb, st, B, g.n3, fp.p1.tw, fp.p2.tw);
+      ct_plane<T>(g.n1, (unsigned)pb, st, B, g.n3, fp.p1.tw, fp.p2.tw, variant);
     }
     {
       ProfScope p("k_zfwd", st);

@@ -12,4 +12,11 @@ template bool launch_hpsi_batch_ct<float>(const HpsiItemDesc<float>*, int, const
                                        cudaStream_t);
 template bool launch_fft3d_ct<float>(cplx<float>*, const GridDims&, const FftPlans<float>&, int, cudaStream_t);
 
+int query_plane_variant(int n1, int n3) { return tuned_plane_variant(n1, n3); }
+bool pin_plane_variant(int v) {
+  if (v < -1 || v >= kPlaneVariants) return false;
+  plane_pin().store(v);
+  return true;
+}
+
 }  // namespace fde

@@ -55,6 +55,12 @@ template <typename T>
 bool launch_hpsi_batch_ct(const HpsiItemDesc<T>* items, int nitems, const GridDims& g, const FftPlans<T>& fp,
                           cudaStream_t st);
 
+// Variant of the FP32 plane pass the tuner chose for plane side n1 and z length n3 (-1: none
+// tuned yet).
+int query_plane_variant(int n1, int n3);
+// Pin the variant (0 .. count - 1) or return to tuning (-1); false for other values.
+bool pin_plane_variant(int v);
+
 // Compile-time-length variants (hpsi_ct.cuh); return false when the grid sizes are not
 // among the instantiated ones, and the runtime-length kernels run instead.
 template <typename T>

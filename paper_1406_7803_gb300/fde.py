@@ -82,6 +82,8 @@ EXPORTS = {
     "fde_gemm_hn_f32": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int,
                                   C.c_void_p, C.c_int, C.c_int]),
     "fde_set_gemm_path": (C.c_int, [C.c_int]),
+    "fde_tuned_plane_variant": (C.c_int, [C.c_int, C.c_int]),
+    "fde_pin_plane_variant": (C.c_int, [C.c_int]),
     "fde_gemm_rot_f32": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int,
                                    C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_int]),
     "fde_dense_eigh": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
@@ -133,6 +135,17 @@ def precond_initial_weights(seed: int = 0) -> np.ndarray:
         out += [W.ravel(), np.zeros(fo)]
     del width
     return np.concatenate(out).astype(np.float32)
+
+
+def tuned_plane_variant(n1: int, n3: int) -> int:
+    """Variant of the FP32 plane pass the tuner chose for this grid shape (-1: none yet)."""
+    return int(load().fde_tuned_plane_variant(int(n1), int(n3)))
+
+
+def pin_plane_variant(variant: int) -> None:
+    """Pin the FP32 plane-pass variant (0..3) for this process, or -1 to return to tuning."""
+    if load().fde_pin_plane_variant(int(variant)) != FDE_OK:
+        raise FDEError(FDE_EINVAL, "fde_pin_plane_variant: variant must be -1..3")
 
 
 def set_gemm_path(path: int) -> None:

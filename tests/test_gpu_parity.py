@@ -152,6 +152,47 @@ def test_batched_hot_step_matches_oracle(prec, tol, graph):
         assert err < tol, (I, k, err)
 
 
+@pytest.fixture(scope="module")
+def slab_system():
+    wl = workloads.molecule_on_slab()
+    return wl, ofde.System(wl)
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+def test_every_plane_variant_matches_oracle(slab_system, variant):
+    """Each compiled variant of the FP32 plane pass (register budget, CTAs per SM, radix order),
+    pinned in turn, gives the oracle's H psi on the full-size molecule-on-slab cell's batched
+    pass within the mixed-precision tolerance (sampled bands of each (subsystem, k))."""
+    wl, sy = slab_system
+    rhos = np.array([workloads.initial_density(wl, I) for I in range(wl.nsub)])
+    stream = torch.cuda.Stream()
+    ctx = fde.context_from_workload(wl, prec="mixed", stream=stream.cuda_stream)
+    for I in range(wl.nsub):
+        ctx.set_density(I, rhos[I])
+    vout = torch.zeros((wl.nsub,) + tuple(wl.grid), dtype=torch.float64, device="cuda")
+    ctx.build_vemb(vout)
+    veff = vout.cpu().numpy()
+    fde.seed_workload(ctx, wl)
+    fde.pin_plane_variant(variant)
+    try:
+        ctx.apply_h_all()
+        torch.cuda.synchronize()
+    finally:
+        fde.pin_plane_variant(-1)
+    for I, s in enumerate(wl.subsystems):
+        for k in range(s.nk):
+            npw = sy.basis[I][k][0].shape[0]
+            psi = torch.zeros((s.nbands, npw), dtype=torch.complex128, device="cuda")
+            ctx.get_orbitals(I, k, psi, s.nbands)
+            out = torch.zeros_like(psi)
+            ctx.get_hpsi(I, k, out)
+            pick = [0, s.nbands - 1]
+            c = psi.cpu().numpy()[pick]
+            want = sy.apply_h(I, k, c, veff[I])
+            got = out.cpu().numpy()[pick]
+            assert np.abs(got - want).max() / np.abs(want).max() < 1e-5, (variant, I, k)
+
+
 def test_apply_h_host_path_matches_device_path():
     wl = workloads.molecule_on_slab_small()
     sy = ofde.System(wl)
