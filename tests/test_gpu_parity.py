@@ -170,7 +170,8 @@ def test_every_plane_variant_matches_oracle(slab_system, variant):
     for I in range(wl.nsub):
         ctx.set_density(I, rhos[I])
     vout = torch.zeros((wl.nsub,) + tuple(wl.grid), dtype=torch.float64, device="cuda")
-    ctx.build_vemb(vout)
+    ctx.build_vemb(vout)  # asynchronous on the context's (non-blocking) stream
+    torch.cuda.synchronize()
     veff = vout.cpu().numpy()
     fde.seed_workload(ctx, wl)
     fde.pin_plane_variant(variant)
