@@ -122,6 +122,22 @@ PLANE_SOURCES = ["paper_1406_7803_gb300/csrc/hpsi_ct.cuh", "paper_1406_7803_gb30
                  "paper_1406_7803_gb300/csrc/fft.cuh", "paper_1406_7803_gb300/csrc/common.cuh"]
 
 
+def max_over_ranks(x, ws, device):
+    """The largest value of x over the ranks of the process group (x itself for one rank)."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job(total_ms_local, steps, units, ws, device):
+    """(ms per step, whole-job units/s): the slowest rank's time, every rank's units."""
+    ms = max_over_ranks(total_ms_local, ws, device) / steps
+    return ms, ws * units / (ms / 1e3)
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -296,12 +312,7 @@ def run_ours(args):
     total_ms = float(np.sum(step_ms))
     prof = {n: ctx.profile_get(n) for n in ("k_zinv", "k_plane", "k_zfwd")}
     ctx.profile_enable(False)
-    if ws > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    ms = total_ms / args.steps
-    value = ws * units / (ms / 1e3)
+    ms, value = whole_job(total_ms, args.steps, units, ws, "cuda")
 
     # the same pass replayed from a captured CUDA graph (launch overhead removed)
     ctx.hot_step(True)
@@ -344,10 +355,7 @@ def run_ours(args):
         e2e_step()
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / ne
-    if ws > 1:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, ws, "cuda")
 
     # roofline of the dominant kernel (the fused plane pass of the local H psi)
     peaks, src = _peaks()
