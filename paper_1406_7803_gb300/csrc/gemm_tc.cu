@@ -18,7 +18,8 @@
 //   registers <- global (8-byte loads, one k-tile of 16 complex ahead) ; split, rotate and
 //   store into the 128-byte-swizzled K-major shared-memory layout the MMA descriptors
 //   describe ; fence.proxy.async ; one elected thread issues 4 k-steps x passes MMAs of
-//   M = 128, N = 128, K = 8 and commits them to the stage's mbarrier ; two stages.
+//   M = 128, N = 128, K = 8 and commits them to the stage's mbarrier ; one stage per CTA,
+//   two CTAs per SM.
 //   Epilogue: tcgen05.ld of the 128 x 128 FP32 accumulator, FP64 partial tile to global;
 //   k_gemm_hn_reduce (linalg.cu) sums the K-splits in a fixed order.
 // Every wait is bounded; on timeout the kernel sets ST_TIMEOUT, waits (bounded) for its
@@ -40,7 +41,10 @@ constexpr int kTcN = 64;       // complex output columns (B rows) per CTA
 constexpr int kTcKc = 16;      // complex K per k-tile (32 floats = one 128-byte row)
 constexpr int kTile = 16384;   // bytes of one 128-row x 128-byte operand tile
 constexpr int kStage = 4 * kTile;  // A hi, A lo, B hi, B lo
-constexpr int kStages = 2;
+// One shared-memory stage per CTA and two CTAs per SM: twice the warps issuing the next
+// k-tile's loads (the kernel is latency-bound) for the same buffering per SM.
+constexpr int kStages = 1;
+constexpr int kCtasPerSm = 2;
 constexpr int kTmemCols = 128;
 constexpr long long kSpin = 1ll << 22;  // bounded mbarrier polls (with back-off: ~1 s)
 
@@ -124,7 +128,7 @@ __device__ __forceinline__ void st2(uint32_t addr, float a, float b) {
 constexpr int kAld = kTcM * kTcKc / kTcThreads;  // A elements per thread per k-tile (8)
 constexpr int kBld = kTcN * kTcKc / kTcThreads;  // B elements per thread per k-tile (4)
 
-__global__ void __launch_bounds__(kTcThreads, 1)
+__global__ void __launch_bounds__(kTcThreads, kCtasPerSm)
 k_gemm_hn_tc(const float2* __restrict__ A, int lda, const float2* __restrict__ B, int ldb, int m, int n, int K,
              int kchunk, int passes, double2* __restrict__ part) {
   extern __shared__ unsigned char smem_raw[];
@@ -195,11 +199,11 @@ k_gemm_hn_tc(const float2* __restrict__ A, int lda, const float2* __restrict__ B
   int issued = 0;  // k-tiles whose MMAs were committed (meaningful in thread 0)
   if (nt > 0) load(0);
   for (int t = 0; t < nt; ++t) {
-    const int s = t & 1;
+    const int s = t % kStages;
     const uint32_t st = base + (uint32_t)s * kStage;
     if (t >= kStages) {
-      // stage s is free once the MMAs of tile t - 2 have completed
-      if (tid == 0 && !mbar_wait(su32(&bars[s]), (unsigned)(((t - kStages) >> 1) & 1))) abort_flag = 1;
+      // stage s is free once the MMAs of tile t - kStages have completed
+      if (tid == 0 && !mbar_wait(su32(&bars[s]), (unsigned)(((t - kStages) / kStages) & 1))) abort_flag = 1;
       __syncthreads();
       if (abort_flag) break;
     }
@@ -285,9 +289,10 @@ constexpr int kRotKi = 16;             // input rows i per k-tile (32 floats)
 constexpr int kRotA = kRotJ * 128;     // bytes of one A tile (16 KB)
 constexpr int kRotB = 2 * kRotG * 128; // bytes of one B tile (32 KB)
 constexpr int kRotStage = 2 * kRotA + 2 * kRotB;
+constexpr int kRotStages = 2;
 constexpr int kRotTmemCols = 256;
 constexpr int kRotPitch = 2 * kRotG + 4;  // floats per row of the staged accumulator
-static_assert((size_t)kRotJ * kRotPitch * 4 <= (size_t)kStages * (2 * kRotJ * 128 + 4 * kRotG * 128),
+static_assert((size_t)kRotJ * kRotPitch * 4 <= (size_t)kRotStages * (2 * kRotJ * 128 + 4 * kRotG * 128),
               "staged accumulator fits the stage buffers");
 constexpr uint32_t kIdescRot = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(2 * kRotG / 8) << 17) |
                                ((uint32_t)(kRotJ / 16) << 24);
@@ -308,7 +313,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 k_gemm_rot_tc(const float2* __restrict__ X, int ldx, const double2* __restrict__ U, int ldu, int m, int n, int K,
               float2* __restrict__ Y, int ldy, float alpha, float beta, int passes) {
   extern __shared__ unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t bars[kStages];
+  __shared__ __align__(8) uint64_t bars[kRotStages];
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -317,7 +322,7 @@ k_gemm_rot_tc(const float2* __restrict__ X, int ldx, const double2* __restrict__
   const int nt = (m + kRotKi - 1) / kRotKi;
 
   if (tid == 0) {
-    for (int q = 0; q < kStages; ++q) mbar_init(su32(&bars[q]), 1);
+    for (int q = 0; q < kRotStages; ++q) mbar_init(su32(&bars[q]), 1);
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -381,10 +386,10 @@ k_gemm_rot_tc(const float2* __restrict__ X, int ldx, const double2* __restrict__
   int issued = 0;
   if (nt > 0) load(0);
   for (int t = 0; t < nt; ++t) {
-    const int s = t & 1;
+    const int s = t % kRotStages;
     const uint32_t st = base + (uint32_t)s * kRotStage;
-    if (t >= kStages) {
-      if (tid == 0 && !mbar_wait(su32(&bars[s]), (unsigned)(((t - kStages) >> 1) & 1))) abort_flag = 1;
+    if (t >= kRotStages) {
+      if (tid == 0 && !mbar_wait(su32(&bars[s]), (unsigned)(((t - kRotStages) / kRotStages) & 1))) abort_flag = 1;
       __syncthreads();
       if (abort_flag) break;
     }
@@ -410,8 +415,8 @@ k_gemm_rot_tc(const float2* __restrict__ X, int ldx, const double2* __restrict__
     if (t + 1 < nt) load(t + 1);
   }
   if (tid == 0) {
-    for (int s = 0; s < kStages && s < issued; ++s) {
-      const int uses = (issued - s + kStages - 1) / kStages;
+    for (int s = 0; s < kRotStages && s < issued; ++s) {
+      const int uses = (issued - s + kRotStages - 1) / kRotStages;
       if (!mbar_wait(su32(&bars[s]), (unsigned)((uses - 1) & 1))) abort_flag = 1;
     }
   }
@@ -473,8 +478,8 @@ k_gemm_rot_tc(const float2* __restrict__ X, int ldx, const double2* __restrict__
 
 }  // namespace
 
-// K-splits of the tensor-core product: about two CTAs per SM over the grid, at least eight
-// k-tiles per split.
+// K-splits of the tensor-core product: about two resident CTAs per SM over the grid, at
+// least eight k-tiles per split.
 int gemm_hn_tc_splits(int m, int n, int K) {
   const int tiles = ceil_div(m, kTcM) * ceil_div(n, kTcN);
   int s = ceil_div(2 * 152, tiles);
@@ -519,7 +524,7 @@ unsigned gemm_tc_take_status(cudaStream_t st) {
 
 namespace fde {
 
-size_t gemm_rot_tc_smem() { return (size_t)kStages * kRotStage + 1024; }
+size_t gemm_rot_tc_smem() { return (size_t)kRotStages * kRotStage + 1024; }
 
 // Y = alpha U^T-combination of the rows of X + beta Y on the tensor cores; returns false if the
 // kernel could not be configured (nothing launched).

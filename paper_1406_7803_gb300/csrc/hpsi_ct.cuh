@@ -17,7 +17,11 @@
 namespace fde {
 
 constexpr int kCtThreads = 256;
-constexpr int kCtCols = 8;  // z-lines per CTA in the z passes and axis transforms
+// Sphere columns (z-lines) per CTA in the z passes: as many as one staged batch keeps every
+// thread busy with (12 for 180-point FP32 lines), at most 16.
+template <typename T, int N3> __host__ __device__ constexpr int ct_zcols() {
+  return ct_lines_per_batch<T, N3, kCtThreads>() < 16 ? ct_lines_per_batch<T, N3, kCtThreads>() : 16;
+}
 
 // Every (subsystem, k) block of bands is an item; the kernels below run a batch of items in
 // one launch (the batch travels as a kernel parameter), so subsystems of uneven size share
@@ -51,20 +55,22 @@ __global__ void __launch_bounds__(kCtThreads)
 k_zinv_ct(const __grid_constant__ HpsiBatch<T> B, const cplx<T>* __restrict__ tw) {
   using C = cplx<T>;
   constexpr int LP = N3 + 1;
-  __shared__ __align__(16) C lines[kCtCols * LP];
+  constexpr int ZC = ct_zcols<T, N3>();
+  __shared__ __align__(16) C lines[ZC * LP];
   const HpsiItem<T>& I = B.it[batch_item(B, blockIdx.x, false)];
   const SphereDev& sp = I.sp;
-  const int ntile = (sp.ncol + kCtCols - 1) / kCtCols;
+  const int ntile = (sp.ncol + ZC - 1) / ZC;
   const int local = blockIdx.x - I.zstart;
-  const int b = local / ntile, c0 = (local - b * ntile) * kCtCols;
+  const int b = local / ntile, c0 = (local - b * ntile) * ZC;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int i = threadIdx.x; i < kCtCols * LP; i += kCtThreads) lines[i] = mk<T>(0, 0);
+  for (int i = threadIdx.x; i < ZC * LP; i += kCtThreads) lines[i] = mk<T>(0, 0);
   __syncthreads();
-  const int c = c0 + w;
-  if (c < sp.ncol) {
+  for (int cc = w; cc < ZC; cc += kCtThreads / 32) {  // one warp per column
+    const int c = c0 + cc;
+    if (c >= sp.ncol) break;
     const int s = sp.col_start[c], e = sp.col_start[c + 1], m3 = sp.col_m3lo[c];
     const C* src = I.psi + (size_t)b * I.ld + s;
-    C* L = lines + w * LP;
+    C* L = lines + cc * LP;
     for (int t = lane; t < e - s; t += 32) {
       int i3 = m3 + t;
       i3 += (i3 < 0) ? N3 : 0;
@@ -72,11 +78,11 @@ k_zinv_ct(const __grid_constant__ HpsiBatch<T> B, const cplx<T>* __restrict__ tw
     }
   }
   __syncthreads();
-  ct_lines<T, N3, kCtThreads>(lines, LinesContig{LP}, kCtCols, tw, +1);
-  const int nc = min(kCtCols, sp.ncol - c0);
+  ct_lines<T, N3, kCtThreads>(lines, LinesContig{LP}, ZC, tw, +1);
+  const int nc = min(ZC, sp.ncol - c0);
   C* dst = I.scratch + (size_t)b * N3 * sp.ncol + c0;
-  for (int idx = threadIdx.x; idx < N3 * kCtCols; idx += kCtThreads) {
-    const int i3 = idx / kCtCols, ww = idx % kCtCols;
+  for (int idx = threadIdx.x; idx < N3 * ZC; idx += kCtThreads) {
+    const int i3 = idx / ZC, ww = idx % ZC;
     if (ww < nc) dst[(size_t)i3 * sp.ncol + ww] = lines[ww * LP + i3];
   }
 }
@@ -86,37 +92,40 @@ __global__ void __launch_bounds__(kCtThreads)
 k_zfwd_ct(const __grid_constant__ HpsiBatch<T> B, T inv_nr, const cplx<T>* __restrict__ tw) {
   using C = cplx<T>;
   constexpr int LP = N3 + 1;
-  __shared__ __align__(16) C lines[kCtCols * LP];
+  constexpr int ZC = ct_zcols<T, N3>();
+  __shared__ __align__(16) C lines[ZC * LP];
   const HpsiItem<T>& I = B.it[batch_item(B, blockIdx.x, false)];
   const SphereDev& sp = I.sp;
-  const int ntile = (sp.ncol + kCtCols - 1) / kCtCols;
+  const int ntile = (sp.ncol + ZC - 1) / ZC;
   const int local = blockIdx.x - I.zstart;
-  const int b = local / ntile, c0 = (local - b * ntile) * kCtCols;
+  const int b = local / ntile, c0 = (local - b * ntile) * ZC;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nc = min(kCtCols, sp.ncol - c0);
+  const int nc = min(ZC, sp.ncol - c0);
   const C* src = I.scratch + (size_t)b * N3 * sp.ncol + c0;
-  for (int idx = threadIdx.x; idx < N3 * kCtCols; idx += kCtThreads) {
-    const int i3 = idx / kCtCols, ww = idx % kCtCols;
+  for (int idx = threadIdx.x; idx < N3 * ZC; idx += kCtThreads) {
+    const int i3 = idx / ZC, ww = idx % ZC;
     lines[ww * LP + i3] = (ww < nc) ? src[(size_t)i3 * sp.ncol + ww] : mk<T>(0, 0);
   }
   __syncthreads();
-  ct_lines<T, N3, kCtThreads>(lines, LinesContig{LP}, kCtCols, tw, -1);
-  const int c = c0 + w;
-  if (c >= sp.ncol) return;
-  const C* L = lines + w * LP;
-  const int s = sp.col_start[c], e = sp.col_start[c + 1], m3 = sp.col_m3lo[c];
+  ct_lines<T, N3, kCtThreads>(lines, LinesContig{LP}, ZC, tw, -1);
   const C* ps = I.psi + (size_t)b * I.ld;
   C* hs = I.hpsi + (size_t)b * I.ld;
-  for (int t = lane; t < e - s; t += 32) {
-    int i3 = m3 + t;
-    i3 += (i3 < 0) ? N3 : 0;
-    const int gidx = s + t;
-    const C x = ps[gidx];
-    const T kk = I.kin[gidx];
-    C o = L[i3];
-    o.x = o.x * inv_nr + kk * x.x;
-    o.y = o.y * inv_nr + kk * x.y;
-    hs[gidx] = o;
+  for (int cc = w; cc < ZC; cc += kCtThreads / 32) {  // one warp per column
+    const int c = c0 + cc;
+    if (c >= sp.ncol) break;
+    const C* L = lines + cc * LP;
+    const int s = sp.col_start[c], e = sp.col_start[c + 1], m3 = sp.col_m3lo[c];
+    for (int t = lane; t < e - s; t += 32) {
+      int i3 = m3 + t;
+      i3 += (i3 < 0) ? N3 : 0;
+      const int gidx = s + t;
+      const C x = ps[gidx];
+      const T kk = I.kin[gidx];
+      C o = L[i3];
+      o.x = o.x * inv_nr + kk * x.x;
+      o.y = o.y * inv_nr + kk * x.y;
+      hs[gidx] = o;
+    }
   }
 }
 
@@ -255,6 +264,17 @@ template <typename T> bool ct_plane_ok(int n1, int n2) {
     return true;
     default: return false;
   }
+}
+
+template <typename T> static int ct_zcols_host(int n3) {
+  switch (n3) {
+#define FDE_CASE(N) \
+  case N:           \
+    return ct_zcols<T, N>();
+    FDE_CT_LINES(FDE_CASE)
+#undef FDE_CASE
+  }
+  return 8;
 }
 
 template <typename T>
@@ -444,7 +464,7 @@ bool launch_hpsi_batch_ct(const HpsiItemDesc<T>* items, int nitems, const GridDi
       it.nb = d.nb;
       it.zstart = zb;
       it.pstart = pb;
-      zb += ceil_div(d.sp.ncol, kCtCols) * d.nb;
+      zb += ceil_div(d.sp.ncol, ct_zcols_host<T>(g.n3)) * d.nb;
       pb += g.n3 * d.nb;
     }
     if (zb == 0) continue;
@@ -482,7 +502,7 @@ bool launch_density_ct(const cplx<T>* psi, int ldpsi, int nb, const double* weig
   HpsiBatch<T> B;
   B.n = 1;
   B.it[0] = HpsiItem<T>{sp, psi, nullptr, nullptr, nullptr, scratch, ldpsi, nb, 0, 0};
-  ct_zinv<T>(g.n3, (unsigned)(ceil_div(sp.ncol, kCtCols) * nb), st, B, fp.p3.tw);
+  ct_zinv<T>(g.n3, (unsigned)(ceil_div(sp.ncol, ct_zcols_host<T>(g.n3)) * nb), st, B, fp.p3.tw);
   ct_plane_density<T>(g.n1, g.n3, st, scratch, sp, nb, weight, rho_plane, accumulate, fp.p1.tw, fp.p2.tw);
   return true;
 }
