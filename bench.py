@@ -100,26 +100,41 @@ class Clocks:
         return out
 
 
-def _profile_traffic(name, files):
+def kernel_source_digest(files, function=None):
+    """SHA-256 (16 hex digits) of the sources a kernel is built from: whole files, plus, for
+    (file, name), the text of the __global__ function `name` in that file."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(f.encode() + b"\0" + fh.read())
+    if function:
+        f, name = function
+        text = open(os.path.join(ROOT, f)).read()
+        a = text.index(name + "(")
+        a = text.rindex("template", 0, a)
+        b = text.index("\n}\n", a) + 3
+        h.update(name.encode() + b"\0" + text[a:b].encode())
+    return h.hexdigest()[:16]
+
+
+def _profile_traffic(name, files, function=None):
     """DRAM bytes per launch of a kernel from its committed ncu summary (profiles/<name>.md),
     or None when the kernel's sources have changed since the counters were taken."""
-    import hashlib
     try:
         text = open(os.path.join(ROOT, "profiles", name + ".md")).read()
     except OSError:
         return None
     fields = dict(l.split(":", 1) for l in text.splitlines() if l.startswith(("traffic_bytes_per_launch:", "source_sha256:")))
-    h = hashlib.sha256()
-    for f in files:
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(f.encode() + b"\0" + fh.read())
-    if fields.get("source_sha256", "").split()[0:1] != [h.hexdigest()[:16]]:
+    if fields.get("source_sha256", "").split()[0:1] != [kernel_source_digest(files, function)]:
         return None
     return float(fields["traffic_bytes_per_launch"])
 
 
-PLANE_SOURCES = ["paper_1406_7803_gb300/csrc/hpsi_ct.cuh", "paper_1406_7803_gb300/csrc/fftct.cuh",
-                 "paper_1406_7803_gb300/csrc/fft.cuh", "paper_1406_7803_gb300/csrc/common.cuh"]
+# the plane pass: its own function text in hpsi_ct.cuh plus the staged-transform core
+PLANE_SOURCES = ["paper_1406_7803_gb300/csrc/fftct.cuh", "paper_1406_7803_gb300/csrc/fft.cuh",
+                 "paper_1406_7803_gb300/csrc/common.cuh"]
+PLANE_FUNCTION = ("paper_1406_7803_gb300/csrc/hpsi_ct.cuh", "k_plane_ct")
 
 
 def max_over_ranks(x, ws, device):
@@ -380,7 +395,8 @@ def run_ours(args):
         if args.prec == "fp64":
             fp_peak = 1.25  # nominal FP64 rate of the part (TFLOP/s)
         achieved = flops_per_launch / sec / 1e12
-        traffic = _profile_traffic("k_plane_ct_molecule_on_slab", PLANE_SOURCES) if args.prec == "mixed" else None
+        traffic = (_profile_traffic("k_plane_ct_molecule_on_slab", PLANE_SOURCES, PLANE_FUNCTION)
+                   if args.prec == "mixed" else None)
         roof = {"bound": "alu", "achieved": achieved, "peak": fp_peak, "unit": "TFLOP/s", "frac": achieved / fp_peak,
                 "traffic": traffic, "kernel": "k_plane", "launches": n_plane,
                 "avg_launch_us": 1e6 * sec, "peak_source": f"{'FP32' if args.prec != 'fp64' else 'FP64'} lanes x "

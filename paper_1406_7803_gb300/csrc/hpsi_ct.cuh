@@ -17,10 +17,12 @@
 namespace fde {
 
 constexpr int kCtThreads = 256;
-// Sphere columns (z-lines) per CTA in the z passes: as many as one staged batch keeps every
-// thread busy with (12 for 180-point FP32 lines), at most 16.
+// Sphere columns (z-lines) per CTA in the z passes: 8 (one warp gathers or scatters each
+// column), fewer when one staged batch holds fewer lines.  Measured on the 72 x 72 x 180 cell:
+// 12 columns of 180 points (the full FP32 batch) made the forward pass 17 % slower (fewer
+// CTAs, two columns per warp in the epilogue) for a 4 % faster inverse pass.
 template <typename T, int N3> __host__ __device__ constexpr int ct_zcols() {
-  return ct_lines_per_batch<T, N3, kCtThreads>() < 16 ? ct_lines_per_batch<T, N3, kCtThreads>() : 16;
+  return ct_lines_per_batch<T, N3, kCtThreads>() < 8 ? ct_lines_per_batch<T, N3, kCtThreads>() : 8;
 }
 
 // Every (subsystem, k) block of bands is an item; the kernels below run a batch of items in
