@@ -663,9 +663,11 @@ template <typename T> struct EngineT : Engine {
     // 2. functionals of the total density
     grid_pw_total(rho_tot.p, gp, func.xc, func.kedf, func.rho_cut, want_pot ? vpart.p : nullptr,
                   (want_pot && grad) ? htot[0].p : nullptr, htot[1].p, htot[2].p, nr, partial.p, st);
-    grid_finalize(partial.p, 2, dv, scal.p + 1, st);
-    grid_dot_partial(vloc.p, rho_tot.p, nr, 0, partial.p, st);
-    grid_finalize(partial.p, 1, dv, scal.p + 3, st);
+    if (want_e) {  // the pointwise kernels always leave their block sums; reduce them only when asked
+      grid_finalize(partial.p, 2, dv, scal.p + 1, st);
+      grid_dot_partial(vloc.p, rho_tot.p, nr, 0, partial.p, st);
+      grid_finalize(partial.p, 1, dv, scal.p + 3, st);
+    }
     if (want_e) {
       grid_assemble_pair(RT, nullptr, nullptr, nullptr, 0, nullptr, g, cell, partial.p, st);
       grid_finalize(partial.p, 1, 0.5 * omega, scal.p + 0, st);
@@ -686,8 +688,10 @@ template <typename T> struct EngineT : Engine {
       grid_pw_pair(A.rho.p, B ? B->rho.p : nullptr, Pa, Pb, Pz, htot[0].p, htot[1].p, htot[2].p,
                    want_pot ? vpart.p : nullptr, want_e ? func.xc : -1, func.kedf, func.rho_cut, pa ? A.veff.p : nullptr,
                    pb ? B->veff.p : nullptr, (pot && grad) ? 1 : 0, nr, partial.p, st);
-      grid_finalize(partial.p, 2, dv, scal.p + 5 + 3 * ia, st);
-      if (hb) grid_finalize(partial.p + 2 * nrb, 2, dv, scal.p + 5 + 3 * ib, st);
+      if (want_e) {
+        grid_finalize(partial.p, 2, dv, scal.p + 5 + 3 * ia, st);
+        if (hb) grid_finalize(partial.p + 2 * nrb, 2, dv, scal.p + 5 + 3 * ib, st);
+      }
       if (!pot) continue;
       if (grad) {
         launch_fft3d<double>(Pa, g, plans64.fp, -1, st);

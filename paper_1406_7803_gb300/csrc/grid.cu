@@ -68,10 +68,13 @@ struct Gpt {
   bool nyq;
 };
 
+// Grid points are indexed in 32 bits here: the context accepts at most 320 points per axis,
+// so a grid has fewer than 2^31 points.
 __device__ __forceinline__ Gpt gvec(long long idx, const GridDims& g, const CellDev& c) {
-  const int i3 = (int)(idx % g.n3);
-  const long long r = idx / g.n3;
-  const int i2 = (int)(r % g.n2), i1 = (int)(r / g.n2);
+  const int id = (int)idx;
+  const int i3 = id % g.n3;
+  const int r = id / g.n3;
+  const int i2 = r % g.n2, i1 = r / g.n2;
   const int m1 = (i1 < (g.n1 + 1) / 2) ? i1 : i1 - g.n1;
   const int m2 = (i2 < (g.n2 + 1) / 2) ? i2 : i2 - g.n2;
   const int m3 = (i3 < (g.n3 + 1) / 2) ? i3 : i3 - g.n3;
@@ -413,12 +416,15 @@ __global__ void k_dot_partial(const double* __restrict__ a, const double* __rest
   block_sum_store(acc, partial + blockIdx.x);
 }
 
+// out[q] = scale * sum_b partial[q][b]: warp q, lane l sums b = l, l + 32, ... and the lane
+// sums are combined by a fixed butterfly (deterministic; the block count is a launch constant).
 __global__ void k_finalize(const double* __restrict__ partial, int nblk, int nq, double scale, double* out) {
-  const int q = threadIdx.x;
+  const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (q >= nq) return;
   double t = 0;
-  for (int b = 0; b < nblk; ++b) t += partial[(size_t)q * nblk + b];
-  out[q] = t * scale;
+  for (int b = lane; b < nblk; b += 32) t += partial[(size_t)q * nblk + b];
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  if (lane == 0) out[q] = t * scale;
 }
 
 // out = sum_k c[k] * (a_k + beta * r_k) for the Pulay step; coefs on the device.
@@ -447,11 +453,12 @@ __global__ void k_nonfinite(const double* __restrict__ a, long long n, unsigned*
 // packs the subsystem densities, gradient components and divergence arguments in pairs, so
 // that it needs half the FP64 transforms while computing the same quantities.
 __device__ __forceinline__ long long neg_index(long long idx, const GridDims& g) {
-  const int i3 = (int)(idx % g.n3);
-  const long long r = idx / g.n3;
-  const int i2 = (int)(r % g.n2), i1 = (int)(r / g.n2);
+  const int id = (int)idx;
+  const int i3 = id % g.n3;
+  const int r = id / g.n3;
+  const int i2 = r % g.n2, i1 = r / g.n2;
   const int j1 = i1 ? g.n1 - i1 : 0, j2 = i2 ? g.n2 - i2 : 0, j3 = i3 ? g.n3 - i3 : 0;
-  return ((long long)j1 * g.n2 + j2) * g.n3 + j3;
+  return (long long)((j1 * g.n2 + j2) * g.n3 + j3);
 }
 __device__ __forceinline__ void unpack2(double2 c, double2 cn, double2* a, double2* b) {
   *a = make_double2(0.5 * (c.x + cn.x), 0.5 * (c.y - cn.y));
@@ -719,7 +726,7 @@ void grid_dot_partial(const double* a, const double* b, long long n, int mode, d
 }
 void grid_finalize(const double* partial, int nq, double scale, double* out, cudaStream_t st) {
   count_launches(1);
-  k_finalize<<<1, 32, 0, st>>>(partial, kRedBlocks, nq, scale, out);
+  k_finalize<<<1, 32 * nq, 0, st>>>(partial, kRedBlocks, nq, scale, out);
 }
 void grid_lincomb(const double* const* ins, const double* const* res, const double* coef, int m, double beta,
                   long long n, double* out, cudaStream_t st) {
