@@ -348,7 +348,7 @@ fde_status fde_set_gemm_path(int path);
  * variant chosen for plane side n1 and z length n3, or -1 if none was tuned yet; the
  * environment variable FDE_PLANE_VARIANT pins one. */
 int fde_tuned_plane_variant(int n1, int n3);
-/* Pin the plane-pass variant used from now on in this process (0 .. 5), or return to tuning
+/* Pin the plane-pass variant used from now on in this process (0 .. 3), or return to tuning
  * (-1).  FDE_EINVAL for other values. */
 fde_status fde_pin_plane_variant(int variant);
 

@@ -135,12 +135,9 @@ k_zfwd_ct(const __grid_constant__ HpsiBatch<T> B, T inv_nr, const cplx<T>* __res
 // columns, then x), potential multiply, 2D forward FFT, columns out.  n1 = n2 = N.
 // Variants of the plane pass (FP32): V selects the staged transform's register budget and
 // radix order (fftct.cuh), MINB the CTAs per SM the registers are bounded for (four FP32 CTAs
-// of 42 KB for a 72 x 72 plane need <= 64 registers), NT the threads per CTA (288 = 9 warps
-// lets one batch hold 36 lines of a radix-9 stage: the ~33 sphere rows in one batch and the
-// 72 columns in two, instead of two and three batches with 256).  FP64 planes (84 KB) fit
-// two CTAs.
-template <typename T, int N, int V = 0, int MINB = (sizeof(T) == 4 ? 4 : 2), int NT = kCtThreads>
-__global__ void __launch_bounds__(NT, MINB)
+// of 42 KB for a 72 x 72 plane need <= 64 registers).  FP64 planes (84 KB) fit two CTAs.
+template <typename T, int N, int V = 0, int MINB = (sizeof(T) == 4 ? 4 : 2)>
+__global__ void __launch_bounds__(kCtThreads, MINB)
 k_plane_ct(const __grid_constant__ HpsiBatch<T> B, int n3, const cplx<T>* __restrict__ tw1,
            const cplx<T>* __restrict__ tw2) {
   using C = cplx<T>;
@@ -153,15 +150,15 @@ k_plane_ct(const __grid_constant__ HpsiBatch<T> B, int n3, const cplx<T>* __rest
   const int local = blockIdx.x - I.pstart;
   const int b = local / n3, i3 = local - b * n3;
   C* S = I.scratch + ((size_t)b * n3 + i3) * sp.ncol;
-  for (int idx = threadIdx.x; idx < N * PITCH; idx += NT) P[idx] = mk<T>(0, 0);
-  for (int r = threadIdx.x; r < sp.nrow; r += NT) rows[r] = sp.row_i1[r];
+  for (int idx = threadIdx.x; idx < N * PITCH; idx += kCtThreads) P[idx] = mk<T>(0, 0);
+  for (int r = threadIdx.x; r < sp.nrow; r += kCtThreads) rows[r] = sp.row_i1[r];
   __syncthreads();
-  for (int c = threadIdx.x; c < sp.ncol; c += NT) P[sp.col_i1[c] * PITCH + sp.col_i2[c]] = S[c];
+  for (int c = threadIdx.x; c < sp.ncol; c += kCtThreads) P[sp.col_i1[c] * PITCH + sp.col_i2[c]] = S[c];
   __syncthreads();
-  ct_lines<T, N, NT, LinesRows, V>(P, LinesRows{rows, PITCH}, sp.nrow, tw2, +1);
-  ct_lines<T, N, NT, LinesCols, V>(P, LinesCols{PITCH}, N, tw1, +1);
+  ct_lines<T, N, kCtThreads, LinesRows, V>(P, LinesRows{rows, PITCH}, sp.nrow, tw2, +1);
+  ct_lines<T, N, kCtThreads, LinesCols, V>(P, LinesCols{PITCH}, N, tw1, +1);
   const T* vp = I.vplane + (size_t)i3 * N * N;
-  for (int idx = threadIdx.x; idx < N * N; idx += NT) {
+  for (int idx = threadIdx.x; idx < N * N; idx += kCtThreads) {
     const int i1 = idx / N, i2 = idx - i1 * N;
     C& z = P[i1 * PITCH + i2];
     const T v = vp[idx];
@@ -169,9 +166,9 @@ k_plane_ct(const __grid_constant__ HpsiBatch<T> B, int n3, const cplx<T>* __rest
     z.y *= v;
   }
   __syncthreads();
-  ct_lines<T, N, NT, LinesCols, V>(P, LinesCols{PITCH}, N, tw1, -1);
-  ct_lines<T, N, NT, LinesRows, V>(P, LinesRows{rows, PITCH}, sp.nrow, tw2, -1);
-  for (int c = threadIdx.x; c < sp.ncol; c += NT) S[c] = P[sp.col_i1[c] * PITCH + sp.col_i2[c]];
+  ct_lines<T, N, kCtThreads, LinesCols, V>(P, LinesCols{PITCH}, N, tw1, -1);
+  ct_lines<T, N, kCtThreads, LinesRows, V>(P, LinesRows{rows, PITCH}, sp.nrow, tw2, -1);
+  for (int c = threadIdx.x; c < sp.ncol; c += kCtThreads) S[c] = P[sp.col_i1[c] * PITCH + sp.col_i2[c]];
 }
 
 template <typename T, int N>
@@ -311,17 +308,17 @@ static void ct_zfwd(int n3, unsigned blocks, cudaStream_t st, const HpsiBatch<T>
 // Plane-pass variants tried by the tuner (FP32 only; FP64 runs variant 0):
 //   0: budget 16, odd radices first, 4 CTAs/SM    1: budget 18, odd first, 2 CTAs/SM
 //   2: budget 16, largest radix first, 4 CTAs/SM  3: budget 18, odd first, 3 CTAs/SM
-//   4: budget 16, odd first, 288 threads, 3 CTAs/SM
-//   5: budget 16, odd first, 288 threads, 2 CTAs/SM
-constexpr int kPlaneVariants = 6;
+// (Measured and dropped: 288-thread CTAs, which hold the ~33 sphere rows in one radix-9 batch
+// and the 72 columns in two, ran 1.75 ms at 3 CTAs/SM and 2.30 ms at 2 against 1.49 ms.)
+constexpr int kPlaneVariants = 4;
 
-template <typename T, int N, int V, int MINB, int NT = kCtThreads>
+template <typename T, int N, int V, int MINB>
 static void ct_plane_launch(unsigned blocks, cudaStream_t st, const HpsiBatch<T>& B, int n3, const cplx<T>* tw1,
                             const cplx<T>* tw2) {
   const size_t sm = (size_t)N * (N + 1) * sizeof(cplx<T>);
-  ct_allow_smem(k_plane_ct<T, N, V, MINB, NT>, sm);
+  ct_allow_smem(k_plane_ct<T, N, V, MINB>, sm);
   count_launches(1);
-  k_plane_ct<T, N, V, MINB, NT><<<blocks, NT, sm, st>>>(B, n3, tw1, tw2);
+  k_plane_ct<T, N, V, MINB><<<blocks, kCtThreads, sm, st>>>(B, n3, tw1, tw2);
 }
 
 template <typename T, int N>
@@ -331,8 +328,6 @@ static void ct_plane_variant(int variant, unsigned blocks, cudaStream_t st, cons
     if (variant == 1) return ct_plane_launch<T, N, 1, 2>(blocks, st, B, n3, tw1, tw2);
     if (variant == 2) return ct_plane_launch<T, N, 16, 4>(blocks, st, B, n3, tw1, tw2);
     if (variant == 3) return ct_plane_launch<T, N, 1, 3>(blocks, st, B, n3, tw1, tw2);
-    if (variant == 4) return ct_plane_launch<T, N, 0, 3, 288>(blocks, st, B, n3, tw1, tw2);
-    if (variant == 5) return ct_plane_launch<T, N, 0, 2, 288>(blocks, st, B, n3, tw1, tw2);
   }
   ct_plane_launch<T, N, 0, (sizeof(T) == 4 ? 4 : 2)>(blocks, st, B, n3, tw1, tw2);
 }
