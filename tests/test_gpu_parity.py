@@ -43,6 +43,14 @@ def _dev(a, dtype=torch.complex128):
 WL_SMALL = [workloads.plain_fde_32, workloads.molecule_on_slab_small]
 
 
+def molecule_on_slab_small_lc94():
+    """The small slab + molecule cell with the LC94 kinetic functional in place of revAPBEK
+    (the second GGA nonadditive kinetic functional named in the Computational Details)."""
+    import dataclasses
+    wl = workloads.molecule_on_slab_small()
+    return dataclasses.replace(wl, kedf=workloads.KEDF_LC94, name=wl.name + "-lc94")
+
+
 @pytest.mark.parametrize("make", WL_SMALL)
 def test_basis_bit_exact(make):
     wl = make()
@@ -208,7 +216,7 @@ def test_apply_h_host_path_matches_device_path():
     assert np.abs(out - want).max() / np.abs(want).max() < 1e-10
 
 
-@pytest.mark.parametrize("make", WL_SMALL)
+@pytest.mark.parametrize("make", WL_SMALL + [molecule_on_slab_small_lc94])
 def test_build_vemb_matches_oracle(make):
     wl = make()
     sy = ofde.System(wl)
