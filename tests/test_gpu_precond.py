@@ -1,6 +1,6 @@
 """Learned preconditioner: GPU forward/backward kernels against the oracle, training on
 pairs harvested from converged eigensolves, and what the trained network gains over the
-kinetic preconditioner it replaces (which stays the fallback and the judge)."""
+kinetic preconditioner it replaces (which stays the fallback and the yardstick)."""
 import numpy as np
 import pytest
 
