@@ -104,63 +104,6 @@ __device__ __forceinline__ void block_sum_store(double v, double* out_slot) {
   __syncthreads();
 }
 
-// v_H(G) = 4 pi rho(G) / |G|^2 from the unscaled forward transform F = N_r rho(G); writes
-// the potential coefficients (scaled to f(G)) and per-block partial sums of
-// |rho(G)|^2 4 pi / G^2 (E_H = Omega/2 times their sum).
-template <typename T>
-__global__ void k_poisson(const cplx<T>* __restrict__ F, cplx<T>* __restrict__ V, GridDims g, CellDev c,
-                          double inv_nr, double* partial) {
-  const long long nr = (long long)g.n1 * g.n2 * g.n3;
-  double acc = 0;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < nr; idx += (long long)gridDim.x * blockDim.x) {
-    const Gpt p = gvec(idx, g, c);
-    cplx<T> o = mk<T>(0, 0);
-    if (p.g2 > 0 && !p.nyq) {
-      const double re = (double)F[idx].x * inv_nr, im = (double)F[idx].y * inv_nr;
-      const double f = 4.0 * M_PI / p.g2;
-      if (V) o = mk<T>((T)(f * re), (T)(f * im));
-      acc += f * (re * re + im * im);
-    }
-    if (V) V[idx] = o;
-  }
-  block_sum_store(acc, partial + blockIdx.x);
-}
-
-// out_c = i G_c F / N_r (c = x, y, z), Nyquist planes zero.
-template <typename T>
-__global__ void k_grad_g(const cplx<T>* __restrict__ F, cplx<T>* __restrict__ ox, cplx<T>* __restrict__ oy,
-                         cplx<T>* __restrict__ oz, GridDims g, CellDev c, double inv_nr) {
-  const long long nr = (long long)g.n1 * g.n2 * g.n3;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < nr; idx += (long long)gridDim.x * blockDim.x) {
-    const Gpt p = gvec(idx, g, c);
-    const double re = (double)F[idx].x * inv_nr, im = (double)F[idx].y * inv_nr;
-    if (p.nyq) {
-      ox[idx] = oy[idx] = oz[idx] = mk<T>(0, 0);
-    } else {
-      ox[idx] = mk<T>((T)(-p.gx * im), (T)(p.gx * re));
-      oy[idx] = mk<T>((T)(-p.gy * im), (T)(p.gy * re));
-      oz[idx] = mk<T>((T)(-p.gz * im), (T)(p.gz * re));
-    }
-  }
-}
-
-// out = sum_c i G_c H_c / N_r, Nyquist planes zero (written into hx).
-template <typename T>
-__global__ void k_div_g(cplx<T>* __restrict__ hx, const cplx<T>* __restrict__ hy, const cplx<T>* __restrict__ hz,
-                        GridDims g, CellDev c, double inv_nr) {
-  const long long nr = (long long)g.n1 * g.n2 * g.n3;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < nr; idx += (long long)gridDim.x * blockDim.x) {
-    const Gpt p = gvec(idx, g, c);
-    if (p.nyq) {
-      hx[idx] = mk<T>(0, 0);
-      continue;
-    }
-    const double re = p.gx * hx[idx].x + p.gy * hy[idx].x + p.gz * hz[idx].x;
-    const double im = p.gx * hx[idx].y + p.gy * hy[idx].y + p.gz * hz[idx].y;
-    hx[idx] = mk<T>((T)(-im * inv_nr), (T)(re * inv_nr));
-  }
-}
-
 // Local potential of all nuclei in reciprocal space (FP64):
 // v(G) = (1/Omega) sum_a -4 pi Z_a / G^2 exp(-G^2 rc^2/4) exp(-i G.R_a), G != 0;
 // v(0) = (1/Omega) sum_a pi Z_a rc^2; Nyquist planes zero.
@@ -331,45 +274,7 @@ __device__ __forceinline__ void point_functional(double rho, double gx, double g
   }
 }
 
-// Pointwise pass over a density: rho (FP64 master), gradient in g[xyz] (real parts of
-// complex grids; NULL when no GGA), writes vpart (FP64) and overwrites g[xyz] with
-// h = hcoef * grad rho; per-block partial energies in partial[0][blk] (xc), [1][blk] (kin).
-// xc_pot = 0: the xc functional contributes its energy only (not vpart or h).
-template <typename T>
-__global__ void k_pointwise(const double* __restrict__ rho, cplx<T>* gx, cplx<T>* gy, cplx<T>* gz, long long nr,
-                            int xc_mode, int xc_pot, int kedf, double rho_cut, double* __restrict__ vpart,
-                            double* partial) {
-  double ax = 0, ak = 0;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < nr; idx += (long long)gridDim.x * blockDim.x) {
-    // The functionals are evaluated in FP64 in both precisions: at low density the PBE
-    // correlation's intermediate A t^2 overflows FP32, and these points cost little
-    // next to the transforms.
-    const double r = rho[idx];
-    double x = 0, y = 0, z = 0;
-    if (gx) { x = (double)gx[idx].x; y = (double)gy[idx].x; z = (double)gz[idx].x; }
-    double v, h;
-    double ex, ek;
-    point_functional(r, x, y, z, xc_mode, xc_pot, kedf, rho_cut, &v, &h, &ex, &ek);
-    if (vpart) vpart[idx] = v;
-    if (gx) {
-      gx[idx] = mk<T>((T)(h * x), 0);
-      gy[idx] = mk<T>((T)(h * y), 0);
-      gz[idx] = mk<T>((T)(h * z), 0);
-    }
-    ax += ex;
-    ak += ek;
-  }
-  block_sum_store(ax, partial + blockIdx.x);
-  block_sum_store(ak, partial + kRedBlocks + blockIdx.x);
-}
-
 // ---- small elementwise kernels -----------------------------------------------------------
-template <typename T>
-__global__ void k_real_to_c(const double* __restrict__ a, cplx<T>* __restrict__ c, long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    c[i] = mk<T>((T)a[i], 0);
-}
-
 template <typename T>
 __global__ void k_c_to_real(const cplx<T>* __restrict__ c, double* __restrict__ a, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
@@ -394,14 +299,6 @@ __global__ void k_scale_c(cplx<T>* __restrict__ a, double s, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     a[i].x = (T)(a[i].x * s);
     a[i].y = (T)(a[i].y * s);
-  }
-}
-
-__global__ void k_sum_rows(const double* __restrict__ a, int nrows, long long n, double* __restrict__ out) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    double v = 0;
-    for (int r = 0; r < nrows; ++r) v += a[(size_t)r * n + i];
-    out[i] = v;
   }
 }
 
@@ -661,42 +558,11 @@ static int gs(long long n) {
   return (int)(b < 4096 ? (b > 0 ? b : 1) : 4096);
 }
 
-template <typename T>
-void grid_poisson(const cplx<T>* F, cplx<T>* V, const GridDims& g, const CellDev& c, double* partial, cudaStream_t st) {
-  count_launches(1);
-  k_poisson<T><<<kRedBlocks, kRedThreads, 0, st>>>(F, V, g, c, 1.0 / ((double)g.n1 * g.n2 * g.n3), partial);
-}
-template <typename T>
-void grid_gradient_g(const cplx<T>* F, cplx<T>* ox, cplx<T>* oy, cplx<T>* oz, const GridDims& g, const CellDev& c,
-                     cudaStream_t st) {
-  const long long nr = (long long)g.n1 * g.n2 * g.n3;
-  count_launches(1);
-  k_grad_g<T><<<gs(nr), 256, 0, st>>>(F, ox, oy, oz, g, c, 1.0 / (double)nr);
-}
-template <typename T>
-void grid_divergence_g(cplx<T>* hx, const cplx<T>* hy, const cplx<T>* hz, const GridDims& g, const CellDev& c,
-                       cudaStream_t st) {
-  const long long nr = (long long)g.n1 * g.n2 * g.n3;
-  count_launches(1);
-  k_div_g<T><<<gs(nr), 256, 0, st>>>(hx, hy, hz, g, c, 1.0 / (double)nr);
-}
 void grid_vloc_g(double2* V, const GridDims& g, const CellDev& c, const double* pos, const double* Z, int natoms,
                  double rc, cudaStream_t st) {
   const long long nr = (long long)g.n1 * g.n2 * g.n3;
   count_launches(1);
   k_vloc_g<<<gs(nr), 256, 0, st>>>(V, g, c, pos, Z, natoms, rc);
-}
-template <typename T>
-void grid_pointwise(const double* rho, cplx<T>* gx, cplx<T>* gy, cplx<T>* gz, long long nr, int xc_mode, int xc_pot,
-                    int kedf, double rho_cut, double* vpart, double* partial, cudaStream_t st) {
-  count_launches(1);
-  k_pointwise<T><<<kRedBlocks, kRedThreads, 0, st>>>(rho, gx, gy, gz, nr, xc_mode, xc_pot, kedf, rho_cut, vpart,
-                                                      partial);
-}
-template <typename T>
-void grid_real_to_c(const double* a, cplx<T>* c, long long n, cudaStream_t st) {
-  count_launches(1);
-  k_real_to_c<T><<<gs(n), 256, 0, st>>>(a, c, n);
 }
 template <typename T>
 void grid_c_to_real(const cplx<T>* c, double* a, long long n, cudaStream_t st) {
@@ -716,10 +582,6 @@ void grid_scale_c(cplx<T>* a, double s, long long n, cudaStream_t st) {
 }
 template void grid_scale_c<float>(float2*, double, long long, cudaStream_t);
 template void grid_scale_c<double>(double2*, double, long long, cudaStream_t);
-void grid_sum_rows(const double* a, int nrows, long long n, double* out, cudaStream_t st) {
-  count_launches(1);
-  k_sum_rows<<<gs(n), 256, 0, st>>>(a, nrows, n, out);
-}
 void grid_dot_partial(const double* a, const double* b, long long n, int mode, double* partial, cudaStream_t st) {
   count_launches(1);
   k_dot_partial<<<kRedBlocks, kRedThreads, 0, st>>>(a, b, n, mode, partial);
@@ -777,15 +639,6 @@ int grid_red_blocks() { return kRedBlocks; }
 
 #define FDE_GRID_INST(T)                                                                                     \
   template void launch_fft3d<T>(cplx<T>*, const GridDims&, const FftPlans<T>&, int, cudaStream_t);           \
-  template void grid_poisson<T>(const cplx<T>*, cplx<T>*, const GridDims&, const CellDev&, double*,          \
-                                cudaStream_t);                                                               \
-  template void grid_gradient_g<T>(const cplx<T>*, cplx<T>*, cplx<T>*, cplx<T>*, const GridDims&,            \
-                                   const CellDev&, cudaStream_t);                                            \
-  template void grid_divergence_g<T>(cplx<T>*, const cplx<T>*, const cplx<T>*, const GridDims&,              \
-                                     const CellDev&, cudaStream_t);                                          \
-  template void grid_pointwise<T>(const double*, cplx<T>*, cplx<T>*, cplx<T>*, long long, int, int, int,     \
-                                  double, double*, double*, cudaStream_t);                                   \
-  template void grid_real_to_c<T>(const double*, cplx<T>*, long long, cudaStream_t);                         \
   template void grid_c_to_real<T>(const cplx<T>*, double*, long long, cudaStream_t);                         \
   template void grid_combine<T>(const double*, const double*, const double*, const cplx<T>*, double, double*, \
                                 long long, cudaStream_t);
