@@ -128,11 +128,9 @@ void launch_kb_couple(const double2* P, const KbBlock& D, int natoms, int nb, do
 void launch_cholesky_inv(const double2* S, int n, double2* L, double2* Linv, unsigned* status, double rel_pivot,
                          cudaStream_t st);
 
-// Hermitian eigenproblem by cyclic Jacobi: A (n x n, destroyed) -> eigenvalues w[n]
-// ascending and eigenvectors V (column j = vector j), FP64.
-void launch_jacobi_eig(double2* A, int n, double* w, double2* V, double2* work, cudaStream_t st);
-// Same result by tridiagonalisation, bisection and inverse iteration (heev.cu); only the
-// eigenvectors of the lowest nvec eigenvalues are formed (other columns of V are zero).
+// Hermitian eigenproblem (FP64): A (n x n) -> eigenvalues w[n] ascending and the eigenvectors
+// of the lowest nvec eigenvalues in the columns of V (other columns zero), by
+// tridiagonalisation, bisection and inverse iteration (dense.cu, heev.cu).
 size_t heev_work_doubles(int n, int nvec);
 void launch_heev(double2* A, int n, int nvec, double* w, double2* V, double* work, cudaStream_t st);
 

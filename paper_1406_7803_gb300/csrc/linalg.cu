@@ -1,8 +1,7 @@
 // linalg.cu -- dense complex algebra of the subspace eigensolver (Eq. KS solved by block
 // Davidson): band-block inner products (Gram / subspace Hamiltonian / projector
-// contractions), band-block rotations, FP64 Cholesky with triangular inverse, FP64 cyclic
-// Jacobi for the small Hermitian eigenproblem, and the row-wise residual / preconditioner
-// helpers.
+// contractions), band-block rotations, FP64 Cholesky with triangular inverse, and the
+// row-wise residual / preconditioner helpers.
 #include <math.h>
 #include <stdlib.h>
 
@@ -341,146 +340,6 @@ void launch_kb_couple(const double2* P, const KbBlock& D, int natoms, int nb, do
   count_launches(1);
   const int blocks = (int)std::min<long long>((n + 255) / 256, 1024);
   k_kb_couple<<<blocks, 256, 0, st>>>(P, D, natoms, nb, Q);
-}
-
-// ---- Hermitian cyclic Jacobi (one CTA, round-robin parallel ordering) ----------------------
-constexpr int kJacobiMaxN = 1024;
-
-__global__ void __launch_bounds__(1024)
-k_jacobi(double2* __restrict__ A, int n, double* __restrict__ w, double2* __restrict__ Vout,
-         double2* __restrict__ V) {
-  __shared__ int pp[kJacobiMaxN / 2], qq[kJacobiMaxN / 2];
-  __shared__ double cc[kJacobiMaxN / 2], ss[kJacobiMaxN / 2];
-  __shared__ double2 uu[kJacobiMaxN / 2];
-  __shared__ double red[32];
-  __shared__ double offn, diagn;
-  const int ne = (n % 2) ? n + 1 : n;  // odd n: a dummy index n sits out each round
-  const int half = ne / 2;
-  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-    const int i = idx / n, j = idx % n;
-    V[idx] = make_double2(i == j ? 1.0 : 0.0, 0.0);
-  }
-  __syncthreads();
-  for (int sweep = 0; sweep < 60; ++sweep) {
-    // convergence test: off-diagonal vs diagonal Frobenius norms
-    double lo = 0, ld = 0;
-    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-      const int i = idx / n, j = idx % n;
-      const double2 a = A[idx];
-      const double m2 = a.x * a.x + a.y * a.y;
-      if (i == j) ld += m2; else lo += m2;
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      lo += __shfl_xor_sync(0xffffffffu, lo, o);
-      ld += __shfl_xor_sync(0xffffffffu, ld, o);
-    }
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = lo;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = 0;
-      for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
-      offn = t;
-    }
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ld;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = 0;
-      for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
-      diagn = t;
-    }
-    __syncthreads();
-    if (offn <= 1e-30 * (diagn + 1e-300) || offn < 1e-300) break;
-    for (int r = 0; r < ne - 1; ++r) {
-      for (int k = threadIdx.x; k < half; k += blockDim.x) {
-        const int a0 = (k == 0) ? 0 : 1 + ((k - 1 + r) % (ne - 1));
-        const int kb = ne - 1 - k;
-        const int b0 = 1 + ((kb - 1 + r) % (ne - 1));
-        int p = min(a0, b0), q = max(a0, b0);
-        double c = 1.0, s = 0.0;
-        double2 u = make_double2(1.0, 0.0);
-        if (q < n) {
-          const double2 apq = A[(size_t)p * n + q];
-          const double bb = sqrt(apq.x * apq.x + apq.y * apq.y);
-          const double app = A[(size_t)p * n + p].x, aqq = A[(size_t)q * n + q].x;
-          if (bb > 1e-300 && bb > 1e-18 * (fabs(app) + fabs(aqq))) {
-            u = make_double2(apq.x / bb, apq.y / bb);
-            const double th = (aqq - app) / (2.0 * bb);
-            const double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-            c = 1.0 / sqrt(t * t + 1.0);
-            s = t * c;
-          }
-        } else {
-          q = -1;
-        }
-        pp[k] = p;
-        qq[k] = q;
-        cc[k] = c;
-        ss[k] = s;
-        uu[k] = u;
-      }
-      __syncthreads();
-      // columns: A J and V J with J_pp = c, J_pq = s, J_qp = -s conj(u), J_qq = c conj(u)
-      for (int idx = threadIdx.x; idx < n * half; idx += blockDim.x) {
-        const int k = idx / n, i = idx % n;
-        const int p = pp[k], q = qq[k];
-        if (q < 0 || ss[k] == 0.0) continue;
-        const double c = cc[k], s = ss[k];
-        const double2 uc = make_double2(uu[k].x, -uu[k].y);
-        {
-          const double2 x = A[(size_t)i * n + p], y = A[(size_t)i * n + q];
-          const double2 yu = cmul(y, uc);
-          A[(size_t)i * n + p] = make_double2(c * x.x - s * yu.x, c * x.y - s * yu.y);
-          A[(size_t)i * n + q] = make_double2(s * x.x + c * yu.x, s * x.y + c * yu.y);
-        }
-        {
-          const double2 x = V[(size_t)i * n + p], y = V[(size_t)i * n + q];
-          const double2 yu = cmul(y, uc);
-          V[(size_t)i * n + p] = make_double2(c * x.x - s * yu.x, c * x.y - s * yu.y);
-          V[(size_t)i * n + q] = make_double2(s * x.x + c * yu.x, s * x.y + c * yu.y);
-        }
-      }
-      __syncthreads();
-      // rows: J^H (A J): row p = c row_p - s u row_q, row q = s row_p + c u row_q
-      for (int idx = threadIdx.x; idx < n * half; idx += blockDim.x) {
-        const int k = idx / n, j = idx % n;
-        const int p = pp[k], q = qq[k];
-        if (q < 0 || ss[k] == 0.0) continue;
-        const double c = cc[k], s = ss[k];
-        const double2 u = uu[k];
-        const double2 x = A[(size_t)p * n + j], y = A[(size_t)q * n + j];
-        const double2 yu = cmul(y, u);
-        A[(size_t)p * n + j] = make_double2(c * x.x - s * yu.x, c * x.y - s * yu.y);
-        A[(size_t)q * n + j] = make_double2(s * x.x + c * yu.x, s * x.y + c * yu.y);
-      }
-      __syncthreads();
-      for (int k = threadIdx.x; k < half; k += blockDim.x) {
-        const int p = pp[k], q = qq[k];
-        if (q < 0 || ss[k] == 0.0) continue;
-        A[(size_t)p * n + q] = make_double2(0, 0);
-        A[(size_t)q * n + p] = make_double2(0, 0);
-        A[(size_t)p * n + p].y = 0.0;
-        A[(size_t)q * n + q].y = 0.0;
-      }
-      __syncthreads();
-    }
-  }
-  // sort ascending by rank (ties by index) and permute the vectors
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const double di = A[(size_t)i * n + i].x;
-    int rank = 0;
-    for (int j = 0; j < n; ++j) {
-      const double dj = A[(size_t)j * n + j].x;
-      rank += (dj < di) || (dj == di && j < i);
-    }
-    w[rank] = di;
-    for (int r = 0; r < n; ++r) Vout[(size_t)r * n + rank] = V[(size_t)r * n + i];
-  }
-}
-
-void launch_jacobi_eig(double2* A, int n, double* w, double2* V, double2* work, cudaStream_t st) {
-  count_launches(1);
-  k_jacobi<<<1, 1024, 0, st>>>(A, n, w, V, work);
 }
 
 __global__ void k_hermitize(double2* A, int n) {
