@@ -352,6 +352,35 @@ int fde_tuned_plane_variant(int n1, int n3);
  * (-1).  FDE_EINVAL for other values. */
 fde_status fde_pin_plane_variant(int variant);
 
+/* ---- host-side numerics (no device work; usable without a GPU) --------------------------
+ * The engine's own host routines, exposed so they can be checked and reused anywhere.
+ * Cells are orthorhombic: lengths [3] bohr (the diagonal of the lattice).
+ *
+ * Plane-wave sphere of the subsystem orbitals (Sec. 2, plane-wave expansion; the full
+ * sphere): every Miller triple m with |k + G_m|^2 / 2 <= ecut (Ha), evaluated in FP64 from
+ * the integer indices, with m1 slowest and m3 fastest (the library's orbital order).  kfrac
+ * [3] is the k-point in crystal coordinates.  *npw receives the count; miller (nullable,
+ * [npw][3]) and kin (nullable, [npw], |k + G|^2 / 2) are filled when given (size them with a
+ * first call passing NULL).  FDE_EINVAL for non-positive lengths or ecut. */
+fde_status fde_host_sphere(const double* lengths, const double* kfrac, double ecut, int* npw, int* miller,
+                           double* kin);
+/* Nuclear repulsion V_NN of Eq. E_FDE: Ewald sum of the point charges Z [natoms] at pos
+ * [natoms][3] (bohr) with a uniform neutralising background, into *energy (Ha). */
+fde_status fde_host_ewald(const double* lengths, int natoms, const double* pos, const double* Z, double* energy);
+/* Occupations (Sec. 2: 2 sum_k w_k sum_j n_jk = N_I, 0 <= n <= 1) of eig [nk][nb] (Ha) with
+ * k weights wk [nk]: sigma > 0 Fermi-Dirac with the chemical potential *mu by bisection to
+ * 1e-13 electrons and *ts = sigma S, S = -2 sum_k w_k sum_j [n ln n + (1-n) ln(1-n)] (the
+ * Mermin term); sigma <= 0 integer occupation of the nelec/2 lowest bands (nk must be 1),
+ * *mu the highest occupied eigenvalue, *ts = 0.  occ [nk][nb] out.  FDE_EINVAL for
+ * inconsistent arguments. */
+fde_status fde_host_occupations(int nk, int nb, const double* eig, const double* wk, double nelec, double sigma,
+                                double* occ, double* mu, double* ts);
+/* Pulay (DIIS) coefficients of the subsystem SCF's density mixing (the paper is silent on
+ * mixing): c [m] minimising |sum_i c_i R_i|^2 with sum_i c_i = 1, from the residual
+ * overlaps overlap [m][m] = <R_i|R_j>.  FDE_ENOCONV (and c = e_m, the newest residual) when
+ * the bordered system is singular. */
+fde_status fde_host_pulay(int m, const double* overlap, double* coef);
+
 /* Synchronise the context stream and check the device status word. */
 fde_status fde_sync(fde_ctx* ctx);
 

@@ -17,6 +17,7 @@
 
 #include "fde.h"
 #include "grid_kernels.h"
+#include "hostmath.h"
 #include "kernels.h"
 #include "prof.h"
 #include "precond.h"
@@ -123,65 +124,8 @@ template <typename T> static void make_plans(Plans<T>& P, const int grid[3], cud
   }
 }
 
-// ---- host-side physics that is not on the data path ---------------------------------------
-// Ewald sum of point charges with a neutralising background (nuclear repulsion V_NN).
-static double ewald_energy(const double A[3][3], const double B[3][3], double omega, const std::vector<double>& pos,
-                           const std::vector<double>& Z) {
-  const int n = (int)Z.size();
-  const double eta = sqrt(M_PI) / cbrt(omega);
-  const double x = sqrt(-log(1e-16));
-  const double rmax = x / eta + 1.0, gmax = 2.0 * eta * x + 1.0;
-  int nl[3], ng[3];
-  for (int j = 0; j < 3; ++j) {
-    const double bn = sqrt(B[j][0] * B[j][0] + B[j][1] * B[j][1] + B[j][2] * B[j][2]);
-    const double an = sqrt(A[j][0] * A[j][0] + A[j][1] * A[j][1] + A[j][2] * A[j][2]);
-    nl[j] = (int)ceil(rmax * bn / (2 * M_PI)) + 1;
-    ng[j] = (int)ceil(gmax * an / (2 * M_PI)) + 1;
-  }
-  double er = 0.0;
-  for (int a = -nl[0]; a <= nl[0]; ++a)
-    for (int b = -nl[1]; b <= nl[1]; ++b)
-      for (int c = -nl[2]; c <= nl[2]; ++c) {
-        double L[3];
-        for (int d = 0; d < 3; ++d) L[d] = a * A[0][d] + b * A[1][d] + c * A[2][d];
-        for (int i = 0; i < n; ++i)
-          for (int j = 0; j < n; ++j) {
-            if (a == 0 && b == 0 && c == 0 && i == j) continue;
-            double r2 = 0;
-            for (int d = 0; d < 3; ++d) {
-              const double dd = pos[3 * i + d] - pos[3 * j + d] + L[d];
-              r2 += dd * dd;
-            }
-            const double r = sqrt(r2);
-            if (r < rmax) er += 0.5 * Z[i] * Z[j] * erfc(eta * r) / r;
-          }
-      }
-  double eg = 0.0;
-  for (int a = -ng[0]; a <= ng[0]; ++a)
-    for (int b = -ng[1]; b <= ng[1]; ++b)
-      for (int c = -ng[2]; c <= ng[2]; ++c) {
-        double G[3];
-        for (int d = 0; d < 3; ++d) G[d] = a * B[0][d] + b * B[1][d] + c * B[2][d];
-        const double g2 = G[0] * G[0] + G[1] * G[1] + G[2] * G[2];
-        if (g2 <= 0 || g2 >= gmax * gmax) continue;
-        double sr = 0, si = 0;
-        for (int i = 0; i < n; ++i) {
-          const double ph = G[0] * pos[3 * i] + G[1] * pos[3 * i + 1] + G[2] * pos[3 * i + 2];
-          sr += Z[i] * cos(ph);
-          si += Z[i] * sin(ph);
-        }
-        eg += exp(-g2 / (4 * eta * eta)) / g2 * (sr * sr + si * si);
-      }
-  eg *= 2.0 * M_PI / omega;
-  double z2 = 0, zs = 0;
-  for (int i = 0; i < n; ++i) { z2 += Z[i] * Z[i]; zs += Z[i]; }
-  return er + eg - eta / sqrt(M_PI) * z2 - M_PI * zs * zs / (2.0 * omega * eta * eta);
-}
-
-static inline double fermi(double x) {  // 1 / (1 + e^x)
-  if (x > 0) { const double e = exp(-x); return e / (1.0 + e); }
-  return 1.0 / (1.0 + exp(x));
-}
+// Host-side physics that is not on the data path (sphere, Ewald, occupations, Pulay
+// coefficients) lives in hostmath.cu.
 
 // ---- per-(subsystem, k) and per-subsystem state ---------------------------------------------
 template <typename T> struct KP {
@@ -389,29 +333,8 @@ template <typename T> struct EngineT : Engine {
 
   // ---- basis ------------------------------------------------------------------------------
   void build_sphere(KP<T>& q) {
-    for (int c = 0; c < 3; ++c) q.kc[c] = q.kfrac[0] * B[0][c] + q.kfrac[1] * B[1][c] + q.kfrac[2] * B[2][c];
-    const double knorm = sqrt(q.kc[0] * q.kc[0] + q.kc[1] * q.kc[1] + q.kc[2] * q.kc[2]);
-    const double qmax = sqrt(2.0 * ecut) + knorm;
-    int lim[3];
-    for (int j = 0; j < 3; ++j) lim[j] = (int)ceil(qmax * A[j][j] / (2.0 * M_PI)) + 1;
-    q.miller.clear();
-    q.kin.clear();
-    for (int m1 = -lim[0]; m1 <= lim[0]; ++m1)
-      for (int m2 = -lim[1]; m2 <= lim[1]; ++m2)
-        for (int m3 = -lim[2]; m3 <= lim[2]; ++m3) {
-          double qv[3];
-          for (int c = 0; c < 3; ++c) {
-            const double gc = (double)m1 * B[0][c] + (double)m2 * B[1][c] + (double)m3 * B[2][c];
-            qv[c] = q.kc[c] + gc;
-          }
-          const double kk = 0.5 * (qv[0] * qv[0] + qv[1] * qv[1] + qv[2] * qv[2]);
-          if (kk <= ecut) {
-            q.miller.push_back(m1);
-            q.miller.push_back(m2);
-            q.miller.push_back(m3);
-            q.kin.push_back(kk);
-          }
-        }
+    const double Lc[3] = {A[0][0], A[1][1], A[2][2]};
+    sphere_miller(Lc, q.kfrac, ecut, q.miller, q.kin, q.kc);
     q.npw = (int)q.kin.size();
     REQ(q.npw > 0, FDE_EINVAL, "empty plane-wave sphere");
     for (int j = 0; j < 3; ++j) {
@@ -569,7 +492,8 @@ template <typename T> struct EngineT : Engine {
     grid_c_to_real<double>(cvl.p, vloc.p, nr, st);
     CK(cudaStreamSynchronize(st));
     cvl.release();
-    enn = ewald_energy(A, B, omega, pos, Z);
+    const double Lc[3] = {A[0][0], A[1][1], A[2][2]};
+    enn = ewald_energy(Lc, pos, Z);
     locked = true;
   }
 
@@ -1154,47 +1078,14 @@ template <typename T> struct EngineT : Engine {
 
   // ---- occupations and density ----------------------------------------------------------------
   void occupations(Sub<T>& s) {
-    if (s.smearing <= 0) {
-      const int no = (int)llround(s.nelec / 2.0);
-      KP<T>& q = s.kp[0];
-      std::vector<int> order(s.nb);
-      for (int j = 0; j < s.nb; ++j) order[j] = j;
-      std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return q.eig[a] < q.eig[b]; });
-      q.occ.assign(s.nb, 0.0);
-      for (int j = 0; j < no; ++j) q.occ[order[j]] = 1.0;
-      s.entropy = 0.0;
-      s.mu = no ? q.eig[order[no - 1]] : q.eig[order[0]];
-      return;
-    }
-    double lo = 1e300, hi = -1e300;
-    for (auto& q : s.kp)
-      for (double e : q.eig) { lo = std::min(lo, e); hi = std::max(hi, e); }
-    lo -= 40.0 * s.smearing;
-    hi += 40.0 * s.smearing;
-    double mu = 0.5 * (lo + hi);
-    for (int it = 0; it < 300; ++it) {
-      mu = 0.5 * (lo + hi);
-      double n = 0;
-      for (int k = 0; k < s.nk; ++k)
-        for (double e : s.kp[k].eig) n += 2.0 * s.wk[k] * fermi((e - mu) / s.smearing);
-      if (fabs(n - s.nelec) < 1e-13) break;
-      if (n < s.nelec) lo = mu; else hi = mu;
-    }
-    double S = 0;
-    for (int k = 0; k < s.nk; ++k) {
-      KP<T>& q = s.kp[k];
-      q.occ.resize(s.nb);
-      for (int j = 0; j < s.nb; ++j) {
-        const double n = fermi((q.eig[j] - mu) / s.smearing);
-        q.occ[j] = n;
-        double t = 0;
-        if (n > 0) t += n * log(n);
-        if (n < 1) t += (1 - n) * log(1 - n);
-        S -= 2.0 * s.wk[k] * t;
-      }
-    }
+    std::vector<double> eig((size_t)s.nk * s.nb), occ((size_t)s.nk * s.nb);
+    for (int k = 0; k < s.nk; ++k) std::copy(s.kp[k].eig.begin(), s.kp[k].eig.end(), eig.begin() + (size_t)k * s.nb);
+    double mu = 0, ts = 0;
+    REQ(occupations_host(s.nk, s.nb, eig.data(), s.wk.data(), s.nelec, s.smearing, occ.data(), &mu, &ts),
+        FDE_EINVAL, "inconsistent occupation arguments");
+    for (int k = 0; k < s.nk; ++k) s.kp[k].occ.assign(occ.begin() + (size_t)k * s.nb, occ.begin() + (size_t)(k + 1) * s.nb);
     s.mu = mu;
-    s.entropy = s.smearing * S;
+    s.entropy = ts;
   }
 
   void density_from_orbitals(Sub<T>& s, double* out) {
@@ -1495,17 +1386,14 @@ template <typename T> struct EngineT : Engine {
     const int m = hist_len;
     std::vector<int> sl(m);
     for (int a = 0; a < m; ++a) sl[a] = (hist_head + a) % H;
-    std::vector<double> Am((m + 1) * (m + 1), 0.0), b(m + 1, 0.0);
+    std::vector<double> ov((size_t)m * m, 0.0);
     for (int a = 0; a < m; ++a)
       for (int c = a; c < m; ++c) {
         const double v = integrate_product(hist_res[sl[a]].p, hist_res[sl[c]].p) * (double)nr / omega;
-        Am[a * (m + 1) + c] = Am[c * (m + 1) + a] = v;
+        ov[a * m + c] = ov[c * m + a] = v;
       }
-    for (int a = 0; a < m; ++a) Am[a * (m + 1) + m] = Am[m * (m + 1) + a] = 1.0;
-    b[m] = 1.0;
     std::vector<double> coef(m, 0.0);
-    if (!solve_dense(Am, b, m + 1)) { coef.assign(m, 0.0); coef[m - 1] = 1.0; }
-    else for (int a = 0; a < m; ++a) coef[a] = b[a];
+    pulay_coefficients(ov.data(), m, coef.data());
     std::vector<const double*> pi(m), pr(m);
     for (int a = 0; a < m; ++a) { pi[a] = hist_in[sl[a]].p; pr[a] = hist_res[sl[a]].p; }
     dptrs.ensure(2 * m);
@@ -1516,27 +1404,6 @@ template <typename T> struct EngineT : Engine {
     grid_lincomb(dptrs.p, dptrs.p + m, dcoef.p, m, beta, nr, rin, st);
     CK(cudaStreamSynchronize(st));
   }
-  // Gaussian elimination with partial pivoting; solution returned in b.
-  static bool solve_dense(std::vector<double>& Am, std::vector<double>& b, int n) {
-    for (int c = 0; c < n; ++c) {
-      int p = c;
-      for (int r = c + 1; r < n; ++r) if (fabs(Am[r * n + c]) > fabs(Am[p * n + c])) p = r;
-      if (fabs(Am[p * n + c]) < 1e-300) return false;
-      if (p != c) { for (int k = 0; k < n; ++k) std::swap(Am[c * n + k], Am[p * n + k]); std::swap(b[c], b[p]); }
-      for (int r = c + 1; r < n; ++r) {
-        const double f = Am[r * n + c] / Am[c * n + c];
-        for (int k = c; k < n; ++k) Am[r * n + k] -= f * Am[c * n + k];
-        b[r] -= f * b[c];
-      }
-    }
-    for (int c = n - 1; c >= 0; --c) {
-      double v = b[c];
-      for (int k = c + 1; k < n; ++k) v -= Am[c * n + k] * b[k];
-      b[c] = v / Am[c * n + c];
-    }
-    return true;
-  }
-
   // ---- subsystem SCF and freeze-and-thaw ------------------------------------------------------
   // Inner-iteration thresholds.  One freeze-and-thaw cycle evaluates the energy with every
   // density refreshed, which is not stationary in the inner-SCF densities, so the density

@@ -82,6 +82,11 @@ EXPORTS = {
     "fde_gemm_hn_f32": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int,
                                   C.c_void_p, C.c_int, C.c_int]),
     "fde_set_gemm_path": (C.c_int, [C.c_int]),
+    "fde_host_sphere": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "fde_host_ewald": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "fde_host_occupations": (C.c_int, [C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_void_p,
+                                       C.c_void_p, C.c_void_p]),
+    "fde_host_pulay": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p]),
     "fde_tuned_plane_variant": (C.c_int, [C.c_int, C.c_int]),
     "fde_pin_plane_variant": (C.c_int, [C.c_int]),
     "fde_gemm_rot_f32": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int,
@@ -146,6 +151,54 @@ def pin_plane_variant(variant: int) -> None:
     """Pin the FP32 plane-pass variant (0..3) for this process, or -1 to return to tuning."""
     if load().fde_pin_plane_variant(int(variant)) != FDE_OK:
         raise FDEError(FDE_EINVAL, "fde_pin_plane_variant: variant must be -1..3")
+
+
+def host_sphere(lengths, kfrac, ecut):
+    """Miller indices [npw, 3] and kinetic energies [npw] of the plane-wave sphere (host code)."""
+    lib = load()
+    L = np.ascontiguousarray(lengths, dtype=np.float64)
+    kf = np.ascontiguousarray(kfrac, dtype=np.float64)
+    n = C.c_int()
+    s = lib.fde_host_sphere(_hptr(L), _hptr(kf), float(ecut), C.byref(n), None, None)
+    if s != FDE_OK:
+        raise FDEError(s, "fde_host_sphere")
+    mil = np.zeros((n.value, 3), dtype=np.int32)
+    kin = np.zeros(n.value)
+    lib.fde_host_sphere(_hptr(L), _hptr(kf), float(ecut), C.byref(n), _hptr(mil), _hptr(kin))
+    return mil, kin
+
+
+def host_ewald(lengths, pos, Z):
+    """Ewald nuclear repulsion (Ha) of point charges in an orthorhombic cell (host code)."""
+    L = np.ascontiguousarray(lengths, dtype=np.float64)
+    p = np.ascontiguousarray(pos, dtype=np.float64)
+    z = np.ascontiguousarray(Z, dtype=np.float64)
+    e = C.c_double()
+    s = load().fde_host_ewald(_hptr(L), int(z.size), _hptr(p), _hptr(z), C.byref(e))
+    if s != FDE_OK:
+        raise FDEError(s, "fde_host_ewald")
+    return e.value
+
+
+def host_occupations(eig, wk, nelec, sigma):
+    """(occ [nk, nb], mu, sigma S) of the eigenvalues eig [nk, nb] (host code)."""
+    ev = np.ascontiguousarray(eig, dtype=np.float64)
+    w = np.ascontiguousarray(wk, dtype=np.float64)
+    occ = np.zeros_like(ev)
+    mu, ts = C.c_double(), C.c_double()
+    s = load().fde_host_occupations(int(ev.shape[0]), int(ev.shape[1]), _hptr(ev), _hptr(w), float(nelec),
+                                    float(sigma), _hptr(occ), C.byref(mu), C.byref(ts))
+    if s != FDE_OK:
+        raise FDEError(s, "fde_host_occupations")
+    return occ, mu.value, ts.value
+
+
+def host_pulay(overlap):
+    """Pulay coefficients from the residual overlaps [m, m] (host code); (coef, solved)."""
+    ov = np.ascontiguousarray(overlap, dtype=np.float64)
+    c = np.zeros(ov.shape[0])
+    s = load().fde_host_pulay(int(ov.shape[0]), _hptr(ov), _hptr(c))
+    return c, s == FDE_OK
 
 
 def set_gemm_path(path: int) -> None:
