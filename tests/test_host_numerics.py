@@ -103,3 +103,16 @@ def test_pulay_singular_history_keeps_the_newest_residual():
     r = np.ones((2, 3))
     c, ok = fde.host_pulay(r @ r.T)  # two identical residuals: singular bordered system
     assert not ok and c.tolist() == [0.0, 1.0]
+
+
+def test_host_entry_points_reject_bad_arguments():
+    lib = fde.load()
+    n = fde.C.c_int()
+    e = fde.C.c_double()
+    L = np.ones(3)
+    assert lib.fde_host_sphere(None, None, 1.0, fde.C.byref(n), None, None) == fde.FDE_EINVAL
+    assert lib.fde_host_sphere(fde._hptr(L), fde._hptr(np.zeros(3)), -1.0, fde.C.byref(n), None, None) == fde.FDE_EINVAL
+    assert lib.fde_host_sphere(fde._hptr(-L), fde._hptr(np.zeros(3)), 1.0, fde.C.byref(n), None, None) == fde.FDE_EINVAL
+    assert lib.fde_host_ewald(fde._hptr(L), 0, None, None, fde.C.byref(e)) == fde.FDE_EINVAL
+    assert lib.fde_host_occupations(0, 1, None, None, 2.0, 0.0, None, None, None) == fde.FDE_EINVAL
+    assert lib.fde_host_pulay(0, None, None) == fde.FDE_EINVAL
