@@ -288,14 +288,20 @@ fde_status fde_launch_count(fde_ctx* ctx, long long* launches);
  *             not overlapping.  cuda_stream: cudaStream_t (NULL: legacy default stream).
  * Working memory is a set of fixed device arrays inside the library (about 26 MB, held by
  * every GPU that loads the library until the process exits); limits: npw <= 65536,
- * <= 8192 (m1, m2) columns, n1, n2 <= 160, n3 <= 320, n1 n2 n3 <= 1048576; larger inputs
- * return FDE_EUNSUPPORTED.  Bands are processed in chunks that fit the arrays.  The first
+ * ncol <= 8192 (m1, m2) columns, n3 x ncol <= 1048576, n1, n2 <= 160, n3 <= 320,
+ * n1 n2 n3 <= 1048576; larger inputs return FDE_EUNSUPPORTED (the column limits are known
+ * only after the sphere has been read on the device, so those two come after one stream
+ * synchronisation).  Bands are processed in chunks that fit the arrays.  d_miller is
+ * checked on the device: (m1, m2) strictly increasing from column to column, m3 contiguous
+ * within a column, every m3 in [-n3, n3), no column longer than n3 and m1, m2 spans within
+ * n1, n2; a list that breaks any of these returns FDE_EINVAL and writes nothing to d_hpsi.  The first
  * call on a device resolves the arrays' device addresses (cudaGetSymbolAddress) and must
  * come before any stream capture.  Calls share the arrays: calls that overlap on the GPU
  * (other streams, other host threads) race and must be serialised by the caller.  The call
  * synchronises the stream once (to read the column count).  Errors: FDE_EINVAL (null or
- * non-positive arguments), FDE_EUNSUPPORTED (sizes above the limits, non-orthorhombic cell,
- * grid sizes not of the form 2^a 3^b 5^c), FDE_ECUDA. */
+ * non-positive arguments, a sphere list that fails the checks above), FDE_EUNSUPPORTED
+ * (sizes above the limits, non-orthorhombic cell, grid sizes not of the form 2^a 3^b 5^c),
+ * FDE_ECUDA. */
 fde_status fde_apply_h_local_static(const fde_cell_desc* cell, const double* kfrac, int npw, const int* d_miller,
                                     const double* d_veff, const double* d_psi, double* d_hpsi, int nb,
                                     void* cuda_stream);
@@ -360,8 +366,11 @@ fde_status fde_pin_plane_variant(int variant);
  * sphere): every Miller triple m with |k + G_m|^2 / 2 <= ecut (Ha), evaluated in FP64 from
  * the integer indices, with m1 slowest and m3 fastest (the library's orbital order).  kfrac
  * [3] is the k-point in crystal coordinates.  *npw receives the count; miller (nullable,
- * [npw][3]) and kin (nullable, [npw], |k + G|^2 / 2) are filled when given (size them with a
- * first call passing NULL).  FDE_EINVAL for non-positive lengths or ecut. */
+ * [npw][3]) and kin (nullable, [npw], |k + G|^2 / 2) are filled when given.  When either is
+ * given, *npw must hold on entry the number of entries the buffers have room for (size them
+ * with a first call passing NULL for both, which ignores the entry value); a smaller
+ * capacity returns FDE_EINVAL with the needed count in *npw and writes nothing.
+ * FDE_EINVAL for non-positive lengths or ecut. */
 fde_status fde_host_sphere(const double* lengths, const double* kfrac, double ecut, int* npw, int* miller,
                            double* kin);
 /* Nuclear repulsion V_NN of Eq. E_FDE: Ewald sum of the point charges Z [natoms] at pos

@@ -12,7 +12,16 @@ paper is silent or garbled are fixed in ``oracle.conventions`` and listed in the
 notes of the repository.
 
 Parity status: every function is pinned by a test in ``tests/test_oracle_*.py`` against
-closed forms, invariants, brute force or library routines, except the absolute energies
-of the synthetic cells, which have no external value ("parity unpinned" beyond the
-invariants; see ``oracle.scf``).
+closed forms, invariants, brute force or library routines, with these exceptions:
+
+* parity unpinned: the absolute energies of the synthetic cells, which have no external
+  value beyond the invariants (see ``oracle.scf``);
+* parity unpinned: revAPBEK kappa = 1.245 and mu = 0.23889 (the cited functional's
+  published constants; the tests pin only the form: F(0) = 1, F''(0) = 2 mu,
+  F(inf) = 1 + kappa);
+* parity unpinned: LC94 a, b, alpha, f and the split of c + d (the tests pin the
+  second-order gradient expansion c + d = 5/27 to 4e-4);
+* PW92 alpha_1, beta_1..beta_4 and A are pinned through the high- and low-density
+  expansions (c0, c1, d0, d1) and PW92's construction beta_2 = 2 A beta_1^2; PBE kappa,
+  beta and gamma through the Lieb-Oxford bound, the Ma-Brueckner coefficient and c0.
 """

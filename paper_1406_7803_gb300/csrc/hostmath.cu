@@ -205,8 +205,10 @@ fde_status fde_host_sphere(const double* lengths, const double* kfrac, double ec
   std::vector<int> m;
   std::vector<double> k;
   double kc[3];
+  const int cap = *npw;
   fde::sphere_miller(lengths, kfrac, ecut, m, k, kc);
   *npw = (int)k.size();
+  if ((miller || kin) && cap < *npw) return FDE_EINVAL;  // output buffers hold cap entries
   if (miller) std::copy(m.begin(), m.end(), miller);
   if (kin) std::copy(k.begin(), k.end(), kin);
   return FDE_OK;

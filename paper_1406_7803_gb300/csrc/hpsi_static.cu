@@ -67,22 +67,50 @@ static fde_status static_setup(int dev, StaticPtrs* out) {
   return FDE_OK;
 }
 
-// Column map of a sorted sphere (one CTA): cols = [start(ncol+1) | m3lo | i1 | i2 | rows];
+// Column map of a sphere (one CTA): cols = [start(ncol+1) | m3lo | i1 | i2 | rows];
 // ncols = {ncol, nrow}.  A column starts where (m1, m2) changes; rows are the distinct i1.
+// The caller's list is checked on the way, because the transforms index shared-memory lines
+// by it: (m1, m2) keys strictly increasing from column to column (sorted, no repeats), m3
+// contiguous inside a column, every m3 in [-n3, n3), every column at most n3 long, and the
+// m1 and m2 spans at most n1 and n2 (so no two columns land on one (i1, i2) slot of a
+// plane).  A list that breaks any of these gives ncols = {0, -2}; more than kStMaxCols
+// columns gives {ncol, -1}.
 __global__ void __launch_bounds__(1024)
-k_static_columns(const int* __restrict__ mil, int npw, int n1, int n2, int* cols, int* ncols) {
+k_static_columns(const int* __restrict__ mil, int npw, int n1, int n2, int n3, int* cols, int* ncols) {
   __shared__ int warp_sums[32];
-  __shared__ int base;
+  __shared__ int base, bad;
+  __shared__ int lo1, hi1, lo2, hi2;
   __shared__ int rowflag[kMaxPlane];
-  if (threadIdx.x == 0) base = 0;
+  if (threadIdx.x == 0) {
+    base = 0;
+    bad = 0;
+    lo1 = lo2 = 1 << 30;
+    hi1 = hi2 = -(1 << 30);
+  }
   for (int i = threadIdx.x; i < kMaxPlane; i += blockDim.x) rowflag[i] = 0;
   __syncthreads();
-  // pass 1: count columns (block-wide exclusive scan over chunks of blockDim points)
+  // pass 1: validate every point and count columns (block-wide scan over chunks of points)
   int* start = cols;
+  int mylo1 = 1 << 30, myhi1 = -(1 << 30), mylo2 = 1 << 30, myhi2 = -(1 << 30), mybad = 0;
   for (int c0 = 0; c0 < npw; c0 += blockDim.x) {
     const int p = c0 + threadIdx.x;
     int f = 0;
-    if (p < npw) f = (p == 0) || mil[3 * p] != mil[3 * (p - 1)] || mil[3 * p + 1] != mil[3 * (p - 1) + 1];
+    if (p < npw) {
+      const int m1 = mil[3 * p], m2 = mil[3 * p + 1], m3 = mil[3 * p + 2];
+      mylo1 = min(mylo1, m1);
+      myhi1 = max(myhi1, m1);
+      mylo2 = min(mylo2, m2);
+      myhi2 = max(myhi2, m2);
+      if (m3 < -n3 || m3 >= n3) mybad = 1;
+      if (p == 0) {
+        f = 1;
+      } else {
+        const int q1 = mil[3 * (p - 1)], q2 = mil[3 * (p - 1) + 1], q3 = mil[3 * (p - 1) + 2];
+        f = (m1 != q1) || (m2 != q2);
+        if (f && (m1 < q1 || (m1 == q1 && m2 < q2))) mybad = 1;  // keys must increase
+        if (!f && m3 != q3 + 1) mybad = 1;                      // m3 contiguous in a column
+      }
+    }
     int x = f;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int o = 1; o < 32; o <<= 1) {
@@ -109,16 +137,30 @@ k_static_columns(const int* __restrict__ mil, int npw, int n1, int n2, int* cols
     if (threadIdx.x == blockDim.x - 1) base += incl;
     __syncthreads();
   }
+  atomicMin(&lo1, mylo1);
+  atomicMax(&hi1, myhi1);
+  atomicMin(&lo2, mylo2);
+  atomicMax(&hi2, myhi2);
+  if (mybad) atomicOr(&bad, 1);
+  __syncthreads();
   const int ncol = base;
   if (ncol > kStMaxCols) {
     if (threadIdx.x == 0) { ncols[0] = ncol; ncols[1] = -1; }
+    return;
+  }
+  if (threadIdx.x == 0) start[ncol] = npw;
+  __syncthreads();
+  for (int c = threadIdx.x; c < ncol; c += blockDim.x)
+    if (start[c + 1] - start[c] > n3) atomicOr(&bad, 1);
+  __syncthreads();
+  if (bad || hi1 - lo1 + 1 > n1 || hi2 - lo2 + 1 > n2) {
+    if (threadIdx.x == 0) { ncols[0] = 0; ncols[1] = -2; }
     return;
   }
   int* m3lo = cols + ncol + 1;
   int* ci1 = m3lo + ncol;
   int* ci2 = ci1 + ncol;
   int* rows = ci2 + ncol;
-  if (threadIdx.x == 0) start[ncol] = npw;
   for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
     const int p = start[c];
     const int m1 = mil[3 * p], m2 = mil[3 * p + 1];
@@ -184,7 +226,6 @@ extern "C" fde_status fde_apply_h_local_static(const fde_cell_desc* cell, const 
   if (n1 < 2 || n2 < 2 || n3 < 2 || n1 > kMaxPlane || n2 > kMaxPlane || n3 > kMaxLine) return FDE_EUNSUPPORTED;
   const long long nr = (long long)n1 * n2 * n3;
   if (nr > kStMaxGrid || npw > kStMaxNpw) return FDE_EUNSUPPORTED;
-  if ((long long)n3 * kMaxPlane > kStScratch) return FDE_EUNSUPPORTED;
   LinePlan<double> lp[3];
   factor_line(n1, lp[0]);
   factor_line(n2, lp[1]);
@@ -199,7 +240,7 @@ extern "C" fde_status fde_apply_h_local_static(const fde_cell_desc* cell, const 
   for (int a = 0; a < 3; ++a) lp[a].tw = P.tw + a * kMaxLine;
   const double b[3] = {2.0 * M_PI * (1.0 / cell->lattice[0][0]), 2.0 * M_PI * (1.0 / cell->lattice[1][1]),
                        2.0 * M_PI * (1.0 / cell->lattice[2][2])};
-  k_static_columns<<<1, 1024, 0, st>>>(d_miller, npw, n1, n2, P.cols, P.ncols);
+  k_static_columns<<<1, 1024, 0, st>>>(d_miller, npw, n1, n2, n3, P.cols, P.ncols);
   k_static_tables<<<1, 320, 0, st>>>(n1, n2, n3, P.tw);
   k_static_kin<<<ceil_div(npw, 256), 256, 0, st>>>(d_miller, npw, b[0], b[1], b[2], kfrac[0] * b[0],
                                                    kfrac[1] * b[1], kfrac[2] * b[2], P.kin);
@@ -208,7 +249,10 @@ extern "C" fde_status fde_apply_h_local_static(const fde_cell_desc* cell, const 
   if (cudaMemcpyAsync(hc, P.ncols, sizeof(hc), cudaMemcpyDeviceToHost, st) != cudaSuccess) return FDE_ECUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return FDE_ECUDA;
   const int ncol = hc[0], nrow = hc[1];
+  if (nrow == -2) return FDE_EINVAL;  // the sphere list is unsorted or does not fit the grid
   if (nrow < 0 || ncol <= 0 || ncol > kStMaxCols) return FDE_EUNSUPPORTED;
+  // the column scratch holds n3 x ncol complex values of at least one band
+  if ((long long)n3 * ncol > kStScratch) return FDE_EUNSUPPORTED;
   SphereDev sp;
   sp.npw = npw;
   sp.ncol = ncol;
@@ -225,7 +269,6 @@ extern "C" fde_status fde_apply_h_local_static(const fde_cell_desc* cell, const 
   const GridDims g{n1, n2, n3};
   const long long per_band = (long long)n3 * ncol;
   const int chunk = (int)std::min<long long>(nb, kStScratch / per_band);
-  if (chunk <= 0) return FDE_EUNSUPPORTED;
   for (int b0 = 0; b0 < nb; b0 += chunk) {
     const int nbc = std::min(chunk, nb - b0);
     launch_hpsi_local<double>((const double2*)d_psi + (size_t)b0 * npw, npw, (double2*)d_hpsi + (size_t)b0 * npw,

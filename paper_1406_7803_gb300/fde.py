@@ -164,7 +164,9 @@ def host_sphere(lengths, kfrac, ecut):
         raise FDEError(s, "fde_host_sphere")
     mil = np.zeros((n.value, 3), dtype=np.int32)
     kin = np.zeros(n.value)
-    lib.fde_host_sphere(_hptr(L), _hptr(kf), float(ecut), C.byref(n), _hptr(mil), _hptr(kin))
+    s = lib.fde_host_sphere(_hptr(L), _hptr(kf), float(ecut), C.byref(n), _hptr(mil), _hptr(kin))
+    if s != FDE_OK or n.value != kin.size:
+        raise FDEError(s, "fde_host_sphere")
     return mil, kin
 
 

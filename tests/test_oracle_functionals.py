@@ -39,19 +39,66 @@ def test_slater_exchange_constant():
         assert np.isclose(fn.e_x_lda(rho) / rho, -0.4581652932831429 / rs, rtol=1e-14)
 
 
-def test_pw92_limits():
-    """High density: eps_c = c0 ln rs - c1 + ..., c0 = (1 - ln 2)/pi^2 (Gell-Mann-Brueckner)
-    and c1 = 0.046644; low density: eps_c -> -d0/rs with d0 = 0.4335."""
+def _eps_c_at(rs):
+    return fn.eps_c_pw92(3.0 / (4 * math.pi * rs ** 3))
+
+
+def test_pw92_high_density_limit():
+    """High density (Gell-Mann-Brueckner): eps_c = c0 ln rs - c1 + O(rs ln rs) with
+    c0 = (1 - ln 2)/pi^2 exactly and c1 = 0.046644.  PW92 builds its beta_1 from c0 and c1
+    and beta_2 = 2 A beta_1^2 so that no rs^{1/2} term appears.  The slope pins A (5 digits),
+    the intercept pins beta_1; a wrong fourth digit of either moves them past the bounds."""
     c0 = (1 - math.log(2)) / math.pi ** 2
-    rs = 1e-8
-    rho = 3.0 / (4 * math.pi * rs ** 3)
-    assert abs(fn.eps_c_pw92(rho) - (c0 * math.log(rs) - 0.046644)) < 2e-5
-    rs = 1e7
-    rho = 3.0 / (4 * math.pi * rs ** 3)
-    assert np.isclose(fn.eps_c_pw92(rho) * rs, -0.4335, rtol=2e-3)
+    r1, r2 = 1e-10, 1e-12
+    e1, e2 = _eps_c_at(r1), _eps_c_at(r2)
+    slope = (e2 - e1) / (math.log(r2) - math.log(r1))
+    assert abs(slope / c0 - 1) < 1.5e-5, slope
+    assert abs((e1 - slope * math.log(r1)) - (-0.046644)) < 2e-6
+    A = fn.PW_A
+    b1, b2 = fn.PW_BETA[0], fn.PW_BETA[1]
+    assert abs(b2 / (2 * A * b1 * b1) - 1) < 5e-5
+
+
+def test_pw92_low_density_limit():
+    """Low density: eps_c = -d0/rs + d1/rs^{3/2} + O(1/rs^2) with d0 = 0.4335 and
+    d1 = 1.4408 (the Wigner-crystal expansion PW92 is built to).  A fit of rs eps_c over
+    rs = 1e3..1e5 recovers both; a wrong fourth digit of alpha_1, beta_3 or beta_4 fails."""
+    rs = np.geomspace(1e3, 1e5, 9)
+    y = np.array([_eps_c_at(r) * r for r in rs])
+    X = np.stack([np.ones_like(rs), rs ** -0.5, rs ** -1.0, rs ** -1.5], axis=1)
+    coef = np.linalg.lstsq(X, y, rcond=None)[0]
+    assert abs(-coef[0] / 0.4335 - 1) < 1.2e-4, coef
+    assert abs(coef[1] / 1.4408 - 1) < 2e-4, coef
     # a mid-range value well inside the published fit range (r_s = 2: about -0.0448 Ha)
-    rho = 3.0 / (4 * math.pi * 8.0)
-    assert -0.0452 < fn.eps_c_pw92(rho) < -0.0443
+    assert -0.0452 < _eps_c_at(2.0) < -0.0443
+
+
+def test_pbe_constants_from_exact_conditions():
+    """PBE's constants come from exact conditions, not fits: F_x(s -> inf) = 1 + kappa is the
+    local Lieb-Oxford bound 1.679 / (C_x 2^{1/3}) (C_x = (3/4)(3/pi)^{1/3}), beta is the
+    Ma-Brueckner gradient coefficient (16/pi)(3 pi^2)^{1/3} 0.004235 and gamma = (1 - ln 2)/pi^2.
+    Evaluated through the energy density where the constant shows up in its output."""
+    rho = 0.3
+    fx_inf = fn.e_xc_pbe(rho, 1e40) / fn.e_x_lda(rho)
+    lo = 1.679 / (0.75 * (3 / math.pi) ** (1 / 3) * 2 ** (1 / 3))
+    assert abs(fx_inf - lo) < 5e-4, (fx_inf, lo)
+    assert abs(fn.PBE_BETA / ((16 / math.pi) * (3 * math.pi ** 2) ** (1 / 3) * 0.004235) - 1) < 1.5e-4
+    assert abs(fn.PBE_GAMMA - (1 - math.log(2)) / math.pi ** 2) < 1e-17
+
+
+def test_lc94_gradient_expansion():
+    """LC94 is fitted to reproduce the second-order gradient expansion of the kinetic energy,
+    T = T_TF + T_W/9, i.e. F(s) = 1 + (5/27) s^2 + O(s^4) (its c + d = 0.18512 against
+    5/27 = 0.18519).  Pins the small-s curvature to 4e-4; the individual constants a, b,
+    alpha, f and the split of c + d have no independent value here (parity unpinned)."""
+    s = np.array([1e-4, 2e-4])
+    F, _ = fn.kedf_F(s, fn.KEDF_LC94)
+    curv = (F - 1.0) / s ** 2
+    assert np.all(np.abs(curv / (5 / 27) - 1) < 4e-4), curv
+    # revAPBEK: F = 1 + mu s^2 + ... with mu = 0.23889 (not the gradient expansion's 5/27);
+    # its kappa and mu are the cited functional's published values (parity unpinned)
+    F, _ = fn.kedf_F(s, fn.KEDF_REVAPBEK)
+    assert np.allclose((F - 1.0) / s ** 2, fn.RAPBEK_MU, rtol=1e-6)
 
 
 def test_pbe_reduces_to_lda_and_limits():
