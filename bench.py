@@ -1,26 +1,33 @@
 """Throughput of the embedded H psi hot path on one GB300 (or N replicas under torchrun).
 
-Workload: the molecule-on-slab cell (16 x 16 x 40 bohr, 72 x 72 x 180 grid, 20 Ha): a 36-atom
-Z=3 slab with 64 bands x 4 k-points (Fermi smearing) plus a 6-atom Z=4 molecule with
-12 bands at Gamma, PBE + revAPBEK, 2 Gaussian KB projectors per atom; seeded synthetic
-inputs (paper_1406_7803_gb300.workloads).
+Workloads (seeded synthetic inputs, paper_1406_7803_gb300.workloads):
+  molecule-on-slab (default): 16 x 16 x 40 bohr, 72 x 72 x 180 grid, 20 Ha; a 36-atom Z=3
+    slab with 64 bands x 4 k-points (Fermi smearing) plus a 6-atom Z=4 molecule with 12 bands
+    at Gamma, PBE + revAPBEK, 2 Gaussian KB projectors per atom: 268 band-applies per step.
+  batched (--workload batched): 24^3 bohr, 96^3 grid, 20 Ha; a 54-atom slab with 96 bands x
+    2 k-points plus 16 molecules of 8..64 bands at Gamma: 778 band-applies per step.
 
 One step = one pass of the hot path over the whole cell: the embedding-potential build
 (rho = sum rho_I, FFT Poisson, FFT gradients, pointwise xc and GGA kinetic potentials,
 divergence, assembly of V_eff^I) followed by H_I psi for every band of every (subsystem,
-k-point): 4 x 64 + 12 = 268 band-applies.  value = band-applies per second over all ranks.
+k-point).  value = band-applies per second over all ranks.
 
-Second part of the metric (N = 1, skipped with --no-ft): seconds per freeze-and-thaw cycle
-at 1e-6 Ha on the same cell, mixed precision (with and without the learned preconditioner)
-against the plain FP64 GPU path ("ft_cycle" in the JSON line).
+Also in the JSON line: a per-kernel table (CUDA events around every launch of a profiled
+pass of the same step, algorithmic bytes or flops per launch and the roof each is held
+to), the FP64 path's band-applies/s on the same cell, the step replayed from a CUDA
+graph, and (N = 1, skipped with --no-ft) seconds per freeze-and-thaw cycle at 1e-6 Ha on
+the molecule-on-slab cell: mixed precision with and without the learned preconditioner,
+against the plain FP64 GPU path ("ft_cycle").
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--prec mixed|fp64]
-                       [--impl ours|reference] [--no-cpu] [--no-ft]
+                       [--workload molecule-on-slab|batched] [--impl ours|reference]
+                       [--no-cpu] [--no-ft]
 """
 from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import subprocess
 import sys
@@ -35,6 +42,8 @@ from paper_1406_7803_gb300 import workloads  # noqa: E402
 
 METRIC = "Embedded H·ψ band-applies/s"
 UNIT = "band-applies/s"
+WORKLOADS = {"molecule-on-slab": workloads.molecule_on_slab, "batched": workloads.batched_uneven}
+REFERENCE_BUDGET_S = 150.0  # wall time the reference arm's K + W steps should stay within
 
 
 def _peaks():
@@ -55,7 +64,6 @@ class Clocks:
         self.path = os.path.join(tempfile.gettempdir(), f"fde_bench_clocks_gpu{index}_{os.getpid()}.csv")
 
     def __enter__(self):
-        os.makedirs(os.path.dirname(self.path), exist_ok=True)
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -126,7 +134,8 @@ def _profile_traffic(name, files, function=None):
         text = open(os.path.join(ROOT, "profiles", name + ".md")).read()
     except OSError:
         return None
-    fields = dict(l.split(":", 1) for l in text.splitlines() if l.startswith(("traffic_bytes_per_launch:", "source_sha256:")))
+    fields = dict(l.split(":", 1) for l in text.splitlines()
+                  if l.startswith(("traffic_bytes_per_launch:", "source_sha256:")))
     if fields.get("source_sha256", "").split()[0:1] != [kernel_source_digest(files, function)]:
         return None
     return float(fields["traffic_bytes_per_launch"])
@@ -161,36 +170,205 @@ def _dist():
     return ws, rank, local
 
 
-def cpu_baseline(wl, max_seconds=15.0):
-    """The FP64 oracle timed on this host's cores on a bounded sample of the workload:
-    one embedding-potential build plus H psi for as many bands as fit in ~max_seconds;
-    band-applies/s of a full step is extrapolated from the two measured parts."""
-    from oracle import basis as obasis
-    from oracle import fde as ofde
+# ---- the oracle's step (reference arm and cpu_baseline) --------------------------------------
+class OracleStep:
+    """One pass of the hot path by the FP64 oracle: one V_eff build for every subsystem, then
+    H psi of a band block of each (subsystem, k), each block in one batched oracle call.
+    The orbitals are drawn once, outside the timed region."""
+
+    def __init__(self, wl, bands=None):
+        from oracle import fde as ofde
+        self.sy = ofde.System(wl)
+        self.rhos = np.array([workloads.initial_density(wl, I) for I in range(wl.nsub)])
+        self.blocks = []
+        for I, s in enumerate(wl.subsystems):
+            for k in range(s.nk):
+                nb = s.nbands if bands is None else min(s.nbands, bands)
+                npw = self.sy.basis[I][k][0].shape[0]
+                self.blocks.append((I, k, workloads.raw_orbitals(5, I, k, nb, npw)))
+        self.units = sum(c.shape[0] for _, _, c in self.blocks)
+
+    def __call__(self):
+        t0 = time.perf_counter()
+        pot = self.sy.build_veff(self.rhos)
+        for I, k, c in self.blocks:
+            self.sy.apply_h(I, k, c, pot["veff"][I])
+        return time.perf_counter() - t0
+
+
+def _cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+def cpu_baseline(wl):
+    """The FP64 oracle timed on this host's cores on one full step of the workload (the
+    same batched oracle call the reference arm times)."""
     t0 = time.perf_counter()
-    sy = ofde.System(wl)
-    rhos = np.array([workloads.initial_density(wl, I) for I in range(wl.nsub)])
-    t1 = time.perf_counter()
-    pot = sy.build_veff(rhos)
-    t_veff = time.perf_counter() - t1
-    done, t_h = 0, 0.0
-    I, k = 0, 0
-    s = wl.subsystems[0]
-    npw = sy.basis[I][k][0].shape[0]
-    while t_h < max_seconds and done < 64:
-        c = workloads.raw_orbitals(5, I, k, 1, npw)
-        t1 = time.perf_counter()
-        sy.apply_h(I, k, c, pot["veff"][I])
-        t_h += time.perf_counter() - t1
-        done += 1
-    t_band = t_h / max(done, 1)
-    units = wl.band_k_pairs()
-    step = t_veff + units * t_band
-    cores = os.cpu_count()
-    return {"value": units / step, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"one FP64 v_eff build ({t_veff:.2f} s) + {done} slab band-applies "
-                      f"({t_band * 1e3:.1f} ms each, scipy.fft workers={cores}), extrapolated to "
-                      f"{units} band-applies per step; setup {t1 - t0:.1f} s excluded"}
+    st = OracleStep(wl)
+    setup = time.perf_counter() - t0
+    sec = st()
+    cores = _cores()
+    return {"value": st.units / sec, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"one full step: FP64 v_eff build of {wl.nsub} subsystems + {st.units} band-applies "
+                      f"in one oracle call per (subsystem, k) ({sec:.2f} s; scipy.fft workers={cores}); "
+                      f"oracle setup {setup:.1f} s excluded"}
+
+
+def run_reference(args):
+    """The reference arm: the FP64 oracle (the slow, obviously correct CPU statement of the
+    method) timed step by step on the host cores, on the same workload and metric.  A step is
+    the whole hot path over the cell when K + W such steps fit the time budget, else the
+    potential build plus an equal band sample of every (subsystem, k)."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    wl = WORKLOADS[args.workload]()
+    full = OracleStep(wl)
+    t_probe = full()  # one step to size the sample (untimed, counts as no warm-up)
+    n = max(1, args.steps + args.warmup)
+    step = full
+    if n * t_probe > REFERENCE_BUDGET_S:
+        per_band = max(t_probe / max(full.units, 1), 1e-4)
+        budget = REFERENCE_BUDGET_S / n
+        nblocks = len(full.blocks)
+        bands = max(1, int((budget * 0.5) / (per_band * nblocks)))
+        step = OracleStep(wl, bands=bands)
+    for _ in range(args.warmup):
+        step()
+    wall0 = time.perf_counter()
+    times = [step() for _ in range(args.steps)]
+    wall = time.perf_counter() - wall0
+    ms = 1e3 * float(np.mean(times))
+    val = step.units / (ms / 1e3)
+    cores = _cores()
+    sample = ("each step the whole hot path: v_eff build + every band" if step is full else
+              f"each step: v_eff build + a {step.units}-band sample ({len(step.blocks)} (subsystem, k) blocks)")
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "band_applies_per_step": step.units, "seed": wl.seed},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": wall}
+    print(json.dumps(line))
+    return 0
+
+
+# ---- per-kernel roofline table ------------------------------------------------------------
+def _sm_count():
+    import torch
+    return int(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
+
+
+def fp_peaks(peaks):
+    """Nominal CUDA-core rates from this device's SM count and the measured maximum SM clock:
+    FP32 128 lanes and FP64 2 lanes per SM, a fused multiply-add counted as 2 flops."""
+    sms = _sm_count()
+    clk = peaks.get("sm_max_mhz", 2070.0) * 1e6
+    return {"sms": sms, "fp32_tflops": sms * 128 * 2 * clk / 1e12, "fp64_tflops": sms * 2 * 2 * clk / 1e12,
+            "tf32_tflops": peaks.get("bf16_tflops", 1900.0) / 2.0}
+
+
+def step_work(wl, ctx, prec):
+    """Algorithmic work of one hot step per kernel family, summed over the step's launches:
+    bytes that must cross HBM (compulsory: every operand read once, every result written once)
+    and flops (5 N log2 N per transformed line of length N, 8 real flops per complex MAC)."""
+    n1, n2, n3 = wl.grid
+    nr = n1 * n2 * n3
+    cw = 8 if prec == "mixed" else 16  # bytes per complex value of the working precision
+    rw = cw // 2
+    w = {k: {"bytes": 0.0, "flops": 0.0} for k in ("k_zinv", "k_plane", "k_zfwd", "k_gemm_hn", "k_gemm_rot",
+                                                  "k_kb_couple", "k_fft_axis_f64")}
+    for I, s in enumerate(wl.subsystems):
+        for k in range(s.nk):
+            mil = ctx.basis(I, k)
+            npw = mil.shape[0]
+            ncol = len({(a, b) for a, b in mil[:, :2].tolist()})
+            nrow = len(np.unique(mil[:, 0]))
+            nb = s.nbands
+            w["k_zinv"]["bytes"] += nb * (npw + n3 * ncol) * cw
+            w["k_zinv"]["flops"] += nb * ncol * 5 * n3 * math.log2(n3)
+            w["k_plane"]["bytes"] += nb * 2 * n3 * ncol * cw
+            w["k_plane"]["flops"] += nb * n3 * (2 * (nrow * 5 * n2 * math.log2(n2) + n2 * 5 * n1 * math.log2(n1))
+                                                + 2 * n1 * n2)
+            w["k_zfwd"]["bytes"] += nb * (n3 * ncol + 2 * npw) * cw
+            w["k_zfwd"]["flops"] += nb * ncol * 5 * n3 * math.log2(n3)
+            npj = len(s.proj_sigma) * s.natoms
+            if npj:
+                w["k_gemm_hn"]["bytes"] += (npj + nb) * npw * cw
+                w["k_gemm_hn"]["flops"] += 8.0 * npj * nb * npw
+                w["k_gemm_rot"]["bytes"] += (npj + 2 * nb) * npw * cw
+                w["k_gemm_rot"]["flops"] += 8.0 * npj * nb * npw
+        w["k_plane"]["bytes"] += nr * rw  # each subsystem's potential planes once
+    # the potential build: 8 complex FP64 3D transforms per pair of subsystems (GGA), each
+    # 3 axis passes reading and writing the grid once
+    npairs = (wl.nsub + 1) // 2
+    ntr = 8 * npairs
+    w["k_fft_axis_f64"]["bytes"] = ntr * 3 * 2 * nr * 16
+    w["k_fft_axis_f64"]["flops"] = ntr * 5 * nr * math.log2(nr)
+    return w
+
+
+def kernel_table(wl, ctx, prec, peaks, src, nsteps=5):
+    """Per-kernel device time of a profiled pass (CUDA events around every launch on the
+    context stream) and each kernel's achieved fraction of the roof that bounds it."""
+    import torch
+    fp = fp_peaks(peaks)
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    names = ["k_zinv", "k_plane", "k_zfwd", "k_fft_axis_f64", "k_pw_total", "k_pw_pair", "k_unpack_density",
+             "k_assemble_pair", "k_finish_pair", "k_pack2", "k_combine", "k_nonfinite", "k_gemm_hn_tc",
+             "k_gemm_hn_partial", "k_gemm_hn_reduce", "k_gemm_rot", "k_gemm_rot_tc", "k_kb_couple"]
+    ctx.sync()
+    ctx.profile_enable(2)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+    ev0.record(stream)
+    for _ in range(nsteps):
+        ctx.hot_step(False)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    step_ms = ev0.elapsed_time(ev1) / nsteps
+    got = {n: ctx.profile_get(n) for n in names}
+    ctx.profile_enable(0)
+    work = step_work(wl, ctx, prec)
+    rows = []
+    for n in names:
+        cnt, ms = got[n]
+        if not cnt:
+            continue
+        per_step_ms = ms / nsteps
+        row = {"kernel": n, "launches_per_step": cnt / nsteps, "avg_us": 1e3 * ms / cnt,
+               "share": per_step_ms / step_ms}
+        fam = "k_gemm_hn" if n in ("k_gemm_hn_tc", "k_gemm_hn_partial") else n
+        fam = "k_gemm_rot" if n in ("k_gemm_rot", "k_gemm_rot_tc") else fam
+        wk = work.get(fam)
+        if wk and (wk["bytes"] or wk["flops"]):
+            sec = per_step_ms / 1e3
+            gbs = wk["bytes"] / sec / 1e9
+            row["hbm"] = {"achieved_gbs": gbs, "peak_gbs": hbm, "frac": gbs / hbm,
+                          "algorithmic_bytes_per_launch": wk["bytes"] / (cnt / nsteps)}
+            if n == "k_fft_axis_f64":
+                tf = wk["flops"] / sec / 1e12
+                row["fp64"] = {"achieved_tflops": tf, "peak_tflops": fp["fp64_tflops"], "frac": tf / fp["fp64_tflops"]}
+            elif n in ("k_gemm_hn_tc",):
+                tf = wk["flops"] / sec / 1e12
+                row["tensor_tf32"] = {"achieved_tflops": tf, "peak_tflops": fp["tf32_tflops"],
+                                      "frac": tf / fp["tf32_tflops"]}
+            elif wk["flops"]:
+                pk = fp["fp32_tflops"] if prec == "mixed" else fp["fp64_tflops"]
+                tf = wk["flops"] / sec / 1e12
+                row["fp32" if prec == "mixed" else "fp64"] = {"achieved_tflops": tf, "peak_tflops": pk,
+                                                               "frac": tf / pk}
+        rows.append(row)
+    rows.sort(key=lambda r: -r["share"])
+    return {"step_ms_profiled": step_ms, "rows": rows,
+            "peaks": {"hbm_gbs": hbm, "hbm_source": src, "fp32_tflops": fp["fp32_tflops"],
+                      "fp64_tflops": fp["fp64_tflops"], "tf32_tflops": fp["tf32_tflops"], "sms": fp["sms"],
+                      "cuda_core_source": "nominal: device SM count x lanes x 2 x measured max SM clock",
+                      "tf32_source": f"measured bf16 burst / 2 ({src})"}}
 
 
 def ft_cycles(tol=1e-6):
@@ -244,43 +422,17 @@ def ft_cycles(tol=1e-6):
     return out
 
 
-def run_reference(args):
-    ws, rank, _ = _dist()
-    if rank != 0:
-        return 0
-    wl = workloads.molecule_on_slab()
-    from oracle import fde as ofde
-    sy = ofde.System(wl)
-    rhos = np.array([workloads.initial_density(wl, I) for I in range(wl.nsub)])
-    units = wl.band_k_pairs()
-    sample_bands = 4
-    npw = sy.basis[0][0][0].shape[0]
-
-    def step():
-        t0 = time.perf_counter()
-        pot = sy.build_veff(rhos)
-        t1 = time.perf_counter()
-        c = workloads.raw_orbitals(5, 0, 0, sample_bands, npw)
-        sy.apply_h(0, 0, c, pot["veff"][0])
-        t2 = time.perf_counter()
-        return (t1 - t0) + units * (t2 - t1) / sample_bands
-
-    for _ in range(args.warmup):
-        step()
-    times = [step() for _ in range(args.steps)]
-    ms = 1e3 * float(np.mean(times))
-    val = units / (ms / 1e3)
-    cores = os.cpu_count()
-    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wl.name, "band_applies_per_step": units, "seed": wl.seed},
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"each step: one FP64 v_eff build + {sample_bands} slab band-applies, "
-                                       f"extrapolated to {units}"},
-            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line))
-    return 0
+def time_steps(ctx, stream, flush, steps, use_graph=False):
+    """Device time (ms) of each of `steps` hot steps, L2 flushed before each."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        ctx.hot_step(use_graph)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
 
 
 def run_ours(args):
@@ -291,7 +443,7 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     from paper_1406_7803_gb300 import fde
-    wl = workloads.molecule_on_slab()
+    wl = WORKLOADS[args.workload]()
     # one non-default stream for the library, the L2 flush and the timing events
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
@@ -302,14 +454,11 @@ def run_ours(args):
     units = wl.band_k_pairs()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
 
-    def step():
-        ctx.hot_step(False)
-
     for _ in range(max(args.warmup, 3)):
-        step()
+        ctx.hot_step(False)
     ctx.sync()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    ctx.profile_enable(True)
+    ctx.profile_enable(1)  # the three H psi passes, timed inside the timed region
     launches0 = ctx.launch_count()
     if ws > 1:
         torch.distributed.barrier()
@@ -319,7 +468,7 @@ def run_ours(args):
         for i in range(args.steps):
             flush.zero_()
             ev[i][0].record(stream)
-            step()
+            ctx.hot_step(False)
             ev[i][1].record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
@@ -327,20 +476,16 @@ def run_ours(args):
     launches = ctx.launch_count() - launches0
     total_ms = float(np.sum(step_ms))
     prof = {n: ctx.profile_get(n) for n in ("k_zinv", "k_plane", "k_zfwd")}
-    ctx.profile_enable(False)
+    ctx.profile_enable(0)
     ms, value = whole_job(total_ms, args.steps, units, ws, "cuda")
 
     # the same pass replayed from a captured CUDA graph (launch overhead removed)
     ctx.hot_step(True)
     torch.cuda.synchronize()
-    gev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    for i in range(args.steps):
-        flush.zero_()
-        gev[i][0].record(stream)
-        ctx.hot_step(True)
-        gev[i][1].record(stream)
-    torch.cuda.synchronize()
-    graph_ms = float(np.mean([a.elapsed_time(b) for a, b in gev]))
+    graph_ms = float(np.mean(time_steps(ctx, stream, flush, args.steps, use_graph=True)))
+
+    peaks, src = _peaks()
+    table = kernel_table(wl, ctx, args.prec, peaks, src) if rank == 0 else None
 
     # end to end through the C ABI with host buffers: densities in, H psi out
     rhos_h = [workloads.initial_density(wl, I) for I in range(wl.nsub)]
@@ -366,47 +511,57 @@ def run_ours(args):
     e2e_step()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    ne = max(2, args.steps // 2)
+    ne = max(2, min(args.steps // 2, 20))
     for _ in range(ne):
         e2e_step()
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / ne
     e2e_s = max_over_ranks(e2e_s, ws, "cuda")
 
-    # roofline of the dominant kernel (the fused plane pass of the local H psi)
-    peaks, src = _peaks()
+    # roofline of the dominant kernel (the fused plane pass of the local H psi), from the
+    # events taken inside the timed region
     n_plane, ms_plane = prof["k_plane"]
     roof = None
     if n_plane:
-        # ALU bound: FFT flops of the (x, y) plane passes the kernel performs, counted with
-        # the 5 N log2 N convention per line, plus the potential multiply.
-        g = wl.grid
-        flops = 0.0
-        for I, s in enumerate(wl.subsystems):
-            for k in range(s.nk):
-                mil = ctx.basis(I, k)
-                nrow = len(np.unique(mil[:, 0]))
-                per_plane = 2 * (nrow * 5 * g[1] * np.log2(g[1]) + g[1] * 5 * g[0] * np.log2(g[0])) + 2 * g[0] * g[1]
-                flops += s.nbands * g[2] * per_plane
-        flops_per_launch = flops * args.steps / n_plane
+        fp = fp_peaks(peaks)
+        work = step_work(wl, ctx, args.prec)["k_plane"]
+        per_launch_flops = work["flops"] * args.steps / n_plane
+        per_launch_bytes = work["bytes"] * args.steps / n_plane
         sec = ms_plane / n_plane / 1e3
-        sm_mhz = peaks.get("clocks_under_load", {}).get("sm_mhz_median") or peaks.get("sm_max_mhz", 2070.0)
-        lanes = 4 * 32  # FP32 lanes per SM
-        fp_peak = 152 * lanes * 2 * (peaks.get("sm_max_mhz", 2070.0) * 1e6) / 1e12  # FMA = 2 flops
-        if args.prec == "fp64":
-            fp_peak = 1.25  # nominal FP64 rate of the part (TFLOP/s)
-        achieved = flops_per_launch / sec / 1e12
+        pk = fp["fp32_tflops"] if args.prec == "mixed" else fp["fp64_tflops"]
+        achieved = per_launch_flops / sec / 1e12
         traffic = (_profile_traffic("k_plane_ct_molecule_on_slab", PLANE_SOURCES, PLANE_FUNCTION)
-                   if args.prec == "mixed" else None)
-        roof = {"bound": "alu", "achieved": achieved, "peak": fp_peak, "unit": "TFLOP/s", "frac": achieved / fp_peak,
-                "traffic": traffic, "kernel": "k_plane", "launches": n_plane,
-                "avg_launch_us": 1e6 * sec, "peak_source": f"{'FP32' if args.prec != 'fp64' else 'FP64'} lanes x "
-                f"clock ({'152 SMs x 128 lanes x 2 x sm_max' if args.prec != 'fp64' else 'nominal'}); "
-                f"HBM peak {peaks.get('hbm_gbs')} GB/s {src}",
+                   if (args.prec == "mixed" and args.workload == "molecule-on-slab") else None)
+        hbm_gbs = per_launch_bytes / sec / 1e9
+        roof = {"bound": "alu", "achieved": achieved, "peak": pk, "unit": "TFLOP/s", "frac": achieved / pk,
+                "traffic": traffic, "kernel": "k_plane", "launches": n_plane, "avg_launch_us": 1e6 * sec,
+                "algorithmic_flops_per_launch": per_launch_flops,
+                "peak_source": f"nominal {'FP32' if args.prec == 'mixed' else 'FP64'} rate: {fp['sms']} SMs (device) "
+                               f"x {'128' if args.prec == 'mixed' else '2'} lanes x 2 flops x "
+                               f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz ({src} max SM clock)",
+                "hbm": {"achieved_gbs": hbm_gbs, "peak_gbs": peaks.get("hbm_gbs"), "frac": hbm_gbs / peaks.get("hbm_gbs"),
+                        "algorithmic_bytes_per_launch": per_launch_bytes, "peak_source": src},
                 "share_of_step": (ms_plane / args.steps) / ms}
-        del sm_mhz
+
+    # the FP64 path's hot step on the same cell (the FP64 half of the metric's comparison)
+    fp64 = None
+    if args.prec == "mixed" and not args.no_fp64:
+        c64 = fde.context_from_workload(wl, prec="fp64", stream=stream.cuda_stream)
+        fde.seed_workload(c64, wl)
+        c64.build_vemb()
+        for _ in range(3):
+            c64.hot_step(False)
+        c64.sync()
+        k64 = max(3, min(args.steps, 20))
+        t64 = time_steps(c64, stream, flush, k64)
+        ms64 = float(np.mean(t64))
+        fp64 = {"value": ws * units / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64, "steps": k64,
+                "dtype": "f64", "note": "the same hot step in an FP64 context, L2 flushed between steps"}
+        del c64
+        torch.cuda.empty_cache()
+
     cpu = cpu_baseline(wl) if (rank == 0 and not args.no_cpu) else None
-    ft = ft_cycles() if (ws == 1 and not args.no_ft) else None
+    ft = ft_cycles() if (ws == 1 and not args.no_ft and args.workload == "molecule-on-slab") else None
     clocks = clk.summary()
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -418,7 +573,8 @@ def run_ours(args):
                            "parallelism": f"replicas x{ws}"},
                 "e2e": {"value": ws * units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
-                "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks, "ft_cycle": ft,
+                "gpu_launches": launches, "roofline": roof, "kernels": table, "fp64": fp64,
+                "cpu_baseline": cpu, "clocks": clocks, "ft_cycle": ft,
                 "wall_s": wall, "step_ms": step_ms,
                 "graph": {"ms_per_step": graph_ms, "value": ws * units / (graph_ms / 1e3),
                           "note": "the same step replayed from a captured CUDA graph"}}
@@ -435,7 +591,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--workload", default="molecule-on-slab", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 context's hot-step timing")
     ap.add_argument("--no-ft", action="store_true", help="skip the freeze-and-thaw cycle timings (~4 min)")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -47,7 +47,7 @@ typedef enum {
   FDE_ECUDA = -3,         /* a CUDA runtime call failed */
   FDE_ENOCONV = -4,       /* an iteration reached its cap before its tolerance */
   FDE_ENONFINITE = -5,    /* a density, potential or energy became NaN/Inf */
-  FDE_ETIMEOUT = -6,      /* reserved: bounded device waits that ran out */
+  FDE_ETIMEOUT = -6,      /* a bounded device wait ran out (tensor-core products) */
   FDE_EUNSUPPORTED = -7   /* a size or option outside what the kernels handle */
 } fde_status;
 
@@ -264,11 +264,37 @@ fde_status fde_scf_subsystem(fde_ctx* ctx, int sub, double tol_ha, int max_scf,
  * out (nullable) receives the energies of the refreshed state. */
 fde_status fde_freeze_thaw_cycle(fde_ctx* ctx, double tol_ha, int max_scf, fde_energies* out);
 
+/* SCF of every subsystem with the total density refreshed after every step: the paper's
+ * default scheme (Sec. 2, text after Fig. 1; Fig. 1b caption: the subsystem SCF is executed
+ * once per exchange of the densities, so at convergence every subsystem density is
+ * self-consistent with every other one; freeze-and-thaw cycles repeated to convergence reach
+ * the same fixed point).  Each step rebuilds V_eff^I of every subsystem from the current
+ * densities, runs the block eigensolver on every (subsystem, k), forms the occupations and
+ * output densities, and mixes the densities of all subsystems together (one Pulay step on
+ * the stacked densities, history 8, weight 0.3).  Converged when the FDE free energy changes by less than tol_ha between steps
+ * and every subsystem's int|rho_out - rho_in| is below 10 tol_ha (mixed contexts: an FP32
+ * stage to max(tol_ha, 1e-5), then the FP64 engine from its densities and orbitals to
+ * tol_ha).  On return the subsystem densities are the last output densities and out
+ * (nullable) holds their energies, iters the number of steps.  FDE_ENOCONV after max_scf
+ * steps.  With a single subsystem this is the plain Kohn-Sham SCF of the supersystem. */
+fde_status fde_scf_refresh(fde_ctx* ctx, double tol_ha, int max_scf, fde_energies* out);
+
+/* Number of misplaced electrons <Delta rho> = 1/2 int |rho(r) - rho_ref(r)| dr (Computational
+ * Details, Eq. deltarho) between the context's total density rho = sum_I rho_I and a caller
+ * device grid d_rho_ref (FP64 [n1][n2][n3], e.g. the density of a supersystem Kohn-Sham
+ * context on the same cell and grid); synchronising. */
+fde_status fde_delta_rho(fde_ctx* ctx, const double* d_rho_ref, double* out);
+
 /* Per-kernel timing of the library's own launches (measurement support; no counterpart in
- * the paper).  fde_profile_enable(ctx, 1) clears the records and starts recording a CUDA
- * event pair around every launch of the timed kernels (k_zinv, k_plane, k_zfwd) on the
- * context stream; 0 stops.  fde_profile_get returns the number of recorded launches of
- * `kernel` and their summed device time in ms (synchronising; 0 launches if none). */
+ * the paper).  fde_profile_enable(ctx, level) clears the records and starts recording a
+ * CUDA event pair around launches on the context stream: level 1 the three passes of the
+ * local H psi (k_zinv, k_plane, k_zfwd), level 2 also the potential build (k_fft_axis_f64 /
+ * k_fft_axis_f32, k_unpack_density, k_pw_total, k_pw_pair, k_assemble_pair, k_finish_pair,
+ * k_pack2, k_combine, k_nonfinite), the band-block products (k_gemm_hn_tc, k_gemm_rot_tc,
+ * k_gemm_hn_partial, k_gemm_hn_reduce, k_gemm_rot, k_kb_couple) and the density passes
+ * (k_zinv_density, k_plane_density); 0 stops.  FDE_EINVAL for other levels.
+ * fde_profile_get returns the number of recorded launches of `kernel` and their summed
+ * device time in ms (synchronising; 0 launches if none). */
 fde_status fde_profile_enable(fde_ctx* ctx, int enable);
 fde_status fde_profile_get(fde_ctx* ctx, const char* kernel, int* launches, double* total_ms);
 
@@ -346,6 +372,17 @@ fde_status fde_gemm_rot_f32(fde_ctx* ctx, const void* d_X, int ldx, const double
  * use the CUDA cores.  Process-wide; the default is 3 (FDE_GEMM_PATH in the environment sets
  * the initial path). */
 fde_status fde_set_gemm_path(int path);
+
+/* Poll limit of the waits a tensor-core product makes for each shared-memory stage of its
+ * K loop (diagnostic support; no counterpart in the paper).  Every device wait of the
+ * library is bounded: when a stage wait runs out the kernel stops issuing, waits (with the
+ * full bound, about a second) for the MMAs it has issued, releases its tensor memory, writes
+ * no result and the call returns FDE_ETIMEOUT.  polls = 0 makes every stage wait run out at
+ * once (so that this path can be exercised on a healthy GPU); polls < 0 restores the default
+ * bound.  Process-wide, current device.  If a kernel ever cannot confirm its issued MMAs
+ * complete it keeps its tensor memory (an MMA may still write it), and every later product
+ * in the process runs on the CUDA cores. */
+fde_status fde_set_tc_wait_limit(long long polls);
 
 /* The FP32 plane pass of H psi (the (x, y) transforms, potential multiply and back) comes in
  * several compiled variants (register budget per thread, CTAs per SM, radix order of the

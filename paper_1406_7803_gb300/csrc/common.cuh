@@ -32,7 +32,7 @@ template <typename C> __host__ __device__ __forceinline__ C cmuli(C a, int sign)
 template <typename C> __host__ __device__ __forceinline__ C cconj(C a) { a.y = -a.y; return a; }
 
 // Device status word bits (checked by the host after synchronising calls).
-enum : unsigned { ST_NONFINITE = 1u, ST_CHOLESKY = 2u, ST_NOCONV = 4u, ST_TIMEOUT = 8u };
+enum : unsigned { ST_NONFINITE = 1u, ST_CHOLESKY = 2u, ST_NOCONV = 4u, ST_TIMEOUT = 8u, ST_TMEM_HELD = 16u };
 
 // Largest supported 1D transform length (one line held by one warp in shared memory).
 constexpr int kMaxLine = 320;

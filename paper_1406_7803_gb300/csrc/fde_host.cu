@@ -178,6 +178,8 @@ struct Engine {
   virtual void energy(fde_energies* out) = 0;
   virtual fde_status scf_subsystem(int sub, double tol, int max_scf, fde_energies* out) = 0;
   virtual fde_status freeze_thaw(double tol, int max_scf, fde_energies* out, const double* start) = 0;
+  virtual fde_status scf_refresh(double tol, int max_scf, fde_energies* out) = 0;
+  virtual double delta_rho(const double* d_ref) = 0;
   virtual void sync() = 0;
   virtual void fft3d(void* data, int sign) = 0;
   virtual void precond_set_weights(const float* h) = 0;
@@ -235,8 +237,13 @@ template <typename T> struct EngineT : Engine {
   DBuf<double> wv, dnorm, deps, dtb, hwork;
   DBuf<int> didx;
   DBuf<double> rho_plane, occw;
-  // Pulay history and freeze-and-thaw copies
-  std::vector<DBuf<double>> hist_in, hist_res;
+  // Pulay histories (one for the subsystem SCF, one per subsystem for the refreshed SCF)
+  // and freeze-and-thaw copies
+  struct PulayHist {
+    std::vector<DBuf<double>> in, res;
+    int len = 0, head = 0;
+  };
+  PulayHist hist, hist_all;
   DBuf<double> rho_in, frozen, fresh;
   DBuf<const double*> dptrs;
   DBuf<double> dcoef;
@@ -278,7 +285,7 @@ template <typename T> struct EngineT : Engine {
     vpart.alloc(nr);
     for (auto& b : htot) b.alloc(nr);
     partial.alloc(64 * (size_t)grid_red_blocks());
-    scal.alloc(128);
+    scal.alloc(256);
     status.alloc(1);
     CK(cudaMemsetAsync(status.p, 0, sizeof(unsigned), st));
     rho_plane.alloc(nr);
@@ -548,10 +555,10 @@ template <typename T> struct EngineT : Engine {
   // (v_a + i v_b) backward: 8 transforms per pair.
   EnergyParts grid_pass(bool want_pot, bool want_e, int which) {
     ensure_vloc();
-    REQ(4 + 3 * subs.size() <= 120, FDE_EUNSUPPORTED, "too many subsystems for one energy pass");
+    REQ(4 + 3 * subs.size() <= 250, FDE_EUNSUPPORTED, "too many subsystems for one energy pass");
     const int nsb = (int)subs.size();
     const int npairs = (nsb + 1) / 2;
-    REQ(npairs <= kMaxPairs, FDE_EUNSUPPORTED, "at most 16 subsystems");
+    REQ(npairs <= kMaxPairs, FDE_EUNSUPPORTED, "at most 64 subsystems");
     const size_t nrb = (size_t)grid_red_blocks();
     const double dv = omega / (double)nr;
     const bool grad = gga_xc() || gga_kin();
@@ -1147,19 +1154,19 @@ template <typename T> struct EngineT : Engine {
     }
   }
 
-  double integrate_product(const double* a, const double* b) {
-    grid_dot_partial(a, b, nr, 0, partial.p, st);
-    grid_finalize(partial.p, 1, omega / (double)nr, scal.p + 127, st);
+  double integrate_product(const double* a, const double* b, long long n = 0) {
+    grid_dot_partial(a, b, n > 0 ? n : nr, 0, partial.p, st);
+    grid_finalize(partial.p, 1, omega / (double)nr, scal.p + 255, st);
     double h = 0;
-    CK(cudaMemcpyAsync(&h, scal.p + 127, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&h, scal.p + 255, sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     return h;
   }
   double integrate_absdiff(const double* a, const double* b) {
     grid_dot_partial(a, b, nr, 1, partial.p, st);
-    grid_finalize(partial.p, 1, omega / (double)nr, scal.p + 127, st);
+    grid_finalize(partial.p, 1, omega / (double)nr, scal.p + 255, st);
     double h = 0;
-    CK(cudaMemcpyAsync(&h, scal.p + 127, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&h, scal.p + 255, sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     return h;
   }
@@ -1366,42 +1373,44 @@ template <typename T> struct EngineT : Engine {
   }
 
   // ---- Pulay mixing -----------------------------------------------------------------------------
-  int hist_len = 0, hist_head = 0;
-  void pulay_reset() { hist_len = 0; hist_head = 0; }
-  // rho_in <- DIIS mix of the history extended by (rho_in, rho_out - rho_in)
-  void pulay(double* rin, const double* rout) {
+  void pulay_reset(PulayHist& h) { h.len = 0; h.head = 0; }
+  void pulay_reset() { pulay_reset(hist); }
+  void pulay(double* rin, const double* rout) { pulay(hist, rin, rout, nr); }
+  // rho_in <- DIIS mix of the history extended by (rho_in, rho_out - rho_in); the vectors
+  // hold n values (one grid, or the stacked grids of every subsystem)
+  void pulay(PulayHist& hs, double* rin, const double* rout, long long n) {
     const int H = 8;
     const double beta = 0.3;
-    if (hist_in.size() < (size_t)H) {
-      hist_in.resize(H);
-      hist_res.resize(H);
-      for (int h = 0; h < H; ++h) { hist_in[h].ensure(nr); hist_res[h].ensure(nr); }
+    if (hs.in.size() < (size_t)H) {
+      hs.in.resize(H);
+      hs.res.resize(H);
     }
-    const int slot = (hist_head + hist_len) % H;
-    if (hist_len == H) hist_head = (hist_head + 1) % H; else ++hist_len;
-    CK(cudaMemcpyAsync(hist_in[slot].p, rin, nr * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    for (int h = 0; h < H; ++h) { hs.in[h].ensure(n); hs.res[h].ensure(n); }
+    const int slot = (hs.head + hs.len) % H;
+    if (hs.len == H) hs.head = (hs.head + 1) % H; else ++hs.len;
+    CK(cudaMemcpyAsync(hs.in[slot].p, rin, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
     // res = rout - rin
-    CK(cudaMemcpyAsync(hist_res[slot].p, rout, nr * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    neg_add(hist_res[slot].p, rin);
-    const int m = hist_len;
+    CK(cudaMemcpyAsync(hs.res[slot].p, rout, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    grid_axpy(hs.res[slot].p, rin, -1.0, n, st);
+    const int m = hs.len;
     std::vector<int> sl(m);
-    for (int a = 0; a < m; ++a) sl[a] = (hist_head + a) % H;
+    for (int a = 0; a < m; ++a) sl[a] = (hs.head + a) % H;
     std::vector<double> ov((size_t)m * m, 0.0);
     for (int a = 0; a < m; ++a)
       for (int c = a; c < m; ++c) {
-        const double v = integrate_product(hist_res[sl[a]].p, hist_res[sl[c]].p) * (double)nr / omega;
+        const double v = integrate_product(hs.res[sl[a]].p, hs.res[sl[c]].p, n) * (double)nr / omega;
         ov[a * m + c] = ov[c * m + a] = v;
       }
     std::vector<double> coef(m, 0.0);
     pulay_coefficients(ov.data(), m, coef.data());
     std::vector<const double*> pi(m), pr(m);
-    for (int a = 0; a < m; ++a) { pi[a] = hist_in[sl[a]].p; pr[a] = hist_res[sl[a]].p; }
+    for (int a = 0; a < m; ++a) { pi[a] = hs.in[sl[a]].p; pr[a] = hs.res[sl[a]].p; }
     dptrs.ensure(2 * m);
     dcoef.ensure(m);
     CK(cudaMemcpyAsync(dptrs.p, pi.data(), m * sizeof(double*), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(dptrs.p + m, pr.data(), m * sizeof(double*), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(dcoef.p, coef.data(), m * sizeof(double), cudaMemcpyHostToDevice, st));
-    grid_lincomb(dptrs.p, dptrs.p + m, dcoef.p, m, beta, nr, rin, st);
+    grid_lincomb(dptrs.p, dptrs.p + m, dcoef.p, m, beta, n, rin, st);
     CK(cudaStreamSynchronize(st));
   }
   // ---- subsystem SCF and freeze-and-thaw ------------------------------------------------------
@@ -1521,6 +1530,83 @@ template <typename T> struct EngineT : Engine {
     sync();
     return worst;
   }
+
+  // SCF of every subsystem with the total density refreshed after every step (the paper's
+  // default: the subsystem SCF of Fig. 1b runs once per exchange of the densities).  Each
+  // step: V_eff^I of every subsystem from the current input densities, eigensolves of every
+  // (subsystem, k), occupations and output densities, then one Pulay (DIIS) step on the
+  // stacked densities of all subsystems (one set of coefficients for every subsystem: they are
+  // coupled through the shared potential).  Converged when the FDE free energy changes by less than tol and every subsystem's
+  // int|rho_out - rho_in| is below 10 tol (mixed precision: max(10 tol, 1e-4)).  The
+  // subsystem densities hold the last output densities on return; out gets their energies.
+  fde_status scf_refresh(double tol, int max_scf, fde_energies* out) override {
+    REQ(!subs.empty(), FDE_EINVAL, "no subsystems");
+    REQ(max_scf > 0 && tol > 0, FDE_EINVAL, "bad SCF arguments");
+    for (auto& sp : subs)
+      for (auto& q : sp->kp) REQ(q.have_orbitals, FDE_EINVAL, "orbitals of every subsystem must be set");
+    ensure_vloc();
+    const size_t ns = subs.size();
+    frozen.ensure(ns * nr);  // the input densities rho_in of every subsystem
+    for (size_t I = 0; I < ns; ++I)
+      CK(cudaMemcpyAsync(frozen.p + I * nr, subs[I]->rho.p, nr * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    fresh.ensure(ns * nr);  // the output densities, stacked for the joint mixing
+    pulay_reset(hist_all);
+    const double dtol = davidson_tol(tol);
+    std::vector<double> dres_prev(ns, 1.0), dres(ns, 0.0);
+    double Fprev = 0;
+    bool have_prev = false;
+    fde_energies en{};
+    for (int it = 1; it <= max_scf; ++it) {
+      for (size_t I = 0; I < ns; ++I)
+        CK(cudaMemcpyAsync(subs[I]->rho.p, frozen.p + I * nr, nr * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      grid_pass(true, false, -1);
+      for (size_t I = 0; I < ns; ++I) {
+        Sub<T>& s = *subs[I];
+        for (int k = 0; k < s.nk; ++k) {
+          int its = 0;
+          subspace_solve((int)I, k, std::max(dtol, std::min(1e-3, 1e-4 * dres_prev[I])), 60, &its, precond_mode);
+          davidson_iters += its;
+        }
+        occupations(s);
+        density_from_orbitals(s, s.rho.p);
+      }
+      sync();
+      energy(&en);
+      double worst = 0;
+      for (size_t I = 0; I < ns; ++I) {
+        dres[I] = integrate_absdiff(subs[I]->rho.p, frozen.p + I * nr);
+        dres_prev[I] = dres[I];
+        worst = std::max(worst, dres[I]);
+      }
+      en.iters = it;
+      en.dE = have_prev ? en.F_fde - Fprev : 0.0;
+      REQ(std::isfinite(en.F_fde), FDE_ENONFINITE, "non-finite energy");
+      if (trace_level() > 0)
+        fprintf(stderr, "[fde] refresh it %d F %.12f dE %.3e max drho %.3e eig_iters %lld\n", it, en.F_fde, en.dE,
+                worst, davidson_iters);
+      if (have_prev && fabs(en.dE) < tol && worst < dres_tol(tol)) {
+        grid_pass(true, false, -1);  // potentials of the returned densities
+        if (out) *out = en;
+        return FDE_OK;
+      }
+      Fprev = en.F_fde;
+      have_prev = true;
+      for (size_t I = 0; I < ns; ++I)
+        CK(cudaMemcpyAsync(fresh.p + I * nr, subs[I]->rho.p, nr * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      pulay(hist_all, frozen.p, fresh.p, (long long)ns * nr);
+    }
+    grid_pass(true, false, -1);
+    if (out) *out = en;
+    return FDE_ENOCONV;
+  }
+
+  // <Delta rho> = 1/2 int |rho - rho_ref| with rho = sum_I rho_I (Computational Details).
+  double delta_rho(const double* d_ref) override {
+    REQ(d_ref, FDE_EINVAL, "null reference density");
+    REQ(!subs.empty(), FDE_EINVAL, "no subsystems");
+    sum_densities();
+    return 0.5 * integrate_absdiff(rho_tot.p, d_ref);
+  }
 };
 
 template <> void EngineT<double>::convert_in(const double2* a, double2* b, size_t n) {
@@ -1612,6 +1698,28 @@ static fde_status mixed_cycle(fde_ctx* c, double tol, int max_scf, fde_energies*
   CK(cudaStreamSynchronize(st));
   fde_energies e2{};
   const fde_status s2 = hi.freeze_thaw(tol, max_scf, &e2, start.p);
+  transfer_state(hi, lo, st);
+  lo.build_vemb(nullptr, nullptr);
+  lo.sync();
+  if (out) {
+    *out = e2;
+    out->iters = e1.iters + e2.iters;
+  }
+  return s2;
+}
+
+// Mixed-precision refreshed SCF: the FP32 engine converges to a relaxed tolerance, the FP64
+// engine continues from its densities and orbitals to the requested one, and the result is
+// copied back to the FP32 engine.
+static fde_status mixed_refresh(fde_ctx* c, double tol, int max_scf, fde_energies* out, cudaStream_t st) {
+  Engine& lo = *c->eng;
+  Engine& hi = *c->eng64;
+  fde_energies e1{};
+  const fde_status s1 = lo.scf_refresh(std::max(tol, 1e-5), max_scf, &e1);
+  if (s1 != FDE_OK && s1 != FDE_ENOCONV) return s1;
+  transfer_state(lo, hi, st);
+  fde_energies e2{};
+  const fde_status s2 = hi.scf_refresh(tol, max_scf, &e2);
   transfer_state(hi, lo, st);
   lo.build_vemb(nullptr, nullptr);
   lo.sync();
@@ -1733,6 +1841,19 @@ fde_status fde_freeze_thaw_cycle(fde_ctx* c, double tol, int max_scf, fde_energi
     return c->eng->freeze_thaw(tol, max_scf, out, nullptr);
   });
 }
+fde_status fde_scf_refresh(fde_ctx* c, double tol, int max_scf, fde_energies* out) {
+  return guard(c, [&]() {
+    if (c->eng64) return fde::mixed_refresh(c, tol, max_scf, out, c->stream);
+    return c->eng->scf_refresh(tol, max_scf, out);
+  });
+}
+fde_status fde_delta_rho(fde_ctx* c, const double* d_rho_ref, double* out) {
+  return guard(c, [&]() {
+    if (!out) throw fde::Err{FDE_EINVAL, "null output"};
+    *out = c->eng->delta_rho(d_rho_ref);
+    return FDE_OK;
+  });
+}
 fde_status fde_set_precond(fde_ctx* c, int precond) {
   return guard(c, [&]() { c->eng->set_precond_mode(precond); return FDE_OK; });
 }
@@ -1821,6 +1942,10 @@ fde_status fde_gemm_rot_f32(fde_ctx* c, const void* d_X, int ldx, const double* 
 int fde_tuned_plane_variant(int n1, int n3) { return fde::query_plane_variant(n1, n3); }
 fde_status fde_pin_plane_variant(int variant) { return fde::pin_plane_variant(variant) ? FDE_OK : FDE_EINVAL; }
 
+fde_status fde_set_tc_wait_limit(long long polls) {
+  return fde::set_tc_stage_spin(polls) ? FDE_OK : FDE_ECUDA;
+}
+
 fde_status fde_set_gemm_path(int path) {
   if (path != 0 && path != 1 && path != 3) return FDE_EINVAL;
   fde::set_gemm_hn_path(path);
@@ -1850,9 +1975,11 @@ fde_status fde_sync(fde_ctx* c) {
 }
 fde_status fde_profile_enable(fde_ctx* c, int enable) {
   return guard(c, [&]() {
+    if (enable < 0 || enable > 2) throw fde::Err{FDE_EINVAL, "profiling level must be 0, 1 or 2"};
     c->eng->sync();
     c->prof.reset();
     c->prof.on = enable != 0;
+    c->prof.level = enable == 2 ? 2 : 1;
     return FDE_OK;
   });
 }

@@ -49,6 +49,9 @@ constexpr int kTmemCols = 128;
 constexpr long long kSpin = 1ll << 22;  // bounded mbarrier polls (with back-off: ~1 s)
 
 __device__ unsigned g_tc_status;
+// Poll limit of the waits for a shared-memory stage inside the K loop (settable from the host
+// so that the timeout path can be exercised; the final drain always uses kSpin).
+__device__ long long g_tc_stage_spin = kSpin;
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -66,8 +69,8 @@ __device__ __forceinline__ bool mbar_test(uint32_t bar, unsigned parity) {
       : "memory");
   return ok != 0;
 }
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, unsigned parity) {
-  for (long long i = 0; i < kSpin; ++i) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, unsigned parity, long long limit = kSpin) {
+  for (long long i = 0; i < limit; ++i) {
     if (mbar_test(bar, parity)) return true;
     if (i > 32) __nanosleep(128);
   }
@@ -203,7 +206,8 @@ k_gemm_hn_tc(const float2* __restrict__ A, int lda, const float2* __restrict__ B
     const uint32_t st = base + (uint32_t)s * kStage;
     if (t >= kStages) {
       // stage s is free once the MMAs of tile t - kStages have completed
-      if (tid == 0 && !mbar_wait(su32(&bars[s]), (unsigned)(((t - kStages) / kStages) & 1))) abort_flag = 1;
+      if (tid == 0 && !mbar_wait(su32(&bars[s]), (unsigned)(((t - kStages) / kStages) & 1), g_tc_stage_spin))
+        abort_flag = 1;
       __syncthreads();
       if (abort_flag) break;
     }
@@ -230,15 +234,17 @@ k_gemm_hn_tc(const float2* __restrict__ A, int lda, const float2* __restrict__ B
   }
 
   // wait for the last commit of each stage: every issued MMA has completed
+  __shared__ int drained;
   if (tid == 0) {
+    drained = 1;
     for (int s = 0; s < kStages && s < issued; ++s) {
       const int uses = (issued - s + kStages - 1) / kStages;
-      if (!mbar_wait(su32(&bars[s]), (unsigned)((uses - 1) & 1))) abort_flag = 1;
+      if (!mbar_wait(su32(&bars[s]), (unsigned)((uses - 1) & 1))) drained = 0;
     }
   }
   __syncthreads();
-  const bool ok = !abort_flag;
-  if (!ok && tid == 0) atomicOr(&g_tc_status, ST_TIMEOUT);
+  const bool ok = !abort_flag && drained;
+  if (!ok && tid == 0) atomicOr(&g_tc_status, drained ? ST_TIMEOUT : (ST_TIMEOUT | ST_TMEM_HELD));
   tc_fence_after();
   if (ok) {
     // warp w reads accumulator lanes 32 (w % 4) .. + 31 (its rows); warps 0-3 take the
@@ -269,7 +275,10 @@ k_gemm_hn_tc(const float2* __restrict__ A, int lda, const float2* __restrict__ B
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) {
+  // Tensor memory is released only once every issued MMA is known to have completed; if the
+  // drain ran out, the columns stay allocated (an MMA may still write them) and the host,
+  // seeing ST_TMEM_HELD, stops using the tensor-core kernels in this process.
+  if (warp == 0 && drained) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
   }
@@ -389,7 +398,8 @@ k_gemm_rot_tc(const float2* __restrict__ X, int ldx, const double2* __restrict__
     const int s = t % kRotStages;
     const uint32_t st = base + (uint32_t)s * kRotStage;
     if (t >= kRotStages) {
-      if (tid == 0 && !mbar_wait(su32(&bars[s]), (unsigned)(((t - kRotStages) / kRotStages) & 1))) abort_flag = 1;
+      if (tid == 0 && !mbar_wait(su32(&bars[s]), (unsigned)(((t - kRotStages) / kRotStages) & 1), g_tc_stage_spin))
+        abort_flag = 1;
       __syncthreads();
       if (abort_flag) break;
     }
@@ -414,15 +424,17 @@ k_gemm_rot_tc(const float2* __restrict__ X, int ldx, const double2* __restrict__
     }
     if (t + 1 < nt) load(t + 1);
   }
+  __shared__ int drained;
   if (tid == 0) {
+    drained = 1;
     for (int s = 0; s < kRotStages && s < issued; ++s) {
       const int uses = (issued - s + kRotStages - 1) / kRotStages;
-      if (!mbar_wait(su32(&bars[s]), (unsigned)((uses - 1) & 1))) abort_flag = 1;
+      if (!mbar_wait(su32(&bars[s]), (unsigned)((uses - 1) & 1))) drained = 0;
     }
   }
   __syncthreads();
-  const bool ok = !abort_flag;
-  if (!ok && tid == 0) atomicOr(&g_tc_status, ST_TIMEOUT);
+  const bool ok = !abort_flag && drained;
+  if (!ok && tid == 0) atomicOr(&g_tc_status, drained ? ST_TIMEOUT : (ST_TIMEOUT | ST_TMEM_HELD));
   tc_fence_after();
   if (ok) {
     // Accumulator -> shared memory (the stage buffers are free: every MMA has completed), then a
@@ -470,7 +482,7 @@ k_gemm_rot_tc(const float2* __restrict__ X, int ldx, const double2* __restrict__
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) {
+  if (warp == 0 && drained) {  // as in k_gemm_hn_tc: held if the drain ran out
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kRotTmemCols) : "memory");
   }
@@ -510,14 +522,22 @@ int launch_gemm_hn_tc(const float2* A, int lda, const float2* B, int ldb, int m,
 }
 
 // Status bits raised by the tensor-core kernels since the last call (read and cleared;
-// synchronises the stream).
+// synchronises the stream).  A kernel that could not confirm its MMAs complete kept its
+// tensor memory (ST_TMEM_HELD): from then on the products run on the CUDA cores.
 unsigned gemm_tc_take_status(cudaStream_t st) {
   unsigned h = 0, z = 0;
   if (cudaMemcpyFromSymbolAsync(&h, g_tc_status, sizeof(unsigned), 0, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
     return 0;  // the stream's own error surfaces at the caller's next check
   if (h) cudaMemcpyToSymbolAsync(g_tc_status, &z, sizeof(unsigned), 0, cudaMemcpyHostToDevice, st);
+  if (h & ST_TMEM_HELD) disable_tensor_cores();
   return h;
+}
+
+// Poll limit of the tensor-core kernels' stage waits (polls < 0: the default bound).
+bool set_tc_stage_spin(long long polls) {
+  const long long v = polls < 0 ? kSpin : std::min(polls, kSpin);
+  return cudaMemcpyToSymbol(g_tc_stage_spin, &v, sizeof(v)) == cudaSuccess;
 }
 
 }  // namespace fde

@@ -573,6 +573,7 @@ template <typename T>
 void grid_combine(const double* a, const double* b, const double* c, const cplx<T>* d, double sd, double* out,
                   long long n, cudaStream_t st) {
   count_launches(1);
+  ProfScope prof_("k_combine", st);
   k_combine<T><<<gs(n), 256, 0, st>>>(a, b, c, d, sd, out, n);
 }
 template <typename T>
@@ -601,38 +602,45 @@ void grid_axpy(double* a, const double* b, double alpha, long long n, cudaStream
 }
 void grid_nonfinite(const double* a, long long n, unsigned* status, cudaStream_t st) {
   count_launches(1);
+  ProfScope prof_("k_nonfinite", st);
   k_nonfinite<<<gs(n), 256, 0, st>>>(a, n, status);
 }
 void grid_pack2(const double* a, const double* b, double2* c, long long n, cudaStream_t st) {
   count_launches(1);
+  ProfScope prof_("k_pack2", st);
   k_pack2<<<gs(n), 256, 0, st>>>(a, b, c, n);
 }
 void grid_unpack_density(const double2* C, int has_b, double2* RT, int accumulate, double2* Pa, double2* Pb,
                          double2* Pz, const GridDims& g, const CellDev& c, double* partial, cudaStream_t st) {
   count_launches(1);
+  ProfScope prof_("k_unpack_density", st);
   k_unpack_density<<<kRedBlocks, kRedThreads, 0, st>>>(C, has_b, RT, accumulate, Pa, Pb, Pz, g, c,
                                                        1.0 / ((double)g.n1 * g.n2 * g.n3), partial);
 }
 void grid_pw_total(const double* rho, const GradPacks& gp, int xc_mode, int kedf, double rho_cut, double* vpart,
                    double* hx, double* hy, double* hz, long long nr, double* partial, cudaStream_t st) {
   count_launches(1);
+  ProfScope prof_("k_pw_total", st);
   k_pw_total<<<kRedBlocks, kRedThreads, 0, st>>>(rho, gp, xc_mode, kedf, rho_cut, vpart, hx, hy, hz, nr, partial);
 }
 void grid_pw_pair(const double* ra, const double* rb, double2* Pa, double2* Pb, double2* Pz, const double* hx,
                   const double* hy, const double* hz, const double* vtot, int xc_mode, int kedf, double rho_cut,
                   double* wa, double* wb, int write_d, long long nr, double* partial, cudaStream_t st) {
   count_launches(1);
+  ProfScope prof_("k_pw_pair", st);
   k_pw_pair<<<kRedBlocks, kRedThreads, 0, st>>>(ra, rb, Pa, Pb, Pz, hx, hy, hz, vtot, xc_mode, kedf, rho_cut, wa, wb,
                                                 write_d, nr, partial);
 }
 void grid_assemble_pair(const double2* RT, const double2* Da, const double2* Db, const double2* Dz, int has_b,
                         double2* F, const GridDims& g, const CellDev& c, double* partial, cudaStream_t st) {
   count_launches(1);
+  ProfScope prof_("k_assemble_pair", st);
   k_assemble_pair<<<kRedBlocks, kRedThreads, 0, st>>>(RT, Da, Db, Dz, has_b, F, g, c,
                                                       1.0 / ((double)g.n1 * g.n2 * g.n3), partial);
 }
 void grid_finish_pair(const double2* F, const double* vloc, double* va, double* vb, long long n, cudaStream_t st) {
   count_launches(1);
+  ProfScope prof_("k_finish_pair", st);
   k_finish_pair<<<gs(n), 256, 0, st>>>(F, vloc, va, vb, n);
 }
 int grid_red_blocks() { return kRedBlocks; }

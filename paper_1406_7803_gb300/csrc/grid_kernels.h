@@ -23,7 +23,7 @@ void grid_axpy(double* a, const double* b, double alpha, long long n, cudaStream
 void grid_nonfinite(const double* a, long long n, unsigned* status, cudaStream_t st);
 
 // ---- packed pairs of real fields (two real grids in one complex transform) ----
-constexpr int kMaxPairs = 8;
+constexpr int kMaxPairs = 32;
 struct GradPacks {  // real-space gradients of the subsystem densities, pairwise packed
   const double2* a[kMaxPairs];  // d/dx + i d/dy of the first density of pair q
   const double2* b[kMaxPairs];  // the same for the second density (when has_b)

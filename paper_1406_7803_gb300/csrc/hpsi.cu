@@ -156,18 +156,18 @@ void launch_hpsi_local(const cplx<T>* psi, int ldpsi, cplx<T>* hpsi, int ldh, in
   allow_smem(k_zfwd<T>, zs);
   allow_smem(k_plane<T>, ps);
   {
-    ProfScope p("k_zinv", st);
+    ProfScope p("k_zinv", st, 1);
     count_launches(1);
     k_zinv<T><<<gz, kColsPerCta * 32, zs, st>>>(psi, ldpsi, scratch, sp, g.n3, fp.p3);
   }
   {
-    ProfScope p("k_plane", st);
+    ProfScope p("k_plane", st, 1);
     count_launches(1);
     k_plane<T><<<dim3(g.n3, nb), kPlaneThreads, ps, st>>>(scratch, sp, vplane, g, fp.p1, fp.p2);
   }
   const T inv_nr = (T)(1.0 / ((double)g.n1 * g.n2 * g.n3));
   {
-    ProfScope p("k_zfwd", st);
+    ProfScope p("k_zfwd", st, 1);
     count_launches(1);
     k_zfwd<T><<<gz, kColsPerCta * 32, zs, st>>>(scratch, psi, ldpsi, hpsi, ldh, kin, sp, g.n3, inv_nr, fp.p3);
   }

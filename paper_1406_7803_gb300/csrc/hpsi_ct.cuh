@@ -433,6 +433,7 @@ static void ct_plane_density(int n, int n3, cudaStream_t st, const cplx<T>* scr,
 
 template <typename T>
 static void ct_axis(int n, long long nlines, long long I, cudaStream_t st, cplx<T>* data, const cplx<T>* tw, int sign) {
+  ProfScope prof_(sizeof(T) == 8 ? "k_fft_axis_f64" : "k_fft_axis_f32", st);
   switch (n) {
 #define FDE_CASE(N)                                                                                    \
   case N:                                                                                              \
@@ -474,15 +475,15 @@ bool launch_hpsi_batch_ct(const HpsiItemDesc<T>* items, int nitems, const GridDi
     if (zb == 0) continue;
     const int variant = plane_variant<T>(g.n1, g.n3, (unsigned)zb, (unsigned)pb, st, B, fp);
     {
-      ProfScope p("k_zinv", st);
+      ProfScope p("k_zinv", st, 1);
       ct_zinv<T>(g.n3, (unsigned)zb, st, B, fp.p3.tw);
     }
     {
-      ProfScope p("k_plane", st);
+      ProfScope p("k_plane", st, 1);
       ct_plane<T>(g.n1, (unsigned)pb, st, B, g.n3, fp.p1.tw, fp.p2.tw, variant);
     }
     {
-      ProfScope p("k_zfwd", st);
+      ProfScope p("k_zfwd", st, 1);
       ct_zfwd<T>(g.n3, (unsigned)zb, st, B, inv_nr, fp.p3.tw);
     }
   }
@@ -506,7 +507,11 @@ bool launch_density_ct(const cplx<T>* psi, int ldpsi, int nb, const double* weig
   HpsiBatch<T> B;
   B.n = 1;
   B.it[0] = HpsiItem<T>{sp, psi, nullptr, nullptr, nullptr, scratch, ldpsi, nb, 0, 0};
-  ct_zinv<T>(g.n3, (unsigned)(ceil_div(sp.ncol, ct_zcols_host<T>(g.n3)) * nb), st, B, fp.p3.tw);
+  {
+    ProfScope prof_("k_zinv_density", st);
+    ct_zinv<T>(g.n3, (unsigned)(ceil_div(sp.ncol, ct_zcols_host<T>(g.n3)) * nb), st, B, fp.p3.tw);
+  }
+  ProfScope prof_("k_plane_density", st);
   ct_plane_density<T>(g.n1, g.n3, st, scratch, sp, nb, weight, rho_plane, accumulate, fp.p1.tw, fp.p2.tw);
   return true;
 }

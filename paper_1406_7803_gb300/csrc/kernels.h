@@ -98,6 +98,9 @@ bool launch_gemm_rot_tc(const float2* X, int ldx, const double2* U, int ldu, int
                         int ldy, double alpha, double beta, int passes, cudaStream_t st);
 // ST_* bits raised by the tensor-core kernels since the last call (read, cleared; syncs).
 unsigned gemm_tc_take_status(cudaStream_t st);
+bool set_tc_stage_spin(long long polls);
+void disable_tensor_cores();
+bool tensor_cores_disabled();
 void launch_gemm_hn_reduce(const double2* part, int nsplit, int m, int n, double2* C, int ldc, cudaStream_t st);
 template <typename T>
 void launch_gemm_hn(const cplx<T>* A, int lda, const cplx<T>* B, int ldb, int m, int n, int K,

@@ -113,9 +113,15 @@ static int initial_gemm_path() {
 static int g_gemm_path = initial_gemm_path();
 void set_gemm_hn_path(int path) { g_gemm_path = (path == 0 || path == 1) ? path : 3; }
 int gemm_hn_path() { return g_gemm_path; }
+// Set once a tensor-core kernel kept its tensor memory (its MMAs could not be confirmed
+// complete): every later product of the process takes the CUDA-core path.
+static bool g_tc_disabled = false;
+void disable_tensor_cores() { g_tc_disabled = true; }
+bool tensor_cores_disabled() { return g_tc_disabled; }
 
 void launch_gemm_hn_reduce(const double2* part, int nsplit, int m, int n, double2* C, int ldc, cudaStream_t st) {
   count_launches(1);
+  ProfScope prof_r("k_gemm_hn_reduce", st);
   k_gemm_hn_reduce<<<ceil_div((long long)m * n, 32), 256, 0, st>>>(part, nsplit, m, n, C, ldc);
 }
 
@@ -127,7 +133,7 @@ static bool gemm_hn_tensor(const cplx<T>*, int, const cplx<T>*, int, int, int, i
 template <>
 bool gemm_hn_tensor<float>(const float2* A, int lda, const float2* B, int ldb, int m, int n, int K, double2* C,
                            int ldc, double2* work, cudaStream_t st) {
-  if (g_gemm_path == 0 || K <= 0) return false;
+  if (g_gemm_path == 0 || g_tc_disabled || K <= 0) return false;
   const int ns = launch_gemm_hn_tc(A, lda, B, ldb, m, n, K, g_gemm_path, work, st);
   if (ns == 0) return false;
   launch_gemm_hn_reduce(work, ns, m, n, C, ldc, st);
@@ -145,8 +151,10 @@ void launch_gemm_hn(const cplx<T>* A, int lda, const cplx<T>* B, int ldb, int m,
   const int ns = ceil_div(K, kchunk > 0 ? kchunk : 1);
   const dim3 grid(ceil_div(m, kGT), ceil_div(n, kGT), ns > 0 ? ns : 1);
   count_launches(1);
+  ProfScope prof_("k_gemm_hn_partial", st);
   k_gemm_hn_partial<T, T><<<grid, 256, 0, st>>>(A, lda, B, ldb, m, n, K, kchunk, work);
   count_launches(1);
+  ProfScope prof_r("k_gemm_hn_reduce", st);
   k_gemm_hn_reduce<<<ceil_div((long long)m * n, 32), 256, 0, st>>>(work, grid.z, m, n, C, ldc);
 }
 
@@ -220,7 +228,7 @@ static bool gemm_rot_tensor(const cplx<T>*, int, const double2*, int, int, int, 
 template <>
 bool gemm_rot_tensor<float>(const float2* X, int ldx, const double2* U, int ldu, int m, int n, int K, float2* Y,
                             int ldy, double alpha, double beta, cudaStream_t st) {
-  if (g_gemm_path == 0 || m <= 0) return false;
+  if (g_gemm_path == 0 || g_tc_disabled || m <= 0) return false;
   return launch_gemm_rot_tc(X, ldx, U, ldu, m, n, K, Y, ldy, alpha, beta, g_gemm_path, st);
 }
 
@@ -231,6 +239,7 @@ void launch_gemm_rot(const cplx<T>* X, int ldx, const double2* U, int ldu, int m
   if (tensor && gemm_rot_tensor<T>(X, ldx, U, ldu, m, n, K, Y, ldy, alpha, beta, st)) return;
   const dim3 grid(ceil_div(K, 64), ceil_div(n, 32));
   count_launches(1);
+  ProfScope prof_("k_gemm_rot", st);
   k_gemm_rot<T><<<grid, 256, 0, st>>>(X, ldx, U, ldu, m, n, K, Y, ldy, (T)alpha, (T)beta);
 }
 
@@ -338,6 +347,7 @@ void launch_kb_couple(const double2* P, const KbBlock& D, int natoms, int nb, do
   const long long n = (long long)natoms * D.np * nb;
   if (n <= 0) return;
   count_launches(1);
+  ProfScope prof_("k_kb_couple", st);
   const int blocks = (int)std::min<long long>((n + 255) / 256, 1024);
   k_kb_couple<<<blocks, 256, 0, st>>>(P, D, natoms, nb, Q);
 }

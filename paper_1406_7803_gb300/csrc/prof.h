@@ -14,6 +14,7 @@ namespace fde {
 
 struct Profiler {
   bool on = false;
+  int level = 1;  // record scopes of this level or below: 1 the H psi passes, 2 every kernel
   long long launches = 0;  // kernel launches made by the context's calls (always counted)
   struct Rec {
     std::vector<cudaEvent_t> a, b;
@@ -60,11 +61,13 @@ inline void count_launches(int n) {
 struct ProfScope {
   const char* n;
   cudaStream_t st;
-  ProfScope(const char* name, cudaStream_t s) : n(name), st(s) {
-    if (tl_prof && tl_prof->on) tl_prof->mark(n, st, true);
+  bool rec;
+  ProfScope(const char* name, cudaStream_t s, int lvl = 2)
+      : n(name), st(s), rec(tl_prof && tl_prof->on && lvl <= tl_prof->level) {
+    if (rec) tl_prof->mark(n, st, true);
   }
   ~ProfScope() {
-    if (tl_prof && tl_prof->on) tl_prof->mark(n, st, false);
+    if (rec) tl_prof->mark(n, st, false);
   }
 };
 

@@ -71,6 +71,8 @@ EXPORTS = {
     "fde_energy": (C.c_int, [C.c_void_p, C.POINTER(Energies)]),
     "fde_scf_subsystem": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_int, C.POINTER(Energies)]),
     "fde_freeze_thaw_cycle": (C.c_int, [C.c_void_p, C.c_double, C.c_int, C.POINTER(Energies)]),
+    "fde_scf_refresh": (C.c_int, [C.c_void_p, C.c_double, C.c_int, C.POINTER(Energies)]),
+    "fde_delta_rho": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]),
     "fde_profile_enable": (C.c_int, [C.c_void_p, C.c_int]),
     "fde_profile_get": (C.c_int, [C.c_void_p, C.c_char_p, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "fde_launch_count": (C.c_int, [C.c_void_p, C.POINTER(C.c_longlong)]),
@@ -82,6 +84,7 @@ EXPORTS = {
     "fde_gemm_hn_f32": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int,
                                   C.c_void_p, C.c_int, C.c_int]),
     "fde_set_gemm_path": (C.c_int, [C.c_int]),
+    "fde_set_tc_wait_limit": (C.c_int, [C.c_longlong]),
     "fde_host_sphere": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
     "fde_host_ewald": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "fde_host_occupations": (C.c_int, [C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_void_p,
@@ -209,6 +212,13 @@ def set_gemm_path(path: int) -> None:
     s = load().fde_set_gemm_path(int(path))
     if s != FDE_OK:
         raise FDEError(s, "fde_set_gemm_path: path must be 0, 1 or 3")
+
+
+def set_tc_wait_limit(polls: int) -> None:
+    """Poll limit of the tensor-core products' stage waits (0: run out at once; -1: default)."""
+    s = load().fde_set_tc_wait_limit(int(polls))
+    if s != FDE_OK:
+        raise FDEError(s, "fde_set_tc_wait_limit")
 
 
 class FDEError(RuntimeError):
@@ -366,6 +376,18 @@ class Context:
         s = self._check(self.lib.fde_freeze_thaw_cycle(self.h, float(tol), int(max_scf), C.byref(e)),
                         "fde_freeze_thaw_cycle")
         return s, e.as_dict()
+
+    def scf_refresh(self, tol, max_scf=200):
+        """SCF of every subsystem with the total density refreshed after every step."""
+        e = Energies()
+        s = self._check(self.lib.fde_scf_refresh(self.h, float(tol), int(max_scf), C.byref(e)), "fde_scf_refresh")
+        return s, e.as_dict()
+
+    def delta_rho(self, rho_ref):
+        """1/2 int |rho - rho_ref| against a device grid rho_ref (torch float64, CUDA)."""
+        out = C.c_double()
+        self._check(self.lib.fde_delta_rho(self.h, _dptr(rho_ref), C.byref(out)), "fde_delta_rho")
+        return out.value
 
     def sync(self):
         return self._check(self.lib.fde_sync(self.h), "fde_sync")

@@ -220,6 +220,30 @@ def batched_uneven(seed: int = 1003, nmol: int = 16) -> Workload:
                     description="slab 54 atoms (96 bands x 2 k) + 16 molecules of 8..64 bands")
 
 
+def supersystem(wl: Workload, extra_bands: int = 0) -> Workload:
+    """The same cell as one subsystem holding every atom and every electron: the input of the
+    supersystem Kohn-Sham reference run (Computational Details: FDE densities are compared
+    with KS-DFT of the whole system on the same grid).  Bands add up (plus extra_bands); the
+    k-points and smearing are those of the first smeared subsystem if there is one (the metal
+    sets the sampling of the whole cell), else Gamma with integer occupations.  Every
+    subsystem must carry the same projector set."""
+    sm = [s for s in wl.subsystems if s.smearing > 0]
+    ref = sm[0] if sm else wl.subsystems[0]
+    sig = {tuple(s.proj_sigma) for s in wl.subsystems}
+    if len(sig) != 1 or len({s.rc for s in wl.subsystems}) != 1:
+        raise ValueError("the supersystem needs one projector set and one r_c")
+    whole = Subsystem(name="supersystem",
+                      pos=np.concatenate([s.pos for s in wl.subsystems], axis=0),
+                      Z=np.concatenate([s.Z for s in wl.subsystems]), rc=ref.rc,
+                      nbands=sum(s.nbands for s in wl.subsystems) + extra_bands,
+                      kpts=ref.kpts.copy(), wk=ref.wk.copy(),
+                      nelec=float(sum(s.nelec for s in wl.subsystems)), smearing=ref.smearing,
+                      proj_sigma=tuple(ref.proj_sigma), proj_D=tuple(ref.proj_D))
+    return Workload(name=wl.name + "-supersystem", lattice=wl.lattice.copy(), grid=wl.grid, ecut=wl.ecut,
+                    subsystems=[whole], xc=wl.xc, kedf=wl.kedf, seed=wl.seed, tol=wl.tol, rho_cut=wl.rho_cut,
+                    description="supersystem KS reference of " + wl.name)
+
+
 def raw_orbitals(seed: int, isub: int, ik: int, nbands: int, npw: int) -> np.ndarray:
     """Raw complex normal draws (N(0,1) + i N(0,1)) for the initial orbitals of one
     (subsystem, k-point).  Shaping and orthonormalisation are done by the solver."""
@@ -237,15 +261,24 @@ def initial_density(wl: Workload, isub: int, alpha: float = 2.0) -> np.ndarray:
     s = wl.subsystems[isub]
     A = np.asarray(wl.lattice, dtype=np.float64)
     n1, n2, n3 = wl.grid
-    f = np.meshgrid(np.arange(n1) / n1, np.arange(n2) / n2, np.arange(n3) / n3, indexing="ij")
-    r = f[0][..., None] * A[0] + f[1][..., None] * A[1] + f[2][..., None] * A[2]
     rho = np.zeros(wl.grid)
-    for p, z in zip(s.pos, s.Z):
-        for i in (-1, 0, 1):
-            for j in (-1, 0, 1):
-                for k in (-1, 0, 1):
-                    d = r - (p + i * A[0] + j * A[1] + k * A[2])
-                    rho += z * (alpha / np.pi) ** 1.5 * np.exp(-alpha * np.sum(d * d, axis=-1))
+    if np.count_nonzero(A - np.diag(np.diag(A))) == 0:
+        # orthorhombic cell: the Gaussian factorises over the axes, and so does the sum over
+        # the 27 images (i, j, k), one axis at a time
+        L = np.diag(A)
+        x = [np.arange(n) / n * L[c] for c, n in enumerate(wl.grid)]
+        for p, z in zip(s.pos, s.Z):
+            g = [sum(np.exp(-alpha * (x[c] - (p[c] + i * L[c])) ** 2) for i in (-1, 0, 1)) for c in range(3)]
+            rho += z * (alpha / np.pi) ** 1.5 * (g[0][:, None, None] * g[1][None, :, None] * g[2][None, None, :])
+    else:
+        f = np.meshgrid(np.arange(n1) / n1, np.arange(n2) / n2, np.arange(n3) / n3, indexing="ij")
+        r = f[0][..., None] * A[0] + f[1][..., None] * A[1] + f[2][..., None] * A[2]
+        for p, z in zip(s.pos, s.Z):
+            for i in (-1, 0, 1):
+                for j in (-1, 0, 1):
+                    for k in (-1, 0, 1):
+                        d = r - (p + i * A[0] + j * A[1] + k * A[2])
+                        rho += z * (alpha / np.pi) ** 1.5 * np.exp(-alpha * np.sum(d * d, axis=-1))
     omega = abs(np.linalg.det(A))
     total = rho.sum() * omega / rho.size
     return rho * (s.nelec / total)

@@ -113,3 +113,38 @@ def test_combinations_match_fp64(ctx, m, n, K, ldx, ldy, alpha, beta):
     assert err[1] < 4e-3, err
     if m >= 16:
         assert err[3] < err[1] / 20, err
+
+
+def test_stage_wait_timeout_returns_etimeout_and_recovers(ctx):
+    """Every device wait of the tensor-core products is bounded.  With the stage-wait poll
+    limit at 0, a product with several k-tiles per CTA runs out at its first stage wait: the
+    kernel stops issuing, drains the MMAs it issued (full bound), frees its tensor memory,
+    writes nothing, and the call returns FDE_ETIMEOUT.  Calls with the default limit then
+    give correct results again (the context, the stream and tensor memory are intact)."""
+    rng = np.random.default_rng(77)
+    m, n, K = 64, 64, 4096
+    a = _draw(rng, m, K, K)
+    b = _draw(rng, n, K, K)
+    dA, dB = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+    out = torch.zeros((m, n), dtype=torch.complex128, device="cuda")
+    U = torch.from_numpy(rng.standard_normal((m, n)) + 1j * rng.standard_normal((m, n))).cuda()
+    Y = torch.zeros((n, K), dtype=torch.complex64, device="cuda")
+    fde.set_tc_wait_limit(0)
+    try:
+        with pytest.raises(fde.FDEError) as e:
+            ctx.gemm_hn_f32(dA, dB, K, out, 3)
+        assert e.value.status == fde.FDE_ETIMEOUT
+        with pytest.raises(fde.FDEError) as e:
+            ctx.gemm_rot_f32(dA, U, K, Y, 1.0, 0.0, 3)
+        assert e.value.status == fde.FDE_ETIMEOUT
+    finally:
+        fde.set_tc_wait_limit(-1)
+    ref = a.astype(np.complex128).conj() @ b.astype(np.complex128).T
+    scale = np.linalg.norm(a, axis=1).max() * np.linalg.norm(b, axis=1).max()
+    ctx.gemm_hn_f32(dA, dB, K, out, 3)
+    assert np.abs(out.cpu().numpy() - ref).max() / scale < 1e-5
+    ctx.gemm_rot_f32(dA, U, K, Y, 1.0, 0.0, 3)
+    u = U.cpu().numpy()
+    want = u.T @ a.astype(np.complex128)
+    rscale = np.linalg.norm(u, axis=0).max() * np.linalg.norm(a, axis=0).max()
+    assert np.abs(Y.cpu().numpy() - want).max() / rscale < 1e-5
