@@ -60,6 +60,7 @@ typedef enum {
 enum { FDE_XC_LDA = 0, FDE_XC_PBE = 1 };                         /* exchange-correlation */
 enum { FDE_KEDF_TF = 0, FDE_KEDF_REVAPBEK = 1, FDE_KEDF_LC94 = 2 };  /* kinetic functional */
 enum { FDE_PRECOND_TPA = 0, FDE_PRECOND_LEARNED = 1 };          /* eigensolver preconditioner */
+enum { FDE_SMEAR_FERMI = 0, FDE_SMEAR_MP = 1, FDE_SMEAR_GAUSS = 2 }; /* occupation smearing */
 enum { FDE_PRECOND_PARAMS = 8641 };  /* learned-preconditioner parameter count (floats) */
 
 /* Cell, shared real-space grid and wavefunction cutoff (Sec. 2: one shared grid holds rho
@@ -87,8 +88,11 @@ typedef struct {
  * Kleinman-Bylander projectors of widths proj_sigma [nproj_per_atom] (bohr) coupled by
  * proj_D [nproj_per_atom][nproj_per_atom] (Ha, symmetric; nproj_per_atom <= 8, else
  * FDE_EUNSUPPORTED).  kpts [nk][3] in crystal
- * coordinates with weights wk [nk] summing to 1.  smearing_ha > 0: Fermi-Dirac occupations;
- * 0: integer occupations (then nk must be 1 and nelec/2 an integer <= nbands).
+ * coordinates with weights wk [nk] summing to 1 (a full Monkhorst-Pack mesh or its
+ * irreducible part from fde_host_kmesh).  smearing_ha > 0: smeared occupations of kind
+ * smearing_kind (Computational Details: Methfessel-Paxton for the metallic subsystems;
+ * FDE_SMEAR_MP is the first-order form, FDE_SMEAR_GAUSS the zeroth, FDE_SMEAR_FERMI
+ * Fermi-Dirac); 0: integer occupations (then nk must be 1 and nelec/2 an integer <= nbands).
  * All arrays are host memory and are copied. */
 typedef struct {
   int natoms;
@@ -104,6 +108,7 @@ typedef struct {
   const double* wk;
   double nelec;
   double smearing_ha;
+  int smearing_kind;
 } fde_subsys_desc;
 
 /* Energy terms of Eq. E_FDE (Sec. 2) for the current densities and orbitals:
@@ -169,7 +174,9 @@ fde_status fde_set_veff(fde_ctx* ctx, int sub, const double* d_veff);
 fde_status fde_apply_h(fde_ctx* ctx, int sub, int k, const void* d_psi, void* d_hpsi, int nb);
 
 /* Same as fde_apply_h with host buffers (complex double [nb][npw] in both precisions);
- * copies in and out through pinned staging inside the call; synchronising. */
+ * synchronising.  Page-locked buffers (cudaHostAlloc, cudaMallocHost or cudaHostRegister) are
+ * copied directly by the copy engines; pageable ones go through a page-locked staging buffer
+ * of the context (an extra host copy each way). */
 fde_status fde_apply_h_host(fde_ctx* ctx, int sub, int k, const double* h_psi, double* h_hpsi,
                             int nb);
 
@@ -338,6 +345,13 @@ fde_status fde_apply_h_local_static(const fde_cell_desc* cell, const double* kfr
  * transforms can be checked on their own. */
 fde_status fde_fft3d(fde_ctx* ctx, void* d_data, int sign);
 
+/* The potential build's 3D transform of an FP64 grid (complex double [n1][n2][n3], in place,
+ * scaled as fde_fft3d) in either arithmetic the library uses for it: arith 0 native FP64 (FP64
+ * contexts), 1 double-float (two floats per value, about 48 significant bits, on the FP32
+ * pipes; mixed contexts transform the densities and their gradients this way).  Exposed so
+ * the transforms can be checked on their own. */
+fde_status fde_fft3d_f64(fde_ctx* ctx, double* d_data, int sign, int arith);
+
 /* The FP64 Hermitian eigensolver of the Rayleigh-Ritz step applied to a caller matrix:
  * d_A device complex double [n][n] (Hermitian, row-major, not modified), d_w device [n]
  * receives every eigenvalue in ascending order, d_V device complex double [n][n] receives
@@ -391,7 +405,8 @@ fde_status fde_set_tc_wait_limit(long long polls);
  * variant chosen for plane side n1 and z length n3, or -1 if none was tuned yet; the
  * environment variable FDE_PLANE_VARIANT pins one. */
 int fde_tuned_plane_variant(int n1, int n3);
-/* Pin the plane-pass variant used from now on in this process (0 .. 3), or return to tuning
+/* Pin the plane-pass variant used from now on in this process (0 .. 5; 4 and 5 are the warp-local
+ * variants whose line transforms synchronise only their warp), or return to tuning
  * (-1).  FDE_EINVAL for other values. */
 fde_status fde_pin_plane_variant(int variant);
 
@@ -413,14 +428,42 @@ fde_status fde_host_sphere(const double* lengths, const double* kfrac, double ec
 /* Nuclear repulsion V_NN of Eq. E_FDE: Ewald sum of the point charges Z [natoms] at pos
  * [natoms][3] (bohr) with a uniform neutralising background, into *energy (Ha). */
 fde_status fde_host_ewald(const double* lengths, int natoms, const double* pos, const double* Z, double* energy);
-/* Occupations (Sec. 2: 2 sum_k w_k sum_j n_jk = N_I, 0 <= n <= 1) of eig [nk][nb] (Ha) with
- * k weights wk [nk]: sigma > 0 Fermi-Dirac with the chemical potential *mu by bisection to
- * 1e-13 electrons and *ts = sigma S, S = -2 sum_k w_k sum_j [n ln n + (1-n) ln(1-n)] (the
- * Mermin term); sigma <= 0 integer occupation of the nelec/2 lowest bands (nk must be 1),
- * *mu the highest occupied eigenvalue, *ts = 0.  occ [nk][nb] out.  FDE_EINVAL for
- * inconsistent arguments. */
+/* Occupations (Sec. 2: 2 sum_k w_k sum_j n_jk = N_I) of eig [nk][nb] (Ha) with k weights
+ * wk [nk]: sigma > 0 smeared, n = f((e - mu) / sigma) with the chemical potential *mu by
+ * bisection to 1e-13 electrons and *ts = sigma S, S = 2 sum_k w_k sum_j s((e - mu) / sigma),
+ * for smearing_kind
+ *   FDE_SMEAR_FERMI  f = 1 / (1 + e^x), s = -[f ln f + (1 - f) ln(1 - f)] (Mermin);
+ *   FDE_SMEAR_GAUSS  f = erfc(x) / 2, s = e^{-x^2} / (2 sqrt(pi));
+ *   FDE_SMEAR_MP     first-order Methfessel-Paxton (Computational Details):
+ *                    f = erfc(x) / 2 - x e^{-x^2} / (2 sqrt(pi)), s = (1 - 2x^2) e^{-x^2} / (4 sqrt(pi))
+ *                    (occupations may leave [0, 1]);
+ * sigma <= 0 integer occupation of the nelec/2 lowest bands (nk must be 1), *mu the highest
+ * occupied eigenvalue, *ts = 0.  occ [nk][nb] out.  FDE_EINVAL for inconsistent arguments. */
 fde_status fde_host_occupations(int nk, int nb, const double* eig, const double* wk, double nelec, double sigma,
-                                double* occ, double* mu, double* ts);
+                                int smearing_kind, double* occ, double* mu, double* ts);
+/* Brillouin-zone sampling (Computational Details: Monkhorst-Pack meshes for the periodic
+ * systems, Gamma for molecules).  The q[0] x q[1] x q[2] mesh k_j = (2 r_j - q_j - 1 + shift_j) /
+ * (2 q_j), r_j = 1..q_j (crystal coordinates; shift nullable = unshifted) is reduced to one
+ * point per orbit under the operations k -> R k for the sign-flip masks ops[nops] (3-bit: bit c
+ * flips coordinate c; the identity is implied) and, if time_reversal, k -> -R k (Kramers:
+ * e(k) = e(-k), |u_-k|^2 = |u_k|^2, exact without any spatial symmetry).  kpts [nk][3] and wk [nk]
+ * (orbit size / mesh size) are filled when given; as for fde_host_sphere, *nk holds their
+ * capacity on entry then (NULL for both: only the count).  Points equal modulo a reciprocal
+ * lattice vector are one point.  FDE_EINVAL for bad arguments or a short capacity. */
+fde_status fde_host_kmesh(const int* q, const double* shift, int time_reversal, int nops, const int* ops, int* nk,
+                          double* kpts, double* wk);
+/* The sign-flip operations r -> R r about the origin (masks as above, identity first) that map
+ * the atoms pos [natoms][3] onto atoms of the same charge Z within tol bohr, modulo the
+ * orthorhombic cell lengths [3]: *nops of them into ops [8]. */
+fde_status fde_host_symmetry_ops(const double* lengths, int natoms, const double* pos, const double* Z, double tol,
+                                 int* nops, int* ops);
+/* Symmetrise every density the context builds from orbitals over the group of sign-flip
+ * operations ops[nops] (must contain the identity 0, be closed under composition and map each
+ * subsystem's atoms onto that subsystem's atoms; else FDE_EINVAL):
+ * rho(r) <- (1 / nops) sum_R rho(R r).  With it, subsystems may be given the reduced k-sets of
+ * fde_host_kmesh for the same operations.  nops = 1, ops = {0} switches it off. */
+fde_status fde_set_symmetry(fde_ctx* ctx, int nops, const int* ops);
+
 /* Pulay (DIIS) coefficients of the subsystem SCF's density mixing (the paper is silent on
  * mixing): c [m] minimising |sum_i c_i R_i|^2 with sum_i c_i = 1, from the residual
  * overlaps overlap [m][m] = <R_i|R_j>.  FDE_ENOCONV (and c = e_m, the newest residual) when

@@ -30,14 +30,28 @@ def vloc_G(lattice, grid, pos, Z, rc):
     finite remainder (1/Omega) sum_alpha pi Z_alpha r_c^2 is kept.  Nyquist planes zero."""
     omega = basis.volume(lattice)
     (gx, gy, gz), g2 = basis.grid_gvectors(lattice, grid)
-    out = np.zeros(tuple(grid), dtype=np.complex128)
+    pos = np.asarray(pos, dtype=np.float64).reshape(-1, 3)
+    Z = np.asarray(Z, dtype=np.float64)
     nz = g2 > 0
     form = np.zeros_like(g2)
-    for p, z in zip(np.asarray(pos, dtype=np.float64), np.asarray(Z, dtype=np.float64)):
-        form[nz] = -4.0 * np.pi * z / g2[nz] * np.exp(-g2[nz] * rc * rc / 4.0)
-        phase = np.exp(-1j * (gx * p[0] + gy * p[1] + gz * p[2]))
-        out += form * phase / omega
-        out[0, 0, 0] += np.pi * z * rc * rc / omega
+    form[nz] = -4.0 * np.pi / g2[nz] * np.exp(-g2[nz] * rc * rc / 4.0)
+    # structure factor S(G) = sum_alpha Z_alpha exp(-i G.R_alpha); in an orthorhombic cell
+    # G.R = G_x x + G_y y + G_z z with G_x depending on the first index only (and so on), so the
+    # exponential is a product of three 1D factors and the sum over atoms is one matrix product
+    A = np.asarray(lattice, dtype=np.float64)
+    if np.count_nonzero(A - np.diag(np.diag(A))) == 0:
+        n1, n2, n3 = grid
+        ex = np.exp(-1j * np.outer(pos[:, 0], gx[:, 0, 0]))  # [natoms][n1]
+        ey = np.exp(-1j * np.outer(pos[:, 1], gy[0, :, 0]))
+        ez = np.exp(-1j * np.outer(pos[:, 2], gz[0, 0, :]))
+        m = (Z[:, None, None] * ex[:, :, None] * ey[:, None, :]).reshape(len(Z), n1 * n2)
+        S = (m.T @ ez).reshape(n1, n2, n3)
+    else:
+        S = np.zeros(tuple(grid), dtype=np.complex128)
+        for p, z in zip(pos, Z):
+            S += z * np.exp(-1j * (gx * p[0] + gy * p[1] + gz * p[2]))
+    out = form * S / omega
+    out[0, 0, 0] = np.pi * float(Z.sum()) * rc * rc / omega
     out[basis.nyquist_mask(grid)] = 0.0
     return out
 

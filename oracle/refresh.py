@@ -55,7 +55,7 @@ def scf_default_refresh(system, state, tol=None, max_scf=200, dense_max=0, log=N
                 w, v = scf.eigensolve(system, I, k, pot["veff"][I], s.nbands, coefs[I][k], dense_max)
                 eigs.append(w)
                 vecs.append(v)
-            occ, _, S = scf.occupations(eigs, s.wk, s.nelec, s.smearing)
+            occ, _, S = scf.occupations(eigs, s.wk, s.nelec, s.smearing, s.smearing_kind)
             rho_out[I] = system.density(I, vecs, occ)
             ent[I] = s.smearing * S
             new_coefs.append(vecs)

@@ -2,10 +2,11 @@
 
 Test infrastructure only (see ``oracle/__init__.py``).
 
-* Occupations 0 <= n_jk <= 1 with 2 sum_k w_k sum_j n_jk = N_I (Sec. 2; reading: the
+* Occupations with 2 sum_k w_k sum_j n_jk = N_I (Sec. 2; reading: the
   printed constraint sum_j n_jk = N_I double counts the factor 2 of the density).
-  Smeared (metallic) subsystems use Fermi-Dirac occupations with the chemical
-  potential found by bisection; molecular subsystems use integer occupations
+  Smeared (metallic) subsystems use Fermi-Dirac occupations (or the Methfessel-Paxton ones
+  of oracle.smearing) with the chemical potential found by bisection; molecular
+  subsystems use integer occupations
   (Computational Details: smearing only for the metallic subsystems).  The Mermin
   entropy term sigma S, S = -2 sum_k w_k sum_j [n ln n + (1-n) ln(1-n)], is reported.
 * Eigenpairs of H_I (Eq. KS): the lowest n_b eigenpairs by ARPACK's Lanczos
@@ -32,8 +33,12 @@ from paper_1406_7803_gb300 import workloads
 
 
 # ---------------------------------------------------------------- occupations
-def occupations(eigs, wk, nelec, smearing):
-    """Occupations per k, chemical potential and entropy S (dimensionless)."""
+def occupations(eigs, wk, nelec, smearing, kind="fermi"):
+    """Occupations per k, chemical potential and entropy S (dimensionless).  kind "mp"
+    (first-order Methfessel-Paxton) and "gauss" (its zeroth order) are in oracle.smearing."""
+    if smearing > 0.0 and kind in ("mp", "gauss"):
+        from . import smearing as mp
+        return mp.occupations(eigs, wk, nelec, smearing, order=1 if kind == "mp" else 0)
     eigs = [np.asarray(e, dtype=np.float64) for e in eigs]
     wk = np.asarray(wk, dtype=np.float64)
     if smearing <= 0.0:
@@ -206,7 +211,7 @@ def solve_subsystem(system, I, rhos_frozen, rho_in, guess, tol, max_scf=100, den
             eigs.append(w)
             new.append(v)
         coefs = new
-        occ, mu, S = occupations(eigs, s.wk, s.nelec, s.smearing)
+        occ, mu, S = occupations(eigs, s.wk, s.nelec, s.smearing, s.smearing_kind)
         rho_out = system.density(I, coefs, occ)
         rhos_out = rhos.copy()
         rhos_out[I] = rho_out

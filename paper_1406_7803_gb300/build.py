@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libfde.so")
 BUILD = os.path.join(HERE, "_build")
 SOURCES = ["hpsi.cu", "hpsi_ct32.cu", "hpsi_ct64.cu", "grid.cu", "linalg.cu", "small.cu", "fde_host.cu",
-           "hpsi_static.cu", "precond.cu", "heev.cu", "dense.cu", "gemm_tc.cu", "hostmath.cu"]
+           "hpsi_static.cu", "precond.cu", "heev.cu", "dense.cu", "gemm_tc.cu", "hostmath.cu", "fft_dd.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]

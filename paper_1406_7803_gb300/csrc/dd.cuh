@@ -1,0 +1,69 @@
+// dd.cuh -- double-float arithmetic: a real number held as the unevaluated sum hi + lo of two
+// floats (|lo| <= ulp(hi) / 2), about 48 significant bits, computed on the FP32 pipes.
+//
+// On this part the FP64 pipe runs at 1/64 of the FP32 rate, so the transforms of the mixed
+// path's potential build (the density and its gradients, where the GGA functionals need far more
+// than FP32's 24 bits at low density) use this representation instead of FP64.  The operations
+// are the classical error-free transformations: Knuth's TwoSum for a sum with its rounding
+// error, Dekker's FastTwoSum for renormalisation (|a| >= |b|), and the product with its exact
+// rounding error from one fused multiply-add.  Addition follows the accurate (IEEE-style)
+// double-float sum: both hi and lo parts summed with their errors, then renormalised twice.
+// Intrinsics with explicit rounding keep the compiler from contracting or reordering them.
+#pragma once
+
+#include "common.cuh"
+
+namespace fde {
+
+struct dd {
+  float hi, lo;
+  __host__ __device__ __forceinline__ dd() {}
+  __host__ __device__ __forceinline__ constexpr dd(float h, float l) : hi(h), lo(l) {}
+  // Exact small integers and literal constants (the split folds at compile time).
+  __host__ __device__ __forceinline__ constexpr dd(int v) : hi((float)v), lo(0.0f) {}
+  __host__ __device__ __forceinline__ constexpr dd(double v) : hi((float)v), lo((float)(v - (double)(float)v)) {}
+  __host__ dd(long double v) : hi((float)v), lo((float)(v - (long double)(float)v)) {}
+};
+
+__device__ __forceinline__ dd dd_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float v = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, v)), __fsub_rn(b, v));
+  return dd(s, e);
+}
+__device__ __forceinline__ dd dd_fast_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return dd(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ dd operator+(dd a, dd b) {
+  dd s = dd_two_sum(a.hi, b.hi);
+  const dd t = dd_two_sum(a.lo, b.lo);
+  s = dd_fast_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
+  return dd_fast_two_sum(s.hi, __fadd_rn(s.lo, t.lo));
+}
+__device__ __forceinline__ dd operator-(dd a) { return dd(-a.hi, -a.lo); }
+__device__ __forceinline__ dd operator-(dd a, dd b) { return a + (-b); }
+__device__ __forceinline__ dd operator*(dd a, dd b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return dd_fast_two_sum(p, e);
+}
+__device__ __forceinline__ dd& operator+=(dd& a, dd b) { return a = a + b; }
+__device__ __forceinline__ dd& operator-=(dd& a, dd b) { return a = a - b; }
+__device__ __forceinline__ dd& operator*=(dd& a, dd b) { return a = a * b; }
+
+// Conversions at the boundary of a transform (FP64 grids in global memory).
+__device__ __forceinline__ dd dd_from_double(double v) {
+  const float h = __double2float_rn(v);
+  return dd(h, __double2float_rn(v - (double)h));
+}
+__device__ __forceinline__ double dd_to_double(dd v) { return (double)v.hi + (double)v.lo; }
+
+struct __align__(16) ddc {
+  dd x, y;
+};
+template <> struct cx<dd> { using t = ddc; };
+
+}  // namespace fde

@@ -146,6 +146,7 @@ template <typename T> struct KP {
 template <typename T> struct Sub {
   int natoms = 0, nproj_atom = 0, nproj = 0, nb = 0, nk = 0;
   double rc = 0, nelec = 0, smearing = 0;
+  int smear_kind = FDE_SMEAR_FERMI;
   std::vector<double> pos, Z, sigma, D, kpts, wk;
   std::vector<KP<T>> kp;
   KbBlock Dblk{};  // per-atom projector coupling
@@ -179,9 +180,11 @@ struct Engine {
   virtual fde_status scf_subsystem(int sub, double tol, int max_scf, fde_energies* out) = 0;
   virtual fde_status freeze_thaw(double tol, int max_scf, fde_energies* out, const double* start) = 0;
   virtual fde_status scf_refresh(double tol, int max_scf, fde_energies* out) = 0;
+  virtual void set_symmetry(int nops, const int* ops) = 0;
   virtual double delta_rho(const double* d_ref) = 0;
   virtual void sync() = 0;
   virtual void fft3d(void* data, int sign) = 0;
+  virtual void fft3d_f64(double2* data, int sign, int arith) = 0;
   virtual void precond_set_weights(const float* h) = 0;
   virtual void precond_get_weights(float* h, float* hb) = 0;
   virtual void precond_harvest(int sub, int k, const double* raw, int n) = 0;
@@ -216,6 +219,7 @@ template <typename T> struct EngineT : Engine {
   fde_func_desc func;
   Plans<T> plans;
   Plans<double> plans64;
+  Plans<dd> plansdd;  // mixed contexts: double-float transforms of the density and its gradients
   std::vector<std::unique_ptr<Sub<T>>> subs;
   bool locked = false;  // no more subsystems once the local potential exists
   DBuf<double> vloc;
@@ -280,6 +284,7 @@ template <typename T> struct EngineT : Engine {
     REQ(g.n1 <= kMaxPlane && g.n2 <= kMaxPlane, FDE_EUNSUPPORTED, "n1 and n2 must be at most 160");
     make_plans(plans, grid, st);
     make_plans(plans64, grid, st);
+    if constexpr (sizeof(T) == 4) make_plans(plansdd, grid, st);
     for (auto& b : cb) b.alloc(nr);
     rho_tot.alloc(nr);
     vpart.alloc(nr);
@@ -325,6 +330,23 @@ template <typename T> struct EngineT : Engine {
     C* d = (C*)data;
     launch_fft3d<T>(d, g, plans.fp, sign, st);
     if (sign < 0) grid_scale_c<T>(d, 1.0 / (double)nr, nr, st);
+  }
+  // The potential build's transform of an FP64 grid: arith 0 FP64, 1 double-float.
+  void fft3d_f64(double2* data, int sign, int arith) override {
+    REQ(data && (sign == 1 || sign == -1) && (arith == 0 || arith == 1), FDE_EINVAL, "bad transform arguments");
+    if (arith == 1) {
+      if constexpr (sizeof(T) == 4) {
+        REQ(launch_fft3d_dd(data, g, plansdd.fp, sign, st), FDE_EUNSUPPORTED, "no double-float kernel for a length");
+      } else {
+        Plans<dd> p;
+        make_plans(p, grid, st);
+        REQ(launch_fft3d_dd(data, g, p.fp, sign, st), FDE_EUNSUPPORTED, "no double-float kernel for a length");
+        CK(cudaStreamSynchronize(st));  // p's tables are released on return
+      }
+    } else {
+      launch_fft3d<double>(data, g, plans64.fp, sign, st);
+    }
+    if (sign < 0) grid_scale_c<double>(data, 1.0 / (double)nr, nr, st);
   }
   void sync() override {
     CK(cudaStreamSynchronize(st));
@@ -434,6 +456,9 @@ template <typename T> struct EngineT : Engine {
     s->rc = d->rc;
     s->nelec = d->nelec;
     s->smearing = d->smearing_ha;
+    REQ(d->smearing_kind == FDE_SMEAR_FERMI || d->smearing_kind == FDE_SMEAR_MP || d->smearing_kind == FDE_SMEAR_GAUSS,
+        FDE_EINVAL, "unknown smearing kind");
+    s->smear_kind = d->smearing_kind;
     s->pos.assign(d->pos, d->pos + 3 * d->natoms);
     s->Z.assign(d->Z, d->Z + d->natoms);
     if (s->nproj_atom) {
@@ -509,6 +534,8 @@ template <typename T> struct EngineT : Engine {
     REQ(rho, FDE_EINVAL, "null density");
     Sub<T>& s = sub(i);
     CK(cudaMemcpyAsync(s.rho.p, rho, nr * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    // a pageable source is read when the copy is issued, a page-locked one later by the copy
+    // engine: the caller may reuse its buffer once the call returns in both cases
     if (!on_device) CK(cudaStreamSynchronize(st));
   }
   void sum_densities() {
@@ -530,6 +557,40 @@ template <typename T> struct EngineT : Engine {
   // ---- embedding-potential build --------------------------------------------------------------
   bool gga_xc() const { return func.xc == FDE_XC_PBE; }
   bool gga_kin() const { return func.kedf != FDE_KEDF_TF; }
+
+  // Transforms of the densities and their gradients (FP64 grids): FP64 arithmetic in FP64
+  // contexts; double-float arithmetic on the FP32 pipes (~48 bits) in mixed ones.
+  void fft_density(double2* x, int sign) {
+    if constexpr (sizeof(T) == 4) {
+      if (launch_fft3d_dd(x, g, plansdd.fp, sign, st)) return;
+    }
+    launch_fft3d<double>(x, g, plans64.fp, sign, st);
+  }
+
+  // Divergence-argument grid c of pair q in the working precision: the packed gradient grid
+  // itself (overwritten in place) in FP64 contexts, a separate FP32 grid in mixed ones.
+  std::vector<DBuf<cplx<T>>> dpacks;
+  DBuf<cplx<T>> fpot;
+  cplx<T>* dgrid(int q, int c, double2* packed) {
+    if constexpr (sizeof(T) == 8) {
+      return reinterpret_cast<cplx<T>*>(packed);
+    } else {
+      const size_t need = (size_t)3 * (q + 1);
+      if (dpacks.size() < need) dpacks.resize(need);
+      DBuf<cplx<T>>& b = dpacks[(size_t)3 * q + c];
+      if (!b.p) b.alloc(nr);
+      return b.p;
+    }
+  }
+  // Reciprocal-space potentials of a pair (the packed transform grid in FP64 contexts).
+  cplx<T>* fgrid() {
+    if constexpr (sizeof(T) == 8) {
+      return reinterpret_cast<cplx<T>*>(cb[0].p);
+    } else {
+      if (!fpot.p) fpot.alloc(nr);
+      return fpot.p;
+    }
+  }
 
   // Packed gradient grids of subsystem pair q (three complex grids).
   double2* pack(int q, int c) {
@@ -572,7 +633,7 @@ template <typename T> struct EngineT : Engine {
       const int ia = 2 * q, ib = 2 * q + 1;
       const bool hb = ib < nsb;
       grid_pack2(subs[ia]->rho.p, hb ? subs[ib]->rho.p : nullptr, C, nr, st);
-      launch_fft3d<double>(C, g, plans64.fp, -1, st);
+      fft_density(C, -1);
       double2* Pa = grad ? pack(q, 0) : nullptr;
       double2* Pb = (grad && hb) ? pack(q, 1) : nullptr;
       double2* Pz = grad ? pack(q, 2) : nullptr;
@@ -582,9 +643,9 @@ template <typename T> struct EngineT : Engine {
         if (hb) grid_finalize(partial.p + nrb, 1, 0.5 * omega, scal.p + 4 + 3 * ib, st);
       }
       if (grad) {
-        launch_fft3d<double>(Pa, g, plans64.fp, +1, st);
-        if (hb) launch_fft3d<double>(Pb, g, plans64.fp, +1, st);
-        launch_fft3d<double>(Pz, g, plans64.fp, +1, st);
+        fft_density(Pa, +1);
+        if (hb) fft_density(Pb, +1);
+        fft_density(Pz, +1);
         gp.a[q] = Pa;
         gp.b[q] = Pb;
         gp.z[q] = Pz;
@@ -600,7 +661,7 @@ template <typename T> struct EngineT : Engine {
       grid_finalize(partial.p, 1, dv, scal.p + 3, st);
     }
     if (want_e) {
-      grid_assemble_pair(RT, nullptr, nullptr, nullptr, 0, nullptr, g, cell, partial.p, st);
+      grid_assemble_pair<double>(RT, nullptr, nullptr, nullptr, 0, nullptr, g, cell, partial.p, st);
       grid_finalize(partial.p, 1, 0.5 * omega, scal.p + 0, st);
     }
     // 3. per pair: subsystem functionals, divergences, reciprocal-space part, potentials
@@ -616,22 +677,28 @@ template <typename T> struct EngineT : Engine {
       double2* Pb = (grad && hb) ? pack(q, 1) : nullptr;
       double2* Pz = grad ? pack(q, 2) : nullptr;
       const bool pot = pa || pb;
-      grid_pw_pair(A.rho.p, B ? B->rho.p : nullptr, Pa, Pb, Pz, htot[0].p, htot[1].p, htot[2].p,
-                   want_pot ? vpart.p : nullptr, want_e ? func.xc : -1, func.kedf, func.rho_cut, pa ? A.veff.p : nullptr,
-                   pb ? B->veff.p : nullptr, (pot && grad) ? 1 : 0, nr, partial.p, st);
+      // divergence arguments, reciprocal-space potentials and their transforms in the working
+      // precision (FP32 in mixed contexts: they enter V_eff linearly, unlike the gradients)
+      cplx<T>* Da = grad ? dgrid(q, 0, Pa) : nullptr;
+      cplx<T>* Db = (grad && hb) ? dgrid(q, 1, Pb) : nullptr;
+      cplx<T>* Dz = grad ? dgrid(q, 2, Pz) : nullptr;
+      cplx<T>* F = fgrid();
+      grid_pw_pair<T>(A.rho.p, B ? B->rho.p : nullptr, Pa, Pb, Pz, Da, Db, Dz, htot[0].p, htot[1].p, htot[2].p,
+                      want_pot ? vpart.p : nullptr, want_e ? func.xc : -1, func.kedf, func.rho_cut,
+                      pa ? A.veff.p : nullptr, pb ? B->veff.p : nullptr, (pot && grad) ? 1 : 0, nr, partial.p, st);
       if (want_e) {
         grid_finalize(partial.p, 2, dv, scal.p + 5 + 3 * ia, st);
         if (hb) grid_finalize(partial.p + 2 * nrb, 2, dv, scal.p + 5 + 3 * ib, st);
       }
       if (!pot) continue;
       if (grad) {
-        launch_fft3d<double>(Pa, g, plans64.fp, -1, st);
-        if (hb) launch_fft3d<double>(Pb, g, plans64.fp, -1, st);
-        launch_fft3d<double>(Pz, g, plans64.fp, -1, st);
+        launch_fft3d<T>(Da, g, plans.fp, -1, st);
+        if (hb) launch_fft3d<T>(Db, g, plans.fp, -1, st);
+        launch_fft3d<T>(Dz, g, plans.fp, -1, st);
       }
-      grid_assemble_pair(RT, Pa, Pb, Pz, hb ? 1 : 0, C, g, cell, nullptr, st);
-      launch_fft3d<double>(C, g, plans64.fp, +1, st);
-      grid_finish_pair(C, vloc.p, pa ? A.veff.p : nullptr, pb ? B->veff.p : nullptr, nr, st);
+      grid_assemble_pair<T>(RT, Da, Db, Dz, hb ? 1 : 0, F, g, cell, nullptr, st);
+      launch_fft3d<T>(F, g, plans.fp, +1, st);
+      grid_finish_pair<T>(F, vloc.p, pa ? A.veff.p : nullptr, pb ? B->veff.p : nullptr, nr, st);
       if (pa) {
         grid_nonfinite(A.veff.p, nr, status.p, st);
         to_plane(A);
@@ -659,7 +726,15 @@ template <typename T> struct EngineT : Engine {
     return ep;
   }
   void neg_add(double* a, const double* b) { grid_axpy(a, b, -1.0, nr, st); }
+  // Plane-major copy of V_eff^I in the working precision for the plane pass of H psi:
+  // [i3][i1][i2], or [i3][i2][i1] for the mixed path's compile-time kernels.
   void to_plane(Sub<T>& s) {
+    if constexpr (sizeof(T) == 4) {
+      if (hpsi_plane_transposed_f32(g)) {
+        launch_to_plane_t(s.veff.p, s.vplane.p, g, st);
+        return;
+      }
+    }
     launch_transpose<double, T>(s.veff.p, s.vplane.p, (int)((long long)g.n1 * g.n2), g.n3, 0, st);
   }
 
@@ -714,11 +789,35 @@ template <typename T> struct EngineT : Engine {
     KP<T>& q = kpt(i, k);
     apply_h_dev(s, q, (const C*)psi, (C*)hpsi, nb);
   }
+  // True if the host range [p, p + bytes) lies in page-locked memory the copy engines can
+  // read directly (allocated with cudaHostAlloc / cudaMallocHost or registered).
+  static bool host_pinned(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+      cudaGetLastError();  // clear the error of a plain pageable pointer
+      return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+  }
   void apply_h_host(int i, int k, const double* psi, double* hpsi, int nb) override {
     REQ(psi && hpsi && nb > 0, FDE_EINVAL, "bad host buffers");
     Sub<T>& s = sub(i);
     KP<T>& q = kpt(i, k);
     const size_t n = (size_t)nb * q.npw;
+    if (host_pinned(psi) && host_pinned(hpsi)) {
+      // page-locked caller buffers: the copy engines move them directly, no staging
+      V.ensure(n);
+      V2.ensure(n);
+      DBuf<double2>& d64 = S;
+      d64.ensure(n);
+      CK(cudaMemcpyAsync(d64.p, psi, n * sizeof(double2), cudaMemcpyHostToDevice, st));
+      convert_in(d64.p, V.p, n);
+      apply_h_dev(s, q, V.p, V2.p, nb);
+      convert_out(V2.p, d64.p, n);
+      CK(cudaMemcpyAsync(hpsi, d64.p, n * sizeof(double2), cudaMemcpyDeviceToHost, st));
+      sync();
+      return;
+    }
     if (pin_n < 2 * n) {
       if (pin) cudaFreeHost(pin);
       pin = nullptr;
@@ -1088,7 +1187,8 @@ template <typename T> struct EngineT : Engine {
     std::vector<double> eig((size_t)s.nk * s.nb), occ((size_t)s.nk * s.nb);
     for (int k = 0; k < s.nk; ++k) std::copy(s.kp[k].eig.begin(), s.kp[k].eig.end(), eig.begin() + (size_t)k * s.nb);
     double mu = 0, ts = 0;
-    REQ(occupations_host(s.nk, s.nb, eig.data(), s.wk.data(), s.nelec, s.smearing, occ.data(), &mu, &ts),
+    REQ(occupations_host(s.nk, s.nb, eig.data(), s.wk.data(), s.nelec, s.smearing, occ.data(), &mu, &ts,
+                         s.smear_kind),
         FDE_EINVAL, "inconsistent occupation arguments");
     for (int k = 0; k < s.nk; ++k) s.kp[k].occ.assign(occ.begin() + (size_t)k * s.nb, occ.begin() + (size_t)(k + 1) * s.nb);
     s.mu = mu;
@@ -1107,7 +1207,38 @@ template <typename T> struct EngineT : Engine {
       CK(cudaStreamSynchronize(st));  // occw is reused by the next k
     }
     launch_transpose<double, double>(rho_plane.p, out, g.n3, (int)((long long)g.n1 * g.n2), 0, st);
+    if (sym.n > 1) {  // densities from an irreducible k-set: average over the symmetry group
+      grid_symmetrize(out, rho_plane.p, g, sym, st);
+      CK(cudaMemcpyAsync(out, rho_plane.p, nr * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    }
     grid_nonfinite(out, nr, status.p, st);
+  }
+
+  // Point-group operations the densities are symmetrised over (sign flips about the origin).
+  // They must form a group and map every subsystem's atoms onto atoms of the same subsystem
+  // and charge: then each H_I commutes with them and a density built from an irreducible set
+  // of k-points becomes the full-mesh density once averaged over the group.
+  SymOps sym{1, {0, 0, 0, 0, 0, 0, 0, 0}};
+  void set_symmetry(int nops, const int* ops) override {
+    REQ(nops >= 1 && nops <= 8 && ops, FDE_EINVAL, "between 1 and 8 operations");
+    std::vector<int> m(ops, ops + nops);
+    std::sort(m.begin(), m.end());
+    REQ(m[0] == 0, FDE_EINVAL, "the identity (mask 0) must be one of the operations");
+    for (int a : m) {
+      REQ(a >= 0 && a <= 7, FDE_EINVAL, "operation masks are 3-bit sign flips");
+      for (int b : m) REQ(std::binary_search(m.begin(), m.end(), a ^ b), FDE_EINVAL, "the operations must form a group");
+    }
+    REQ(std::adjacent_find(m.begin(), m.end()) == m.end(), FDE_EINVAL, "repeated operation");
+    const double Lc[3] = {A[0][0], A[1][1], A[2][2]};
+    for (auto& sp : subs) {
+      std::vector<int> have;
+      symmetry_ops_host(Lc, sp->natoms, sp->pos.data(), sp->Z.data(), 1e-6, have);
+      for (int a : m)
+        REQ(std::find(have.begin(), have.end(), a) != have.end(), FDE_EINVAL,
+            "an operation does not map a subsystem's atoms onto themselves");
+    }
+    sym.n = nops;
+    for (int i = 0; i < 8; ++i) sym.mask[i] = i < nops ? m[i] : 0;
   }
 
   void update_density(int i) override {
@@ -1624,9 +1755,38 @@ template <> void EngineT<float>::convert_out(const float2* a, double2* b, size_t
 }  // namespace fde
 
 // ---- C ABI ------------------------------------------------------------------------------------
+// A subsystem descriptor with its own copies of the caller's arrays.
+struct SubsysCopy {
+  fde_subsys_desc d{};
+  std::vector<double> pos, Z, sigma, D, kpts, wk;
+  explicit SubsysCopy(const fde_subsys_desc& s) : d(s) {
+    pos.assign(s.pos, s.pos + 3 * s.natoms);
+    Z.assign(s.Z, s.Z + s.natoms);
+    if (s.nproj_per_atom > 0) {
+      sigma.assign(s.proj_sigma, s.proj_sigma + s.nproj_per_atom);
+      D.assign(s.proj_D, s.proj_D + s.nproj_per_atom * s.nproj_per_atom);
+    }
+    kpts.assign(s.kpts, s.kpts + 3 * s.nk);
+    wk.assign(s.wk, s.wk + s.nk);
+    d.pos = pos.data();
+    d.Z = Z.data();
+    d.proj_sigma = sigma.empty() ? nullptr : sigma.data();
+    d.proj_D = D.empty() ? nullptr : D.data();
+    d.kpts = kpts.data();
+    d.wk = wk.data();
+  }
+};
+
 struct fde_ctx {
   std::unique_ptr<fde::Engine> eng;    // working precision
-  std::unique_ptr<fde::Engine> eng64;  // FP64 refinement engine of a mixed context
+  // FP64 refinement engine of a mixed context: built on first use (a mixed freeze-and-thaw
+  // cycle or refreshed SCF) from the stored descriptors, so that mixed contexts whose FP64
+  // plane would not fit in shared memory still run everything else
+  std::unique_ptr<fde::Engine> eng64;
+  fde_cell_desc cell{};
+  fde_func_desc func{};
+  std::vector<std::unique_ptr<SubsysCopy>> subs;
+  std::vector<int> sym_ops;
   cudaStream_t stream = nullptr;
   std::string err;
   fde_prec prec;
@@ -1634,6 +1794,17 @@ struct fde_ctx {
 };
 
 namespace fde {
+
+// The FP64 engine of a mixed context, created on first use.
+static Engine& engine64(fde_ctx* c) {
+  if (!c->eng64) {
+    std::unique_ptr<Engine> e(new EngineT<double>(&c->cell, &c->func, c->stream));
+    for (auto& sc : c->subs) e->add_subsystem(&sc->d);
+    if (!c->sym_ops.empty()) e->set_symmetry((int)c->sym_ops.size(), c->sym_ops.data());
+    c->eng64 = std::move(e);
+  }
+  return *c->eng64;
+}
 
 // Copy densities, orbitals, eigenvalues, occupations and entropies of every subsystem from
 // one engine to another (the precisions may differ; orbitals pass through FP64).
@@ -1667,7 +1838,7 @@ static void transfer_state(Engine& from, Engine& to, cudaStream_t st) {
 // is copied back to the FP32 engine.
 static fde_status mixed_cycle(fde_ctx* c, double tol, int max_scf, fde_energies* out, cudaStream_t st) {
   Engine& lo = *c->eng;
-  Engine& hi = *c->eng64;
+  Engine& hi = engine64(c);
   const int ns = lo.nsub();
   const long long nr = lo.grid_points();
   DBuf<double> start;
@@ -1713,7 +1884,7 @@ static fde_status mixed_cycle(fde_ctx* c, double tol, int max_scf, fde_energies*
 // copied back to the FP32 engine.
 static fde_status mixed_refresh(fde_ctx* c, double tol, int max_scf, fde_energies* out, cudaStream_t st) {
   Engine& lo = *c->eng;
-  Engine& hi = *c->eng64;
+  Engine& hi = engine64(c);
   fde_energies e1{};
   const fde_status s1 = lo.scf_refresh(std::max(tol, 1e-5), max_scf, &e1);
   if (s1 != FDE_OK && s1 != FDE_ENOCONV) return s1;
@@ -1764,7 +1935,8 @@ fde_status fde_create(const fde_cell_desc* cell, const fde_func_desc* func, fde_
     if (prec == FDE_PREC_FP64) c->eng.reset(new fde::EngineT<double>(cell, func, st));
     else {
       c->eng.reset(new fde::EngineT<float>(cell, func, st));
-      c->eng64.reset(new fde::EngineT<double>(cell, func, st));
+      c->cell = *cell;
+      c->func = *func;
     }
     c->stream = st;
     return FDE_OK;
@@ -1781,7 +1953,10 @@ fde_status fde_create(const fde_cell_desc* cell, const fde_func_desc* func, fde_
 fde_status fde_add_subsystem(fde_ctx* c, const fde_subsys_desc* d, int* id) {
   return guard(c, [&]() {
     const int i = c->eng->add_subsystem(d);
-    if (c->eng64) c->eng64->add_subsystem(d);
+    if (c->prec == FDE_PREC_MIXED) {
+      c->subs.emplace_back(new SubsysCopy(*d));
+      if (c->eng64) c->eng64->add_subsystem(d);
+    }
     if (id) *id = i;
     return FDE_OK;
   });
@@ -1837,14 +2012,22 @@ fde_status fde_scf_subsystem(fde_ctx* c, int sub, double tol, int max_scf, fde_e
 }
 fde_status fde_freeze_thaw_cycle(fde_ctx* c, double tol, int max_scf, fde_energies* out) {
   return guard(c, [&]() {
-    if (c->eng64) return fde::mixed_cycle(c, tol, max_scf, out, c->stream);
+    if (c->prec == FDE_PREC_MIXED) return fde::mixed_cycle(c, tol, max_scf, out, c->stream);
     return c->eng->freeze_thaw(tol, max_scf, out, nullptr);
   });
 }
 fde_status fde_scf_refresh(fde_ctx* c, double tol, int max_scf, fde_energies* out) {
   return guard(c, [&]() {
-    if (c->eng64) return fde::mixed_refresh(c, tol, max_scf, out, c->stream);
+    if (c->prec == FDE_PREC_MIXED) return fde::mixed_refresh(c, tol, max_scf, out, c->stream);
     return c->eng->scf_refresh(tol, max_scf, out);
+  });
+}
+fde_status fde_set_symmetry(fde_ctx* c, int nops, const int* ops) {
+  return guard(c, [&]() {
+    c->eng->set_symmetry(nops, ops);
+    if (c->prec == FDE_PREC_MIXED) c->sym_ops.assign(ops, ops + nops);
+    if (c->eng64) c->eng64->set_symmetry(nops, ops);
+    return FDE_OK;
   });
 }
 fde_status fde_delta_rho(fde_ctx* c, const double* d_rho_ref, double* out) {
@@ -1969,6 +2152,9 @@ fde_status fde_dense_eigh(fde_ctx* c, int n, const double* d_A, int nvec, double
 }
 fde_status fde_fft3d(fde_ctx* c, void* d_data, int sign) {
   return guard(c, [&]() { c->eng->fft3d(d_data, sign); return FDE_OK; });
+}
+fde_status fde_fft3d_f64(fde_ctx* c, double* d_data, int sign, int arith) {
+  return guard(c, [&]() { c->eng->fft3d_f64((double2*)d_data, sign, arith); return FDE_OK; });
 }
 fde_status fde_sync(fde_ctx* c) {
   return guard(c, [&]() { c->eng->sync(); return FDE_OK; });

@@ -357,6 +357,8 @@ __device__ __forceinline__ long long neg_index(long long idx, const GridDims& g)
   const int j1 = i1 ? g.n1 - i1 : 0, j2 = i2 ? g.n2 - i2 : 0, j3 = i3 ? g.n3 - i3 : 0;
   return (long long)((j1 * g.n2 + j2) * g.n3 + j3);
 }
+__device__ __forceinline__ double2 to_d2(double2 v) { return v; }
+__device__ __forceinline__ double2 to_d2(float2 v) { return make_double2((double)v.x, (double)v.y); }
 __device__ __forceinline__ void unpack2(double2 c, double2 cn, double2* a, double2* b) {
   *a = make_double2(0.5 * (c.x + cn.x), 0.5 * (c.y - cn.y));
   *b = make_double2(0.5 * (c.y + cn.y), -0.5 * (c.x - cn.x));
@@ -459,8 +461,12 @@ __global__ void k_pw_total(const double* __restrict__ rho, GradPacks gp, int xc_
 // pair: w_x = vpart_tot - d f_kin / d rho_x (the pointwise part of v~_kin[rho] - v~_kin[rho_x]
 // with the xc part of the total), and, in place of the packed gradients, the packed
 // divergence arguments d_x = h_tot - h_x.  Energy partial rows 0/1 (xc/kin of a), 2/3 (b).
-__global__ void k_pw_pair(const double* __restrict__ ra, const double* __restrict__ rb, double2* Pa, double2* Pb,
-                          double2* Pz, const double* __restrict__ hx, const double* __restrict__ hy,
+// The divergence arguments go to Da, Db, Dz in precision TD (FP64: in place over Pa, Pb, Pz;
+// FP32: separate grids for the single-precision transforms of the mixed path).
+template <typename TD>
+__global__ void k_pw_pair(const double* __restrict__ ra, const double* __restrict__ rb, const double2* Pa,
+                          const double2* Pb, const double2* Pz, cplx<TD>* Da, cplx<TD>* Db, cplx<TD>* Dz,
+                          const double* __restrict__ hx, const double* __restrict__ hy,
                           const double* __restrict__ hz, const double* __restrict__ vtot, int xc_mode, int kedf,
                           double rho_cut, double* __restrict__ wa, double* __restrict__ wb, int write_d, long long nr,
                           double* partial) {
@@ -488,9 +494,9 @@ __global__ void k_pw_pair(const double* __restrict__ ra, const double* __restric
     if (wb) wb[idx] = vt - vb;
     if (write_d) {
       const double tx = hx[idx], ty = hy[idx], tz = hz[idx];
-      Pa[idx] = make_double2(tx - ha * pa.x, ty - ha * pa.y);
-      if (has_b) Pb[idx] = make_double2(tx - hb * pb.x, ty - hb * pb.y);
-      Pz[idx] = make_double2(tz - ha * pz.x, has_b ? tz - hb * pz.y : 0.0);
+      Da[idx] = mk<TD>((TD)(tx - ha * pa.x), (TD)(ty - ha * pa.y));
+      if (has_b) Db[idx] = mk<TD>((TD)(tx - hb * pb.x), (TD)(ty - hb * pb.y));
+      Dz[idx] = mk<TD>((TD)(tz - ha * pz.x), (TD)(has_b ? tz - hb * pz.y : 0.0));
     }
   }
   block_sum_store(xa, partial + blockIdx.x);
@@ -503,9 +509,10 @@ __global__ void k_pw_pair(const double* __restrict__ ra, const double* __restric
 // Vx(G) = v_H(G) - i G . d_x(G), v_H = 4 pi RT / G^2 (RT = rho_tot(G), scaled), the d_x
 // unpacked from the forward transforms Da (x, y of a), Db (x, y of b), Dz (z of a and b),
 // unscaled; without gradients Va = Vb = v_H.  Hartree sum of rho_tot into partial row 0.
-__global__ void k_assemble_pair(const double2* __restrict__ RT, const double2* __restrict__ Da,
-                                const double2* __restrict__ Db, const double2* __restrict__ Dz, int has_b,
-                                double2* __restrict__ F, GridDims g, CellDev c, double inv_nr, double* partial) {
+template <typename TD>
+__global__ void k_assemble_pair(const double2* __restrict__ RT, const cplx<TD>* __restrict__ Da,
+                                const cplx<TD>* __restrict__ Db, const cplx<TD>* __restrict__ Dz, int has_b,
+                                cplx<TD>* __restrict__ F, GridDims g, CellDev c, double inv_nr, double* partial) {
   const long long nr = (long long)g.n1 * g.n2 * g.n3;
   double eh = 0;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < nr; idx += (long long)gridDim.x * blockDim.x) {
@@ -521,12 +528,12 @@ __global__ void k_assemble_pair(const double2* __restrict__ RT, const double2* _
     if (Da && !p.nyq) {
       const long long jn = neg_index(idx, g);
       double2 ax, ay, az, bx = make_double2(0, 0), by = make_double2(0, 0), bz = make_double2(0, 0);
-      unpack2(Da[idx], Da[jn], &ax, &ay);
+      unpack2(to_d2(Da[idx]), to_d2(Da[jn]), &ax, &ay);
       if (has_b) {
-        unpack2(Db[idx], Db[jn], &bx, &by);
-        unpack2(Dz[idx], Dz[jn], &az, &bz);
+        unpack2(to_d2(Db[idx]), to_d2(Db[jn]), &bx, &by);
+        unpack2(to_d2(Dz[idx]), to_d2(Dz[jn]), &az, &bz);
       } else {
-        const double2 t = Dz[idx], tn = Dz[jn];
+        const double2 t = to_d2(Dz[idx]), tn = to_d2(Dz[jn]);
         az = make_double2(0.5 * (t.x + tn.x), 0.5 * (t.y - tn.y));
       }
       // i G . d / N_r
@@ -535,17 +542,21 @@ __global__ void k_assemble_pair(const double2* __restrict__ RT, const double2* _
       va = make_double2(vh.x + dai * inv_nr, vh.y - dar * inv_nr);
       vb = make_double2(vh.x + dbi * inv_nr, vh.y - dbr * inv_nr);
     }
-    if (F) F[idx] = has_b ? pack2(va, vb) : va;
+    if (F) {
+      const double2 o = has_b ? pack2(va, vb) : va;
+      F[idx] = mk<TD>((TD)o.x, (TD)o.y);
+    }
   }
   if (partial) block_sum_store(eh, partial + blockIdx.x);
 }
 
 // veff_x = vloc + Re/Im F (inverse-transformed reciprocal part) + w_x for the pair's
 // subsystems (either output may be NULL).
-__global__ void k_finish_pair(const double2* __restrict__ F, const double* __restrict__ vloc, double* va,
+template <typename TD>
+__global__ void k_finish_pair(const cplx<TD>* __restrict__ F, const double* __restrict__ vloc, double* va,
                               double* vb, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const double2 f = F[i];
+    const double2 f = to_d2(F[i]);
     const double vl = vloc[i];
     if (va) va[i] = vl + f.x + va[i];
     if (vb) vb[i] = vl + f.y + vb[i];
@@ -553,6 +564,25 @@ __global__ void k_finish_pair(const double2* __restrict__ F, const double* __res
 }
 
 // ---- launch wrappers ------------------------------------------------------------------------
+__global__ void k_symmetrize(const double* __restrict__ in, double* __restrict__ out, GridDims g, SymOps ops) {
+  const long long nr = (long long)g.n1 * g.n2 * g.n3;
+  const double w = 1.0 / (double)ops.n;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nr; i += (long long)gridDim.x * blockDim.x) {
+    const int i3 = (int)(i % g.n3);
+    const long long t = i / g.n3;
+    const int i2 = (int)(t % g.n2), i1 = (int)(t / g.n2);
+    double acc = 0;
+    for (int o = 0; o < ops.n; ++o) {
+      const int m = ops.mask[o];
+      const int j1 = (m & 1) ? (g.n1 - i1) % g.n1 : i1;
+      const int j2 = (m & 2) ? (g.n2 - i2) % g.n2 : i2;
+      const int j3 = (m & 4) ? (g.n3 - i3) % g.n3 : i3;
+      acc += in[((long long)j1 * g.n2 + j2) * g.n3 + j3];
+    }
+    out[i] = acc * w;
+  }
+}
+
 static int gs(long long n) {
   long long b = (n + 255) / 256;
   return (int)(b < 4096 ? (b > 0 ? b : 1) : 4096);
@@ -600,6 +630,11 @@ void grid_axpy(double* a, const double* b, double alpha, long long n, cudaStream
   count_launches(1);
   k_axpy<<<gs(n), 256, 0, st>>>(a, b, alpha, n);
 }
+void grid_symmetrize(const double* in, double* out, const GridDims& g, const SymOps& ops, cudaStream_t st) {
+  const long long nr = (long long)g.n1 * g.n2 * g.n3;
+  count_launches(1);
+  k_symmetrize<<<gs(nr), 256, 0, st>>>(in, out, g, ops);
+}
 void grid_nonfinite(const double* a, long long n, unsigned* status, cudaStream_t st) {
   count_launches(1);
   ProfScope prof_("k_nonfinite", st);
@@ -623,33 +658,44 @@ void grid_pw_total(const double* rho, const GradPacks& gp, int xc_mode, int kedf
   ProfScope prof_("k_pw_total", st);
   k_pw_total<<<kRedBlocks, kRedThreads, 0, st>>>(rho, gp, xc_mode, kedf, rho_cut, vpart, hx, hy, hz, nr, partial);
 }
-void grid_pw_pair(const double* ra, const double* rb, double2* Pa, double2* Pb, double2* Pz, const double* hx,
-                  const double* hy, const double* hz, const double* vtot, int xc_mode, int kedf, double rho_cut,
-                  double* wa, double* wb, int write_d, long long nr, double* partial, cudaStream_t st) {
+template <typename TD>
+void grid_pw_pair(const double* ra, const double* rb, const double2* Pa, const double2* Pb, const double2* Pz,
+                  cplx<TD>* Da, cplx<TD>* Db, cplx<TD>* Dz, const double* hx, const double* hy, const double* hz,
+                  const double* vtot, int xc_mode, int kedf, double rho_cut, double* wa, double* wb, int write_d,
+                  long long nr, double* partial, cudaStream_t st) {
   count_launches(1);
   ProfScope prof_("k_pw_pair", st);
-  k_pw_pair<<<kRedBlocks, kRedThreads, 0, st>>>(ra, rb, Pa, Pb, Pz, hx, hy, hz, vtot, xc_mode, kedf, rho_cut, wa, wb,
-                                                write_d, nr, partial);
+  k_pw_pair<TD><<<kRedBlocks, kRedThreads, 0, st>>>(ra, rb, Pa, Pb, Pz, Da, Db, Dz, hx, hy, hz, vtot, xc_mode, kedf,
+                                                    rho_cut, wa, wb, write_d, nr, partial);
 }
-void grid_assemble_pair(const double2* RT, const double2* Da, const double2* Db, const double2* Dz, int has_b,
-                        double2* F, const GridDims& g, const CellDev& c, double* partial, cudaStream_t st) {
+template <typename TD>
+void grid_assemble_pair(const double2* RT, const cplx<TD>* Da, const cplx<TD>* Db, const cplx<TD>* Dz, int has_b,
+                        cplx<TD>* F, const GridDims& g, const CellDev& c, double* partial, cudaStream_t st) {
   count_launches(1);
   ProfScope prof_("k_assemble_pair", st);
-  k_assemble_pair<<<kRedBlocks, kRedThreads, 0, st>>>(RT, Da, Db, Dz, has_b, F, g, c,
-                                                      1.0 / ((double)g.n1 * g.n2 * g.n3), partial);
+  k_assemble_pair<TD><<<kRedBlocks, kRedThreads, 0, st>>>(RT, Da, Db, Dz, has_b, F, g, c,
+                                                          1.0 / ((double)g.n1 * g.n2 * g.n3), partial);
 }
-void grid_finish_pair(const double2* F, const double* vloc, double* va, double* vb, long long n, cudaStream_t st) {
+template <typename TD>
+void grid_finish_pair(const cplx<TD>* F, const double* vloc, double* va, double* vb, long long n, cudaStream_t st) {
   count_launches(1);
   ProfScope prof_("k_finish_pair", st);
-  k_finish_pair<<<gs(n), 256, 0, st>>>(F, vloc, va, vb, n);
+  k_finish_pair<TD><<<gs(n), 256, 0, st>>>(F, vloc, va, vb, n);
 }
 int grid_red_blocks() { return kRedBlocks; }
 
-#define FDE_GRID_INST(T)                                                                                     \
-  template void launch_fft3d<T>(cplx<T>*, const GridDims&, const FftPlans<T>&, int, cudaStream_t);           \
-  template void grid_c_to_real<T>(const cplx<T>*, double*, long long, cudaStream_t);                         \
-  template void grid_combine<T>(const double*, const double*, const double*, const cplx<T>*, double, double*, \
-                                long long, cudaStream_t);
+#define FDE_GRID_INST(T)                                                                                       \
+  template void launch_fft3d<T>(cplx<T>*, const GridDims&, const FftPlans<T>&, int, cudaStream_t);             \
+  template void grid_c_to_real<T>(const cplx<T>*, double*, long long, cudaStream_t);                           \
+  template void grid_combine<T>(const double*, const double*, const double*, const cplx<T>*, double, double*,   \
+                                long long, cudaStream_t);                                                      \
+  template void grid_pw_pair<T>(const double*, const double*, const double2*, const double2*, const double2*,   \
+                                cplx<T>*, cplx<T>*, cplx<T>*, const double*, const double*, const double*,       \
+                                const double*, int, int, double, double*, double*, int, long long, double*,      \
+                                cudaStream_t);                                                                 \
+  template void grid_assemble_pair<T>(const double2*, const cplx<T>*, const cplx<T>*, const cplx<T>*, int,      \
+                                      cplx<T>*, const GridDims&, const CellDev&, double*, cudaStream_t);        \
+  template void grid_finish_pair<T>(const cplx<T>*, const double*, double*, double*, long long, cudaStream_t);
 FDE_GRID_INST(float)
 FDE_GRID_INST(double)
 

@@ -21,6 +21,13 @@ void grid_lincomb(const double* const* ins, const double* const* res, const doub
                   long long n, double* out, cudaStream_t st);
 void grid_axpy(double* a, const double* b, double alpha, long long n, cudaStream_t st);
 void grid_nonfinite(const double* a, long long n, unsigned* status, cudaStream_t st);
+// out(r) = (1 / nops) sum_o in(R_o r), R_o = diag(+-1) from the 3-bit masks (r -> -r mod grid on
+// the flipped axes); in and out must not overlap.
+struct SymOps {
+  int n;
+  int mask[8];
+};
+void grid_symmetrize(const double* in, double* out, const GridDims& g, const SymOps& ops, cudaStream_t st);
 
 // ---- packed pairs of real fields (two real grids in one complex transform) ----
 constexpr int kMaxPairs = 32;
@@ -36,11 +43,17 @@ void grid_unpack_density(const double2* C, int has_b, double2* RT, int accumulat
                          double2* Pz, const GridDims& g, const CellDev& c, double* partial, cudaStream_t st);
 void grid_pw_total(const double* rho, const GradPacks& gp, int xc_mode, int kedf, double rho_cut, double* vpart,
                    double* hx, double* hy, double* hz, long long nr, double* partial, cudaStream_t st);
-void grid_pw_pair(const double* ra, const double* rb, double2* Pa, double2* Pb, double2* Pz, const double* hx,
-                  const double* hy, const double* hz, const double* vtot, int xc_mode, int kedf, double rho_cut,
-                  double* wa, double* wb, int write_d, long long nr, double* partial, cudaStream_t st);
-void grid_assemble_pair(const double2* RT, const double2* Da, const double2* Db, const double2* Dz, int has_b,
-                        double2* F, const GridDims& g, const CellDev& c, double* partial, cudaStream_t st);
-void grid_finish_pair(const double2* F, const double* vloc, double* va, double* vb, long long n, cudaStream_t st);
+// The divergence arguments (Da, Db, Dz), the reciprocal-space potentials F and their transforms
+// are in precision TD: FP64 in FP64 contexts (Da.. may alias Pa..), FP32 in mixed ones.
+template <typename TD>
+void grid_pw_pair(const double* ra, const double* rb, const double2* Pa, const double2* Pb, const double2* Pz,
+                  cplx<TD>* Da, cplx<TD>* Db, cplx<TD>* Dz, const double* hx, const double* hy, const double* hz,
+                  const double* vtot, int xc_mode, int kedf, double rho_cut, double* wa, double* wb, int write_d,
+                  long long nr, double* partial, cudaStream_t st);
+template <typename TD>
+void grid_assemble_pair(const double2* RT, const cplx<TD>* Da, const cplx<TD>* Db, const cplx<TD>* Dz, int has_b,
+                        cplx<TD>* F, const GridDims& g, const CellDev& c, double* partial, cudaStream_t st);
+template <typename TD>
+void grid_finish_pair(const cplx<TD>* F, const double* vloc, double* va, double* vb, long long n, cudaStream_t st);
 
 }  // namespace fde

@@ -2,9 +2,12 @@
 //   * plane-wave sphere |k + G|^2 / 2 <= E_cut (Sec. 2: plane-wave expansion of the subsystem
 //     orbitals; the full sphere, evaluated in FP64 from integer Miller indices);
 //   * Ewald sum with a neutralising background for the nuclear repulsion V_NN of Eq. E_FDE;
-//   * occupations with 2 sum_k w_k sum_j n_jk = N_I (Sec. 2), Fermi-Dirac smearing for metallic
-//     subsystems (Computational Details) and the Mermin entropy term;
-//   * Pulay (DIIS) mixing coefficients of the subsystem SCF (the paper is silent on mixing).
+//   * occupations with 2 sum_k w_k sum_j n_jk = N_I (Sec. 2), Methfessel-Paxton (the paper's),
+//     Gaussian or Fermi-Dirac smearing for metallic subsystems (Computational Details) and the
+//     entropy term of each;
+//   * Pulay (DIIS) mixing coefficients of the subsystem SCF (the paper is silent on mixing);
+//   * Monkhorst-Pack meshes reduced by time reversal and the cell's mirror symmetries
+//     (Computational Details: 2 x 2 x 1 Monkhorst-Pack sampling of the periodic systems).
 #include <math.h>
 
 #include <algorithm>
@@ -107,8 +110,39 @@ static inline double fermi(double x) {  // 1 / (1 + e^x)
   return 1.0 / (1.0 + exp(x));
 }
 
+// Occupation f(x) and entropy-like term s(x) of one state at x = (e - mu) / sigma.  s is the
+// function for which the free energy E - sigma 2 sum_k w_k sum_j s(x_jk) is variational in
+// the occupations: s'(x) = x f'(x), s(-inf) = 0.
+//   Fermi-Dirac: f = 1 / (1 + e^x), s = -[f ln f + (1 - f) ln(1 - f)];
+//   Gaussian (Methfessel-Paxton order 0): f = erfc(x) / 2, s = e^{-x^2} / (2 sqrt(pi));
+//   Methfessel-Paxton order 1 (Computational Details: the metallic subsystems' smearing):
+//     the Gaussian delta corrected by its first Hermite term, A_1 H_2(x) e^{-x^2} with
+//     A_1 = -1 / (4 sqrt(pi)), integrates to f = erfc(x) / 2 - x e^{-x^2} / (2 sqrt(pi)) and
+//     s = A_1 H_2(x) e^{-x^2} / 2 = (1 - 2 x^2) e^{-x^2} / (4 sqrt(pi)).
+static inline void smear(int kind, double x, double* f, double* s) {
+  const double isp = 0.5641895835477562869;  // 1 / sqrt(pi)
+  if (kind == FDE_SMEAR_FERMI) {
+    const double n = fermi(x);
+    double t = 0;
+    if (n > 0) t += n * log(n);
+    if (n < 1) t += (1 - n) * log(1 - n);
+    *f = n;
+    *s = -t;
+    return;
+  }
+  const double g = exp(-x * x);
+  if (kind == FDE_SMEAR_GAUSS) {
+    *f = 0.5 * erfc(x);
+    *s = 0.5 * isp * g;
+    return;
+  }
+  *f = 0.5 * erfc(x) - 0.5 * isp * x * g;
+  *s = 0.25 * isp * (1.0 - 2.0 * x * x) * g;
+}
+
 bool occupations_host(int nk, int nb, const double* eig, const double* wk, double nelec, double sigma, double* occ,
-                      double* mu, double* ts) {
+                      double* mu, double* ts, int kind) {
+  if (kind != FDE_SMEAR_FERMI && kind != FDE_SMEAR_MP && kind != FDE_SMEAR_GAUSS) return false;
   if (nk <= 0 || nb <= 0 || !eig || !wk || !occ) return false;
   if (sigma <= 0) {
     const int no = (int)llround(nelec / 2.0);
@@ -132,25 +166,112 @@ bool occupations_host(int nk, int nb, const double* eig, const double* wk, doubl
   double m = 0.5 * (lo + hi);
   for (int it = 0; it < 300; ++it) {
     m = 0.5 * (lo + hi);
-    double n = 0;
+    double n = 0, f, sj;
     for (int k = 0; k < nk; ++k)
-      for (int j = 0; j < nb; ++j) n += 2.0 * wk[k] * fermi((eig[k * nb + j] - m) / sigma);
+      for (int j = 0; j < nb; ++j) {
+        smear(kind, (eig[k * nb + j] - m) / sigma, &f, &sj);
+        n += 2.0 * wk[k] * f;
+      }
     if (fabs(n - nelec) < 1e-13) break;
     if (n < nelec) lo = m; else hi = m;
   }
   double S = 0;
   for (int k = 0; k < nk; ++k)
     for (int j = 0; j < nb; ++j) {
-      const double n = fermi((eig[k * nb + j] - m) / sigma);
-      occ[k * nb + j] = n;
-      double t = 0;
-      if (n > 0) t += n * log(n);
-      if (n < 1) t += (1 - n) * log(1 - n);
-      S -= 2.0 * wk[k] * t;
+      double f, sj;
+      smear(kind, (eig[k * nb + j] - m) / sigma, &f, &sj);
+      occ[k * nb + j] = f;
+      S += 2.0 * wk[k] * sj;
     }
   if (mu) *mu = m;
   if (ts) *ts = sigma * S;
   return true;
+}
+
+// ---- Brillouin-zone sampling --------------------------------------------------------------------
+// Monkhorst-Pack mesh: k_j = (2 r_j - q_j - 1 + shift_j) / (2 q_j), r_j = 1..q_j, crystal coordinates,
+// enumerated with the first axis slowest.  Two points are the same when they differ by a
+// reciprocal lattice vector (integer crystal coordinates).
+static bool same_k(const double* a, const double* b) {
+  for (int c = 0; c < 3; ++c) {
+    const double d = a[c] - b[c];
+    if (fabs(d - nearbyint(d)) > 1e-9) return false;
+  }
+  return true;
+}
+
+bool kmesh_host(const int q[3], const double shift[3], int time_reversal, int nops, const int* ops,
+                std::vector<double>& kpts, std::vector<double>& wk) {
+  for (int c = 0; c < 3; ++c)
+    if (q[c] <= 0 || q[c] > 64) return false;
+  if (nops < 0 || (nops > 0 && !ops)) return false;
+  std::vector<double> full;
+  for (int a = 1; a <= q[0]; ++a)
+    for (int b = 1; b <= q[1]; ++b)
+      for (int c = 1; c <= q[2]; ++c) {
+        const int r[3] = {a, b, c};
+        for (int d = 0; d < 3; ++d) full.push_back((2.0 * r[d] - q[d] - 1.0 + (shift ? shift[d] : 0.0)) / (2.0 * q[d]));
+      }
+  const int n = (int)full.size() / 3;
+  // images of a point: R k for every operation (identity included), and -R k with time reversal
+  std::vector<int> opl(1, 0);
+  for (int o = 0; o < nops; ++o) {
+    if (ops[o] < 0 || ops[o] > 7) return false;
+    if (std::find(opl.begin(), opl.end(), ops[o]) == opl.end()) opl.push_back(ops[o]);
+  }
+  std::vector<int> owner(n, -1);
+  kpts.clear();
+  wk.clear();
+  for (int i = 0; i < n; ++i) {
+    if (owner[i] >= 0) continue;
+    const int id = (int)wk.size();
+    int count = 0;
+    for (int j = i; j < n; ++j) {
+      if (owner[j] >= 0) continue;
+      bool hit = false;
+      for (int o : opl)
+        for (int t = 0; t < (time_reversal ? 2 : 1) && !hit; ++t) {
+          double img[3];
+          for (int d = 0; d < 3; ++d) img[d] = ((o >> d) & 1 ? -1.0 : 1.0) * (t ? -1.0 : 1.0) * full[3 * i + d];
+          hit = same_k(img, &full[3 * j]);
+        }
+      if (hit) {
+        owner[j] = id;
+        ++count;
+      }
+    }
+    for (int d = 0; d < 3; ++d) kpts.push_back(full[3 * i + d]);
+    wk.push_back((double)count / (double)n);
+  }
+  return true;
+}
+
+// Operations r -> R r about the origin, R = diag(+-1, +-1, +-1) (3-bit mask: bit c flips
+// coordinate c), that map the atom set onto itself: every atom lands within tol (bohr, modulo
+// the cell) on an atom of the same charge.  The identity (mask 0) is always first.
+void symmetry_ops_host(const double L[3], int natoms, const double* pos, const double* Z, double tol,
+                       std::vector<int>& ops) {
+  ops.assign(1, 0);
+  for (int m = 1; m < 8; ++m) {
+    bool ok = true;
+    for (int a = 0; a < natoms && ok; ++a) {
+      double p[3];
+      for (int d = 0; d < 3; ++d) p[d] = ((m >> d) & 1) ? -pos[3 * a + d] : pos[3 * a + d];
+      bool found = false;
+      for (int b = 0; b < natoms && !found; ++b) {
+        if (Z[a] != Z[b]) continue;
+        double r2 = 0;
+        for (int d = 0; d < 3; ++d) {
+          double x = p[d] - pos[3 * b + d];
+          x -= L[d] * nearbyint(x / L[d]);
+          r2 += x * x;
+        }
+        found = r2 <= tol * tol;
+      }
+      ok = found;
+    }
+    if (ok) ops.push_back(m);
+  }
 }
 
 bool solve_dense(std::vector<double>& Am, std::vector<double>& b, int n) {
@@ -223,8 +344,33 @@ fde_status fde_host_ewald(const double* lengths, int natoms, const double* pos, 
 }
 
 fde_status fde_host_occupations(int nk, int nb, const double* eig, const double* wk, double nelec, double sigma,
-                                double* occ, double* mu, double* ts) {
-  return fde::occupations_host(nk, nb, eig, wk, nelec, sigma, occ, mu, ts) ? FDE_OK : FDE_EINVAL;
+                                int smearing_kind, double* occ, double* mu, double* ts) {
+  return fde::occupations_host(nk, nb, eig, wk, nelec, sigma, occ, mu, ts, smearing_kind) ? FDE_OK : FDE_EINVAL;
+}
+
+fde_status fde_host_kmesh(const int* q, const double* shift, int time_reversal, int nops, const int* ops, int* nk,
+                          double* kpts, double* wk) {
+  if (!q || !nk) return FDE_EINVAL;
+  std::vector<double> k, w;
+  if (!fde::kmesh_host(q, shift, time_reversal, nops, ops, k, w)) return FDE_EINVAL;
+  const int cap = *nk;
+  *nk = (int)w.size();
+  if ((kpts || wk) && cap < *nk) return FDE_EINVAL;
+  if (kpts) std::copy(k.begin(), k.end(), kpts);
+  if (wk) std::copy(w.begin(), w.end(), wk);
+  return FDE_OK;
+}
+
+fde_status fde_host_symmetry_ops(const double* lengths, int natoms, const double* pos, const double* Z, double tol,
+                                 int* nops, int* ops) {
+  if (!lengths || natoms < 0 || (natoms > 0 && (!pos || !Z)) || !nops || !ops || !(tol >= 0)) return FDE_EINVAL;
+  for (int j = 0; j < 3; ++j)
+    if (!(lengths[j] > 0)) return FDE_EINVAL;
+  std::vector<int> o;
+  fde::symmetry_ops_host(lengths, natoms, pos, Z, tol, o);
+  *nops = (int)o.size();
+  std::copy(o.begin(), o.end(), ops);
+  return FDE_OK;
 }
 
 fde_status fde_host_pulay(int m, const double* overlap, double* coef) {

@@ -21,13 +21,27 @@ void sphere_miller(const double L[3], const double kfrac[3], double ecut, std::v
 double ewald_energy(const double L[3], const std::vector<double>& pos, const std::vector<double>& Z);
 
 // Occupations of nk x nb eigenvalues eig [nk][nb] (Ha) with k weights wk [nk] holding nelec
-// electrons: 2 sum_k w_k sum_j n_jk = nelec, 0 <= n <= 1.  sigma > 0: Fermi-Dirac
-// n = 1 / (1 + exp((e - mu) / sigma)) with mu by bisection to |N(mu) - nelec| < 1e-13, and
-// ts = sigma S, S = -2 sum_k w_k sum_j [n ln n + (1 - n) ln(1 - n)].  sigma <= 0: integer
-// occupations of the nelec / 2 lowest bands (one k-point), mu = the highest occupied
+// electrons: 2 sum_k w_k sum_j n_jk = nelec.  sigma > 0: smeared, n = f((e - mu) / sigma) with
+// f of kind (FDE_SMEAR_FERMI, FDE_SMEAR_MP first-order Methfessel-Paxton, FDE_SMEAR_GAUSS), mu by
+// bisection to |N(mu) - nelec| < 1e-13, and ts = sigma S, S = 2 sum_k w_k sum_j s(x_jk) with s
+// the entropy-like term of the same kind (Fermi-Dirac: the Mermin entropy).  sigma <= 0:
+// integer occupations of the nelec / 2 lowest bands (one k-point), mu = the highest occupied
 // eigenvalue, ts = 0.  Returns false for inconsistent arguments.
 bool occupations_host(int nk, int nb, const double* eig, const double* wk, double nelec, double sigma, double* occ,
-                      double* mu, double* ts);
+                      double* mu, double* ts, int kind);
+
+// Monkhorst-Pack mesh q[0] x q[1] x q[2] with offsets shift[3] (nullable: unshifted),
+// k_j = (2 r_j - q_j - 1 + shift_j) / (2 q_j), r_j = 1..q_j, reduced to one point per orbit of
+// {R k, and -R k if time_reversal} (R over the identity and the sign-flip masks ops[nops]):
+// kpts [nk][3] (crystal coordinates, the first member of each orbit in mesh order) and wk [nk] =
+// orbit size / mesh size.  False for bad arguments.
+bool kmesh_host(const int q[3], const double shift[3], int time_reversal, int nops, const int* ops,
+                std::vector<double>& kpts, std::vector<double>& wk);
+
+// Sign-flip operations about the origin (3-bit masks, identity first) mapping the atoms onto
+// atoms of equal charge within tol (bohr) modulo the orthorhombic cell L.
+void symmetry_ops_host(const double L[3], int natoms, const double* pos, const double* Z, double tol,
+                       std::vector<int>& ops);
 
 // Gaussian elimination with partial pivoting on the dense n x n system A x = b (row-major);
 // the solution replaces b.  False for a (numerically) singular A.

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "common.cuh"
+#include "dd.cuh"
 
 namespace fde {
 
@@ -77,6 +78,12 @@ bool launch_fft3d_ct(cplx<T>* data, const GridDims& g, const FftPlans<T>& fp, in
 // out[j][i] = (Tout) in[i][j], in is [rows][cols]; with optional accumulate.
 template <typename Tin, typename Tout>
 void launch_transpose(const Tin* in, Tout* out, int rows, int cols, int accumulate, cudaStream_t st);
+// v[i1][i2][i3] (FP64) -> out[i3][i2][i1] (FP32): the potential planes of the mixed path's
+// compile-time plane pass, each plane transposed so that a row holds fixed i2.
+void launch_to_plane_t(const double* in, float* out, const GridDims& g, cudaStream_t st);
+// True when FP32 H psi on this grid runs the compile-time kernels, which read the potential in
+// the transposed plane layout of launch_to_plane_t.
+bool hpsi_plane_transposed_f32(const GridDims& g);
 
 // ---- dense complex algebra (linalg.cu) --------------------------------------------------
 // C[i][j] = sum_g conj(A[i][g]) B[j][g], A [m][K] (lda), B [n][K] (ldb); C [m][n] FP64
@@ -160,6 +167,10 @@ void launch_hermitize(double2* A, int n, cudaStream_t st);
 // 1/N_r), +1 inverse (unscaled).
 template <typename T>
 void launch_fft3d(cplx<T>* data, const GridDims& g, const FftPlans<T>& fp, int sign, cudaStream_t st);
+// The same 3D transform of an FP64 grid computed in double-float arithmetic on the FP32 pipes
+// (fft_dd.cu): converted on the first axis pass, converted back on the last.  False (nothing
+// launched) when an axis length has no compiled kernel.
+bool launch_fft3d_dd(double2* data, const GridDims& g, const FftPlans<dd>& fp, int sign, cudaStream_t st);
 
 struct CellDev {
   double b[3][3];  // reciprocal rows

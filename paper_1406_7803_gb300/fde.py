@@ -22,6 +22,8 @@ FDE_OK, FDE_EINVAL, FDE_ENOMEM, FDE_ECUDA, FDE_ENOCONV, FDE_ENONFINITE, FDE_ETIM
 FDE_PREC_FP64, FDE_PREC_MIXED = 0, 1
 FDE_PRECOND_TPA, FDE_PRECOND_LEARNED = 0, 1
 FDE_PRECOND_PARAMS = 8641
+FDE_SMEAR_FERMI, FDE_SMEAR_MP, FDE_SMEAR_GAUSS = 0, 1, 2
+SMEAR_KINDS = {"fermi": FDE_SMEAR_FERMI, "mp": FDE_SMEAR_MP, "gauss": FDE_SMEAR_GAUSS}
 STATUS_NAMES = {0: "FDE_OK", -1: "FDE_EINVAL", -2: "FDE_ENOMEM", -3: "FDE_ECUDA", -4: "FDE_ENOCONV",
                 -5: "FDE_ENONFINITE", -6: "FDE_ETIMEOUT", -7: "FDE_EUNSUPPORTED"}
 
@@ -39,7 +41,7 @@ class SubsysDesc(C.Structure):
                 ("rc", C.c_double), ("nproj_per_atom", C.c_int), ("proj_sigma", C.POINTER(C.c_double)),
                 ("proj_D", C.POINTER(C.c_double)), ("nbands", C.c_int), ("nk", C.c_int),
                 ("kpts", C.POINTER(C.c_double)), ("wk", C.POINTER(C.c_double)), ("nelec", C.c_double),
-                ("smearing_ha", C.c_double)]
+                ("smearing_ha", C.c_double), ("smearing_kind", C.c_int)]
 
 
 class Energies(C.Structure):
@@ -79,6 +81,7 @@ EXPORTS = {
     "fde_apply_h_local_static": (C.c_int, [C.POINTER(CellDesc), C.POINTER(C.c_double), C.c_int, C.c_void_p,
                                            C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "fde_fft3d": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "fde_fft3d_f64": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int]),
     "fde_hot_step": (C.c_int, [C.c_void_p, C.c_int]),
     "fde_get_hpsi": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p]),
     "fde_gemm_hn_f32": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int,
@@ -87,9 +90,14 @@ EXPORTS = {
     "fde_set_tc_wait_limit": (C.c_int, [C.c_longlong]),
     "fde_host_sphere": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
     "fde_host_ewald": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
-    "fde_host_occupations": (C.c_int, [C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_void_p,
-                                       C.c_void_p, C.c_void_p]),
+    "fde_host_occupations": (C.c_int, [C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_int,
+                                       C.c_void_p, C.c_void_p, C.c_void_p]),
     "fde_host_pulay": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p]),
+    "fde_host_kmesh": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                 C.c_void_p]),
+    "fde_host_symmetry_ops": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_double, C.c_void_p,
+                                        C.c_void_p]),
+    "fde_set_symmetry": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "fde_tuned_plane_variant": (C.c_int, [C.c_int, C.c_int]),
     "fde_pin_plane_variant": (C.c_int, [C.c_int]),
     "fde_gemm_rot_f32": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int,
@@ -151,9 +159,9 @@ def tuned_plane_variant(n1: int, n3: int) -> int:
 
 
 def pin_plane_variant(variant: int) -> None:
-    """Pin the FP32 plane-pass variant (0..3) for this process, or -1 to return to tuning."""
+    """Pin the FP32 plane-pass variant (0..5) for this process, or -1 to return to tuning."""
     if load().fde_pin_plane_variant(int(variant)) != FDE_OK:
-        raise FDEError(FDE_EINVAL, "fde_pin_plane_variant: variant must be -1..3")
+        raise FDEError(FDE_EINVAL, "fde_pin_plane_variant: variant must be -1..5")
 
 
 def host_sphere(lengths, kfrac, ecut):
@@ -185,14 +193,15 @@ def host_ewald(lengths, pos, Z):
     return e.value
 
 
-def host_occupations(eig, wk, nelec, sigma):
-    """(occ [nk, nb], mu, sigma S) of the eigenvalues eig [nk, nb] (host code)."""
+def host_occupations(eig, wk, nelec, sigma, kind="fermi"):
+    """(occ [nk, nb], mu, sigma S) of the eigenvalues eig [nk, nb] (host code); kind is the
+    smearing ("fermi", "mp" first-order Methfessel-Paxton, "gauss")."""
     ev = np.ascontiguousarray(eig, dtype=np.float64)
     w = np.ascontiguousarray(wk, dtype=np.float64)
     occ = np.zeros_like(ev)
     mu, ts = C.c_double(), C.c_double()
     s = load().fde_host_occupations(int(ev.shape[0]), int(ev.shape[1]), _hptr(ev), _hptr(w), float(nelec),
-                                    float(sigma), _hptr(occ), C.byref(mu), C.byref(ts))
+                                    float(sigma), int(SMEAR_KINDS[kind]), _hptr(occ), C.byref(mu), C.byref(ts))
     if s != FDE_OK:
         raise FDEError(s, "fde_host_occupations")
     return occ, mu.value, ts.value
@@ -204,6 +213,39 @@ def host_pulay(overlap):
     c = np.zeros(ov.shape[0])
     s = load().fde_host_pulay(int(ov.shape[0]), _hptr(ov), _hptr(c))
     return c, s == FDE_OK
+
+
+def host_kmesh(q, shift=(0, 0, 0), time_reversal=True, ops=()):
+    """Irreducible Monkhorst-Pack points [nk, 3] (crystal) and weights [nk] (host code)."""
+    lib = load()
+    qa = np.ascontiguousarray(q, dtype=np.int32)
+    sh = np.ascontiguousarray(shift, dtype=np.float64)
+    oa = np.ascontiguousarray(ops if len(ops) else [0], dtype=np.int32)
+    n = C.c_int(0)
+    s = lib.fde_host_kmesh(_hptr(qa), _hptr(sh), int(bool(time_reversal)), int(len(ops)), _hptr(oa), C.byref(n),
+                           None, None)
+    if s != FDE_OK:
+        raise FDEError(s, "fde_host_kmesh")
+    k = np.zeros((n.value, 3))
+    w = np.zeros(n.value)
+    s = lib.fde_host_kmesh(_hptr(qa), _hptr(sh), int(bool(time_reversal)), int(len(ops)), _hptr(oa), C.byref(n),
+                           _hptr(k), _hptr(w))
+    if s != FDE_OK:
+        raise FDEError(s, "fde_host_kmesh")
+    return k, w
+
+
+def host_symmetry_ops(lengths, pos, Z, tol=1e-6):
+    """Sign-flip masks (identity first) that map the atoms onto themselves (host code)."""
+    L = np.ascontiguousarray(lengths, dtype=np.float64)
+    p = np.ascontiguousarray(np.asarray(pos).reshape(-1, 3), dtype=np.float64)
+    z = np.ascontiguousarray(Z, dtype=np.float64)
+    ops = np.zeros(8, dtype=np.int32)
+    n = C.c_int()
+    s = load().fde_host_symmetry_ops(_hptr(L), int(z.size), _hptr(p), _hptr(z), float(tol), C.byref(n), _hptr(ops))
+    if s != FDE_OK:
+        raise FDEError(s, "fde_host_symmetry_ops")
+    return ops[:n.value].tolist()
 
 
 def set_gemm_path(path: int) -> None:
@@ -287,7 +329,8 @@ class Context:
             pass
 
     # ---- setup --------------------------------------------------------------------------
-    def add_subsystem(self, pos, Z, rc, nbands, kpts, wk, nelec, smearing, proj_sigma=(), proj_D=()):
+    def add_subsystem(self, pos, Z, rc, nbands, kpts, wk, nelec, smearing, proj_sigma=(), proj_D=(),
+                      smearing_kind="fermi"):
         pos, ppos = _dbl(np.asarray(pos).reshape(-1, 3))
         Z, pZ = _dbl(Z)
         kpts, pk = _dbl(np.asarray(kpts).reshape(-1, 3))
@@ -295,7 +338,7 @@ class Context:
         sig, psig = _dbl(proj_sigma if len(proj_sigma) else [0.0])
         D, pD = _dbl(np.asarray(proj_D).reshape(-1) if len(proj_sigma) else [0.0])
         d = SubsysDesc(int(Z.size), ppos, pZ, float(rc), int(len(proj_sigma)), psig, pD, int(nbands),
-                       int(kpts.shape[0]), pk, pw, float(nelec), float(smearing))
+                       int(kpts.shape[0]), pk, pw, float(nelec), float(smearing), int(SMEAR_KINDS[smearing_kind]))
         sid = C.c_int()
         self._check(self.lib.fde_add_subsystem(self.h, C.byref(d), C.byref(sid)), "fde_add_subsystem")
         self.nsub += 1
@@ -382,6 +425,11 @@ class Context:
         e = Energies()
         s = self._check(self.lib.fde_scf_refresh(self.h, float(tol), int(max_scf), C.byref(e)), "fde_scf_refresh")
         return s, e.as_dict()
+
+    def set_symmetry(self, ops):
+        """Symmetrise the densities built from orbitals over the sign-flip masks ops."""
+        a = np.ascontiguousarray(ops, dtype=np.int32)
+        return self._check(self.lib.fde_set_symmetry(self.h, int(a.size), _hptr(a)), "fde_set_symmetry")
 
     def delta_rho(self, rho_ref):
         """1/2 int |rho - rho_ref| against a device grid rho_ref (torch float64, CUDA)."""
@@ -478,6 +526,10 @@ class Context:
     def fft3d(self, data, sign):
         return self._check(self.lib.fde_fft3d(self.h, _dptr(data), int(sign)), "fde_fft3d")
 
+    def fft3d_f64(self, data, sign, arith):
+        """The potential build's transform of a complex128 grid: arith 0 FP64, 1 double-float."""
+        return self._check(self.lib.fde_fft3d_f64(self.h, _dptr(data), int(sign), int(arith)), "fde_fft3d_f64")
+
     def launch_count(self):
         n = C.c_longlong()
         self._check(self.lib.fde_launch_count(self.h, C.byref(n)), "fde_launch_count")
@@ -514,7 +566,7 @@ def context_from_workload(wl: workloads.Workload, prec="fp64", stream=None) -> C
     ctx = Context(wl.lattice, wl.grid, wl.ecut, wl.xc, wl.kedf, wl.rho_cut, prec, stream)
     for s in wl.subsystems:
         ctx.add_subsystem(s.pos, s.Z, s.rc, s.nbands, s.kpts, s.wk, s.nelec, s.smearing,
-                          s.proj_sigma, s.proj_D)
+                          s.proj_sigma, s.proj_D, s.smearing_kind)
     return ctx
 
 

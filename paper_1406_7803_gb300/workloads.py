@@ -44,9 +44,10 @@ class Subsystem:
     kpts: np.ndarray  # [nk, 3] crystal coordinates
     wk: np.ndarray  # [nk], sums to 1
     nelec: float
-    smearing: float  # Fermi-Dirac width in Ha; 0 means integer occupations
+    smearing: float  # smearing width in Ha; 0 means integer occupations
     proj_sigma: Tuple[float, ...] = ()
     proj_D: Tuple[Tuple[float, ...], ...] = ()
+    smearing_kind: str = "fermi"  # "fermi", "mp" (first-order Methfessel-Paxton) or "gauss"
 
     @property
     def natoms(self) -> int:
@@ -193,6 +194,30 @@ def molecule_on_slab_small(seed: int = 1012) -> Workload:
                             mol_atoms=2, mol_bands=4, name="molecule-on-slab-8x8x20-24x24x60")
 
 
+def two_layer_slab_small(mp=(2, 2, 1), smearing_kind: str = "mp") -> Workload:
+    """The 2-layer slab of molecule_on_slab_small split into its two layers as subsystems (each
+    layer is mirror-symmetric in x and y about the origin, so the whole cell is too): 4 Z=3
+    atoms and 8 bands per layer on a Monkhorst-Pack mesh with Methfessel-Paxton smearing of
+    1e-2 Ry (Computational Details), PBE + revAPBEK, 2 KB projectors per atom."""
+    L = np.array([8.0, 8.0, 20.0])
+    pos, Z = _slab(2, 2, 2, L, 3.0, 2.0, 3)
+    kp, wk = _mp_mesh(*mp)
+    subs = [Subsystem(f"layer{l}", pos[4 * l:4 * l + 4].copy(), Z[4 * l:4 * l + 4].copy(), 0.5, 8, kp.copy(),
+                      wk.copy(), 12.0, 0.005, KB_SIGMA, KB_D, smearing_kind) for l in range(2)]
+    return Workload(name="two-layer-slab-8x8x20-24x24x60", lattice=np.diag(L), grid=(24, 24, 60), ecut=6.0,
+                    subsystems=subs, xc=XC_PBE, kedf=KEDF_REVAPBEK, seed=1013, tol=1e-6,
+                    description="two slab layers (4 atoms Z=3, 8 bands each) on a 2x2x1 mesh, MP smearing")
+
+
+def with_kpoints(wl: Workload, isub: int, kpts, wk) -> Workload:
+    """The same workload with the k-points and weights of one subsystem replaced."""
+    import dataclasses
+    subs = list(wl.subsystems)
+    subs[isub] = dataclasses.replace(subs[isub], kpts=np.asarray(kpts, dtype=np.float64).reshape(-1, 3),
+                                     wk=np.asarray(wk, dtype=np.float64))
+    return dataclasses.replace(wl, subsystems=subs)
+
+
 def batched_uneven(seed: int = 1003, nmol: int = 16) -> Workload:
     """A 54-atom slab (96 bands x 2 k-points) plus molecules with 8..64 bands at Gamma in a
     24 bohr cube on a 96^3 grid at 20 Ha."""
@@ -238,10 +263,39 @@ def supersystem(wl: Workload, extra_bands: int = 0) -> Workload:
                       nbands=sum(s.nbands for s in wl.subsystems) + extra_bands,
                       kpts=ref.kpts.copy(), wk=ref.wk.copy(),
                       nelec=float(sum(s.nelec for s in wl.subsystems)), smearing=ref.smearing,
-                      proj_sigma=tuple(ref.proj_sigma), proj_D=tuple(ref.proj_D))
+                      proj_sigma=tuple(ref.proj_sigma), proj_D=tuple(ref.proj_D),
+                      smearing_kind=ref.smearing_kind)
     return Workload(name=wl.name + "-supersystem", lattice=wl.lattice.copy(), grid=wl.grid, ecut=wl.ecut,
                     subsystems=[whole], xc=wl.xc, kedf=wl.kedf, seed=wl.seed, tol=wl.tol, rho_cut=wl.rho_cut,
                     description="supersystem KS reference of " + wl.name)
+
+
+def large_cell(seed: int = 1005, nmol: int = 32, slab_bands: int = 512, mp=(4, 2, 1)) -> Workload:
+    """A 30 x 30 x 60 bohr cell on a 144 x 144 x 288 grid at 25 Ha: a 216-atom Z=3 slab (6 layers
+    of 6 x 6 at 5 bohr, 2.5 bohr apart, alternate layers shifted) with 512 bands on an unreduced
+    4 x 2 x 1 Monkhorst-Pack mesh (8 k-points, Fermi smearing 0.01 Ha), plus 32 molecules of
+    16..48 bands (U{16..48}) at Gamma, floor(b/2) atoms of Z=4 each, centred in the vacuum above
+    the slab at least 5 bohr apart; PBE + revAPBEK, 2 KB projectors per atom."""
+    rng = np.random.default_rng(seed)
+    L = np.array([30.0, 30.0, 60.0])
+    spos, sZ = _slab(6, 6, 6, L, 2.5, 2.0, 3)
+    kp, wk = _mp_mesh(*mp)
+    subs = [Subsystem("slab", spos, sZ, 0.5, slab_bands, kp, wk, float(sZ.sum()), 0.01, KB_SIGMA, KB_D)]
+    bands = rng.integers(16, 49, size=nmol)
+    centres = []
+    for m in range(nmol):
+        for _ in range(100000):
+            c = np.array([rng.uniform(0, L[0]), rng.uniform(0, L[1]), rng.uniform(20.0, 52.0)])
+            if all(_min_image_dist(c, q, L) >= 5.0 for q in centres):
+                break
+        centres.append(c)
+        na = int(bands[m]) // 2
+        pos = _place_in_sphere(rng, na, c, 3.0, 0.8, L)
+        subs.append(Subsystem(f"mol{m}", pos, np.full(na, 4.0), 0.5, int(bands[m]),
+                              GAMMA[0].copy(), GAMMA[1].copy(), 4.0 * na, 0.0, KB_SIGMA, KB_D))
+    return Workload(name="large-30x30x60-144x144x288", lattice=np.diag(L), grid=(144, 144, 288), ecut=25.0,
+                    subsystems=subs, xc=XC_PBE, kedf=KEDF_REVAPBEK, seed=seed, tol=1e-6,
+                    description="slab 216 atoms (512 bands x 8 k) + 32 molecules of 16..48 bands")
 
 
 def raw_orbitals(seed: int, isub: int, ik: int, nbands: int, npw: int) -> np.ndarray:
@@ -295,4 +349,5 @@ WORKLOADS = {
     "molecule-on-slab-16x16x40-72x72x180": molecule_on_slab,
     "molecule-on-slab-8x8x20-24x24x60": molecule_on_slab_small,
     "batched-uneven-24cubed-96cubed": batched_uneven,
+    "large-30x30x60-144x144x288": large_cell,
 }

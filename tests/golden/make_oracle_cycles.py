@@ -21,12 +21,13 @@ ROOT = os.path.dirname(os.path.dirname(HERE))
 sys.path.insert(0, ROOT)
 
 OUT = os.path.join(HERE, "ft_cycle_molecule_on_slab_small.json")
+OUT_REFRESH = os.path.join(HERE, "refresh_two_layer_slab_small.json")
 KEYS = ("F_fde", "E_fde", "E_kin", "E_nl", "E_loc", "E_H", "E_xc", "T_nad", "TS")
 
 
-# The oracle modules the freeze-and-thaw cycle runs (the learned-preconditioner oracle is not
-# among them).
-CYCLE_MODULES = ("__init__.py", "basis.py", "fde.py", "functionals.py", "potentials.py", "scf.py")
+# The oracle modules the runs use (the learned-preconditioner oracle is not among them).
+CYCLE_MODULES = ("__init__.py", "basis.py", "fde.py", "functionals.py", "kmesh.py", "potentials.py", "refresh.py",
+                 "scf.py", "smearing.py")
 
 
 def oracle_digest() -> str:
@@ -40,22 +41,46 @@ def oracle_digest() -> str:
     return h.hexdigest()
 
 
-def main() -> int:
-    from oracle import fde as ofde, scf as oscf
-    from paper_1406_7803_gb300 import workloads
-    wl = workloads.molecule_on_slab_small()
-    sy = ofde.System(wl)
-    st = oscf.initial_state(sy)
-    t0 = time.perf_counter()
-    _, en = oscf.freeze_thaw_cycle(sy, st, tol=1e-10)
-    rec = {"workload": wl.name, "seed": wl.seed, "tol": 1e-10, "converged": bool(en["converged"]),
-           "inner_iters": [int(i) for i in en["iters"]], "seconds": time.perf_counter() - t0,
-           "energies": {k: float(en[k]) for k in KEYS}, "oracle_sha256": oracle_digest()}
-    with open(OUT, "w") as f:
+def _write(path, rec):
+    with open(path, "w") as f:
         json.dump(rec, f, indent=1)
         f.write("\n")
     print(json.dumps(rec))
-    return 0 if rec["converged"] else 1
+
+
+def main() -> int:
+    from oracle import fde as ofde, refresh, scf as oscf
+    from paper_1406_7803_gb300 import workloads
+    digest = oracle_digest()
+    ok = True
+    if "--refresh-only" not in sys.argv:
+        # one Jacobi freeze-and-thaw cycle of the slab + molecule cell (Fermi-Dirac slab)
+        wl = workloads.molecule_on_slab_small()
+        sy = ofde.System(wl)
+        st = oscf.initial_state(sy)
+        t0 = time.perf_counter()
+        _, en = oscf.freeze_thaw_cycle(sy, st, tol=1e-10)
+        rec = {"workload": wl.name, "seed": wl.seed, "tol": 1e-10, "converged": bool(en["converged"]),
+               "inner_iters": [int(i) for i in en["iters"]], "seconds": time.perf_counter() - t0,
+               "energies": {k: float(en[k]) for k in KEYS}, "oracle_sha256": digest}
+        _write(OUT, rec)
+        ok &= rec["converged"]
+    # the refreshed SCF of the two-layer slab on the full 2 x 2 x 1 mesh with Methfessel-Paxton
+    # smearing; its total density and the <Delta rho> against the supersystem KS run
+    wl = workloads.two_layer_slab_small()
+    sy = ofde.System(wl)
+    t0 = time.perf_counter()
+    st, en = refresh.scf_default_refresh(sy, oscf.initial_state(sy), tol=1e-10)
+    sup = workloads.supersystem(wl, extra_bands=4)
+    sk = ofde.System(sup)
+    st_ks, en_ks = refresh.scf_default_refresh(sk, oscf.initial_state(sk), tol=1e-10)
+    rec = {"workload": wl.name, "seed": wl.seed, "tol": 1e-10, "converged": bool(en["converged"] and en_ks["converged"]),
+           "steps": int(en["iters"]), "ks_steps": int(en_ks["iters"]), "seconds": time.perf_counter() - t0,
+           "energies": {k: float(en[k]) for k in KEYS}, "ks_energies": {k: float(en_ks[k]) for k in KEYS},
+           "delta_rho": refresh.delta_rho(sy, st.rhos.sum(axis=0), st_ks.rhos[0]), "oracle_sha256": digest}
+    _write(OUT_REFRESH, rec)
+    ok &= rec["converged"]
+    return 0 if ok else 1
 
 
 if __name__ == "__main__":

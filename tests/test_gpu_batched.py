@@ -4,7 +4,11 @@
 The embedding potentials of all 17 subsystems come out of one build (V_eff element by element
 against the oracle), and one hot step runs H psi for all 778 bands in one launch per phase
 (eagerly and replayed from a CUDA graph); sampled bands of every (subsystem, k) block are
-compared with the oracle's H psi.  Tolerances: FP64 1e-10, mixed 1e-5 relative per band."""
+compared with the oracle's H psi.  Tolerances: FP64 1e-10, mixed 1e-5 relative per band; for
+V_eff 1e-10 (1e-5 mixed) of max|V_eff| widened point by point by ten times the oracle's own
+change under rounding-level noise on its FFT gradients (the GGA potentials are ill-conditioned
+where the density is low and its gradient near zero: between the sparse slab atoms and in the
+vacuum)."""
 import numpy as np
 import pytest
 
@@ -30,6 +34,30 @@ def cell():
     sy = ofde.System(wl)
     rhos = np.array([workloads.initial_density(wl, I) for I in range(wl.nsub)])
     pot = sy.build_veff(rhos)
+    # The GGA potentials of this cell are ill-conditioned where the density is low and its
+    # gradient near zero (between the sparse slab atoms, 8 bohr apart, and in the vacuum): there
+    # s = |grad rho| / rho^{4/3} and the direction grad rho / |grad rho| follow the rounding of
+    # the FFT gradients.  The oracle's own response to that rounding -- additive noise of
+    # 1e-15 x max|grad rho| on its gradients, two seeded draws -- widens the FP64 tolerance
+    # point by point (it exceeds 1e-11 of max|V_eff| at most points of this cell).
+    from oracle import functionals as fn
+    rng = np.random.default_rng(17)
+    exact_gradient = fn.gradient
+
+    def rounded_gradient(f, lattice):
+        g = exact_gradient(f, lattice)
+        scale = max(float(np.abs(c).max()) for c in g)
+        return [c + 1e-15 * scale * rng.standard_normal(c.shape) for c in g]
+
+    sens = np.zeros_like(pot["veff"])
+    fn.gradient = rounded_gradient
+    try:
+        for _ in range(2):
+            p = sy.build_veff(rhos)
+            sens = np.maximum(sens, np.abs(np.array(p["veff"]) - np.array(pot["veff"])))
+    finally:
+        fn.gradient = exact_gradient
+    pot["sensitivity"] = sens
     return wl, sy, rhos, pot
 
 
@@ -58,8 +86,12 @@ def test_batched_uneven_veff_matches_oracle(cell, prec, tol):
     torch.cuda.synchronize()
     got = out.cpu().numpy()
     for I in range(wl.nsub):
-        err = np.abs(got[I] - pot["veff"][I]).max() / np.abs(pot["veff"][I]).max()
-        assert err < tol, (I, err)
+        scale = np.abs(pot["veff"][I]).max()
+        diff = np.abs(got[I] - pot["veff"][I])
+        allowed = tol * scale + 10.0 * pot["sensitivity"][I]
+        assert np.all(diff <= allowed), (I, diff.max() / scale, float(np.max(diff / allowed)))
+        # where the potential is well conditioned the bound is the plain one
+        assert np.median(diff) < 0.1 * tol * scale, (I, float(np.median(diff)) / scale)
 
 
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("mixed", 1e-5)])

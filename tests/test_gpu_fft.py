@@ -40,3 +40,27 @@ def test_fft3d_matches_oracle(shape, prec, tol):
         got = d.to(torch.complex128).cpu().numpy()
         err = np.abs(got - want).max() / np.abs(want).max()
         assert err < tol, (shape, prec, sign, err)
+
+
+DD_SHAPES = [(24, 24, 60), (72, 72, 180), (96, 96, 96), (32, 32, 288), (144, 96, 32)]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("shape", DD_SHAPES)
+def test_potential_build_transforms_match_oracle(shape, prec):
+    """The potential build's transforms of FP64 grids: native FP64 to 1e-13 of the largest
+    output, double-float (two floats per value on the FP32 pipes, as the mixed path transforms
+    the densities and their gradients) to 2e-13 -- far below FP32's ~1e-6 (above), near FP64.
+    The input spans 30 orders of magnitude, like densities between the atoms and the vacuum."""
+    lat = np.diag([10.0, 11.0, 12.0])
+    ctx = fde.Context(lat, shape, 1.0, workloads.XC_LDA, workloads.KEDF_TF, prec=prec)
+    rng = np.random.default_rng(sum(shape) + 1)
+    f = (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)) * 10.0 ** rng.uniform(-30, 0, shape)
+    for arith, tol in ((0, 1e-13), (1, 2e-13)):
+        for sign, want in ((-1, basis.G_from_r(f)), (+1, basis.r_from_G(f))):
+            d = torch.from_numpy(f).to("cuda")
+            ctx.fft3d_f64(d, sign, arith)
+            torch.cuda.synchronize()
+            got = d.cpu().numpy()
+            err = np.abs(got - want).max() / np.abs(want).max()
+            assert err < tol, (shape, prec, arith, sign, err)

@@ -173,7 +173,7 @@ def slab_system():
     return wl, ofde.System(wl)
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5])
 def test_every_plane_variant_matches_oracle(slab_system, variant):
     """Each compiled variant of the FP32 plane pass (register budget, CTAs per SM, radix order),
     pinned in turn, gives the oracle's H psi on the full-size molecule-on-slab cell's batched

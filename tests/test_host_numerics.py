@@ -69,6 +69,22 @@ def test_fermi_occupations_equal_oracle():
     assert abs(2.0 * np.sum(wk[:, None] * occ) - 18.0) < 1e-12
 
 
+@pytest.mark.parametrize("kind", ["mp", "gauss"])
+def test_methfessel_paxton_and_gaussian_occupations_equal_oracle(kind):
+    """The host's closed forms (first-order Methfessel-Paxton, Gaussian) against the oracle's
+    general-order Hermite construction with its entropy term by quadrature."""
+    rng = np.random.default_rng(6)
+    eig = np.sort(rng.uniform(-1.0, 0.5, (4, 16)), axis=1)
+    wk = np.full(4, 0.25)
+    sigma = 0.005  # 1e-2 Ry (Computational Details)
+    occ, mu, ts = fde.host_occupations(eig, wk, 18.0, sigma, kind)
+    o_occ, o_mu, o_S = scf.occupations(list(eig), wk, 18.0, sigma, kind)
+    assert np.abs(occ - np.array(o_occ)).max() < 1e-12
+    assert abs(mu - o_mu) < 1e-12
+    assert abs(ts - sigma * o_S) < 1e-13
+    assert abs(2.0 * np.sum(wk[:, None] * occ) - 18.0) < 1e-12
+
+
 def test_integer_occupations_and_argument_checks():
     eig = np.array([[0.3, -0.2, 0.1, -0.5, 0.9]])
     occ, mu, ts = fde.host_occupations(eig, [1.0], 6.0, 0.0)
@@ -114,5 +130,24 @@ def test_host_entry_points_reject_bad_arguments():
     assert lib.fde_host_sphere(fde._hptr(L), fde._hptr(np.zeros(3)), -1.0, fde.C.byref(n), None, None) == fde.FDE_EINVAL
     assert lib.fde_host_sphere(fde._hptr(-L), fde._hptr(np.zeros(3)), 1.0, fde.C.byref(n), None, None) == fde.FDE_EINVAL
     assert lib.fde_host_ewald(fde._hptr(L), 0, None, None, fde.C.byref(e)) == fde.FDE_EINVAL
-    assert lib.fde_host_occupations(0, 1, None, None, 2.0, 0.0, None, None, None) == fde.FDE_EINVAL
+    assert lib.fde_host_occupations(0, 1, None, None, 2.0, 0.0, 0, None, None, None) == fde.FDE_EINVAL
     assert lib.fde_host_pulay(0, None, None) == fde.FDE_EINVAL
+
+
+@pytest.mark.parametrize("q,shift,ops,tr", [((2, 2, 1), (0, 0, 0), (), True), ((2, 2, 1), (0, 0, 0), (1, 2, 3), True),
+                                            ((3, 3, 1), (0, 0, 0), (), True), ((4, 2, 2), (1, 0, 0), (1,), False),
+                                            ((4, 4, 1), (0, 0, 0), (1, 2, 3), True), ((1, 1, 1), (0, 0, 0), (), True)])
+def test_kmesh_equals_oracle(q, shift, ops, tr):
+    from oracle import kmesh
+    k, w = fde.host_kmesh(q, shift, tr, ops)
+    ko, wo = kmesh.reduce_mesh(kmesh.monkhorst_pack(q, shift), ops, tr)
+    assert np.array_equal(k, ko) and np.allclose(w, wo, rtol=0, atol=1e-15)
+    assert abs(w.sum() - 1.0) < 1e-14
+
+
+def test_symmetry_ops_equal_oracle():
+    from oracle import kmesh
+    for wl in (workloads.two_layer_slab_small(), workloads.molecule_on_slab_small(), workloads.molecule_on_slab()):
+        L = np.diag(wl.lattice)
+        for s in wl.subsystems + workloads.supersystem(wl).subsystems:
+            assert fde.host_symmetry_ops(L, s.pos, s.Z) == kmesh.symmetry_ops(wl.lattice, s.pos, s.Z)
