@@ -93,7 +93,14 @@ typedef struct {
  * smearing_kind (Computational Details: Methfessel-Paxton for the metallic subsystems;
  * FDE_SMEAR_MP is the first-order form, FDE_SMEAR_GAUSS the zeroth, FDE_SMEAR_FERMI
  * Fermi-Dirac); 0: integer occupations (then nk must be 1 and nelec/2 an integer <= nbands).
- * All arrays are host memory and are copied. */
+ * aug_sigma > 0 makes the atoms ultrasoft-like (Appendix: PAW / ultrasoft pseudopotentials with
+ * subsystem-specific projectors; here a model of them): the projectors also define the overlap
+ * S_I = 1 + sum_{a in I} sum_ij |beta_ai> q_ij <beta_aj| with proj_Q = q [nproj_per_atom]^2
+ * (symmetric, positive definite), the subsystem's eigenproblem becomes H_I psi = e S_I psi, its
+ * density gains the augmentation charges q_ij g_a(r) <psi|beta_ai><beta_aj|psi> with g_a the
+ * normalised Gaussian (pi aug_sigma^2)^{-3/2} exp(-|r - R_a|^2 / aug_sigma^2), and each atom's
+ * coupling is screened, D_a = D + q int V_eff^I g_a.  aug_sigma = 0: norm-conserving (proj_Q
+ * unused).  All arrays are host memory and are copied. */
 typedef struct {
   int natoms;
   const double* pos;
@@ -109,6 +116,8 @@ typedef struct {
   double nelec;
   double smearing_ha;
   int smearing_kind;
+  const double* proj_Q;
+  double aug_sigma;
 } fde_subsys_desc;
 
 /* Energy terms of Eq. E_FDE (Sec. 2) for the current densities and orbitals:
@@ -173,6 +182,11 @@ fde_status fde_set_veff(fde_ctx* ctx, int sub, const double* d_veff);
  * FDE_PREC_MIXED contexts; they must not overlap.  Asynchronous on the context stream. */
 fde_status fde_apply_h(fde_ctx* ctx, int sub, int k, const void* d_psi, void* d_hpsi, int nb);
 
+/* The subsystem's overlap S_I psi = psi + sum_{a in I} sum_ij beta_ai q_ij <beta_aj|psi> for a block
+ * of nb orbitals of (sub, k) (Appendix: subsystem-specific PAW / ultrasoft projectors; a copy of
+ * psi for norm-conserving subsystems).  Layout and precision as fde_apply_h; asynchronous. */
+fde_status fde_apply_s(fde_ctx* ctx, int sub, int k, const void* d_psi, void* d_spsi, int nb);
+
 /* Same as fde_apply_h with host buffers (complex double [nb][npw] in both precisions);
  * synchronising.  Page-locked buffers (cudaHostAlloc, cudaMallocHost or cudaHostRegister) are
  * copied directly by the copy engines; pageable ones go through a page-locked staging buffer
@@ -192,7 +206,8 @@ fde_status fde_apply_h_all(fde_ctx* ctx);
 fde_status fde_hot_step(fde_ctx* ctx, int use_graph);
 
 /* Copy the stored H psi of (sub, k) (written by fde_apply_h_all / fde_hot_step and by the
- * eigensolver) to a caller device buffer, complex double [nbands][npw]. */
+ * eigensolver) to a caller device buffer, complex double [nbands][npw].  Asynchronous on
+ * the context stream: read d_hpsi from another stream only after fde_sync. */
 fde_status fde_get_hpsi(fde_ctx* ctx, int sub, int k, double* d_hpsi);
 
 /* Initial orbitals of (sub, k) from raw complex draws h_raw [nbands][npw][2] (host):
@@ -200,7 +215,9 @@ fde_status fde_get_hpsi(fde_ctx* ctx, int sub, int k, double* d_hpsi);
 fde_status fde_init_orbitals(fde_ctx* ctx, int sub, int k, const double* h_raw);
 
 /* Replace / read the stored orbitals of (sub, k): device complex double [nbands][npw].
- * h_eig, h_occ (nullable): host [nbands] eigenvalues and occupations. */
+ * h_eig, h_occ (nullable): host [nbands] eigenvalues and occupations.  fde_set_orbitals is
+ * asynchronous on the context stream: d_psi must stay valid (and unchanged) until the stream
+ * has consumed it (fde_sync); fde_get_orbitals synchronises. */
 fde_status fde_set_orbitals(fde_ctx* ctx, int sub, int k, const double* d_psi);
 fde_status fde_get_orbitals(fde_ctx* ctx, int sub, int k, double* d_psi, double* h_eig,
                             double* h_occ);
@@ -224,9 +241,14 @@ fde_status fde_update_density(fde_ctx* ctx, int sub);
  * network: three tanh layers of width 64 and a linear output on the features
  * (log(1 + y), log T_j, |R_jG| / rms_G |R_j|).  Parameters: FDE_PRECOND_PARAMS floats,
  * W1[64][3] b1[64] W2[64][64] b2[64] W3[64][64] b3[64] W4[64] b4.  Inference uses the
- * weights rounded to bfloat16 with FP32 accumulation; training keeps FP32 master weights.
+ * weights rounded to bfloat16 with FP32 accumulation: the two 64 x 64 layers as BF16
+ * tensor-core MMAs (activations split into two bf16 terms, ~2^-18 relative; the default) or
+ * on the CUDA cores (fde_set_precond_path); training keeps FP32 master weights.
  * Training pairs (R, D): D the ideal correction of residual R.  The loss is
  * sum_j sum_G |m_jG R_jG - D_jG|^2 / |D_j|^2; training takes full-batch Adam steps. */
+/* Where the learned preconditioner's inference runs, process-wide: 1 tensor cores (default),
+ * 0 CUDA cores.  FDE_EINVAL for other values. */
+fde_status fde_set_precond_path(int path);
 fde_status fde_set_precond(fde_ctx* ctx, int precond); /* preconditioner of fde_scf_subsystem /
                                                           fde_freeze_thaw_cycle solves */
 fde_status fde_precond_set_weights(fde_ctx* ctx, const float* h_params);      /* resets Adam */
@@ -388,7 +410,8 @@ fde_status fde_gemm_rot_f32(fde_ctx* ctx, const void* d_X, int ldx, const double
 fde_status fde_set_gemm_path(int path);
 
 /* Poll limit of the waits a tensor-core product makes for each shared-memory stage of its
- * K loop (diagnostic support; no counterpart in the paper).  Every device wait of the
+ * K loop, and of the waits of the learned preconditioner's tensor-core inference for each
+ * layer's MMAs (diagnostic support; no counterpart in the paper).  Every device wait of the
  * library is bounded: when a stage wait runs out the kernel stops issuing, waits (with the
  * full bound, about a second) for the MMAs it has issued, releases its tensor memory, writes
  * no result and the call returns FDE_ETIMEOUT.  polls = 0 makes every stage wait run out at
@@ -400,14 +423,15 @@ fde_status fde_set_tc_wait_limit(long long polls);
 
 /* The FP32 plane pass of H psi (the (x, y) transforms, potential multiply and back) comes in
  * several compiled variants (register budget per thread, CTAs per SM, radix order of the
- * 72-point transforms).  The first large batch of a grid shape times each once on the batch
+ * line transforms, fused x pass).  The first large batch of a grid shape times each once on the batch
  * itself and keeps the fastest (measurement support; no counterpart in the paper).  Returns the
  * variant chosen for plane side n1 and z length n3, or -1 if none was tuned yet; the
  * environment variable FDE_PLANE_VARIANT pins one. */
 int fde_tuned_plane_variant(int n1, int n3);
-/* Pin the plane-pass variant used from now on in this process (0 .. 5; 4 and 5 are the warp-local
- * variants whose line transforms synchronise only their warp), or return to tuning
- * (-1).  FDE_EINVAL for other values. */
+/* Pin the plane-pass variant used from now on in this process (0 .. 5; 4 and 5 fuse the x pass:
+ * the inverse transform's last stage, the potential multiply and the forward transform's first
+ * stage on the same registers; FP64 plane passes run a pinned 4 as 4 and any other as 0), or
+ * return to tuning (-1).  FDE_EINVAL for other values. */
 fde_status fde_pin_plane_variant(int variant);
 
 /* ---- host-side numerics (no device work; usable without a GPU) --------------------------

@@ -47,6 +47,10 @@ class System:
         self.basis = []  # [I][k] -> (miller, kin)
         self.proj = []  # [I][k] -> beta [nproj, npw]
         self.Dmat = []  # [I] -> block-diagonal coupling
+        # [I] -> block-diagonal augmentation coefficients q of ultrasoft-like atoms (None: the
+        # subsystem is norm-conserving)
+        self.Qmat = [potentials.kb_coupling(s.natoms, s.proj_Q) if getattr(s, "aug_sigma", 0.0) > 0 else None
+                     for s in self.subs]
         for s in self.subs:
             bk, pk = [], []
             for k in s.kpts:
@@ -72,12 +76,26 @@ class System:
         return basis.r_from_G(basis.to_grid(coef, mil, self.grid)) / np.sqrt(self.omega)
 
     def density(self, I, coefs, occ):
-        """rho_I(r) = 2 sum_k w_k sum_j n_jk |u_jk(r)|^2."""
+        """rho_I(r) = 2 sum_k w_k sum_j n_jk |u_jk(r)|^2, plus for ultrasoft-like atoms the
+        augmentation sum_a g_a(r) sum_ij q_ij 2 sum_k w_k sum_j n_jk Re <u|beta_ai><beta_aj|u>
+        (it makes int rho_I = N_I for S-normalised orbitals)."""
         s = self.subs[I]
         rho = np.zeros(self.grid)
         for k in range(s.nk):
             u = self.orbitals_r(I, k, coefs[k])
             rho += 2.0 * s.wk[k] * np.einsum("j,jxyz->xyz", occ[k], np.abs(u) ** 2)
+        if self.uspp(I):
+            npj = len(s.proj_sigma)
+            q = np.asarray(s.proj_Q, dtype=np.float64)
+            ca = np.zeros(s.natoms)
+            for k in range(s.nk):
+                P = self.proj[I][k].conj() @ np.atleast_2d(coefs[k]).T  # [natoms * npj, nb]
+                for a in range(s.natoms):
+                    Pa = P[a * npj:(a + 1) * npj]
+                    B = np.real(Pa.conj() @ (occ[k][:, None] * Pa.T))  # sum_j n_j conj(P_i) P_i'
+                    ca[a] += 2.0 * s.wk[k] * float(np.sum(q * B))
+            rho += np.real(basis.r_from_G(potentials.augmentation_G(self.lattice, self.grid, s.pos, ca,
+                                                                       s.aug_sigma)))
         return rho
 
     # ------------------------------------------------------------ potentials
@@ -117,10 +135,42 @@ class System:
             out.append(self.vloc_sub[I] + vH[I] + vxc_I[I] + vemb)
         return out
 
+    # ------------------------------------------------------------ ultrasoft-like atoms
+    def uspp(self, I):
+        return self.Qmat[I] is not None and self.Qmat[I].size > 0
+
+    def coupling(self, I, veff_I):
+        """Nonlocal coupling of subsystem I: the bare D, plus for ultrasoft-like atoms the
+        screening q_ij int v_eff^I g_a (the augmentation charges q_ij g_a sit in the density, so
+        the energy's derivative by <psi|beta_i><beta_j|psi> picks up their potential energy)."""
+        if not self.uspp(I):
+            return self.Dmat[I]
+        s = self.subs[I]
+        ov = potentials.augmentation_overlaps(self.lattice, self.grid, s.pos, s.aug_sigma, veff_I)
+        q = np.asarray(s.proj_Q, dtype=np.float64)
+        return self.Dmat[I] + np.kron(np.diag(ov), q)
+
+    def apply_s(self, I, k, coef):
+        """S_I psi = psi + sum_{a in I} beta q <beta|psi> (identity for norm-conserving I)."""
+        coef = np.atleast_2d(coef)
+        if not self.uspp(I):
+            return coef.copy()
+        beta = self.proj[I][k]
+        return coef + (beta.T @ (self.Qmat[I] @ (beta.conj() @ coef.T))).T
+
+    def dense_s(self, I, k):
+        npw = self.basis[I][k][0].shape[0]
+        S = np.eye(npw, dtype=np.complex128)
+        if self.uspp(I):
+            beta = self.proj[I][k]
+            S = S + beta.T @ self.Qmat[I] @ beta.conj()
+        return S
+
     # ------------------------------------------------------------ Hamiltonian
-    def apply_h(self, I, k, coef, veff_I):
+    def apply_h(self, I, k, coef, veff_I, coupling=None):
         """H_I psi for a block of orbitals [nb, npw], FFT form:
-        1/2|k+G|^2 c_G + P_sphere FFT[v_eff . IFFT c] + sum_{a in I} beta D <beta|psi>."""
+        1/2|k+G|^2 c_G + P_sphere FFT[v_eff . IFFT c] + sum_{a in I} beta D <beta|psi>
+        (D screened for ultrasoft-like atoms; ``coupling`` may pass it precomputed)."""
         mil, kin = self.basis[I][k]
         coef = np.atleast_2d(coef)
         psi_r = basis.r_from_G(basis.to_grid(coef, mil, self.grid))
@@ -128,8 +178,9 @@ class System:
         out = kin[None, :] * coef + loc
         beta = self.proj[I][k]
         if beta.shape[0]:
+            D = self.coupling(I, veff_I) if coupling is None else coupling
             P = beta.conj() @ coef.T
-            out = out + (beta.T @ (self.Dmat[I] @ P)).T
+            out = out + (beta.T @ (D @ P)).T
         return out
 
     def dense_h(self, I, k, veff_I):
@@ -142,7 +193,7 @@ class System:
         H = H + np.diag(kin)
         beta = self.proj[I][k]
         if beta.shape[0]:
-            H = H + beta.T @ self.Dmat[I] @ beta.conj()
+            H = H + beta.T @ self.coupling(I, veff_I) @ beta.conj()
         return H
 
     # ------------------------------------------------------------ energies

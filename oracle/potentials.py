@@ -152,3 +152,35 @@ def kb_coupling(natoms, D):
     if D.size == 0:
         return np.zeros((0, 0))
     return np.kron(np.eye(natoms), D)
+
+
+def augmentation_G(lattice, grid, pos, coef, sigma):
+    """sum_a coef_a g_a(G) for the normalised Gaussians g_a(r) = (pi sigma^2)^{-3/2}
+    exp(-|r - R_a|^2 / sigma^2) of the ultrasoft-like augmentation charges (Appendix,
+    subsystem-specific projectors; the paper's PAW/ultrasoft data are replaced by this model):
+    g_a(G) = (1/Omega) exp(-G^2 sigma^2 / 4) exp(-i G.R_a), Nyquist planes zero, so that
+    int g_a = 1 on the grid."""
+    omega = basis.volume(lattice)
+    (gx, gy, gz), g2 = basis.grid_gvectors(lattice, grid)
+    shape = np.exp(-g2 * sigma * sigma / 4.0) / omega
+    out = np.zeros(tuple(grid), dtype=np.complex128)
+    for p, c in zip(np.asarray(pos, dtype=np.float64).reshape(-1, 3), np.asarray(coef, dtype=np.float64)):
+        out += c * shape * np.exp(-1j * (gx * p[0] + gy * p[1] + gz * p[2]))
+    out[basis.nyquist_mask(grid)] = 0.0
+    return out
+
+
+def augmentation_overlaps(lattice, grid, pos, sigma, v_r):
+    """int v(r) g_a(r) dr for every atom a, with g_a the grid augmentation shape above:
+    Parseval, (Omega / N_r) sum_r v g_a = Omega sum_G v(G) conj(g_a(G))."""
+    omega = basis.volume(lattice)
+    (gx, gy, gz), g2 = basis.grid_gvectors(lattice, grid)
+    vG = basis.G_from_r(v_r)
+    vG[basis.nyquist_mask(grid)] = 0.0
+    shape = np.exp(-g2 * sigma * sigma / 4.0)
+    out = []
+    for p in np.asarray(pos, dtype=np.float64).reshape(-1, 3):
+        out.append(float(np.real(np.sum(vG * shape * np.exp(1j * (gx * p[0] + gy * p[1] + gz * p[2]))))))
+    del omega
+    return np.array(out)
+

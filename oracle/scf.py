@@ -78,26 +78,49 @@ def occupations(eigs, wk, nelec, smearing, kind="fermi"):
 
 # ---------------------------------------------------------------- eigensolvers
 def eig_dense(system, I, k, veff_I, nb):
+    """Lowest nb eigenpairs of H psi = e S psi (S = 1 for norm-conserving subsystems) by
+    LAPACK; the eigenvectors are S-orthonormal."""
     H = system.dense_h(I, k, veff_I)
-    w, v = scipy.linalg.eigh(H, subset_by_index=[0, nb - 1])
+    if system.uspp(I):
+        w, v = scipy.linalg.eigh(H, system.dense_s(I, k), subset_by_index=[0, nb - 1])
+    else:
+        w, v = scipy.linalg.eigh(H, subset_by_index=[0, nb - 1])
     return w, v.T.copy()
 
 
 def eig_lanczos(system, I, k, veff_I, nb, guess=None, tol=1e-13):
+    """The same by ARPACK's Lanczos on the FFT-form H (generalised mode with S and its inverse
+    S^{-1} = 1 - B^H (q^{-1} + B B^H)^{-1} B, B the projector rows, for ultrasoft-like I)."""
     mil, kin = system.basis[I][k]
     npw = mil.shape[0]
+    D = system.coupling(I, veff_I)
 
     def mv(x):
-        return system.apply_h(I, k, x.reshape(1, -1), veff_I).reshape(-1)
+        return system.apply_h(I, k, x.reshape(1, -1), veff_I, coupling=D).reshape(-1)
 
     op = scipy.sparse.linalg.LinearOperator((npw, npw), matvec=mv, dtype=np.complex128)
+    M = Minv = None
+    if system.uspp(I):
+        B = system.proj[I][k].conj()  # rows <beta|
+        Q = system.Qmat[I]
+        inner = np.linalg.inv(np.linalg.inv(Q) + B @ B.conj().T)
+        M = scipy.sparse.linalg.LinearOperator(
+            (npw, npw), matvec=lambda x: system.apply_s(I, k, x.reshape(1, -1)).reshape(-1), dtype=np.complex128)
+        Minv = scipy.sparse.linalg.LinearOperator(
+            (npw, npw), matvec=lambda x: x.reshape(-1) - B.conj().T @ (inner @ (B @ x.reshape(-1))),
+            dtype=np.complex128)
     v0 = None
     if guess is not None:
         v0 = np.asarray(guess).sum(axis=0)
     ncv = min(npw, max(2 * nb + 20, 40))
-    w, v = scipy.sparse.linalg.eigsh(op, k=nb, which="SA", tol=tol, v0=v0, ncv=ncv, maxiter=20000)
+    w, v = scipy.sparse.linalg.eigsh(op, k=nb, M=M, Minv=Minv, which="SA", tol=tol, v0=v0, ncv=ncv,
+                                     maxiter=20000)
     order = np.argsort(w)
-    return w[order], v[:, order].T.copy()
+    v = v[:, order].T.copy()
+    if system.uspp(I):  # S-normalise (eigsh returns M-orthonormal vectors; renormalise exactly)
+        nrm = np.real(np.sum(v.conj() * system.apply_s(I, k, v), axis=1))
+        v = v / np.sqrt(nrm)[:, None]
+    return w[order], v
 
 
 def eigensolve(system, I, k, veff_I, nb, guess=None, dense_max=0):

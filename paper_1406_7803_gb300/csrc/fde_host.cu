@@ -153,6 +153,13 @@ template <typename T> struct Sub {
   DBuf<double> rho, veff;
   DBuf<T> vplane;
   double entropy = 0, mu = 0;
+  // ultrasoft-like augmentation (aug_sigma > 0): overlap S = 1 + sum_a |beta_a> q <beta_a|,
+  // charges q_ij g_a(r) in the density, and the coupling of each atom screened by its potential
+  bool uspp = false;
+  double aug_sigma = 0;
+  std::vector<double> Q;
+  KbBlock Qblk{};
+  DBuf<double> aug_pos, Dscr;
 };
 
 struct EnergyParts {
@@ -171,6 +178,7 @@ struct Engine {
   virtual void apply_h(int sub, int k, const void* psi, void* hpsi, int nb) = 0;
   virtual void apply_h_host(int sub, int k, const double* psi, double* hpsi, int nb) = 0;
   virtual void apply_h_all() = 0;
+  virtual void apply_s_dev(int sub, int k, const void* psi, void* spsi, int nb) = 0;
   virtual void init_orbitals(int sub, int k, const double* raw) = 0;
   virtual void set_orbitals(int sub, int k, const double* d_psi) = 0;
   virtual void get_orbitals(int sub, int k, double* d_psi, double* eig, double* occ) = 0;
@@ -358,6 +366,8 @@ template <typename T> struct EngineT : Engine {
     }
     if (sizeof(T) == 4 && (gemm_tc_take_status(st) & ST_TIMEOUT))
       throw Err{FDE_ETIMEOUT, "a tensor-core product timed out waiting for its MMAs"};
+    if (precond_tc_take_status(st) & ST_TIMEOUT)
+      throw Err{FDE_ETIMEOUT, "the learned preconditioner's tensor-core inference timed out"};
   }
 
   // ---- basis ------------------------------------------------------------------------------
@@ -482,6 +492,22 @@ template <typename T> struct EngineT : Engine {
     if (s->nproj) {
       s->Dblk.np = s->nproj_atom;
       for (int i = 0; i < s->nproj_atom * s->nproj_atom; ++i) s->Dblk.d[i] = s->D[i];
+    }
+    if (d->aug_sigma > 0) {
+      REQ(s->nproj > 0 && d->proj_Q, FDE_EINVAL, "augmentation needs projectors and their q matrix");
+      s->uspp = true;
+      s->aug_sigma = d->aug_sigma;
+      s->Q.assign(d->proj_Q, d->proj_Q + s->nproj_atom * s->nproj_atom);
+      s->Qblk.np = s->nproj_atom;
+      for (int i = 0; i < s->nproj_atom * s->nproj_atom; ++i) s->Qblk.d[i] = s->Q[i];
+      s->aug_pos.alloc(3 * (size_t)s->natoms);
+      CK(cudaMemcpy(s->aug_pos.p, s->pos.data(), 3 * (size_t)s->natoms * sizeof(double), cudaMemcpyHostToDevice));
+      // the screened couplings start as the bare one (until the first potential)
+      std::vector<double> d0((size_t)s->natoms * s->nproj_atom * s->nproj_atom);
+      for (int a = 0; a < s->natoms; ++a)
+        std::copy(s->D.begin(), s->D.end(), d0.begin() + (size_t)a * s->nproj_atom * s->nproj_atom);
+      s->Dscr.alloc(d0.size());
+      CK(cudaMemcpy(s->Dscr.p, d0.data(), d0.size() * sizeof(double), cudaMemcpyHostToDevice));
     }
     s->rho.alloc(nr);
     s->veff.alloc(nr);
@@ -702,10 +728,12 @@ template <typename T> struct EngineT : Engine {
       if (pa) {
         grid_nonfinite(A.veff.p, nr, status.p, st);
         to_plane(A);
+        refresh_screening(A);
       }
       if (pb) {
         grid_nonfinite(B->veff.p, nr, status.p, st);
         to_plane(*B);
+        refresh_screening(*B);
       }
     }
     EnergyParts ep;
@@ -727,14 +755,8 @@ template <typename T> struct EngineT : Engine {
   }
   void neg_add(double* a, const double* b) { grid_axpy(a, b, -1.0, nr, st); }
   // Plane-major copy of V_eff^I in the working precision for the plane pass of H psi:
-  // [i3][i1][i2], or [i3][i2][i1] for the mixed path's compile-time kernels.
+  // [i3][i1][i2].
   void to_plane(Sub<T>& s) {
-    if constexpr (sizeof(T) == 4) {
-      if (hpsi_plane_transposed_f32(g)) {
-        launch_to_plane_t(s.veff.p, s.vplane.p, g, st);
-        return;
-      }
-    }
     launch_transpose<double, T>(s.veff.p, s.vplane.p, (int)((long long)g.n1 * g.n2), g.n3, 0, st);
   }
 
@@ -761,6 +783,30 @@ template <typename T> struct EngineT : Engine {
     Sub<T>& s = sub(i);
     CK(cudaMemcpyAsync(s.veff.p, d_v, nr * sizeof(double), cudaMemcpyDeviceToDevice, st));
     to_plane(s);
+    refresh_screening(s);
+  }
+
+  // Screened couplings of an ultrasoft-like subsystem from its current V_eff^I:
+  // D_a = D + q int V_eff^I g_a, the integral by Parseval against V_eff^I's transform.
+  void refresh_screening(Sub<T>& s) {
+    if (!s.uspp) return;
+    double2* C = cb[0].p;
+    grid_pack2(s.veff.p, nullptr, C, nr, st);
+    launch_fft3d<double>(C, g, plans64.fp, -1, st);
+    grid_scale_c<double>(C, 1.0 / (double)nr, nr, st);
+    grid_aug_screening(C, g, cell, s.aug_pos.p, s.natoms, s.aug_sigma, s.Dblk, s.Qblk, s.Dscr.p, st);
+  }
+
+  // S_I psi = psi + sum_{a in I} beta q <beta|psi> (a copy of psi for norm-conserving I).
+  void apply_s(Sub<T>& s, KP<T>& q, const C* psi, C* spsi, int nb) {
+    CK(cudaMemcpyAsync(spsi, psi, (size_t)nb * q.npw * sizeof(C), cudaMemcpyDeviceToDevice, st));
+    if (!s.uspp) return;
+    gwork.ensure(gemm_hn_work(s.nproj, nb, q.npw));
+    Pm.ensure((size_t)s.nproj * nb);
+    Qm.ensure((size_t)s.nproj * nb);
+    launch_gemm_hn<T>(q.beta.p, q.npw, psi, q.npw, s.nproj, nb, q.npw, Pm.p, nb, gwork.p, st);
+    launch_kb_couple(Pm.p, s.Qblk, s.natoms, nb, Qm.p, st);
+    launch_gemm_rot<T>(q.beta.p, q.npw, Qm.p, nb, s.nproj, nb, q.npw, spsi, q.npw, 1.0, 1.0, st);
   }
 
   // ---- H psi ----------------------------------------------------------------------------------
@@ -778,7 +824,8 @@ template <typename T> struct EngineT : Engine {
       Pm.ensure((size_t)s.nproj * nb);
       Qm.ensure((size_t)s.nproj * nb);
       launch_gemm_hn<T>(q.beta.p, q.npw, psi, q.npw, s.nproj, nb, q.npw, Pm.p, nb, gwork.p, st);
-      launch_kb_couple(Pm.p, s.Dblk, s.natoms, nb, Qm.p, st);
+      if (s.uspp) launch_kb_couple_atoms(Pm.p, s.Dscr.p, s.nproj_atom, s.natoms, nb, Qm.p, st);
+      else launch_kb_couple(Pm.p, s.Dblk, s.natoms, nb, Qm.p, st);
       launch_gemm_rot<T>(q.beta.p, q.npw, Qm.p, nb, s.nproj, nb, q.npw, hpsi, q.npw, 1.0, 1.0, st);
     }
   }
@@ -798,6 +845,10 @@ template <typename T> struct EngineT : Engine {
       return false;
     }
     return a.type == cudaMemoryTypeHost;
+  }
+  void apply_s_dev(int i, int k, const void* psi, void* spsi, int nb) override {
+    REQ(psi && spsi && nb > 0, FDE_EINVAL, "bad orbital buffers");
+    apply_s(sub(i), kpt(i, k), (const C*)psi, (C*)spsi, nb);
   }
   void apply_h_host(int i, int k, const double* psi, double* hpsi, int nb) override {
     REQ(psi && hpsi && nb > 0, FDE_EINVAL, "bad host buffers");
@@ -920,17 +971,22 @@ template <typename T> struct EngineT : Engine {
     CK(cudaMemcpyAsync(tmpd.p, raw, n * sizeof(double2), cudaMemcpyHostToDevice, st));
     convert_in(tmpd.p, q.X.p, n);
     launch_shape_init<T>(q.X.p, q.npw, q.kin_d.p, s.nb, q.npw, st);
-    orthonormalize(q, s.nb);
+    orthonormalize(s, q, s.nb);
     CK(cudaStreamSynchronize(st));
     q.have_orbitals = true;
     q.have_eig = false;
   }
-  // X <- X L^{-H} with S = X^H X = L L^H (Cholesky-QR)
-  void orthonormalize(KP<T>& q, int nb) {
+  // X <- X L^{-H} with X^H S_I X = L L^H (Cholesky-QR in the metric of the subsystem's overlap)
+  void orthonormalize(Sub<T>& sb, KP<T>& q, int nb) {
     ensure_small(nb);
     V2.ensure((size_t)nb * q.npw);
     gwork.ensure(gemm_hn_work(nb, nb, q.npw));
-    launch_gemm_hn<T>(q.X.p, q.npw, q.X.p, q.npw, nb, nb, q.npw, S.p, nb, gwork.p, st);
+    if (sb.uspp) {
+      apply_s(sb, q, q.X.p, V2.p, nb);
+      launch_gemm_hn<T>(q.X.p, q.npw, V2.p, q.npw, nb, nb, q.npw, S.p, nb, gwork.p, st);
+    } else {
+      launch_gemm_hn<T>(q.X.p, q.npw, q.X.p, q.npw, nb, nb, q.npw, S.p, nb, gwork.p, st);
+    }
     launch_hermitize(S.p, nb, st);
     launch_cholesky_inv(S.p, nb, L.p, Li.p, status.p, rel_pivot(), st);
     check_cholesky();
@@ -997,10 +1053,14 @@ template <typename T> struct EngineT : Engine {
 
   // ---- Rayleigh-Ritz on the n rows of V / HV; keeps the lowest nb pairs in V2 / HV2 ------------
   // The coefficients of the kept pairs stay in Cc ([n][n], column j = pair j).
+  // With use_s (ultrasoft-like subsystems) the rows of SV are the S-images of V: the subspace
+  // overlap is V^H S V and the kept S-images are rotated into SV2 alongside.
+  bool use_s = false;
+  DBuf<C> SV, SV2, SPb;
   void rayleigh_ritz(KP<T>& q, int n, int nb, std::vector<double>& eps) {
     const int K = q.npw;
     gwork.ensure(gemm_hn_work(n, n, K));
-    launch_gemm_hn<T>(V.p, K, V.p, K, n, n, K, S.p, n, gwork.p, st);
+    launch_gemm_hn<T>(V.p, K, use_s ? SV.p : V.p, K, n, n, K, S.p, n, gwork.p, st);
     launch_gemm_hn<T>(V.p, K, HV.p, K, n, n, K, Hs.p, n, gwork.p, st);
     launch_hermitize(S.p, n, st);
     launch_hermitize(Hs.p, n, st);
@@ -1014,20 +1074,23 @@ template <typename T> struct EngineT : Engine {
     launch_small_gemm(Li.p, n, 1, Y.p, n, 0, n, n, n, Cc.p, n, st);
     launch_gemm_rot<T>(V.p, K, Cc.p, n, n, nb, K, V2.p, K, 1.0, 0.0, st);
     launch_gemm_rot<T>(HV.p, K, Cc.p, n, n, nb, K, HV2.p, K, 1.0, 0.0, st);
+    if (use_s) launch_gemm_rot<T>(SV.p, K, Cc.p, n, n, nb, K, SV2.p, K, 1.0, 0.0, st);
     eps.resize(n);
     CK(cudaMemcpyAsync(eps.data(), wv.p, n * sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     eps.resize(nb);
   }
 
-  // Orthogonalise the m rows B against the nb current orbitals (rows 0..nb of V), apply the
-  // same change to their H-images HB when given, and normalise the rows (HB alike).
-  void orth_block(KP<T>& q, int nb, C* Bk, C* HBk, int m) {
+  // Orthogonalise the m rows B against the nb current orbitals (rows 0..nb of V; in the S
+  // metric, with their S-images in SV, when use_s), apply the same change to their H-images HB
+  // and S-images SB when given, and normalise the rows (HB, SB alike).
+  void orth_block(KP<T>& q, int nb, C* Bk, C* HBk, int m, C* SBk = nullptr) {
     const int K = q.npw;
     gwork.ensure(gemm_hn_work(nb, m, K));
-    launch_gemm_hn<T>(V.p, K, Bk, K, nb, m, K, Cc.p, m, gwork.p, st);
+    launch_gemm_hn<T>(use_s ? SV.p : V.p, K, Bk, K, nb, m, K, Cc.p, m, gwork.p, st);
     launch_gemm_rot<T>(V.p, K, Cc.p, m, nb, m, K, Bk, K, -1.0, 1.0, st);
     if (HBk) launch_gemm_rot<T>(HV.p, K, Cc.p, m, nb, m, K, HBk, K, -1.0, 1.0, st);
+    if (SBk) launch_gemm_rot<T>(SV.p, K, Cc.p, m, nb, m, K, SBk, K, -1.0, 1.0, st);
     std::vector<double> sc(m);
     launch_row_norms<T>(Bk, K, m, K, nullptr, dnorm.p, nullptr, st);
     CK(cudaMemcpyAsync(sc.data(), dnorm.p, m * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -1036,6 +1099,7 @@ template <typename T> struct EngineT : Engine {
     CK(cudaMemcpyAsync(dtb.p, sc.data(), m * sizeof(double), cudaMemcpyHostToDevice, st));
     launch_scale_rows<T>(Bk, K, m, K, dtb.p, st);
     if (HBk) launch_scale_rows<T>(HBk, K, m, K, dtb.p, st);
+    if (SBk) launch_scale_rows<T>(SBk, K, m, K, dtb.p, st);
   }
 
   // Block eigensolver (LOBPCG form of block Davidson): the search space of every iteration is
@@ -1060,18 +1124,30 @@ template <typename T> struct EngineT : Engine {
     Pb.ensure((size_t)nb * K);
     HPb.ensure((size_t)nb * K);
     ensure_small(3 * nb);
+    // ultrasoft-like subsystems solve H psi = e S psi: every search vector carries its S-image
+    use_s = s.uspp;
+    if (use_s) {
+      // the learned preconditioner is trained on norm-conserving residuals: the kinetic one
+      // serves ultrasoft-like subsystems, and their iterates are not recorded
+      fallback = true;
+      SV.ensure((size_t)3 * nb * K);
+      SV2.ensure((size_t)nb * K);
+      SPb.ensure((size_t)nb * K);
+    }
     std::vector<double> eps;
     CK(cudaMemcpyAsync(V.p, q.X.p, nb * rowsz, cudaMemcpyDeviceToDevice, st));
     apply_h_dev(s, q, V.p, HV.p, nb);
+    if (use_s) apply_s(s, q, V.p, SV.p, nb);
     rayleigh_ritz(q, nb, nb, eps);
     CK(cudaMemcpyAsync(V.p, V2.p, nb * rowsz, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(HV.p, HV2.p, nb * rowsz, cudaMemcpyDeviceToDevice, st));
+    if (use_s) CK(cudaMemcpyAsync(SV.p, SV2.p, nb * rowsz, cudaMemcpyDeviceToDevice, st));
     int it = 0;
     bool conv = false, havep = false;
     std::vector<double> rn(nb), tb(nb);
     for (;;) {
       CK(cudaMemcpyAsync(deps.p, eps.data(), nb * sizeof(double), cudaMemcpyHostToDevice, st));
-      launch_residual<T>(HV.p, V.p, deps.p, nb, K, K, R.p, K, st);
+      launch_residual<T>(HV.p, use_s ? SV.p : V.p, deps.p, nb, K, K, R.p, K, st);  // R = H psi - e S psi
       launch_row_norms<T>(R.p, K, nb, K, nullptr, dnorm.p, nullptr, st);
       CK(cudaMemcpyAsync(rn.data(), dnorm.p, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
@@ -1082,7 +1158,7 @@ template <typename T> struct EngineT : Engine {
       }
       if (sel.empty()) { conv = true; break; }
       if (it >= max_iter) break;
-      if (it < precond_record) {
+      if (it < precond_record && !use_s) {
         // keep (R, X) of this iterate; the correction target (1 - P) X is formed once the
         // converged block P is known
         auto p = std::make_unique<Pairs>();
@@ -1134,12 +1210,15 @@ template <typename T> struct EngineT : Engine {
       if (havep) {
         C* P = V.p + (size_t)(nb + m) * K;
         C* HP = HV.p + (size_t)(nb + m) * K;
+        C* SP = use_s ? SV.p + (size_t)(nb + m) * K : nullptr;
         launch_gather_rows<T>(Pb.p, K, didx.p, m, K, P, K, st);
         launch_gather_rows<T>(HPb.p, K, didx.p, m, K, HP, K, st);
-        orth_block(q, nb, P, HP, m);
+        if (use_s) launch_gather_rows<T>(SPb.p, K, didx.p, m, K, SP, K, st);
+        orth_block(q, nb, P, HP, m, SP);
         np = m;
       }
       apply_h_dev(s, q, W, HV.p + (size_t)nb * K, m);
+      if (use_s) apply_s(s, q, W, SV.p + (size_t)nb * K, m);
       int n = nb + m + np;
       try {
         rayleigh_ritz(q, n, nb, eps);
@@ -1154,11 +1233,14 @@ template <typename T> struct EngineT : Engine {
           break;
         }
       }
-      // update directions P = [W P] C[nb:n, :nb] (and their H-images)
+      // update directions P = [W P] C[nb:n, :nb] (and their H- and S-images)
       launch_gemm_rot<T>(V.p + (size_t)nb * K, K, Cc.p + (size_t)nb * n, n, n - nb, nb, K, Pb.p, K, 1.0, 0.0, st);
       launch_gemm_rot<T>(HV.p + (size_t)nb * K, K, Cc.p + (size_t)nb * n, n, n - nb, nb, K, HPb.p, K, 1.0, 0.0, st);
+      if (use_s)
+        launch_gemm_rot<T>(SV.p + (size_t)nb * K, K, Cc.p + (size_t)nb * n, n, n - nb, nb, K, SPb.p, K, 1.0, 0.0, st);
       CK(cudaMemcpyAsync(V.p, V2.p, nb * rowsz, cudaMemcpyDeviceToDevice, st));
       CK(cudaMemcpyAsync(HV.p, HV2.p, nb * rowsz, cudaMemcpyDeviceToDevice, st));
+      if (use_s) CK(cudaMemcpyAsync(SV.p, SV2.p, nb * rowsz, cudaMemcpyDeviceToDevice, st));
       havep = true;
     }
     if (conv) {
@@ -1207,11 +1289,48 @@ template <typename T> struct EngineT : Engine {
       CK(cudaStreamSynchronize(st));  // occw is reused by the next k
     }
     launch_transpose<double, double>(rho_plane.p, out, g.n3, (int)((long long)g.n1 * g.n2), 0, st);
+    if (s.uspp) augment_density(s, out);
     if (sym.n > 1) {  // densities from an irreducible k-set: average over the symmetry group
       grid_symmetrize(out, rho_plane.p, g, sym, st);
       CK(cudaMemcpyAsync(out, rho_plane.p, nr * sizeof(double), cudaMemcpyDeviceToDevice, st));
     }
     grid_nonfinite(out, nr, status.p, st);
+  }
+
+  // Augmentation charges of an ultrasoft-like subsystem added to its density:
+  // rho += sum_a g_a(r) c_a, c_a = sum_ij q_ij 2 sum_k w_k sum_j n_jk Re <u_jk|beta_ai><beta_aj|u_jk>,
+  // so that int rho_I = N_I for S-normalised orbitals.  The projections come to the host (a
+  // natoms x nproj x nb block per k), the charges are placed in reciprocal space and transformed.
+  void augment_density(Sub<T>& s, double* out) {
+    std::vector<double> ca(s.natoms, 0.0);
+    const int np = s.nproj_atom;
+    for (int k = 0; k < s.nk; ++k) {
+      KP<T>& q = s.kp[k];
+      gwork.ensure(gemm_hn_work(s.nproj, s.nb, q.npw));
+      Pm.ensure((size_t)s.nproj * s.nb);
+      launch_gemm_hn<T>(q.beta.p, q.npw, q.X.p, q.npw, s.nproj, s.nb, q.npw, Pm.p, s.nb, gwork.p, st);
+      std::vector<double2> P((size_t)s.nproj * s.nb);
+      CK(cudaMemcpyAsync(P.data(), Pm.p, P.size() * sizeof(double2), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      for (int a = 0; a < s.natoms; ++a)
+        for (int i = 0; i < np; ++i)
+          for (int i2 = 0; i2 < np; ++i2) {
+            double b = 0;
+            for (int j = 0; j < s.nb; ++j) {
+              const double2 x = P[(size_t)(a * np + i) * s.nb + j], y = P[(size_t)(a * np + i2) * s.nb + j];
+              b += q.occ[j] * (x.x * y.x + x.y * y.y);
+            }
+            ca[a] += 2.0 * s.wk[k] * s.Q[i * np + i2] * b;
+          }
+    }
+    DBuf<double> dc;
+    dc.alloc(s.natoms);
+    CK(cudaMemcpyAsync(dc.p, ca.data(), s.natoms * sizeof(double), cudaMemcpyHostToDevice, st));
+    double2* A = cb[0].p;
+    grid_aug_density_g(A, g, cell, s.aug_pos.p, dc.p, s.natoms, s.aug_sigma, st);
+    launch_fft3d<double>(A, g, plans64.fp, +1, st);
+    grid_combine<double>(out, nullptr, nullptr, A, 1.0, out, nr, st);
+    CK(cudaStreamSynchronize(st));  // dc is released on return
   }
 
   // Point-group operations the densities are symmetrised over (sign flips about the origin).
@@ -1500,7 +1619,7 @@ template <typename T> struct EngineT : Engine {
     CK(cudaMemcpyAsync(tb.p, tband, nb * sizeof(double), cudaMemcpyHostToDevice, st));
     launch_row_norms<T>((const C*)r, q.npw, nb, q.npw, nullptr, ss.p, nullptr, st);
     launch_precond_apply<T>((const C*)r, q.npw, q.kin_d.p, tb.p, ss.p, nb, q.npw, pwb.p, (C*)w, q.npw, st);
-    CK(cudaStreamSynchronize(st));
+    sync();
   }
 
   // ---- Pulay mixing -----------------------------------------------------------------------------
@@ -1758,7 +1877,7 @@ template <> void EngineT<float>::convert_out(const float2* a, double2* b, size_t
 // A subsystem descriptor with its own copies of the caller's arrays.
 struct SubsysCopy {
   fde_subsys_desc d{};
-  std::vector<double> pos, Z, sigma, D, kpts, wk;
+  std::vector<double> pos, Z, sigma, D, Qa, kpts, wk;
   explicit SubsysCopy(const fde_subsys_desc& s) : d(s) {
     pos.assign(s.pos, s.pos + 3 * s.natoms);
     Z.assign(s.Z, s.Z + s.natoms);
@@ -1766,8 +1885,11 @@ struct SubsysCopy {
       sigma.assign(s.proj_sigma, s.proj_sigma + s.nproj_per_atom);
       D.assign(s.proj_D, s.proj_D + s.nproj_per_atom * s.nproj_per_atom);
     }
+    if (s.aug_sigma > 0 && s.proj_Q && s.nproj_per_atom > 0)
+      Qa.assign(s.proj_Q, s.proj_Q + s.nproj_per_atom * s.nproj_per_atom);
     kpts.assign(s.kpts, s.kpts + 3 * s.nk);
     wk.assign(s.wk, s.wk + s.nk);
+    d.proj_Q = Qa.empty() ? nullptr : Qa.data();
     d.pos = pos.data();
     d.Z = Z.data();
     d.proj_sigma = sigma.empty() ? nullptr : sigma.data();
@@ -1979,6 +2101,9 @@ fde_status fde_set_veff(fde_ctx* c, int sub, const double* d_v) {
 fde_status fde_apply_h(fde_ctx* c, int sub, int k, const void* psi, void* hpsi, int nb) {
   return guard(c, [&]() { c->eng->apply_h(sub, k, psi, hpsi, nb); return FDE_OK; });
 }
+fde_status fde_apply_s(fde_ctx* c, int sub, int k, const void* psi, void* spsi, int nb) {
+  return guard(c, [&]() { c->eng->apply_s_dev(sub, k, psi, spsi, nb); return FDE_OK; });
+}
 fde_status fde_apply_h_host(fde_ctx* c, int sub, int k, const double* psi, double* hpsi, int nb) {
   return guard(c, [&]() { c->eng->apply_h_host(sub, k, psi, hpsi, nb); return FDE_OK; });
 }
@@ -2126,7 +2251,13 @@ int fde_tuned_plane_variant(int n1, int n3) { return fde::query_plane_variant(n1
 fde_status fde_pin_plane_variant(int variant) { return fde::pin_plane_variant(variant) ? FDE_OK : FDE_EINVAL; }
 
 fde_status fde_set_tc_wait_limit(long long polls) {
-  return fde::set_tc_stage_spin(polls) ? FDE_OK : FDE_ECUDA;
+  return fde::set_tc_stage_spin(polls) && fde::set_precond_tc_spin(polls) ? FDE_OK : FDE_ECUDA;
+}
+
+fde_status fde_set_precond_path(int path) {
+  if (path != 0 && path != 1) return FDE_EINVAL;
+  fde::set_precond_tensor_cores(path == 1);
+  return FDE_OK;
 }
 
 fde_status fde_set_gemm_path(int path) {

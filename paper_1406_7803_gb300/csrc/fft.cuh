@@ -23,12 +23,15 @@ template <typename C> __device__ __forceinline__ void dft2(C* v, int) {
   v[1] = csub(a, b);
 }
 
+// Constants are constexpr so that every arithmetic type (float, double, double-float) gets them
+// folded at compile time.
 template <typename C> __device__ __forceinline__ void dft3(C* v, int sign) {
   using T = decltype(v[0].x);
-  const T h = (T)0.86602540378443864676;  // sin(2 pi / 3)
+  constexpr T h = T(0.86602540378443864676);  // sin(2 pi / 3)
+  constexpr T half = T(0.5);
   C t1 = cadd(v[1], v[2]);
   C t2 = cmuli(cscale(csub(v[1], v[2]), h), sign);
-  C m = csub(v[0], cscale(t1, (T)0.5));
+  C m = csub(v[0], cscale(t1, half));
   v[0] = cadd(v[0], t1);
   v[1] = cadd(m, t2);
   v[2] = csub(m, t2);
@@ -45,10 +48,10 @@ template <typename C> __device__ __forceinline__ void dft4(C* v, int sign) {
 
 template <typename C> __device__ __forceinline__ void dft5(C* v, int sign) {
   using T = decltype(v[0].x);
-  const T c1 = (T)0.30901699437494742410;   // cos(2 pi / 5)
-  const T c2 = (T)-0.80901699437494742410;  // cos(4 pi / 5)
-  const T s1 = (T)0.95105651629515357212;   // sin(2 pi / 5)
-  const T s2 = (T)0.58778525229247312917;   // sin(4 pi / 5)
+  constexpr T c1 = T(0.30901699437494742410);   // cos(2 pi / 5)
+  constexpr T c2 = T(-0.80901699437494742410);  // cos(4 pi / 5)
+  constexpr T s1 = T(0.95105651629515357212);   // sin(2 pi / 5)
+  constexpr T s2 = T(0.58778525229247312917);   // sin(4 pi / 5)
   C t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]);
   C t3 = csub(v[1], v[4]), t4 = csub(v[2], v[3]);
   C a1 = cadd(v[0], cadd(cscale(t1, c1), cscale(t2, c2)));

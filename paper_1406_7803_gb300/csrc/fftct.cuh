@@ -49,10 +49,21 @@ __host__ __device__ constexpr CtPlan ct_factor(int n, int order = 0) {
 // thread for FP32 data, 9 for FP64; 1: 18 / 9), bit 4 the radix order of ct_factor.
 __host__ __device__ constexpr int ct_order(int V) { return (V >> 4) & 1; }
 
+// The same radices in the opposite order: the plan of a forward transform that starts where an
+// inverse transform of plan p ended (its first stage reads the groups p's last stage wrote).
+__host__ __device__ constexpr CtPlan ct_reverse(CtPlan p) {
+  CtPlan q = p;
+  for (int s = 0; s < p.ns; ++s) q.r[s] = p.r[p.ns - 1 - s];
+  return q;
+}
+template <int N, int V, bool REV> __host__ __device__ constexpr CtPlan ct_plan() {
+  return REV ? ct_reverse(ct_factor(N, ct_order(V))) : ct_factor(N, ct_order(V));
+}
+
 // 8- and 9-point DFTs as 2 x 4 and 3 x 3 Cooley-Tukey in registers.
 template <typename C> __device__ __forceinline__ void dft8(C* v, int sign) {
   using T = decltype(v[0].x);
-  const T h = (T)0.70710678118654752440;  // cos(pi/4)
+  constexpr T h = T(0.70710678118654752440);  // cos(pi/4)
   C e[4] = {v[0], v[2], v[4], v[6]}, o[4] = {v[1], v[3], v[5], v[7]};
   dft4(e, sign);
   dft4(o, sign);
@@ -71,9 +82,9 @@ template <typename C> __device__ __forceinline__ void dft8(C* v, int sign) {
 template <typename C> __device__ __forceinline__ void dft9(C* v, int sign) {
   using T = decltype(v[0].x);
   // W_9^1, W_9^2, W_9^4 for sign = -1 (conjugated for sign = +1)
-  const T c1 = (T)0.76604444311897803520, s1 = (T)0.64278760968653932632;   // 2 pi / 9
-  const T c2 = (T)0.17364817766693034885, s2 = (T)0.98480775301220805936;   // 4 pi / 9
-  const T c4 = (T)-0.93969262078590838405, s4 = (T)0.34202014332566873304;  // 8 pi / 9
+  constexpr T c1 = T(0.76604444311897803520), s1 = T(0.64278760968653932632);   // 2 pi / 9
+  constexpr T c2 = T(0.17364817766693034885), s2 = T(0.98480775301220805936);   // 4 pi / 9
+  constexpr T c4 = T(-0.93969262078590838405), s4 = T(0.34202014332566873304);  // 8 pi / 9
   C a[3][3];
 #pragma unroll
   for (int n2 = 0; n2 < 3; ++n2) {
@@ -206,6 +217,76 @@ __device__ __forceinline__ void ct_stages(cplx<T>* buf, const A& addr, int l0, i
   }
 }
 
+// Stages S .. SE - 1 of the plan, reversed radix order when REV; NS = product of the radices
+// of the stages before S.
+template <typename T, int N, int NT, int NL, int S, int SE, int NS, int V, bool REV, typename A>
+__device__ __forceinline__ void ct_stage_range(cplx<T>* buf, const A& addr, int l0, int nl, const cplx<T>* tw,
+                                               int sign) {
+  constexpr CtPlan P = ct_plan<N, V, REV>();
+  if constexpr (S < SE) {
+    constexpr int R = P.r[S];
+    ct_stage<T, N, R, NS, NT, NL, V>(buf, addr, l0, nl, tw, sign);
+    ct_stage_range<T, N, NT, NL, S + 1, SE, NS * R, V, REV>(buf, addr, l0, nl, tw, sign);
+  }
+}
+
+// Strided lines (plane columns, element stride pitch): the last stage of the inverse transform
+// (radix R, Ns = N / R), the product with a real potential and the first stage of the forward
+// transform in the reversed radix order (radix R, Ns = 1), on the same registers.  Butterfly j
+// ends the inverse holding the outputs j + q N/R, which are exactly the inputs j + r N/R of the
+// forward stage's butterfly j; it writes the forward stage's outputs to j R + q.  The potential
+// of element i of line l is vp[i * vpitch + l].  Saves one exchange through shared memory and
+// the separate multiply pass.
+template <typename T, int N, int R, int NT, int NL, int V>
+__device__ __forceinline__ void ct_stage_vmul(cplx<T>* buf, int pitch, int l0, int nl,
+                                              const cplx<T>* __restrict__ tw, const T* __restrict__ vp,
+                                              int vpitch) {
+  using C = cplx<T>;
+  constexpr int NB = N / R;
+  constexpr int IPT = ct_ipt<T, R, V>();
+  const int items = nl * NB;
+  C v[IPT][R];
+#pragma unroll
+  for (int it = 0; it < IPT; ++it) {
+    const int w = threadIdx.x + it * NT;
+    if (w < items) {
+      const int j = w / NL, l = w - j * NL;
+      const C* a = buf + (l0 + l);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        C x = a[(j + r * NB) * pitch];
+        if (r > 0 && NB > 1) {
+          C t = tw[r * j];  // W_N^{r j} of the last stage, conjugated for the inverse sign
+          t.y = -t.y;
+          x = cmul(x, t);
+        }
+        v[it][r] = x;
+      }
+      dft_ct<R>(v[it], +1);
+      const T* vl = vp + (l0 + l);
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        const T s = vl[(j + q * NB) * vpitch];
+        v[it][q].x *= s;
+        v[it][q].y *= s;
+      }
+      dft_ct<R>(v[it], -1);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int it = 0; it < IPT; ++it) {
+    const int w = threadIdx.x + it * NT;
+    if (w < items) {
+      const int j = w / NL, l = w - j * NL;
+      C* a = buf + (l0 + l);
+#pragma unroll
+      for (int q = 0; q < R; ++q) a[(j * R + q) * pitch] = v[it][q];
+    }
+  }
+  __syncthreads();
+}
+
 // Largest divisor of N not above LB (batch size of strided lines, so every batch is full).
 template <int N, int LB> __host__ __device__ constexpr int ct_full_batch() {
   int b = LB < N ? LB : N;
@@ -224,6 +305,22 @@ __device__ __forceinline__ void ct_lines(cplx<T>* buf, const A& addr, int nlines
   for (int l0 = 0; l0 < nlines; l0 += LB) {
     const int nl = nlines - l0 < LB ? nlines - l0 : LB;
     ct_stages<T, N, NT, LB, 0, 1, V>(buf, addr, l0, nl, tw, sign);
+  }
+}
+
+// The N columns of an N x N plane (element stride pitch): inverse transform (sign +1), product
+// with the potential vp[i * N + l] and forward transform (sign -1), batch by batch, with the
+// inverse's last stage and the forward's first fused (ct_stage_vmul).
+template <typename T, int N, int NT, int V = 0>
+__device__ __forceinline__ void ct_cols_vmul(cplx<T>* buf, int pitch, const cplx<T>* tw, const T* vp) {
+  constexpr CtPlan P = ct_factor(N, ct_order(V));
+  static_assert(P.ns > 0, "length must factor into 2, 3, 5");
+  constexpr int RL = P.r[P.ns - 1];
+  constexpr int LB = ct_full_batch<N, ct_lines_per_batch<T, N, NT, V>()>();
+  for (int l0 = 0; l0 < N; l0 += LB) {
+    ct_stage_range<T, N, NT, LB, 0, P.ns - 1, 1, V, false>(buf, LinesCols{pitch}, l0, LB, tw, +1);
+    ct_stage_vmul<T, N, RL, NT, LB, V>(buf, pitch, l0, LB, tw, vp, N);
+    ct_stage_range<T, N, NT, LB, 1, P.ns, RL, V, true>(buf, LinesCols{pitch}, l0, LB, tw, -1);
   }
 }
 

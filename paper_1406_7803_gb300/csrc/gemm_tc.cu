@@ -30,6 +30,7 @@
 
 #include "kernels.h"
 #include "prof.h"
+#include "tc.cuh"
 
 namespace fde {
 
@@ -46,44 +47,12 @@ constexpr int kStage = 4 * kTile;  // A hi, A lo, B hi, B lo
 constexpr int kStages = 1;
 constexpr int kCtasPerSm = 2;
 constexpr int kTmemCols = 128;
-constexpr long long kSpin = 1ll << 22;  // bounded mbarrier polls (with back-off: ~1 s)
+constexpr long long kSpin = kTcSpin;
 
 __device__ unsigned g_tc_status;
 // Poll limit of the waits for a shared-memory stage inside the K loop (settable from the host
 // so that the timeout path can be exercised; the final drain always uses kSpin).
 __device__ long long g_tc_stage_spin = kSpin;
-
-__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ bool mbar_test(uint32_t bar, unsigned parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, unsigned parity, long long limit = kSpin) {
-  for (long long i = 0; i < limit; ++i) {
-    if (mbar_test(bar, parity)) return true;
-    if (i > 32) __nanosleep(128);
-  }
-  return false;
-}
-
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row groups 1024 B
-// apart (stride byte offset), leading byte offset unused for this layout (1), descriptor
-// version 1, base offset 0 (tiles are 1024-byte aligned).
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
-  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
-         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
-}
 
 // Instruction descriptor, kind::tf32: D f32 (bits 4-5 = 1), A and B tf32 (bits 7-9, 10-12
 // = 2), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28.
@@ -98,26 +67,6 @@ __device__ __forceinline__ void mma_tf32(uint32_t dt, uint64_t a, uint64_t b, ui
       "l"(a), "l"(b), "r"(kIdesc), "r"(acc)
       : "memory");
 }
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-               : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
 __device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
 
 // Byte offset of floats (c, c + 1) of row r in a 128-byte-swizzled tile (c even).

@@ -563,6 +563,61 @@ __global__ void k_finish_pair(const cplx<TD>* __restrict__ F, const double* __re
   }
 }
 
+// ---- ultrasoft-like augmentation (Appendix: subsystem-specific projectors) -------------------
+// Augmentation charges q_ij g_a(r) with g_a the normalised Gaussian (pi s^2)^{-3/2}
+// exp(-|r - R_a|^2 / s^2): g_a(G) = (1/Omega) exp(-G^2 s^2 / 4) exp(-i G.R_a), Nyquist planes zero.
+
+// rho_aug(G) = sum_a c_a g_a(G) into A (complex grid), for the inverse transform.
+__global__ void k_aug_density_g(double2* __restrict__ A, GridDims g, CellDev c, const double* __restrict__ pos,
+                                const double* __restrict__ coef, int natoms, double sigma) {
+  const long long nr = (long long)g.n1 * g.n2 * g.n3;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < nr; idx += (long long)gridDim.x * blockDim.x) {
+    const Gpt p = gvec(idx, g, c);
+    double re = 0, im = 0;
+    if (!p.nyq) {
+      const double f = exp(-p.g2 * sigma * sigma / 4.0) / c.omega;
+      for (int a = 0; a < natoms; ++a) {
+        double sn, cs;
+        sincos(p.gx * pos[3 * a] + p.gy * pos[3 * a + 1] + p.gz * pos[3 * a + 2], &sn, &cs);
+        re += f * coef[a] * cs;
+        im -= f * coef[a] * sn;
+      }
+    }
+    A[idx] = make_double2(re, im);
+  }
+}
+
+// Screened coupling of each atom: Dscr_a = D + q int v g_a, with
+// int v g_a = Re sum_G v(G) exp(-G^2 s^2 / 4) exp(+i G.R_a) (Parseval; VG = v's forward transform
+// scaled by 1/N_r).  One CTA per atom; D and q are np x np (row-major).
+__global__ void k_aug_screening(const double2* __restrict__ VG, GridDims g, CellDev c, const double* __restrict__ pos,
+                                double sigma, KbBlock D, KbBlock q, double* __restrict__ Dscr) {
+  const long long nr = (long long)g.n1 * g.n2 * g.n3;
+  const int a = blockIdx.x;
+  const double x = pos[3 * a], y = pos[3 * a + 1], z = pos[3 * a + 2];
+  double acc = 0;
+  for (long long idx = threadIdx.x; idx < nr; idx += blockDim.x) {
+    const Gpt p = gvec(idx, g, c);
+    if (p.nyq) continue;
+    double sn, cs;
+    sincos(p.gx * x + p.gy * y + p.gz * z, &sn, &cs);
+    const double2 v = VG[idx];
+    acc += exp(-p.g2 * sigma * sigma / 4.0) * (v.x * cs - v.y * sn);
+  }
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+    red[0] = t;
+  }
+  __syncthreads();
+  const double ov = red[0];
+  for (int e = threadIdx.x; e < D.np * D.np; e += blockDim.x) Dscr[(size_t)a * D.np * D.np + e] = D.d[e] + q.d[e] * ov;
+}
+
 // ---- launch wrappers ------------------------------------------------------------------------
 __global__ void k_symmetrize(const double* __restrict__ in, double* __restrict__ out, GridDims g, SymOps ops) {
   const long long nr = (long long)g.n1 * g.n2 * g.n3;
@@ -586,6 +641,21 @@ __global__ void k_symmetrize(const double* __restrict__ in, double* __restrict__
 static int gs(long long n) {
   long long b = (n + 255) / 256;
   return (int)(b < 4096 ? (b > 0 ? b : 1) : 4096);
+}
+
+void grid_aug_density_g(double2* A, const GridDims& g, const CellDev& c, const double* pos, const double* coef,
+                        int natoms, double sigma, cudaStream_t st) {
+  const long long nr = (long long)g.n1 * g.n2 * g.n3;
+  count_launches(1);
+  ProfScope prof_("k_aug_density_g", st);
+  k_aug_density_g<<<gs(nr), 256, 0, st>>>(A, g, c, pos, coef, natoms, sigma);
+}
+void grid_aug_screening(const double2* VG, const GridDims& g, const CellDev& c, const double* pos, int natoms,
+                        double sigma, const KbBlock& D, const KbBlock& q, double* Dscr, cudaStream_t st) {
+  if (natoms <= 0) return;
+  count_launches(1);
+  ProfScope prof_("k_aug_screening", st);
+  k_aug_screening<<<natoms, 512, 0, st>>>(VG, g, c, pos, sigma, D, q, Dscr);
 }
 
 void grid_vloc_g(double2* V, const GridDims& g, const CellDev& c, const double* pos, const double* Z, int natoms,

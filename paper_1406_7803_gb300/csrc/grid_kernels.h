@@ -29,6 +29,14 @@ struct SymOps {
 };
 void grid_symmetrize(const double* in, double* out, const GridDims& g, const SymOps& ops, cudaStream_t st);
 
+// ---- ultrasoft-like augmentation: charges q_ij g_a(r), g_a a normalised Gaussian of width sigma ----
+// A = sum_a coef_a g_a(G) (complex grid; its inverse transform is the augmentation density).
+void grid_aug_density_g(double2* A, const GridDims& g, const CellDev& c, const double* pos, const double* coef,
+                        int natoms, double sigma, cudaStream_t st);
+// Dscr[a] = D + q int v g_a for every atom (VG: v's forward transform, scaled by 1/N_r).
+void grid_aug_screening(const double2* VG, const GridDims& g, const CellDev& c, const double* pos, int natoms,
+                        double sigma, const KbBlock& D, const KbBlock& q, double* Dscr, cudaStream_t st);
+
 // ---- packed pairs of real fields (two real grids in one complex transform) ----
 constexpr int kMaxPairs = 32;
 struct GradPacks {  // real-space gradients of the subsystem densities, pairwise packed

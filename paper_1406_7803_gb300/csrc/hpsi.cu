@@ -63,7 +63,7 @@ k_zinv(const cplx<T>* __restrict__ psi, int ldpsi, cplx<T>* __restrict__ scratch
 template <typename T>
 __global__ void __launch_bounds__(kPlaneThreads)
 k_plane(cplx<T>* __restrict__ scratch, SphereDev sp, const T* __restrict__ vplane, GridDims g,
-        LinePlan<T> p1, LinePlan<T> p2, int vtrans) {
+        LinePlan<T> p1, LinePlan<T> p2) {
   using C = cplx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* P = reinterpret_cast<C*>(smem_raw);
@@ -83,7 +83,7 @@ k_plane(cplx<T>* __restrict__ scratch, SphereDev sp, const T* __restrict__ vplan
   for (int idx = threadIdx.x; idx < n1 * n2; idx += blockDim.x) {
     const int i1 = idx / n2, i2 = idx - i1 * n2;
     C& z = P[i1 * pitch + i2];
-    const T v = vtrans ? V[i2 * n1 + i1] : V[idx];  // [i2][i1] planes when vtrans
+    const T v = V[idx];
     z.x *= v;
     z.y *= v;
   }
@@ -163,8 +163,7 @@ void launch_hpsi_local(const cplx<T>* psi, int ldpsi, cplx<T>* hpsi, int ldh, in
   {
     ProfScope p("k_plane", st, 1);
     count_launches(1);
-    const int vtrans = (sizeof(T) == 4 && hpsi_plane_transposed_f32(g)) ? 1 : 0;
-    k_plane<T><<<dim3(g.n3, nb), kPlaneThreads, ps, st>>>(scratch, sp, vplane, g, fp.p1, fp.p2, vtrans);
+    k_plane<T><<<dim3(g.n3, nb), kPlaneThreads, ps, st>>>(scratch, sp, vplane, g, fp.p1, fp.p2);
   }
   const T inv_nr = (T)(1.0 / ((double)g.n1 * g.n2 * g.n3));
   {
@@ -251,28 +250,6 @@ void launch_transpose(const Tin* in, Tout* out, int rows, int cols, int accumula
   dim3 grid(ceil_div(cols, 32), ceil_div(rows, 32));
   count_launches(1);
   k_transpose<Tin, Tout><<<grid, dim3(32, 8), 0, st>>>(in, out, rows, cols, accumulate);
-}
-
-// out[(i3 n2 + i2) n1 + i1] = in[(i1 n2 + i2) n3 + i3]: for each i2 a 32 x 32-tiled transpose of
-// the (i1, i3) matrix, reading along i3 and writing along i1.
-__global__ void k_to_plane_t(const double* __restrict__ in, float* __restrict__ out, int n1, int n2, int n3) {
-  __shared__ float tile[32][33];
-  const int i2 = blockIdx.z;
-  const int b3 = blockIdx.x * 32, b1 = blockIdx.y * 32;
-  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
-    const int i1 = b1 + j, i3 = b3 + threadIdx.x;
-    if (i1 < n1 && i3 < n3) tile[j][threadIdx.x] = (float)in[((size_t)i1 * n2 + i2) * n3 + i3];
-  }
-  __syncthreads();
-  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
-    const int i3 = b3 + j, i1 = b1 + threadIdx.x;
-    if (i1 < n1 && i3 < n3) out[((size_t)i3 * n2 + i2) * n1 + i1] = tile[threadIdx.x][j];
-  }
-}
-
-void launch_to_plane_t(const double* in, float* out, const GridDims& g, cudaStream_t st) {
-  count_launches(1);
-  k_to_plane_t<<<dim3(ceil_div(g.n3, 32), ceil_div(g.n1, 32), g.n2), dim3(32, 8), 0, st>>>(in, out, g.n1, g.n2, g.n3);
 }
 
 template void launch_hpsi_local<float>(const float2*, int, float2*, int, int, const float*, const float*, float2*,

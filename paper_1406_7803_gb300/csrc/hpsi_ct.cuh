@@ -132,11 +132,15 @@ k_zfwd_ct(const __grid_constant__ HpsiBatch<T> B, T inv_nr, const cplx<T>* __res
 }
 
 // One CTA per (item, band, z-plane): columns in, 2D inverse FFT (y on the rows holding
-// columns, then x), potential multiply, 2D forward FFT, columns out.  n1 = n2 = N.
-// Variants of the plane pass (FP32): V selects the staged transform's register budget and
-// radix order (fftct.cuh), MINB the CTAs per SM the registers are bounded for (four FP32 CTAs
-// of 42 KB for a 72 x 72 plane need <= 64 registers).  FP64 planes (84 KB) fit two CTAs.
-template <typename T, int N, int V = 0, int MINB = (sizeof(T) == 4 ? 4 : 2)>
+// columns, then x), potential multiply, 2D forward FFT, columns out.  n1 = n2 = N; the plane is
+// P[i1][i2] (pitch N + 1) and the potential plane vplane[i3][i1][i2].
+// Variants of the plane pass: V selects the staged transform's register budget and radix
+// order (fftct.cuh), MINB the CTAs per SM the registers are bounded for (four FP32 CTAs of
+// 42 KB for a 72 x 72 plane need <= 64 registers; FP64 planes of 84 KB fit two), FX fuses the
+// x pass: the inverse's last stage, the potential multiply and the forward's first stage run on
+// the same registers (ct_cols_vmul), one shared-memory round trip and one barrier pair fewer
+// per column batch and no separate multiply pass.
+template <typename T, int N, int V = 0, int MINB = (sizeof(T) == 4 ? 4 : 2), bool FX = false>
 __global__ void __launch_bounds__(kCtThreads, MINB)
 k_plane_ct(const __grid_constant__ HpsiBatch<T> B, int n3, const cplx<T>* __restrict__ tw1,
            const cplx<T>* __restrict__ tw2) {
@@ -156,169 +160,23 @@ k_plane_ct(const __grid_constant__ HpsiBatch<T> B, int n3, const cplx<T>* __rest
   for (int c = threadIdx.x; c < sp.ncol; c += kCtThreads) P[sp.col_i1[c] * PITCH + sp.col_i2[c]] = S[c];
   __syncthreads();
   ct_lines<T, N, kCtThreads, LinesRows, V>(P, LinesRows{rows, PITCH}, sp.nrow, tw2, +1);
-  ct_lines<T, N, kCtThreads, LinesCols, V>(P, LinesCols{PITCH}, N, tw1, +1);
-  // potential plane: [i1][i2] in FP64 contexts, [i2][i1] in mixed ones (the layout the
-  // warp-local variant reads row by row)
   const T* vp = I.vplane + (size_t)i3 * N * N;
-  for (int idx = threadIdx.x; idx < N * N; idx += kCtThreads) {
-    const int a = idx / N, b = idx - a * N;
-    C& z = (sizeof(T) == 4) ? P[b * PITCH + a] : P[a * PITCH + b];
-    const T v = vp[idx];
-    z.x *= v;
-    z.y *= v;
-  }
-  __syncthreads();
-  ct_lines<T, N, kCtThreads, LinesCols, V>(P, LinesCols{PITCH}, N, tw1, -1);
-  ct_lines<T, N, kCtThreads, LinesRows, V>(P, LinesRows{rows, PITCH}, sp.nrow, tw2, -1);
-  for (int c = threadIdx.x; c < sp.ncol; c += kCtThreads) S[c] = P[sp.col_i1[c] * PITCH + sp.col_i2[c]];
-}
-
-// ---- warp-local plane pass --------------------------------------------------------------
-// Every line transform of the plane is done by one warp on lines it owns, so the stages of a
-// transform synchronise the warp only; the CTA synchronises five times per plane (after the
-// zero fill, the scatter, the inverse column pass, the row passes and the forward column
-// pass) instead of twice per stage and batch.  The plane is held transposed, P[i2][i1]: a
-// P-row is an x-line (fixed i2), a P-column a y-line (fixed i1).  Order per plane:
-//   scatter the sphere columns; inverse y on the P-columns that hold data (the distinct i1);
-//   per warp, on its own P-rows in groups: inverse x, multiply by the potential row
-//   v[i3][i2][:] (contiguous in the [i3][i2][i1] layout), forward x -- no CTA barrier inside;
-//   forward y on the data P-columns; gather the sphere columns.
-template <int N> __host__ __device__ constexpr int wl_max_nb() {
-  constexpr CtPlan P = ct_factor(N, 0);
-  int m = 0;
-  for (int s = 0; s < P.ns; ++s) m = (N / P.r[s]) > m ? (N / P.r[s]) : m;
-  return m;
-}
-// Lines per group: as many as keep one butterfly per lane in the stage with most butterflies.
-template <int N> __host__ __device__ constexpr int wl_group() { return wl_max_nb<N>() >= 32 ? 1 : 32 / wl_max_nb<N>(); }
-
-struct WlRows {  // P-rows first .. first + G - 1, unit element stride
-  int pitch, first;
-  __device__ __forceinline__ int base(int l) const { return (first + l) * pitch; }
-  static constexpr bool kUnit = true;
-};
-struct WlCols {  // P-columns ids[0 .. G - 1], element stride pitch
-  const int* ids;
-  int pitch;
-  __device__ __forceinline__ int base(int l) const { return ids[l]; }
-  static constexpr bool kUnit = false;
-};
-
-template <typename T, int N, int R, int NS, typename A>
-__device__ __forceinline__ void wl_stage(cplx<T>* buf, const A& addr, int nl, const cplx<T>* __restrict__ tw,
-                                         int sign, int lane) {
-  using C = cplx<T>;
-  constexpr int NB = N / R;
-  constexpr int TWS = N / (NS * R);
-  constexpr int G = wl_group<N>();
-  constexpr int IPT = (G * NB + 31) / 32;
-  const int es = A::kUnit ? 1 : addr.pitch;
-  const int items = nl * NB;
-  C v[IPT][R];
-#pragma unroll
-  for (int it = 0; it < IPT; ++it) {
-    const int w = lane + 32 * it;
-    if (w < items) {
-      int l, j;
-      if (A::kUnit) { l = w / NB; j = w - l * NB; } else { j = w / nl; l = w - j * nl; }
-      const int k = j % NS;
-      const C* a = buf + addr.base(l);
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        C x = a[(j + r * NB) * es];
-        if (r > 0 && NS > 1) {
-          C t = tw[r * k * TWS];
-          if (sign > 0) t.y = -t.y;
-          x = cmul(x, t);
-        }
-        v[it][r] = x;
-      }
-      dft_ct<R>(v[it], sign);
-    }
-  }
-  __syncwarp();
-#pragma unroll
-  for (int it = 0; it < IPT; ++it) {
-    const int w = lane + 32 * it;
-    if (w < items) {
-      int l, j;
-      if (A::kUnit) { l = w / NB; j = w - l * NB; } else { j = w / nl; l = w - j * nl; }
-      const int k = j % NS;
-      const int d = (j / NS) * NS * R + k;
-      C* a = buf + addr.base(l);
-#pragma unroll
-      for (int q = 0; q < R; ++q) a[(d + q * NS) * es] = v[it][q];
-    }
-  }
-  __syncwarp();
-}
-
-template <typename T, int N, int S, int NS, typename A>
-__device__ __forceinline__ void wl_stages(cplx<T>* buf, const A& addr, int nl, const cplx<T>* tw, int sign,
-                                          int lane) {
-  constexpr CtPlan P = ct_factor(N, 0);
-  if constexpr (S < P.ns) {
-    constexpr int R = P.r[S];
-    wl_stage<T, N, R, NS>(buf, addr, nl, tw, sign, lane);
-    wl_stages<T, N, S + 1, NS * R>(buf, addr, nl, tw, sign, lane);
-  }
-}
-
-// The warp's share [c0, c1) of the data P-columns ids[], in groups of wl_group<N>() lines.
-template <typename T, int N>
-__device__ __forceinline__ void wl_columns(cplx<T>* P, const int* ids, int c0, int c1, const cplx<T>* tw, int sign,
-                                           int lane) {
-  constexpr int G = wl_group<N>();
-  for (int c = c0; c < c1; c += G) {
-    const int nl = c1 - c < G ? c1 - c : G;
-    wl_stages<T, N, 0, 1>(P, WlCols{ids + c, N + 1}, nl, tw, sign, lane);
-  }
-}
-
-template <typename T, int N, int MINB>
-__global__ void __launch_bounds__(kCtThreads, MINB)
-k_plane_wl(const __grid_constant__ HpsiBatch<T> B, int n3, const cplx<T>* __restrict__ tw1,
-           const cplx<T>* __restrict__ tw2) {
-  using C = cplx<T>;
-  constexpr int PITCH = N + 1;
-  constexpr int NW = kCtThreads / 32;
-  constexpr int G = wl_group<N>();
-  static_assert(N % NW == 0, "the plane's rows are split evenly over the warps");
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* P = reinterpret_cast<C*>(smem_raw);
-  __shared__ int ids[N];
-  const HpsiItem<T>& I = B.it[batch_item(B, blockIdx.x, true)];
-  const SphereDev& sp = I.sp;
-  const int local = blockIdx.x - I.pstart;
-  const int b = local / n3, i3 = local - b * n3;
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  C* S = I.scratch + ((size_t)b * n3 + i3) * sp.ncol;
-  for (int idx = threadIdx.x; idx < N * PITCH; idx += kCtThreads) P[idx] = mk<T>(0, 0);
-  for (int r = threadIdx.x; r < sp.nrow; r += kCtThreads) ids[r] = sp.row_i1[r];
-  __syncthreads();
-  for (int c = threadIdx.x; c < sp.ncol; c += kCtThreads) P[sp.col_i2[c] * PITCH + sp.col_i1[c]] = S[c];
-  __syncthreads();
-  const int c0 = (w * sp.nrow) / NW, c1 = ((w + 1) * sp.nrow) / NW;
-  wl_columns<T, N>(P, ids, c0, c1, tw2, +1, lane);  // inverse along y
-  __syncthreads();
-  const T* vrow = I.vplane + (size_t)i3 * N * N;
-  for (int r0 = w * (N / NW); r0 < (w + 1) * (N / NW); r0 += G) {
-    const int nl = (w + 1) * (N / NW) - r0 < G ? (w + 1) * (N / NW) - r0 : G;
-    wl_stages<T, N, 0, 1>(P, WlRows{PITCH, r0}, nl, tw1, +1, lane);  // inverse along x
-    for (int e = lane; e < nl * N; e += 32) {
-      const int l = e / N, i1 = e - l * N;
-      C& z = P[(r0 + l) * PITCH + i1];
-      const T v = vrow[(size_t)(r0 + l) * N + i1];
+  if constexpr (FX) {
+    ct_cols_vmul<T, N, kCtThreads, V>(P, PITCH, tw1, vp);
+  } else {
+    ct_lines<T, N, kCtThreads, LinesCols, V>(P, LinesCols{PITCH}, N, tw1, +1);
+    for (int idx = threadIdx.x; idx < N * N; idx += kCtThreads) {
+      const int a = idx / N, c = idx - a * N;
+      C& z = P[a * PITCH + c];
+      const T v = vp[idx];
       z.x *= v;
       z.y *= v;
     }
-    __syncwarp();
-    wl_stages<T, N, 0, 1>(P, WlRows{PITCH, r0}, nl, tw1, -1, lane);  // forward along x
+    __syncthreads();
+    ct_lines<T, N, kCtThreads, LinesCols, V>(P, LinesCols{PITCH}, N, tw1, -1);
   }
-  __syncthreads();
-  wl_columns<T, N>(P, ids, c0, c1, tw2, -1, lane);  // forward along y
-  __syncthreads();
-  for (int c = threadIdx.x; c < sp.ncol; c += kCtThreads) S[c] = P[sp.col_i2[c] * PITCH + sp.col_i1[c]];
+  ct_lines<T, N, kCtThreads, LinesRows, V>(P, LinesRows{rows, PITCH}, sp.nrow, tw2, -1);
+  for (int c = threadIdx.x; c < sp.ncol; c += kCtThreads) S[c] = P[sp.col_i1[c] * PITCH + sp.col_i2[c]];
 }
 
 template <typename T, int N>
@@ -455,21 +313,25 @@ static void ct_zfwd(int n3, unsigned blocks, cudaStream_t st, const HpsiBatch<T>
   }
 }
 
-// Plane-pass variants tried by the tuner (FP32 only; FP64 runs variant 0):
+// Plane-pass variants tried by the tuner (FP32; FP64 tries 0 and 4):
 //   0: budget 16, odd radices first, 4 CTAs/SM    1: budget 18, odd first, 2 CTAs/SM
 //   2: budget 16, largest radix first, 4 CTAs/SM  3: budget 18, odd first, 3 CTAs/SM
+//   4: variant 0 with the fused x pass (FX)        5: the same at 3 CTAs/SM (no spills)
 // (Measured and dropped: 288-thread CTAs, which hold the ~33 sphere rows in one radix-9 batch
-// and the 72 columns in two, ran 1.75 ms at 3 CTAs/SM and 2.30 ms at 2 against 1.49 ms.)
-//   4: warp-local line transforms (k_plane_wl), 3 CTAs/SM   5: the same, 4 CTAs/SM
+// and the 72 columns in two, ran 1.75 ms at 3 CTAs/SM and 2.30 ms at 2 against 1.49 ms; warp-
+// local line transforms, each line owned by one warp so that a stage synchronises only that
+// warp, ran 2.21 ms against 1.50 ms: the plane pass is bound by shared-memory bandwidth, not
+// by its barriers, and the warp-local layout conflicts on more banks.)
 constexpr int kPlaneVariants = 6;
+template <typename T> constexpr bool plane_variant_ok(int v) { return sizeof(T) == 4 ? (v >= 0 && v < kPlaneVariants) : (v == 0 || v == 4); }
 
-template <typename T, int N, int V, int MINB>
+template <typename T, int N, int V, int MINB, bool FX = false>
 static void ct_plane_launch(unsigned blocks, cudaStream_t st, const HpsiBatch<T>& B, int n3, const cplx<T>* tw1,
                             const cplx<T>* tw2) {
   const size_t sm = (size_t)N * (N + 1) * sizeof(cplx<T>);
-  ct_allow_smem(k_plane_ct<T, N, V, MINB>, sm);
+  ct_allow_smem(k_plane_ct<T, N, V, MINB, FX>, sm);
   count_launches(1);
-  k_plane_ct<T, N, V, MINB><<<blocks, kCtThreads, sm, st>>>(B, n3, tw1, tw2);
+  k_plane_ct<T, N, V, MINB, FX><<<blocks, kCtThreads, sm, st>>>(B, n3, tw1, tw2);
 }
 
 template <typename T, int N>
@@ -479,18 +341,10 @@ static void ct_plane_variant(int variant, unsigned blocks, cudaStream_t st, cons
     if (variant == 1) return ct_plane_launch<T, N, 1, 2>(blocks, st, B, n3, tw1, tw2);
     if (variant == 2) return ct_plane_launch<T, N, 16, 4>(blocks, st, B, n3, tw1, tw2);
     if (variant == 3) return ct_plane_launch<T, N, 1, 3>(blocks, st, B, n3, tw1, tw2);
-    if (variant == 4 || variant == 5) {
-      const size_t sm = (size_t)N * (N + 1) * sizeof(cplx<T>);
-      count_launches(1);
-      if (variant == 4) {
-        ct_allow_smem(k_plane_wl<T, N, 3>, sm);
-        k_plane_wl<T, N, 3><<<blocks, kCtThreads, sm, st>>>(B, n3, tw1, tw2);
-      } else {
-        ct_allow_smem(k_plane_wl<T, N, 4>, sm);
-        k_plane_wl<T, N, 4><<<blocks, kCtThreads, sm, st>>>(B, n3, tw1, tw2);
-      }
-      return;
-    }
+    if (variant == 4) return ct_plane_launch<T, N, 0, 4, true>(blocks, st, B, n3, tw1, tw2);
+    if (variant == 5) return ct_plane_launch<T, N, 0, 3, true>(blocks, st, B, n3, tw1, tw2);
+  } else {
+    if (variant == 4) return ct_plane_launch<T, N, 0, 2, true>(blocks, st, B, n3, tw1, tw2);
   }
   ct_plane_launch<T, N, 0, (sizeof(T) == 4 ? 4 : 2)>(blocks, st, B, n3, tw1, tw2);
 }
@@ -514,7 +368,7 @@ static void ct_plane(int n, unsigned blocks, cudaStream_t st, const HpsiBatch<T>
 // for that shape.  Smaller batches (the eigensolver's residual blocks) use the tuned choice
 // when there is one, else variant 0.  Never runs while the stream is being captured.
 // FDE_PLANE_VARIANT=<v> in the environment pins the variant (reproducible rounding across
-// machines).
+// machines); an FP64 plane pass runs a pinned 4 as 4 and every other pin as 0.
 constexpr unsigned kTuneMinPlanes = 4096;
 struct PlaneTuner {
   std::mutex mu;
@@ -543,9 +397,8 @@ inline int tuned_plane_variant(int n, int n3) {
 template <typename T>
 static int plane_variant(int n, int n3, unsigned zb, unsigned pb, cudaStream_t st, const HpsiBatch<T>& B,
                          const FftPlans<T>& fp) {
-  if (sizeof(T) != 4) return 0;
   const int pinned = plane_pin().load();
-  if (pinned >= 0) return pinned;
+  if (pinned >= 0) return plane_variant_ok<T>(pinned) ? pinned : 0;
   const auto key = std::make_tuple(n, n3, (int)sizeof(T));
   PlaneTuner& tuner = plane_tuner();
   std::lock_guard<std::mutex> lock(tuner.mu);
@@ -561,6 +414,7 @@ static int plane_variant(int n, int n3, unsigned zb, unsigned pb, cudaStream_t s
   int bestv = 0;
   float bestt = 1e30f;
   for (int v = 0; v < kPlaneVariants; ++v) {
+    if (!plane_variant_ok<T>(v)) continue;
     ct_zinv<T>(n3, zb, st, B, fp.p3.tw);
     cudaEventRecord(a, st);
     ct_plane<T>(n, pb, st, B, n3, fp.p1.tw, fp.p2.tw, v);

@@ -13,7 +13,6 @@ template bool launch_hpsi_batch_ct<float>(const HpsiItemDesc<float>*, int, const
 template bool launch_fft3d_ct<float>(cplx<float>*, const GridDims&, const FftPlans<float>&, int, cudaStream_t);
 
 int query_plane_variant(int n1, int n3) { return tuned_plane_variant(n1, n3); }
-bool hpsi_plane_transposed_f32(const GridDims& g) { return ct_plane_ok<float>(g.n1, g.n2) && ct_line_ok<float>(g.n3); }
 bool pin_plane_variant(int v) {
   if (v < -1 || v >= kPlaneVariants) return false;
   plane_pin().store(v);

@@ -78,12 +78,6 @@ bool launch_fft3d_ct(cplx<T>* data, const GridDims& g, const FftPlans<T>& fp, in
 // out[j][i] = (Tout) in[i][j], in is [rows][cols]; with optional accumulate.
 template <typename Tin, typename Tout>
 void launch_transpose(const Tin* in, Tout* out, int rows, int cols, int accumulate, cudaStream_t st);
-// v[i1][i2][i3] (FP64) -> out[i3][i2][i1] (FP32): the potential planes of the mixed path's
-// compile-time plane pass, each plane transposed so that a row holds fixed i2.
-void launch_to_plane_t(const double* in, float* out, const GridDims& g, cudaStream_t st);
-// True when FP32 H psi on this grid runs the compile-time kernels, which read the potential in
-// the transposed plane layout of launch_to_plane_t.
-bool hpsi_plane_transposed_f32(const GridDims& g);
 
 // ---- dense complex algebra (linalg.cu) --------------------------------------------------
 // C[i][j] = sum_g conj(A[i][g]) B[j][g], A [m][K] (lda), B [n][K] (ldb); C [m][n] FP64
@@ -130,6 +124,8 @@ struct KbBlock {
 // Q[a np + i][b] = sum_j D[i][j] P[a np + j][b] for natoms atoms and nb columns (FP64 complex,
 // leading dimension nb).
 void launch_kb_couple(const double2* P, const KbBlock& D, int natoms, int nb, double2* Q, cudaStream_t st);
+// The same with its own np x np block for every atom: D [natoms][np][np] (device).
+void launch_kb_couple_atoms(const double2* P, const double* D, int np, int natoms, int nb, double2* Q, cudaStream_t st);
 
 // Cholesky S = L L^H (n x n, FP64 complex, lower, in place into L) and Linv = L^{-1};
 // sets status bit ST_CHOLESKY on a pivot not above rel_pivot S_jj (the squared norm of a

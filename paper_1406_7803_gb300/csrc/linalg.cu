@@ -352,6 +352,38 @@ void launch_kb_couple(const double2* P, const KbBlock& D, int natoms, int nb, do
   k_kb_couple<<<blocks, 256, 0, st>>>(P, D, natoms, nb, Q);
 }
 
+// The same with a different block for every atom: D [natoms][np][np] in device memory (the
+// screened couplings of ultrasoft-like atoms).
+__global__ void k_kb_couple_atoms(const double2* __restrict__ P, const double* __restrict__ D, int np, int natoms,
+                                  int nb, double2* __restrict__ Q) {
+  const long long n = (long long)natoms * np * nb;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n; idx += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(idx % nb);
+    const long long r = idx / nb;
+    const int i = (int)(r % np);
+    const int a = (int)(r / np);
+    const long long base = (r - i) * nb + b;
+    const double* Da = D + (size_t)a * np * np;
+    double re = 0, im = 0;
+    for (int j = 0; j < np; ++j) {
+      const double d = Da[i * np + j];
+      const double2 p = P[base + (long long)j * nb];
+      re += d * p.x;
+      im += d * p.y;
+    }
+    Q[idx] = make_double2(re, im);
+  }
+}
+
+void launch_kb_couple_atoms(const double2* P, const double* D, int np, int natoms, int nb, double2* Q, cudaStream_t st) {
+  const long long n = (long long)natoms * np * nb;
+  if (n <= 0) return;
+  count_launches(1);
+  ProfScope prof_("k_kb_couple", st);
+  const int blocks = (int)std::min<long long>((n + 255) / 256, 1024);
+  k_kb_couple_atoms<<<blocks, 256, 0, st>>>(P, D, np, natoms, nb, Q);
+}
+
 __global__ void k_hermitize(double2* A, int n) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= n * n) return;

@@ -10,10 +10,12 @@
 // a_j = <m R_j, D_j> / |m R_j|^2 comes from a first pass; by the envelope theorem the
 // gradient of the minimised loss is that of |a m R - D|^2 at fixed a.
 #include <cuda_bf16.h>
+#include <algorithm>
 #include <math.h>
 
 #include "precond.h"
 #include "prof.h"
+#include "tc.cuh"
 
 namespace fde {
 
@@ -96,6 +98,177 @@ k_precond_apply(const cplx<T>* __restrict__ R, int ldr, const T* __restrict__ ki
     const float o = mlp_forward(w, f, ha, hb, ha);  // the third layer reuses the first's registers
     const float m = tpa_f(y) * expf(o);
     W[(size_t)j * ldw + g] = mk<T>((T)(m * (float)r.x), (T)(m * (float)r.y));
+  }
+}
+
+// ---- inference on the tensor cores ----------------------------------------------------------
+// The two 64 x 64 hidden layers as BF16 tcgen05 MMAs (kind::f16, M = 128 points, N = 64
+// neurons, K = 16 per MMA, FP32 accumulation in tensor memory).  The weights are the bf16
+// inference weights, so only the activations are rounded: each is split h = hi + lo with
+// hi = bf16(h) and lo = bf16(h - hi) (|h - hi - lo| <= 2^-18 |h|), and a layer is W hi + W lo,
+// two passes of four MMAs.  The first layer (three inputs), the tanh of every layer, the
+// output layer and the multiplier run on the CUDA cores, one thread per point.  Persistent
+// CTAs of 128 threads loop over tiles of 128 points (consecutive G of one band); thread t owns
+// point t of a tile, which is row t of the A operand and lane t of the accumulator.
+// tanh(x) = (e^{2x} - 1) / (e^{2x} + 1) with the hardware exponential and division
+// (absolute error ~2e-7), the argument clamped to |x| <= 15 where tanh is 1 in FP32.
+constexpr int kPcThreads = 128;
+constexpr int kPcCtasPerSm = 4;
+constexpr int kPcAct = kPcThreads * 128;  // bytes of one 128 x 64 bf16 activation tile
+constexpr int kPcW = kH * 128;            // bytes of one 64 x 64 bf16 weight tile
+constexpr int kPcSmem = 1024 + 2 * kPcAct + 2 * kPcW;
+constexpr int kPcTmemCols = 64;
+// kind::f16 instruction descriptor: D f32 (bits 4-5 = 1), A and B bf16 (bits 7-9, 10-12 = 1),
+// both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+constexpr uint32_t kPcIdesc =
+    (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kH / 8) << 17) | ((uint32_t)(kPcThreads / 16) << 24);
+// small parameters in shared memory (float): W1, b1, b2, b3, W4, b4
+constexpr int sW1 = 0, sb1 = sW1 + 3 * kH, sb2 = sb1 + kH, sb3 = sb2 + kH, sW4 = sb3 + kH, sb4 = sW4 + kH,
+              sEnd = sb4 + 1;
+
+__device__ unsigned g_pc_status;
+__device__ long long g_pc_spin = kTcSpin;
+
+__device__ __forceinline__ float tanh_tc(float x) {
+  const float t = __expf(2.f * fminf(fmaxf(x, -15.f), 15.f));
+  return __fdividef(t - 1.f, t + 1.f);
+}
+__device__ __forceinline__ uint32_t bf16x2_bits(float a, float b) {  // a in the low half
+  const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+// Row t of the hi and lo activation tiles (128-byte rows, 16-byte chunks swizzled by t mod 8).
+__device__ __forceinline__ void store_split(uint32_t a_hi, uint32_t a_lo, int t, const float* h) {
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    uint32_t hb[4], lb[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float x0 = h[8 * c + 2 * q], x1 = h[8 * c + 2 * q + 1];
+      hb[q] = bf16x2_bits(x0, x1);
+      const __nv_bfloat162 hv = *reinterpret_cast<const __nv_bfloat162*>(&hb[q]);
+      lb[q] = bf16x2_bits(x0 - __low2float(hv), x1 - __high2float(hv));
+    }
+    const uint32_t off = (uint32_t)(t * 128 + ((c ^ (t & 7)) << 4));
+    st_shared_v4(a_hi + off, make_uint4(hb[0], hb[1], hb[2], hb[3]));
+    st_shared_v4(a_lo + off, make_uint4(lb[0], lb[1], lb[2], lb[3]));
+  }
+}
+__device__ __forceinline__ void mma_bf16(uint32_t dt, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dt),
+      "l"(a), "l"(b), "r"(kPcIdesc), "r"(acc)
+      : "memory");
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kPcThreads, kPcCtasPerSm)
+k_precond_apply_tc(const cplx<T>* __restrict__ R, int ldr, const T* __restrict__ kin, const double* __restrict__ tband,
+                   const double* __restrict__ sumsq, int nb, int K, const __nv_bfloat16* __restrict__ wb,
+                   cplx<T>* __restrict__ W, int ldw) {
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ float ws[sEnd];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag, drained;
+  const int t = threadIdx.x, warp = t >> 5;
+  const uint32_t base = (su32(smem_raw) + 1023u) & ~1023u;
+  const uint32_t a_hi = base, a_lo = base + kPcAct, w2s = base + 2 * kPcAct, w3s = w2s + kPcW;
+  for (int i = t; i < 3 * kH; i += kPcThreads) ws[sW1 + i] = __bfloat162float(wb[oW1 + i]);
+  for (int i = t; i < kH; i += kPcThreads) {
+    ws[sb1 + i] = __bfloat162float(wb[ob1 + i]);
+    ws[sb2 + i] = __bfloat162float(wb[ob2 + i]);
+    ws[sb3 + i] = __bfloat162float(wb[ob3 + i]);
+    ws[sW4 + i] = __bfloat162float(wb[oW4 + i]);
+  }
+  if (t == 0) ws[sb4] = __bfloat162float(wb[ob4]);
+  // B operands: row i of W2 / W3 (the weights into neuron i), K-major, 128-byte swizzle
+  for (int q = t; q < 2 * kH * 8; q += kPcThreads) {
+    const int m = q / (kH * 8), r = (q >> 3) % kH, c = q & 7;
+    const uint4 v = reinterpret_cast<const uint4*>(wb + (m ? oW3 : oW2) + r * kH)[c];
+    st_shared_v4((m ? w3s : w2s) + (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4)), v);
+  }
+  if (t == 0) {
+    mbar_init(su32(&bar), 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_slot)),
+                 "r"(kPcTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_proxy_async();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
+  const int tiles_per_band = (K + kPcThreads - 1) / kPcThreads;
+  const long long ntiles = (long long)nb * tiles_per_band;
+  unsigned phase = 0;
+  bool ok = true;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int j = (int)(tile / tiles_per_band);
+    const int g = (int)(tile - (long long)j * tiles_per_band) * kPcThreads + t;
+    const bool valid = g < K;
+    const cplx<T> r = valid ? R[(size_t)j * ldr + g] : mk<T>(0, 0);
+    const float rx = (float)r.x, ry = (float)r.y;
+    float f[3], y;
+    features(valid ? (float)kin[g] : 0.f, (float)tband[j], sqrtf(rx * rx + ry * ry),
+             (float)sqrt(sumsq[j] / (double)K), f, &y);
+    float h[kH];
+#pragma unroll
+    for (int i = 0; i < kH; ++i)
+      h[i] = tanh_tc(ws[sb1 + i] + ws[sW1 + 3 * i] * f[0] + ws[sW1 + 3 * i + 1] * f[1] + ws[sW1 + 3 * i + 2] * f[2]);
+    store_split(a_hi, a_lo, t, h);
+#pragma unroll 1
+    for (int layer = 0; layer < 2; ++layer) {
+      tc_fence_proxy_async();
+      tc_fence_before();
+      __syncthreads();
+      if (t == 0) {
+        tc_fence_after();
+        const uint32_t wsm = layer ? w3s : w2s;
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) mma_bf16(tmem, sdesc(a_hi + 32u * kk), sdesc(wsm + 32u * kk), kk > 0 ? 1u : 0u);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) mma_bf16(tmem, sdesc(a_lo + 32u * kk), sdesc(wsm + 32u * kk), 1u);
+        mma_commit(su32(&bar));
+        if (!mbar_wait(su32(&bar), phase, g_pc_spin)) abort_flag = 1;
+      }
+      __syncthreads();
+      phase ^= 1u;
+      if (abort_flag) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+#pragma unroll
+      for (int c = 0; c < kH; c += 16) tmem_ld16(trow + (uint32_t)c, h + c);
+      const float* bl = ws + (layer ? sb3 : sb2);
+#pragma unroll
+      for (int i = 0; i < kH; ++i) h[i] = tanh_tc(h[i] + bl[i]);
+      if (layer == 0) store_split(a_hi, a_lo, t, h);  // the MMAs that read the tile have completed
+    }
+    if (!ok) break;
+    float o = ws[sb4];
+#pragma unroll
+    for (int k = 0; k < kH; ++k) o += ws[sW4 + k] * h[k];
+    const float m = tpa_f(y) * expf(o);
+    if (valid) W[(size_t)j * ldw + g] = mk<T>((T)(m * rx), (T)(m * ry));
+  }
+  // after a timeout: wait (bounded) for the outstanding MMAs before tensor memory is released
+  if (t == 0) drained = ok ? 1 : (mbar_wait(su32(&bar), phase ^ 1u) ? 1 : 0);
+  tc_fence_before();
+  __syncthreads();
+  if (!ok && t == 0) atomicOr(&g_pc_status, drained ? ST_TIMEOUT : (ST_TIMEOUT | ST_TMEM_HELD));
+  if (warp == 0 && drained) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kPcTmemCols) : "memory");
   }
 }
 
@@ -304,13 +477,56 @@ __global__ void k_precond_to_bf16(const float* __restrict__ wf, __nv_bfloat16* _
   if (rounded) rounded[p] = __bfloat162float(wb[p]);
 }
 
+static bool g_pc_tc = true;  // tensor-core inference (default) or the CUDA-core kernel
+void set_precond_tensor_cores(bool on) { g_pc_tc = on; }
+bool precond_tensor_cores() { return g_pc_tc && !tensor_cores_disabled(); }
+
 template <typename T>
 void launch_precond_apply(const cplx<T>* R, int ldr, const T* kin, const double* tband, const double* sumsq, int nb,
                           int K, const void* wb, cplx<T>* W, int ldw, cudaStream_t st) {
-  if (nb <= 0) return;
+  if (nb <= 0 || K <= 0) return;
+  if (precond_tensor_cores()) {
+    static int attr = 0, sms = 0;  // 1 configured, -1 failed
+    if (attr == 0) {
+      int dev = 0;
+      const bool ok = cudaGetDevice(&dev) == cudaSuccess &&
+                      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+                      cudaFuncSetAttribute(k_precond_apply_tc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           kPcSmem) == cudaSuccess &&
+                      cudaFuncSetAttribute(k_precond_apply_tc<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           kPcSmem) == cudaSuccess;
+      attr = ok ? 1 : -1;
+    }
+    if (attr > 0) {
+      const long long tiles = (long long)nb * ceil_div(K, kPcThreads);
+      const int grid = (int)std::min<long long>(tiles, (long long)sms * kPcCtasPerSm);
+      count_launches(1);
+      ProfScope p("k_precond_apply_tc", st);
+      k_precond_apply_tc<T><<<grid, kPcThreads, kPcSmem, st>>>(R, ldr, kin, tband, sumsq, nb, K,
+                                                               (const __nv_bfloat16*)wb, W, ldw);
+      return;
+    }
+  }
   count_launches(1);
+  ProfScope p("k_precond_apply", st);
   k_precond_apply<T><<<dim3(ceil_div(K, 128 * 4), nb), 128, 0, st>>>(R, ldr, kin, tband, sumsq, K,
                                                                       (const __nv_bfloat16*)wb, W, ldw);
+}
+
+// Status bits raised by the tensor-core inference since the last call (read and cleared;
+// synchronises the stream); a kernel that kept its tensor memory turns the tensor cores off.
+unsigned precond_tc_take_status(cudaStream_t st) {
+  unsigned h = 0, z = 0;
+  if (cudaMemcpyFromSymbolAsync(&h, g_pc_status, sizeof(unsigned), 0, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return 0;
+  if (h) cudaMemcpyToSymbolAsync(g_pc_status, &z, sizeof(unsigned), 0, cudaMemcpyHostToDevice, st);
+  if (h & ST_TMEM_HELD) disable_tensor_cores();
+  return h;
+}
+bool set_precond_tc_spin(long long polls) {
+  const long long v = polls < 0 ? kTcSpin : std::min(polls, kTcSpin);
+  return cudaMemcpyToSymbol(g_pc_spin, &v, sizeof(v)) == cudaSuccess;
 }
 
 int precond_grad_blocks(int nb, int K) { return ceil_div((long long)nb * K, kGradBlock); }

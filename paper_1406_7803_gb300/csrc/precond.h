@@ -14,6 +14,13 @@ template <typename T>
 void launch_precond_apply(const cplx<T>* R, int ldr, const T* kin, const double* tband, const double* sumsq, int nb,
                           int K, const void* wb, cplx<T>* W, int ldw, cudaStream_t st);
 
+// Inference on the tensor cores (default) or on the CUDA cores; status bits of the
+// tensor-core inference (read and cleared, synchronising); its mbarrier poll limit.
+void set_precond_tensor_cores(bool on);
+bool precond_tensor_cores();
+unsigned precond_tc_take_status(cudaStream_t st);
+bool set_precond_tc_spin(long long polls);
+
 // Loss sum_j min_a |a m R_j - D_j|^2 / |D_j|^2 (a complex) and its gradient over nb x K pairs;
 // part: precond_grad_blocks(nb, K) x (kPrecondParams + 1) floats; awork:
 // precond_alpha_work(nb) doubles; out[kPrecondParams + 1] (gradient, then the loss) is

@@ -41,7 +41,8 @@ class SubsysDesc(C.Structure):
                 ("rc", C.c_double), ("nproj_per_atom", C.c_int), ("proj_sigma", C.POINTER(C.c_double)),
                 ("proj_D", C.POINTER(C.c_double)), ("nbands", C.c_int), ("nk", C.c_int),
                 ("kpts", C.POINTER(C.c_double)), ("wk", C.POINTER(C.c_double)), ("nelec", C.c_double),
-                ("smearing_ha", C.c_double), ("smearing_kind", C.c_int)]
+                ("smearing_ha", C.c_double), ("smearing_kind", C.c_int), ("proj_Q", C.POINTER(C.c_double)),
+                ("aug_sigma", C.c_double)]
 
 
 class Energies(C.Structure):
@@ -63,6 +64,7 @@ EXPORTS = {
     "fde_set_veff": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "fde_apply_h": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int]),
     "fde_apply_h_host": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int]),
+    "fde_apply_s": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int]),
     "fde_apply_h_all": (C.c_int, [C.c_void_p]),
     "fde_init_orbitals": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p]),
     "fde_set_orbitals": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p]),
@@ -88,6 +90,7 @@ EXPORTS = {
                                   C.c_void_p, C.c_int, C.c_int]),
     "fde_set_gemm_path": (C.c_int, [C.c_int]),
     "fde_set_tc_wait_limit": (C.c_int, [C.c_longlong]),
+    "fde_set_precond_path": (C.c_int, [C.c_int]),
     "fde_host_sphere": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
     "fde_host_ewald": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "fde_host_occupations": (C.c_int, [C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_int,
@@ -263,6 +266,14 @@ def set_tc_wait_limit(polls: int) -> None:
         raise FDEError(s, "fde_set_tc_wait_limit")
 
 
+def set_precond_path(path: int) -> None:
+    """Where the learned preconditioner's inference runs: 1 tensor cores (default), 0 CUDA
+    cores.  Process-wide."""
+    s = load().fde_set_precond_path(int(path))
+    if s != FDE_OK:
+        raise FDEError(s, "fde_set_precond_path: path must be 0 or 1")
+
+
 class FDEError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -330,15 +341,17 @@ class Context:
 
     # ---- setup --------------------------------------------------------------------------
     def add_subsystem(self, pos, Z, rc, nbands, kpts, wk, nelec, smearing, proj_sigma=(), proj_D=(),
-                      smearing_kind="fermi"):
+                      smearing_kind="fermi", proj_Q=(), aug_sigma=0.0):
         pos, ppos = _dbl(np.asarray(pos).reshape(-1, 3))
         Z, pZ = _dbl(Z)
         kpts, pk = _dbl(np.asarray(kpts).reshape(-1, 3))
         wk, pw = _dbl(wk)
         sig, psig = _dbl(proj_sigma if len(proj_sigma) else [0.0])
         D, pD = _dbl(np.asarray(proj_D).reshape(-1) if len(proj_sigma) else [0.0])
+        Q, pQ = _dbl(np.asarray(proj_Q).reshape(-1) if len(proj_Q) else [0.0])
         d = SubsysDesc(int(Z.size), ppos, pZ, float(rc), int(len(proj_sigma)), psig, pD, int(nbands),
-                       int(kpts.shape[0]), pk, pw, float(nelec), float(smearing), int(SMEAR_KINDS[smearing_kind]))
+                       int(kpts.shape[0]), pk, pw, float(nelec), float(smearing), int(SMEAR_KINDS[smearing_kind]),
+                       pQ if len(proj_Q) else None, float(aug_sigma))
         sid = C.c_int()
         self._check(self.lib.fde_add_subsystem(self.h, C.byref(d), C.byref(sid)), "fde_add_subsystem")
         self.nsub += 1
@@ -372,6 +385,9 @@ class Context:
 
     def apply_h(self, sub, k, psi, hpsi, nb):
         return self._check(self.lib.fde_apply_h(self.h, sub, k, _dptr(psi), _dptr(hpsi), int(nb)), "fde_apply_h")
+
+    def apply_s(self, sub, k, psi, spsi, nb):
+        return self._check(self.lib.fde_apply_s(self.h, sub, k, _dptr(psi), _dptr(spsi), int(nb)), "fde_apply_s")
 
     def apply_h_host(self, sub, k, psi, hpsi, nb):
         return self._check(self.lib.fde_apply_h_host(self.h, sub, k, _hptr(psi), _hptr(hpsi), int(nb)),
@@ -566,7 +582,7 @@ def context_from_workload(wl: workloads.Workload, prec="fp64", stream=None) -> C
     ctx = Context(wl.lattice, wl.grid, wl.ecut, wl.xc, wl.kedf, wl.rho_cut, prec, stream)
     for s in wl.subsystems:
         ctx.add_subsystem(s.pos, s.Z, s.rc, s.nbands, s.kpts, s.wk, s.nelec, s.smearing,
-                          s.proj_sigma, s.proj_D, s.smearing_kind)
+                          s.proj_sigma, s.proj_D, s.smearing_kind, s.proj_Q, s.aug_sigma)
     return ctx
 
 

@@ -48,6 +48,11 @@ class Subsystem:
     proj_sigma: Tuple[float, ...] = ()
     proj_D: Tuple[Tuple[float, ...], ...] = ()
     smearing_kind: str = "fermi"  # "fermi", "mp" (first-order Methfessel-Paxton) or "gauss"
+    # ultrasoft augmentation of the atoms of this subsystem (empty: norm-conserving): the overlap
+    # S = 1 + sum_a |beta_a> q <beta_a| and augmentation charges q_ij g_a(r), g_a a normalised
+    # Gaussian of width aug_sigma on the atom
+    proj_Q: Tuple[Tuple[float, ...], ...] = ()
+    aug_sigma: float = 0.0
 
     @property
     def natoms(self) -> int:
@@ -209,6 +214,21 @@ def two_layer_slab_small(mp=(2, 2, 1), smearing_kind: str = "mp") -> Workload:
                     description="two slab layers (4 atoms Z=3, 8 bands each) on a 2x2x1 mesh, MP smearing")
 
 
+USPP_Q = ((0.25, 0.05), (0.05, 0.10))
+USPP_SIGMA = 0.7
+
+
+def uspp_small(q=USPP_Q, sigma: float = USPP_SIGMA) -> Workload:
+    """The small slab + molecule cell with ultrasoft-like atoms: every atom's two Gaussian
+    projectors also define the overlap S = 1 + sum_a |beta_a> q <beta_a| and augmentation
+    charges q_ij g_a(r) (g_a a normalised Gaussian of width sigma), subsystem by subsystem
+    (Appendix: subsystem-specific PAW / ultrasoft projectors)."""
+    import dataclasses
+    wl = molecule_on_slab_small()
+    subs = [dataclasses.replace(s, proj_Q=q, aug_sigma=sigma) for s in wl.subsystems]
+    return dataclasses.replace(wl, subsystems=subs, name=wl.name + "-uspp")
+
+
 def with_kpoints(wl: Workload, isub: int, kpts, wk) -> Workload:
     """The same workload with the k-points and weights of one subsystem replaced."""
     import dataclasses
@@ -254,7 +274,7 @@ def supersystem(wl: Workload, extra_bands: int = 0) -> Workload:
     subsystem must carry the same projector set."""
     sm = [s for s in wl.subsystems if s.smearing > 0]
     ref = sm[0] if sm else wl.subsystems[0]
-    sig = {tuple(s.proj_sigma) for s in wl.subsystems}
+    sig = {(tuple(s.proj_sigma), tuple(s.proj_Q), s.aug_sigma) for s in wl.subsystems}
     if len(sig) != 1 or len({s.rc for s in wl.subsystems}) != 1:
         raise ValueError("the supersystem needs one projector set and one r_c")
     whole = Subsystem(name="supersystem",
@@ -264,7 +284,7 @@ def supersystem(wl: Workload, extra_bands: int = 0) -> Workload:
                       kpts=ref.kpts.copy(), wk=ref.wk.copy(),
                       nelec=float(sum(s.nelec for s in wl.subsystems)), smearing=ref.smearing,
                       proj_sigma=tuple(ref.proj_sigma), proj_D=tuple(ref.proj_D),
-                      smearing_kind=ref.smearing_kind)
+                      smearing_kind=ref.smearing_kind, proj_Q=tuple(ref.proj_Q), aug_sigma=ref.aug_sigma)
     return Workload(name=wl.name + "-supersystem", lattice=wl.lattice.copy(), grid=wl.grid, ecut=wl.ecut,
                     subsystems=[whole], xc=wl.xc, kedf=wl.kedf, seed=wl.seed, tol=wl.tol, rho_cut=wl.rho_cut,
                     description="supersystem KS reference of " + wl.name)

@@ -79,6 +79,7 @@ def test_large_cell_veff_and_hot_step_match_oracle(cell):
             npw = ctx.basis(I, k).shape[0]
             c = workloads.raw_orbitals(51, I, k, s.nbands, npw)
             ctx.set_orbitals(I, k, torch.from_numpy(c).cuda())
+            ctx.sync()  # the copy is read on the context's stream
             if (I == 0 and k == SLAB_K) or I in (1, 16, 32):
                 picks[I, k] = c[[0, s.nbands // 2, s.nbands - 1]]
             del c
@@ -90,6 +91,7 @@ def test_large_cell_veff_and_hot_step_match_oracle(cell):
         assert np.array_equal(ctx.basis(I, k), sy.basis[I][0][0])
         got = torch.zeros((s.nbands, npw), dtype=torch.complex128, device="cuda")
         ctx.get_hpsi(I, k, got)
+        ctx.sync()  # the copy runs on the context's stream
         g = got.cpu().numpy()[[0, s.nbands // 2, s.nbands - 1]]
         want = sy.apply_h(I, 0, c, pot["veff"][I])
         assert band_err(g, want) < 1e-5, (I, k, band_err(g, want))

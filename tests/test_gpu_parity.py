@@ -154,6 +154,7 @@ def test_batched_hot_step_matches_oracle(prec, tol, graph):
             c = sy.initial_orbitals(I, k, workloads.raw_orbitals(31, I, k, s.nbands, npw))
             orbitals[I, k] = c
             ctx.set_orbitals(I, k, _dev(c))
+            ctx.sync()  # the upload is read on the context's stream
     ctx.hot_step(graph)
     if graph:
         ctx.hot_step(graph)  # a replay of the captured graph
@@ -162,6 +163,7 @@ def test_batched_hot_step_matches_oracle(prec, tol, graph):
         want = sy.apply_h(I, k, c, pot["veff"][I])
         out = torch.zeros_like(_dev(c))
         ctx.get_hpsi(I, k, out)
+        ctx.sync()  # the copy runs on the context's stream
         err = band_err(out.cpu().numpy(), want)
         # the GPU potential itself differs from the oracle's by < 1e-10 (FP64 build)
         assert err < tol, (I, k, err)
@@ -175,8 +177,8 @@ def slab_system():
 
 @pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5])
 def test_every_plane_variant_matches_oracle(slab_system, variant):
-    """Each compiled variant of the FP32 plane pass (register budget, CTAs per SM, radix order),
-    pinned in turn, gives the oracle's H psi on the full-size molecule-on-slab cell's batched
+    """Each compiled variant of the FP32 plane pass (register budget, CTAs per SM, radix order,
+    fused x pass), pinned in turn, gives the oracle's H psi on the full-size molecule-on-slab cell's batched
     pass within the mixed-precision tolerance (sampled bands of each (subsystem, k))."""
     wl, sy = slab_system
     rhos = np.array([workloads.initial_density(wl, I) for I in range(wl.nsub)])
@@ -202,11 +204,44 @@ def test_every_plane_variant_matches_oracle(slab_system, variant):
             ctx.get_orbitals(I, k, psi, s.nbands)
             out = torch.zeros_like(psi)
             ctx.get_hpsi(I, k, out)
+            ctx.sync()  # the copy runs on the context's stream
             pick = [0, s.nbands - 1]
             c = psi.cpu().numpy()[pick]
             want = sy.apply_h(I, k, c, veff[I])
             got = out.cpu().numpy()[pick]
             assert band_err(got, want) < 1e-5, (variant, I, k)
+
+
+@pytest.mark.parametrize("variant", [0, 4])
+def test_fp64_plane_variants_match_oracle(variant):
+    """The FP64 plane pass, plain and with the fused x pass (inverse last stage, potential
+    multiply and forward first stage on the same registers), gives the oracle's H psi to 1e-10
+    per band on the small molecule-on-slab cell (24 x 24 x 60)."""
+    wl = workloads.molecule_on_slab_small()
+    sy = ofde.System(wl)
+    rhos = np.array([workloads.initial_density(wl, I) for I in range(wl.nsub)])
+    pot = sy.build_veff(rhos)
+    ctx = fde.context_from_workload(wl, prec="fp64")
+    for I in range(wl.nsub):
+        ctx.set_density(I, rhos[I])
+    ctx.build_vemb()
+    fde.seed_workload(ctx, wl)
+    fde.pin_plane_variant(variant)
+    try:
+        ctx.apply_h_all()
+        ctx.sync()
+    finally:
+        fde.pin_plane_variant(-1)
+    for I, s in enumerate(wl.subsystems):
+        for k in range(s.nk):
+            npw = sy.basis[I][k][0].shape[0]
+            psi = torch.zeros((s.nbands, npw), dtype=torch.complex128, device="cuda")
+            ctx.get_orbitals(I, k, psi, s.nbands)
+            out = torch.zeros_like(psi)
+            ctx.get_hpsi(I, k, out)
+            ctx.sync()  # the copy runs on the context's stream
+            want = sy.apply_h(I, k, psi.cpu().numpy(), pot["veff"][I])
+            assert band_err(out.cpu().numpy(), want) < 1e-10, (variant, I, k)
 
 
 def test_apply_h_host_path_matches_device_path():

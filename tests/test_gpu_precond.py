@@ -80,7 +80,11 @@ def test_loss_and_gradient_match_oracle(pairs):
     assert np.abs(g - gr).max() < 2e-4 * np.abs(gr).max(), np.abs(g - gr).max() / np.abs(gr).max()
 
 
-def test_inference_matches_oracle_with_bf16_weights(pairs):
+@pytest.mark.parametrize("path", [1, 0])
+def test_inference_matches_oracle_with_bf16_weights(pairs, path):
+    """Inference with the bf16 weights against the oracle's FP64 evaluation of the same
+    weights: on the tensor cores (path 1: the two hidden layers as BF16 MMAs with the
+    activations split into two bf16 terms) and on the CUDA cores (path 0)."""
     wl, data = pairs
     w = _weights(6)
     ctx = fde.context_from_workload(wl)
@@ -88,13 +92,42 @@ def test_inference_matches_oracle_with_bf16_weights(pairs):
     _, wb = ctx.precond_get_weights()
     assert np.array_equal(wb.astype(np.float64), opre.bf16_round(w))
     pb = _unflat(opre.bf16_round(w))
-    for I, k, r, d, tb, kin in data:
-        want = opre.apply(pb, kin, tb, r)
-        rr = torch.from_numpy(r).cuda()
-        out = torch.zeros_like(rr)
-        ctx.precond_apply(I, k, rr, out, r.shape[0], tb)
-        got = out.cpu().numpy()
-        assert np.abs(got - want).max() < 2e-5 * np.abs(want).max()
+    fde.set_precond_path(path)
+    try:
+        for I, k, r, d, tb, kin in data:
+            want = opre.apply(pb, kin, tb, r)
+            rr = torch.from_numpy(r).cuda()
+            out = torch.zeros_like(rr)
+            ctx.precond_apply(I, k, rr, out, r.shape[0], tb)
+            got = out.cpu().numpy()
+            assert np.abs(got - want).max() < 2e-5 * np.abs(want).max(), (path, np.abs(got - want).max() / np.abs(want).max())
+    finally:
+        fde.set_precond_path(1)
+
+
+def test_tensor_core_inference_timeout_returns_etimeout_and_recovers(pairs):
+    """The tensor-core inference waits for each layer's MMAs with a bounded poll; with the
+    limit at 0 the first wait runs out, the kernel drains its issued MMAs (full bound), frees
+    its tensor memory and the call returns FDE_ETIMEOUT; with the default limit the next call
+    is correct again."""
+    wl, data = pairs
+    w = _weights(6)
+    ctx = fde.context_from_workload(wl)
+    ctx.precond_set_weights(w)
+    pb = _unflat(opre.bf16_round(w))
+    I, k, r, d, tb, kin = data[1]
+    rr = torch.from_numpy(r).cuda()
+    out = torch.zeros_like(rr)
+    fde.set_tc_wait_limit(0)
+    try:
+        with pytest.raises(fde.FDEError) as e:
+            ctx.precond_apply(I, k, rr, out, r.shape[0], tb)
+        assert e.value.status == fde.FDE_ETIMEOUT
+    finally:
+        fde.set_tc_wait_limit(-1)
+    ctx.precond_apply(I, k, rr, out, r.shape[0], tb)
+    want = opre.apply(pb, kin, tb, r)
+    assert np.abs(out.cpu().numpy() - want).max() < 2e-5 * np.abs(want).max()
 
 
 def _solve_all(ctx, wl, precond, tol):
