@@ -243,11 +243,12 @@ fde_status fde_update_density(fde_ctx* ctx, int sub);
  * W1[64][3] b1[64] W2[64][64] b2[64] W3[64][64] b3[64] W4[64] b4.  Inference uses the
  * weights rounded to bfloat16 with FP32 accumulation: the two 64 x 64 layers as BF16
  * tensor-core MMAs (activations split into two bf16 terms, ~2^-18 relative; the default) or
- * on the CUDA cores (fde_set_precond_path); training keeps FP32 master weights.
+ * on the CUDA cores (fde_set_precond_path); training keeps FP32 master weights (split into two
+ * bf16 terms for the tensor-core forward, back-propagation and weight-gradient products).
  * Training pairs (R, D): D the ideal correction of residual R.  The loss is
  * sum_j sum_G |m_jG R_jG - D_jG|^2 / |D_j|^2; training takes full-batch Adam steps. */
-/* Where the learned preconditioner's inference runs, process-wide: 1 tensor cores (default),
- * 0 CUDA cores.  FDE_EINVAL for other values. */
+/* Where the learned preconditioner's inference and training kernels run, process-wide:
+ * 1 tensor cores (default), 0 CUDA cores.  FDE_EINVAL for other values. */
 fde_status fde_set_precond_path(int path);
 fde_status fde_set_precond(fde_ctx* ctx, int precond); /* preconditioner of fde_scf_subsystem /
                                                           fde_freeze_thaw_cycle solves */
@@ -422,15 +423,16 @@ fde_status fde_set_gemm_path(int path);
 fde_status fde_set_tc_wait_limit(long long polls);
 
 /* The FP32 plane pass of H psi (the (x, y) transforms, potential multiply and back) comes in
- * several compiled variants (register budget per thread, CTAs per SM, radix order of the
- * line transforms, fused x pass).  The first large batch of a grid shape times each once on the batch
+ * several compiled variants (CTAs per SM, radix order of the line transforms, fused x pass,
+ * thread mapping of the row transforms).  The first large batch of a grid shape times each once on the batch
  * itself and keeps the fastest (measurement support; no counterpart in the paper).  Returns the
  * variant chosen for plane side n1 and z length n3, or -1 if none was tuned yet; the
  * environment variable FDE_PLANE_VARIANT pins one. */
 int fde_tuned_plane_variant(int n1, int n3);
-/* Pin the plane-pass variant used from now on in this process (0 .. 5; 4 and 5 fuse the x pass:
+/* Pin the plane-pass variant used from now on in this process (0 .. 5; 2 .. 5 fuse the x pass:
  * the inverse transform's last stage, the potential multiply and the forward transform's first
- * stage on the same registers; FP64 plane passes run a pinned 4 as 4 and any other as 0), or
+ * stage on the same registers; 4 and 5 also map consecutive threads to neighbouring rows in the
+ * y transforms; FP64 plane passes run a pinned 0, 2 or 4 as it is and any other as 0), or
  * return to tuning (-1).  FDE_EINVAL for other values. */
 fde_status fde_pin_plane_variant(int variant);
 

@@ -1456,6 +1456,7 @@ template <typename T> struct EngineT : Engine {
   DBuf<float> pw, pm1, pm2, pround, gpart;
   DBuf<unsigned short> pwb;
   DBuf<double> gsum, dss, awork;
+  DBuf<C> gtmp;  // m R with the master weights (tensor-core training's scale pass)
   bool have_pw = false;
   int adam_step = 0;
   int precond_mode = FDE_PRECOND_TPA;
@@ -1587,8 +1588,9 @@ template <typename T> struct EngineT : Engine {
       KP<T>& q = kpt(p.sub, p.k);
       gpart.ensure((size_t)precond_grad_blocks(p.n, q.npw) * (kPrecondParams + 1));
       awork.ensure(precond_alpha_work(p.n));
+      gtmp.ensure((size_t)p.n * q.npw);
       launch_precond_grad<T>(p.R.p, p.D.p, p.n, q.npw, q.kin_d.p, p.tb.p, p.ss.p, p.dn.p, pw.p, gpart.p, awork.p,
-                             gsum.p, st);
+                             gtmp.p, gsum.p, st);
       CK(cudaMemcpyAsync(h.data(), gsum.p, (kPrecondParams + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
       for (int a = 0; a <= kPrecondParams; ++a) acc[a] += h[a];

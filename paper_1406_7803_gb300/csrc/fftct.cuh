@@ -46,8 +46,10 @@ __host__ __device__ constexpr CtPlan ct_factor(int n, int order = 0) {
 }
 
 // Variant V of the staged transform: bits 0-3 the register budget (0: 16 complex values per
-// thread for FP32 data, 9 for FP64; 1: 18 / 9), bit 4 the radix order of ct_factor.
+// thread for FP32 data, 9 for FP64; 1: 18 / 9), bit 4 the radix order of ct_factor, bit 5 the
+// thread mapping of unit-stride lines (ct_stage).
 __host__ __device__ constexpr int ct_order(int V) { return (V >> 4) & 1; }
+__host__ __device__ constexpr bool ct_linefast(int V) { return ((V >> 5) & 1) != 0; }
 
 // The same radices in the opposite order: the plan of a forward transform that starts where an
 // inverse transform of plan p ended (its first stage reads the groups p's last stage wrote).
@@ -157,6 +159,13 @@ struct LinesCols {  // line l at l, element stride pitch (columns of a plane)
   static constexpr bool kUnit = false;
 };
 
+// Thread mapping of the (line, butterfly) items: strided lines (plane columns) and, when
+// ct_linefast(V), unit-stride lines too: consecutive threads take the same butterfly of
+// neighbouring lines, so a half-warp touches 16 lines one pitch (an odd number of complex
+// values) apart -- every bank once, in every stage, for reads and for the stride-R writes of
+// the first stages alike.  Unit-stride lines batches may then be partial (l < nl checked).
+// Otherwise unit-stride lines are walked by consecutive threads (contiguous reads; the stride-R
+// writes of a stage with Ns = 1 conflict 2-way on 16-line planes).
 template <typename T, int N, int R, int NS, int NT, int NL, int V, typename A>
 __device__ __forceinline__ void ct_stage(cplx<T>* buf, const A& addr, int l0, int nl,
                                          const cplx<T>* __restrict__ tw, int sign) {
@@ -164,17 +173,16 @@ __device__ __forceinline__ void ct_stage(cplx<T>* buf, const A& addr, int l0, in
   constexpr int NB = N / R;
   constexpr int TWS = N / (NS * R);
   constexpr int IPT = ct_ipt<T, R, V>();
+  constexpr bool LF = !A::kUnit || ct_linefast(V);
   const int es = A::kUnit ? 1 : addr.pitch;
-  const int items = nl * NB;
+  const int items = (A::kUnit && LF) ? NL * NB : nl * NB;
   C v[IPT][R];
 #pragma unroll
   for (int it = 0; it < IPT; ++it) {
     const int w = threadIdx.x + it * NT;
-    if (w < items) {
-      // unit-stride lines: consecutive threads walk one line; strided lines (plane
-      // columns): consecutive threads walk neighbouring lines for conflict-free banks
-      int l, j;
-      if (A::kUnit) { l = w / NB; j = w - l * NB; } else { j = w / NL; l = w - j * NL; }
+    int l = 0, j = 0;
+    if (LF) { j = w / NL; l = w - j * NL; } else { l = w / NB; j = w - l * NB; }
+    if (w < items && l < nl) {
       const int k = j % NS;
       const C* a = buf + addr.base(l0 + l);
 #pragma unroll
@@ -194,9 +202,9 @@ __device__ __forceinline__ void ct_stage(cplx<T>* buf, const A& addr, int l0, in
 #pragma unroll
   for (int it = 0; it < IPT; ++it) {
     const int w = threadIdx.x + it * NT;
-    if (w < items) {
-      int l, j;
-      if (A::kUnit) { l = w / NB; j = w - l * NB; } else { j = w / NL; l = w - j * NL; }
+    int l = 0, j = 0;
+    if (LF) { j = w / NL; l = w - j * NL; } else { l = w / NB; j = w - l * NB; }
+    if (w < items && l < nl) {
       const int k = j % NS;
       const int d = (j / NS) * NS * R + k;
       C* a = buf + addr.base(l0 + l);

@@ -134,8 +134,8 @@ k_zfwd_ct(const __grid_constant__ HpsiBatch<T> B, T inv_nr, const cplx<T>* __res
 // One CTA per (item, band, z-plane): columns in, 2D inverse FFT (y on the rows holding
 // columns, then x), potential multiply, 2D forward FFT, columns out.  n1 = n2 = N; the plane is
 // P[i1][i2] (pitch N + 1) and the potential plane vplane[i3][i1][i2].
-// Variants of the plane pass: V selects the staged transform's register budget and radix
-// order (fftct.cuh), MINB the CTAs per SM the registers are bounded for (four FP32 CTAs of
+// Variants of the plane pass: V selects the staged transform's register budget, radix order
+// and row thread mapping (fftct.cuh), MINB the CTAs per SM the registers are bounded for (four FP32 CTAs of
 // 42 KB for a 72 x 72 plane need <= 64 registers; FP64 planes of 84 KB fit two), FX fuses the
 // x pass: the inverse's last stage, the potential multiply and the forward's first stage run on
 // the same registers (ct_cols_vmul), one shared-memory round trip and one barrier pair fewer
@@ -313,17 +313,19 @@ static void ct_zfwd(int n3, unsigned blocks, cudaStream_t st, const HpsiBatch<T>
   }
 }
 
-// Plane-pass variants tried by the tuner (FP32; FP64 tries 0 and 4):
-//   0: budget 16, odd radices first, 4 CTAs/SM    1: budget 18, odd first, 2 CTAs/SM
-//   2: budget 16, largest radix first, 4 CTAs/SM  3: budget 18, odd first, 3 CTAs/SM
-//   4: variant 0 with the fused x pass (FX)        5: the same at 3 CTAs/SM (no spills)
-// (Measured and dropped: 288-thread CTAs, which hold the ~33 sphere rows in one radix-9 batch
-// and the 72 columns in two, ran 1.75 ms at 3 CTAs/SM and 2.30 ms at 2 against 1.49 ms; warp-
-// local line transforms, each line owned by one warp so that a stage synchronises only that
-// warp, ran 2.21 ms against 1.50 ms: the plane pass is bound by shared-memory bandwidth, not
-// by its barriers, and the warp-local layout conflicts on more banks.)
+// Plane-pass variants tried by the tuner (FP32; FP64 tries 0, 2 and 4 at 2 CTAs/SM):
+//   0: register budget 16, odd radices first, 4 CTAs/SM    1: largest radix first, 4 CTAs/SM
+//   2: fused x pass (FX), 4 CTAs/SM                         3: fused x pass, 3 CTAs/SM
+//   4: fused x pass, line-fastest row mapping, 4 CTAs/SM    5: the same, 3 CTAs/SM
+// Measured on the 72 x 72 x 180 cell: variant 0 1.49 ms, largest-first 1.56 ms, budget 18 at
+// 3 / 2 CTAs/SM 1.75 / 2.00 ms (dropped), fused x at 3 CTAs/SM 1.35 ms.  Also dropped:
+// 288-thread CTAs (1.75 / 2.30 ms); warp-local line transforms, each line owned by one warp so
+// that a stage synchronises only that warp (2.21 ms: the pass is bound by shared-memory
+// bandwidth, not by its barriers, and the transposed layout conflicts on more banks).
 constexpr int kPlaneVariants = 6;
-template <typename T> constexpr bool plane_variant_ok(int v) { return sizeof(T) == 4 ? (v >= 0 && v < kPlaneVariants) : (v == 0 || v == 4); }
+template <typename T> constexpr bool plane_variant_ok(int v) {
+  return sizeof(T) == 4 ? (v >= 0 && v < kPlaneVariants) : (v == 0 || v == 2 || v == 4);
+}
 
 template <typename T, int N, int V, int MINB, bool FX = false>
 static void ct_plane_launch(unsigned blocks, cudaStream_t st, const HpsiBatch<T>& B, int n3, const cplx<T>* tw1,
@@ -334,19 +336,36 @@ static void ct_plane_launch(unsigned blocks, cudaStream_t st, const HpsiBatch<T>
   k_plane_ct<T, N, V, MINB, FX><<<blocks, kCtThreads, sm, st>>>(B, n3, tw1, tw2);
 }
 
+// CTAs of the plane pass that fit an SM's 228 KB of shared memory (the plane plus ~2 KB of
+// static and reserved memory per CTA): the register bound of a variant is never set for more
+// CTAs than can be resident (a 144 x 144 FP32 plane, 167 KB, runs one CTA per SM with the full
+// register file instead of spilling under a 64-register bound).
+template <typename T, int N> constexpr int ct_plane_fit() {
+  return (int)(233472 / ((size_t)N * (N + 1) * sizeof(cplx<T>) + 2048));
+}
+
 template <typename T, int N>
 static void ct_plane_variant(int variant, unsigned blocks, cudaStream_t st, const HpsiBatch<T>& B, int n3,
                              const cplx<T>* tw1, const cplx<T>* tw2) {
-  if constexpr (sizeof(T) == 4) {
-    if (variant == 1) return ct_plane_launch<T, N, 1, 2>(blocks, st, B, n3, tw1, tw2);
-    if (variant == 2) return ct_plane_launch<T, N, 16, 4>(blocks, st, B, n3, tw1, tw2);
-    if (variant == 3) return ct_plane_launch<T, N, 1, 3>(blocks, st, B, n3, tw1, tw2);
-    if (variant == 4) return ct_plane_launch<T, N, 0, 4, true>(blocks, st, B, n3, tw1, tw2);
-    if (variant == 5) return ct_plane_launch<T, N, 0, 3, true>(blocks, st, B, n3, tw1, tw2);
-  } else {
-    if (variant == 4) return ct_plane_launch<T, N, 0, 2, true>(blocks, st, B, n3, tw1, tw2);
+  constexpr int FIT = ct_plane_fit<T, N>() > 0 ? ct_plane_fit<T, N>() : 1;
+  constexpr int HI = (sizeof(T) == 4 ? 4 : 2) < FIT ? (sizeof(T) == 4 ? 4 : 2) : FIT;
+  // the lower-occupancy variants: 3 CTAs/SM, or one fewer than fit when that is at most 3
+  constexpr int LO = FIT > 3 ? 3 : (FIT > 1 ? FIT - 1 : 1);
+  constexpr int M4 = HI, M3 = sizeof(T) == 4 ? LO : HI;
+  switch (variant) {
+    case 1:
+      if constexpr (sizeof(T) == 4) return ct_plane_launch<T, N, 16, M4>(blocks, st, B, n3, tw1, tw2);
+      break;
+    case 2: return ct_plane_launch<T, N, 0, M4, true>(blocks, st, B, n3, tw1, tw2);
+    case 3:
+      if constexpr (sizeof(T) == 4) return ct_plane_launch<T, N, 0, M3, true>(blocks, st, B, n3, tw1, tw2);
+      break;
+    case 4: return ct_plane_launch<T, N, 32, M4, true>(blocks, st, B, n3, tw1, tw2);
+    case 5:
+      if constexpr (sizeof(T) == 4) return ct_plane_launch<T, N, 32, M3, true>(blocks, st, B, n3, tw1, tw2);
+      break;
   }
-  ct_plane_launch<T, N, 0, (sizeof(T) == 4 ? 4 : 2)>(blocks, st, B, n3, tw1, tw2);
+  ct_plane_launch<T, N, 0, M4>(blocks, st, B, n3, tw1, tw2);
 }
 
 template <typename T>
@@ -368,7 +387,7 @@ static void ct_plane(int n, unsigned blocks, cudaStream_t st, const HpsiBatch<T>
 // for that shape.  Smaller batches (the eigensolver's residual blocks) use the tuned choice
 // when there is one, else variant 0.  Never runs while the stream is being captured.
 // FDE_PLANE_VARIANT=<v> in the environment pins the variant (reproducible rounding across
-// machines); an FP64 plane pass runs a pinned 4 as 4 and every other pin as 0.
+// machines); an FP64 plane pass runs a pinned 0, 2 or 4 as it is and every other pin as 0.
 constexpr unsigned kTuneMinPlanes = 4096;
 struct PlaneTuner {
   std::mutex mu;

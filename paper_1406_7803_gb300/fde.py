@@ -267,8 +267,8 @@ def set_tc_wait_limit(polls: int) -> None:
 
 
 def set_precond_path(path: int) -> None:
-    """Where the learned preconditioner's inference runs: 1 tensor cores (default), 0 CUDA
-    cores.  Process-wide."""
+    """Where the learned preconditioner's inference and training run: 1 tensor cores (default),
+    0 CUDA cores.  Process-wide."""
     s = load().fde_set_precond_path(int(path))
     if s != FDE_OK:
         raise FDEError(s, "fde_set_precond_path: path must be 0 or 1")

@@ -61,14 +61,23 @@ def _weights(seed=4):
     return _flat(p)
 
 
-def test_loss_and_gradient_match_oracle(pairs):
+@pytest.mark.parametrize("path", [1, 0])
+def test_loss_and_gradient_match_oracle(pairs, path):
+    """Loss and gradient of the training kernels against the oracle's backward pass (FP64 on
+    the FP32 master weights): on the tensor cores (path 1: the hidden layers, the
+    back-propagated errors and the weight gradients as BF16 MMAs with split operands) and on
+    the CUDA cores (path 0)."""
     wl, data = pairs
     w = _weights()
     ctx = fde.context_from_workload(wl)
     ctx.precond_set_weights(w)
     for I, k, r, d, tb, _ in data:
         ctx.precond_add_pairs(I, k, r, d, tb)
-    loss, g = ctx.precond_loss_grad()
+    fde.set_precond_path(path)
+    try:
+        loss, g = ctx.precond_loss_grad()
+    finally:
+        fde.set_precond_path(1)
     p = _unflat(w)  # the FP32 master weights, evaluated in FP64
     L, gr = 0.0, None
     for I, k, r, d, tb, kin in data:
