@@ -539,11 +539,9 @@ def run_ours(args):
         d2h += o.nbytes
 
     def e2e_step():
-        for I, r in enumerate(rhos_h):
-            ctx.set_density(I, r)
-        ctx.build_vemb()
-        for (I, k, nb, c), o in zip(psi_h, h_out):
-            ctx.apply_h_host(I, k, c, o, nb)
+        # densities and every orbital block in, every H psi block out, through the host form
+        # of the hot step (orbital uploads overlap the potential build)
+        ctx.hot_step_host(rhos_h, [c for (_, _, _, c) in psi_h], h_out)
 
     e2e_s = None
     if not large:

@@ -205,9 +205,19 @@ fde_status fde_apply_h_all(fde_ctx* ctx);
  * stream (FDE_EINVAL).  Asynchronous. */
 fde_status fde_hot_step(fde_ctx* ctx, int use_graph);
 
+/* fde_hot_step with host buffers, the end-to-end form of the hot path: h_rho[nsub] the
+ * subsystem densities (double [N_r], grid order), h_psi[nblocks] the orbital blocks and
+ * h_hpsi[nblocks] their H psi (complex double [nbands][npw]), one block per (sub, k) in
+ * subsystem-major, k-minor order.  The orbital blocks go up on a copy stream of the context
+ * while the densities go up and the potentials are built on the context stream; every band
+ * then goes through the batched H psi and the results come back block by block.  The blocks
+ * replace the stored orbitals (their eigenvalues are dropped).  Page-locked host buffers are
+ * copied by the copy engines directly (pageable ones work, without overlap).  Synchronising. */
+fde_status fde_hot_step_host(fde_ctx* ctx, const double* const* h_rho, const double* const* h_psi,
+                             double* const* h_hpsi);
+
 /* Copy the stored H psi of (sub, k) (written by fde_apply_h_all / fde_hot_step and by the
- * eigensolver) to a caller device buffer, complex double [nbands][npw].  Asynchronous on
- * the context stream: read d_hpsi from another stream only after fde_sync. */
+ * eigensolver) to a caller device buffer, complex double [nbands][npw].  Synchronising. */
 fde_status fde_get_hpsi(fde_ctx* ctx, int sub, int k, double* d_hpsi);
 
 /* Initial orbitals of (sub, k) from raw complex draws h_raw [nbands][npw][2] (host):

@@ -54,12 +54,43 @@ __device__ __forceinline__ dd& operator+=(dd& a, dd b) { return a = a + b; }
 __device__ __forceinline__ dd& operator-=(dd& a, dd b) { return a = a - b; }
 __device__ __forceinline__ dd& operator*=(dd& a, dd b) { return a = a * b; }
 
-// Conversions at the boundary of a transform (FP64 grids in global memory).
-__device__ __forceinline__ dd dd_from_double(double v) {
+// Conversions at the boundary of a transform (FP64 grids in global memory).  The FP64 pipe
+// runs at 1/64 of the FP32 rate here, so the split and the join work on the bit patterns with
+// integer and FP32 instructions where the exponents allow, and fall back to the FP64
+// conversions (same results) for zero, tiny or huge values.
+__device__ __forceinline__ dd dd_from_double_fp64(double v) {
   const float h = __double2float_rn(v);
   return dd(h, __double2float_rn(v - (double)h));
 }
-__device__ __forceinline__ double dd_to_double(dd v) { return (double)v.hi + (double)v.lo; }
+// v = (-1)^s 2^e (1 + m 2^-52): hi keeps the top 23 mantissa bits rounded to nearest even (a
+// carry out of the mantissa correctly increments the exponent field), and v - hi, which is
+// exactly the remaining bits minus the rounding increment times 2^(e - 52), is rounded to a
+// float by the integer-to-float conversion and scaled by an exact power of two.
+__device__ __forceinline__ dd dd_from_double(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const int e = (int)((b >> 52) & 0x7FF) - 1023;
+  if (e < -70 || e > 126) return dd_from_double_fp64(v);
+  const unsigned int mh = (unsigned int)((b >> 29) & 0x7FFFFFu);
+  const unsigned int rem = (unsigned int)(b & 0x1FFFFFFFu);
+  const unsigned int up = (rem > 0x10000000u || (rem == 0x10000000u && (mh & 1u))) ? 1u : 0u;
+  const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
+  const float hi = __uint_as_float(sign | ((((unsigned int)(e + 127)) << 23) + mh + up));
+  const int diff = (int)rem - (up ? 0x20000000 : 0);
+  float lo = __int2float_rn(diff) * __uint_as_float((unsigned int)(e - 52 + 127) << 23);
+  if (sign) lo = -lo;
+  return dd(hi, lo);
+}
+// Exact float -> double on the bit pattern (normal floats and zero), else the FP64 conversion.
+__device__ __forceinline__ double float_to_double_bits(float f) {
+  const unsigned int u = __float_as_uint(f);
+  const unsigned int ef = (u >> 23) & 0xFFu;
+  const unsigned long long s = (unsigned long long)(u >> 31) << 63;
+  if ((u << 1) == 0u) return __longlong_as_double((long long)s);
+  if (ef == 0u || ef == 255u) return (double)f;
+  return __longlong_as_double((long long)(s | ((unsigned long long)(ef - 127u + 1023u) << 52) |
+                                          ((unsigned long long)(u & 0x7FFFFFu) << 29)));
+}
+__device__ __forceinline__ double dd_to_double(dd v) { return float_to_double_bits(v.hi) + float_to_double_bits(v.lo); }
 
 struct __align__(16) ddc {
   dd x, y;

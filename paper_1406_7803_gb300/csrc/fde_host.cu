@@ -205,6 +205,7 @@ struct Engine {
   virtual void stats(long long* dav, long long* hpsi) = 0;
   virtual void set_precond_record(int n) = 0;
   virtual void hot_step(bool use_graph) = 0;
+  virtual void hot_step_host(const double* const* rho, const double* const* psi, double* const* hpsi) = 0;
   virtual void get_hpsi(int sub, int k, double* d_hpsi) = 0;
   virtual int nsub() const = 0;
   virtual long long grid_points() const = 0;
@@ -306,6 +307,8 @@ template <typename T> struct EngineT : Engine {
   ~EngineT() override {
     if (pin) cudaFreeHost(pin);
     if (step_exec) cudaGraphExecDestroy(step_exec);
+    for (cudaEvent_t e : hev) cudaEventDestroy(e);
+    if (hcs) cudaStreamDestroy(hcs);
   }
 
   Sub<T>& sub(int i) {
@@ -680,7 +683,8 @@ template <typename T> struct EngineT : Engine {
     }
     // 2. functionals of the total density
     grid_pw_total(rho_tot.p, gp, func.xc, func.kedf, func.rho_cut, want_pot ? vpart.p : nullptr,
-                  (want_pot && grad) ? htot[0].p : nullptr, htot[1].p, htot[2].p, nr, partial.p, st);
+                  (want_pot && grad) ? htot[0].p : nullptr, htot[1].p, htot[2].p, nr, partial.p, sizeof(T) == 4,
+                  st);
     if (want_e) {  // the pointwise kernels always leave their block sums; reduce them only when asked
       grid_finalize(partial.p, 2, dv, scal.p + 1, st);
       grid_dot_partial(vloc.p, rho_tot.p, nr, 0, partial.p, st);
@@ -915,6 +919,72 @@ template <typename T> struct EngineT : Engine {
         hpsi_bands += sp->nb;
         apply_nl(*sp, q, q.X.p, q.HX.p, sp->nb);
       }
+  }
+
+  // One pass of the hot path with host buffers: every subsystem density and every (subsystem,
+  // k) orbital block in, every H psi block out.  The orbital blocks go up on a copy stream
+  // while the context stream uploads the densities and builds the potentials; each block is
+  // converted to the working precision once its copy has landed, all bands go through the
+  // batched H psi, and the results come back block by block.  The blocks replace the stored
+  // orbitals.  Synchronising.
+  cudaStream_t hcs = nullptr;
+  std::vector<cudaEvent_t> hev;
+  DBuf<double2> hstage;  // FP64 images of every block, end to end (orbitals in, then H psi out)
+  void hot_step_host(const double* const* rho, const double* const* psi, double* const* hpsi) override {
+    REQ(rho && psi && hpsi, FDE_EINVAL, "null host buffer table");
+    REQ(!subs.empty(), FDE_EINVAL, "no subsystems");
+    ensure_vloc();
+    std::vector<size_t> off;
+    size_t tot = 0;
+    for (auto& sp : subs)
+      for (auto& q : sp->kp) {
+        REQ(psi[off.size()] && hpsi[off.size()], FDE_EINVAL, "null orbital block");
+        off.push_back(tot);
+        tot += (size_t)sp->nb * q.npw;
+      }
+    for (size_t I = 0; I < subs.size(); ++I) REQ(rho[I], FDE_EINVAL, "null density");
+    const int nblk = (int)off.size();
+    hstage.ensure(tot);
+    if (!hcs) CK(cudaStreamCreateWithFlags(&hcs, cudaStreamNonBlocking));
+    while ((int)hev.size() < nblk + 1) {
+      cudaEvent_t e;
+      CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      hev.push_back(e);
+    }
+    // the staging buffer is free once the context stream's earlier work (a previous call's
+    // output copies) is done
+    CK(cudaEventRecord(hev[nblk], st));
+    CK(cudaStreamWaitEvent(hcs, hev[nblk], 0));
+    int b = 0;
+    for (auto& sp : subs)
+      for (auto& q : sp->kp) {
+        CK(cudaMemcpyAsync(hstage.p + off[b], psi[b], (size_t)sp->nb * q.npw * sizeof(double2),
+                           cudaMemcpyHostToDevice, hcs));
+        CK(cudaEventRecord(hev[b], hcs));
+        ++b;
+      }
+    for (size_t I = 0; I < subs.size(); ++I)
+      CK(cudaMemcpyAsync(subs[I]->rho.p, rho[I], nr * sizeof(double), cudaMemcpyHostToDevice, st));
+    grid_pass(true, false, -1);
+    b = 0;
+    for (auto& sp : subs)
+      for (auto& q : sp->kp) {
+        CK(cudaStreamWaitEvent(st, hev[b], 0));
+        convert_in(hstage.p + off[b], q.X.p, (size_t)sp->nb * q.npw);
+        q.have_orbitals = true;
+        q.have_eig = false;
+        ++b;
+      }
+    apply_h_all();
+    b = 0;
+    for (auto& sp : subs)
+      for (auto& q : sp->kp) {
+        const size_t n = (size_t)sp->nb * q.npw;
+        convert_out(q.HX.p, hstage.p + off[b], n);
+        CK(cudaMemcpyAsync(hpsi[b], hstage.p + off[b], n * sizeof(double2), cudaMemcpyDeviceToHost, st));
+        ++b;
+      }
+    sync();
   }
 
   // One pass of the hot path over the whole cell (potential build + every band's H psi),
@@ -2182,6 +2252,13 @@ fde_status fde_precond_add_pairs(fde_ctx* c, int sub, int k, int n, const double
 }
 fde_status fde_get_hpsi(fde_ctx* c, int sub, int k, double* d_hpsi) {
   return guard(c, [&]() { c->eng->get_hpsi(sub, k, d_hpsi); return FDE_OK; });
+}
+fde_status fde_hot_step_host(fde_ctx* c, const double* const* h_rho, const double* const* h_psi,
+                             double* const* h_hpsi) {
+  return guard(c, [&]() {
+    c->eng->hot_step_host(h_rho, h_psi, h_hpsi);
+    return FDE_OK;
+  });
 }
 fde_status fde_hot_step(fde_ctx* c, int use_graph) {
   return guard(c, [&]() {

@@ -131,16 +131,20 @@ __global__ void k_vloc_g(double2* __restrict__ V, GridDims g, CellDev c, const d
 
 // ---- pointwise functionals ------------------------------------------------------------------
 // Energy densities with their partial derivatives along rho and sigma = |grad rho|^2, in
-// closed form.  Every rho power comes from one cube root (rho^{1/3}, 1/rho^{1/3} = rho^{2/3}
-// / rho), and each chain-rule factor is written next to the quantity it differentiates, so
-// the potentials are the exact derivatives of the coded energy densities.
-struct Pt {
-  double rho, ir, r13, ir13;  // rho, 1/rho, rho^{1/3}, rho^{-1/3}
+// closed form, in the arithmetic type R (FP64 in FP64 contexts; FP32 in the mixed path, where
+// the density and its gradients come from the double-float transforms and only the pointwise
+// evaluation is single precision).  Every rho power comes from one cube root (rho^{1/3},
+// 1/rho^{1/3} = rho^{2/3} / rho), and each chain-rule factor is written next to the quantity
+// it differentiates, so the potentials are the exact derivatives of the coded energy
+// densities.  Forms that would overflow FP32 at low density with noisy gradients (A^2 t^4 in
+// PBE's H, t^4 in its A derivative) are written in the reciprocal variable there.
+template <typename R> struct Pt {
+  R rho, ir, r13, ir13;  // rho, 1/rho, rho^{1/3}, rho^{-1/3}
 };
-__device__ __forceinline__ Pt make_pt(double rho) {
-  Pt p;
+template <typename R> __device__ __forceinline__ Pt<R> make_pt(R rho) {
+  Pt<R> p;
   p.rho = rho;
-  p.ir = 1.0 / rho;
+  p.ir = R(1) / rho;
   p.r13 = cbrt(rho);
   p.ir13 = p.r13 * p.r13 * p.ir;
   return p;
@@ -148,89 +152,104 @@ __device__ __forceinline__ Pt make_pt(double rho) {
 
 // Slater exchange of the uniform gas per volume, e_x = C_x rho^{4/3}, and its rho derivative.
 constexpr double kCx = -0.75 * 0.98474502184269654;  // -(3/4)(3/pi)^{1/3}
-__device__ __forceinline__ void slater(const Pt& p, double* e, double* de) {
-  *e = kCx * p.rho * p.r13;
-  *de = (4.0 / 3.0) * kCx * p.r13;
+template <typename R> __device__ __forceinline__ void slater(const Pt<R>& p, R* e, R* de) {
+  *e = R(kCx) * p.rho * p.r13;
+  *de = R(4.0 / 3.0 * kCx) * p.r13;
 }
 
 // PW92 correlation energy per particle of the unpolarised gas, eps_c(r_s), and d eps_c / d rho.
 // r_s = (3 / (4 pi rho))^{1/3};  eps_c = -2A (1 + a1 r_s) ln(1 + 1/D),
 // D = 2A (b1 r_s^{1/2} + b2 r_s + b3 r_s^{3/2} + b4 r_s^2).
-__device__ __forceinline__ void pw92(const Pt& p, double* ec, double* dec) {
-  const double A = 0.031091, a1 = 0.21370, b1 = 7.5957, b2 = 3.5876, b3 = 1.6382, b4 = 0.49294;
-  const double rs = 0.62035049089940001667 * p.ir13;  // (3/(4 pi))^{1/3}
-  const double srs = sqrt(rs);
-  const double D = 2.0 * A * (b1 * srs + b2 * rs + b3 * rs * srs + b4 * rs * rs);
-  const double dD = 2.0 * A * (0.5 * b1 / srs + b2 + 1.5 * b3 * srs + 2.0 * b4 * rs);  // dD/dr_s
-  const double iD = 1.0 / D;
-  const double L = log1p(iD);
-  const double dL = -iD * iD / (1.0 + iD);  // d ln(1 + 1/D) / dD
-  *ec = -2.0 * A * (1.0 + a1 * rs) * L;
-  const double dec_drs = -2.0 * A * (a1 * L + (1.0 + a1 * rs) * dL * dD);
-  *dec = dec_drs * (-rs * p.ir / 3.0);  // d r_s / d rho = -r_s / (3 rho)
+template <typename R> __device__ __forceinline__ void pw92(const Pt<R>& p, R* ec, R* dec) {
+  const R A = R(0.031091), a1 = R(0.21370), b1 = R(7.5957), b2 = R(3.5876), b3 = R(1.6382), b4 = R(0.49294);
+  const R rs = R(0.62035049089940001667) * p.ir13;  // (3/(4 pi))^{1/3}
+  const R srs = sqrt(rs);
+  const R D = R(2) * A * (b1 * srs + b2 * rs + b3 * rs * srs + b4 * rs * rs);
+  const R dD = R(2) * A * (R(0.5) * b1 / srs + b2 + R(1.5) * b3 * srs + R(2) * b4 * rs);  // dD/dr_s
+  const R iD = R(1) / D;
+  const R L = log1p(iD);
+  const R dL = -iD * iD / (R(1) + iD);  // d ln(1 + 1/D) / dD
+  *ec = R(-2) * A * (R(1) + a1 * rs) * L;
+  const R dec_drs = R(-2) * A * (a1 * L + (R(1) + a1 * rs) * dL * dD);
+  *dec = dec_drs * (-rs * p.ir / R(3));  // d r_s / d rho = -r_s / (3 rho)
 }
 
 // PBE exchange-correlation energy per volume e(rho, sigma) with e_rho, e_sigma:
 //   e = e_x^unif F_x(s) + rho (eps_c + H),  F_x = 1 + kappa - kappa / (1 + mu s^2 / kappa),
 //   s^2 = sigma / (4 k_F^2 rho^2),  k_F = (3 pi^2 rho)^{1/3},
-//   H = gamma ln(1 + (beta/gamma) t^2 (1 + A t^2) / (1 + A t^2 + A^2 t^4)),
+//   H = gamma ln(1 + (beta/gamma) t^2 P(A t^2)),  P(x) = (1 + x) / (1 + x + x^2),
 //   t^2 = sigma / (4 k_s^2 rho^2),  k_s^2 = 4 k_F / pi,  A = (beta/gamma) / (exp(-eps_c/gamma) - 1).
-__device__ __forceinline__ void pbe(const Pt& p, double sig, double* e, double* er, double* es) {
-  const double kappa = 0.804, mu = 0.2195149727645171;
-  const double beta = 0.06672455060314922, gamma = (1.0 - 0.69314718055994530942) / (M_PI * M_PI);
-  const double bg = beta / gamma;
+// With x = A t^2: P, x P'(x) and x^2 P'(x) for x <= 1 directly, for x > 1 in y = 1/x
+// (P = y (1 + y) / (1 + y + y^2), x P' = -y (1 + 2y) / (1 + y + y^2)^2,
+// x^2 P' = -(1 + 2y) / (1 + y + y^2)^2); then dQ/dt^2 = (beta/gamma)(P + x P') and
+// dQ/dA = (beta/gamma) x^2 P' / A^2 need no t^4.
+template <typename R> __device__ __forceinline__ void pbe(const Pt<R>& p, R sig, R* e, R* er, R* es) {
+  const R kappa = R(0.804), mu = R(0.2195149727645171);
+  const R gamma = R((1.0 - 0.69314718055994530942) / (M_PI * M_PI));
+  const R bg = R(0.06672455060314922 / ((1.0 - 0.69314718055994530942) / (M_PI * M_PI)));
   const double ckf = 3.0936677262801359310;  // (3 pi^2)^{1/3}
-  double ex, dex, ec, dec;
+  R ex, dex, ec, dec;
   slater(p, &ex, &dex);
   pw92(p, &ec, &dec);
-  const double ir2 = p.ir * p.ir;
+  const R ir2 = p.ir * p.ir;
   // s^2 = sigma / (4 ckf^2) rho^{-8/3}
-  const double s2_s = ir2 * p.ir13 * p.ir13 / (4.0 * ckf * ckf);  // d s^2 / d sigma
-  const double s2 = sig * s2_s;
-  const double u = 1.0 + mu * s2 / kappa, iu = 1.0 / u;
-  const double Fx = 1.0 + kappa - kappa * iu;
-  const double dFx = mu * iu * iu;  // dF_x / d s^2
+  const R s2_s = ir2 * p.ir13 * p.ir13 * R(1.0 / (4.0 * ckf * ckf));  // d s^2 / d sigma
+  const R s2 = sig * s2_s;
+  const R u = R(1) + mu * s2 / kappa, iu = R(1) / u;
+  const R Fx = R(1) + kappa - kappa * iu;
+  const R dFx = mu * iu * iu;  // dF_x / d s^2
   // t^2 = sigma pi / (16 ckf) rho^{-7/3}
-  const double t2_s = ir2 * p.ir13 * (M_PI / (16.0 * ckf));  // d t^2 / d sigma
-  const double t2 = sig * t2_s;
-  const double em1 = expm1(-ec / gamma);
-  const double Aa = bg / em1;
-  const double dA = Aa * Aa * (em1 + 1.0) / (bg * gamma);  // dA / d eps_c
-  const double x = Aa * t2;
-  const double Dn = 1.0 + x + x * x, iDn = 1.0 / Dn;
-  const double P = (1.0 + x) * iDn;
-  const double dP = -x * (2.0 + x) * iDn * iDn;  // dP / dx
-  const double Q = bg * t2 * P;
-  const double H = gamma * log1p(Q);
-  const double dHdQ = gamma / (1.0 + Q);
-  const double dQ_t2 = bg * (P + t2 * Aa * dP);  // dQ / dt^2 at fixed A
-  const double dQ_A = bg * t2 * t2 * dP;         // dQ / dA at fixed t^2
+  const R t2_s = ir2 * p.ir13 * R(M_PI / (16.0 * ckf));  // d t^2 / d sigma
+  const R t2 = sig * t2_s;
+  const R em1 = expm1(-ec / gamma);
+  const R Aa = bg / em1;
+  const R dA = Aa * Aa * (em1 + R(1)) / (bg * gamma);  // dA / d eps_c
+  const R x = Aa * t2;
+  R P, xdP, x2dP;
+  if (x <= R(1)) {
+    const R iDn = R(1) / (R(1) + x + x * x);
+    P = (R(1) + x) * iDn;
+    const R dP = -x * (R(2) + x) * iDn * iDn;
+    xdP = x * dP;
+    x2dP = x * xdP;
+  } else {
+    const R y = R(1) / x, iDy = R(1) / (R(1) + y + y * y);
+    P = y * (R(1) + y) * iDy;
+    x2dP = -(R(1) + R(2) * y) * iDy * iDy;
+    xdP = y * x2dP;
+  }
+  const R Q = bg * t2 * P;
+  const R H = gamma * log1p(Q);
+  const R dHdQ = gamma / (R(1) + Q);
+  const R dQ_t2 = bg * (P + xdP);           // dQ / dt^2 at fixed A
+  const R dQ_A = bg * x2dP / (Aa * Aa);     // dQ / dA at fixed t^2
   *e = ex * Fx + p.rho * (ec + H);
   // rho derivatives: d s^2/d rho = -(8/3) s^2 / rho, d t^2/d rho = -(7/3) t^2 / rho
-  const double dH_r = dHdQ * (dQ_t2 * (-7.0 / 3.0) * t2 * p.ir + dQ_A * dA * dec);
-  *er = dex * Fx + ex * dFx * (-8.0 / 3.0) * s2 * p.ir + ec + H + p.rho * (dec + dH_r);
+  const R dH_r = dHdQ * (dQ_t2 * R(-7.0 / 3.0) * t2 * p.ir + dQ_A * dA * dec);
+  *er = dex * Fx + ex * dFx * R(-8.0 / 3.0) * s2 * p.ir + ec + H + p.rho * (dec + dH_r);
   *es = ex * dFx * s2_s + p.rho * dHdQ * dQ_t2 * t2_s;
 }
 
 // Kinetic enhancement factors F(s) and F'(s).
-__device__ __forceinline__ void kedf_F(int kind, double s, double* F, double* dF) {
+template <typename R> __device__ __forceinline__ void kedf_F(int kind, R s, R* F, R* dF) {
   if (kind == 0) { *F = 1; *dF = 0; return; }
   if (kind == 1) {  // revAPBEK
-    const double k = 1.245, mu = 0.23889;
-    const double id = 1.0 / (1.0 + mu * s * s / k);
-    *F = 1.0 + k - k * id;
-    *dF = 2.0 * mu * s * id * id;
+    const R k = R(1.245), mu = R(0.23889);
+    const R id = R(1) / (R(1) + mu * s * s / k);
+    *F = R(1) + k - k * id;
+    *dF = R(2) * mu * s * id * id;
     return;
   }
-  // LC94 (PW91 form)
-  const double a = 0.093907, b = 76.32, c = 0.26608, dd = -0.0809615, al = 100, f = 0.000057767;
-  const double ash = asinh(b * s), ex = exp(-al * s * s);
-  const double num = 1.0 + a * s * ash + (c + dd * ex) * s * s;
-  const double den = 1.0 + a * s * ash + f * s * s * s * s;
-  const double dash = a * ash + a * s * b / sqrt(1.0 + b * b * s * s);
-  const double dnum = dash + 2.0 * s * (c + dd * ex) - 2.0 * al * dd * s * s * s * ex;
-  const double dden = dash + 4.0 * f * s * s * s;
-  const double iden = 1.0 / den;
+  // LC94 (PW91 form); at very large s (noisy gradients of a vanishing density) the s^4 term
+  // overflows FP32 to infinity, and F and F' correctly go to zero
+  const R a = R(0.093907), b = R(76.32), c = R(0.26608), dd = R(-0.0809615), al = R(100), f = R(0.000057767);
+  const R ash = asinh(b * s), ex = exp(-al * s * s);
+  const R num = R(1) + a * s * ash + (c + dd * ex) * s * s;
+  const R den = R(1) + a * s * ash + f * s * s * s * s;
+  const R dash = a * ash + a * s * b / sqrt(R(1) + b * b * s * s);
+  const R dnum = dash + R(2) * s * (c + dd * ex) - R(2) * al * dd * s * s * s * ex;
+  const R dden = dash + R(4) * f * s * s * s;
+  const R iden = R(1) / den;
   *F = num * iden;
   *dF = (dnum - num * iden * dden) * iden;
 }
@@ -238,39 +257,39 @@ __device__ __forceinline__ void kedf_F(int kind, double s, double* F, double* dF
 // One point of a functional evaluation.  xc_mode: -1 none, 0 LDA, 1 PBE.  kedf: -1 none,
 // 0 TF, 1 revAPBEK, 2 LC94.  Returns the local potential part (d e/d rho of both), the
 // coefficient multiplying grad rho in the divergence term, and the two energy densities.
-__device__ __forceinline__ void point_functional(double rho, double gx, double gy, double gz, int xc_mode,
-                                                 int xc_pot, int kedf, double rho_cut, double* vloc, double* hcoef,
-                                                 double* exc, double* ekin) {
+template <typename R>
+__device__ __forceinline__ void point_functional(R rho, R gx, R gy, R gz, int xc_mode, int xc_pot, int kedf,
+                                                 R rho_cut, R* vloc, R* hcoef, R* exc, R* ekin) {
   *vloc = 0; *hcoef = 0; *exc = 0; *ekin = 0;
   if (!(rho >= rho_cut)) return;
-  const double sig = gx * gx + gy * gy + gz * gz;
-  const Pt p = make_pt(rho);
+  const R sig = gx * gx + gy * gy + gz * gz;
+  const Pt<R> p = make_pt(rho);
   if (xc_mode == 0) {
-    double ex, dex, ec, dec;
+    R ex, dex, ec, dec;
     slater(p, &ex, &dex);
     pw92(p, &ec, &dec);
     if (xc_pot) *vloc += dex + ec + rho * dec;
     *exc = ex + rho * ec;
   } else if (xc_mode == 1) {
-    double e, er, es;
+    R e, er, es;
     pbe(p, sig, &e, &er, &es);
     if (xc_pot) {
       *vloc += er;
-      *hcoef += 2.0 * es;
+      *hcoef += R(2) * es;
     }
     *exc = e;
   }
   if (kedf >= 0) {
-    const double ctf = 2.8712340001881918;   // (3/10)(3 pi^2)^{2/3}
-    const double cs = 0.16162045967399548;   // 1 / (2 (3 pi^2)^{1/3})
-    const double r23 = p.r13 * p.r13;
-    const double gn = sqrt(sig);
-    const double s = cs * gn * p.ir * p.ir13;  // cs |grad rho| / rho^{4/3}
-    double F, dF;
+    const R ctf = R(2.8712340001881918);   // (3/10)(3 pi^2)^{2/3}
+    const R cs = R(0.16162045967399548);   // 1 / (2 (3 pi^2)^{1/3})
+    const R r23 = p.r13 * p.r13;
+    const R gn = sqrt(sig);
+    const R s = cs * gn * p.ir * p.ir13;  // cs |grad rho| / rho^{4/3}
+    R F, dF;
     kedf_F(kedf, s, &F, &dF);
     *ekin = ctf * rho * r23 * F;
-    *vloc += ctf * r23 * ((5.0 / 3.0) * F - (4.0 / 3.0) * s * dF);
-    if (kedf > 0) *hcoef += ctf * cs * p.r13 * dF / (gn > 1e-30 ? gn : 1e-30);
+    *vloc += ctf * r23 * (R(5.0 / 3.0) * F - R(4.0 / 3.0) * s * dF);
+    if (kedf > 0) *hcoef += ctf * cs * p.r13 * dF / (gn > R(1e-30) ? gn : R(1e-30));
   }
 }
 
@@ -424,6 +443,7 @@ __global__ void k_unpack_density(const double2* __restrict__ C, int has_b, doubl
 // subsystem gradients held in the packed grids of each pair.  Writes vpart (d f / d rho) and
 // h = (d f / d grad rho) in hx, hy, hz (real; when there are gradients); energy partial rows
 // 0 (xc) and 1 (kinetic).
+template <typename R>
 __global__ void k_pw_total(const double* __restrict__ rho, GradPacks gp, int xc_mode, int kedf, double rho_cut,
                            double* __restrict__ vpart, double* __restrict__ hx, double* __restrict__ hy,
                            double* __restrict__ hz, long long nr, double* partial) {
@@ -442,16 +462,16 @@ __global__ void k_pw_total(const double* __restrict__ rho, GradPacks gp, int xc_
         z += pz.y;
       }
     }
-    double v, h, ex, ek;
-    point_functional(rho[idx], x, y, z, xc_mode, 1, kedf, rho_cut, &v, &h, &ex, &ek);
-    if (vpart) vpart[idx] = v;
+    R v, h, ex, ek;
+    point_functional<R>((R)rho[idx], (R)x, (R)y, (R)z, xc_mode, 1, kedf, (R)rho_cut, &v, &h, &ex, &ek);
+    if (vpart) vpart[idx] = (double)v;
     if (hx) {
-      hx[idx] = h * x;
-      hy[idx] = h * y;
-      hz[idx] = h * z;
+      hx[idx] = (double)h * x;
+      hy[idx] = (double)h * y;
+      hz[idx] = (double)h * z;
     }
-    ax += ex;
-    ak += ek;
+    ax += (double)ex;
+    ak += (double)ek;
   }
   block_sum_store(ax, partial + blockIdx.x);
   block_sum_store(ak, partial + kRedBlocks + blockIdx.x);
@@ -479,24 +499,27 @@ __global__ void k_pw_pair(const double* __restrict__ ra, const double* __restric
       pz = Pz[idx];
       if (has_b) pb = Pb[idx];
     }
-    double va, ha, ex, ek;
-    point_functional(ra[idx], pa.x, pa.y, pz.x, xc_mode, 0, kedf, rho_cut, &va, &ha, &ex, &ek);
-    xa += ex;
-    ka += ek;
-    double vb = 0, hb = 0;
+    TD va, ha, ex, ek;
+    point_functional<TD>((TD)ra[idx], (TD)pa.x, (TD)pa.y, (TD)pz.x, xc_mode, 0, kedf, (TD)rho_cut, &va, &ha, &ex,
+                         &ek);
+    xa += (double)ex;
+    ka += (double)ek;
+    TD vb = 0, hb = 0;
     if (has_b) {
-      point_functional(rb[idx], pb.x, pb.y, pz.y, xc_mode, 0, kedf, rho_cut, &vb, &hb, &ex, &ek);
-      xb += ex;
-      kb += ek;
+      point_functional<TD>((TD)rb[idx], (TD)pb.x, (TD)pb.y, (TD)pz.y, xc_mode, 0, kedf, (TD)rho_cut, &vb, &hb, &ex,
+                           &ek);
+      xb += (double)ex;
+      kb += (double)ek;
     }
     const double vt = vtot ? vtot[idx] : 0.0;
-    if (wa) wa[idx] = vt - va;
-    if (wb) wb[idx] = vt - vb;
+    if (wa) wa[idx] = vt - (double)va;
+    if (wb) wb[idx] = vt - (double)vb;
     if (write_d) {
       const double tx = hx[idx], ty = hy[idx], tz = hz[idx];
-      Da[idx] = mk<TD>((TD)(tx - ha * pa.x), (TD)(ty - ha * pa.y));
-      if (has_b) Db[idx] = mk<TD>((TD)(tx - hb * pb.x), (TD)(ty - hb * pb.y));
-      Dz[idx] = mk<TD>((TD)(tz - ha * pz.x), (TD)(has_b ? tz - hb * pz.y : 0.0));
+      const double hda = (double)ha, hdb = (double)hb;
+      Da[idx] = mk<TD>((TD)(tx - hda * pa.x), (TD)(ty - hda * pa.y));
+      if (has_b) Db[idx] = mk<TD>((TD)(tx - hdb * pb.x), (TD)(ty - hdb * pb.y));
+      Dz[idx] = mk<TD>((TD)(tz - hda * pz.x), (TD)(has_b ? tz - hdb * pz.y : 0.0));
     }
   }
   block_sum_store(xa, partial + blockIdx.x);
@@ -723,10 +746,15 @@ void grid_unpack_density(const double2* C, int has_b, double2* RT, int accumulat
                                                        1.0 / ((double)g.n1 * g.n2 * g.n3), partial);
 }
 void grid_pw_total(const double* rho, const GradPacks& gp, int xc_mode, int kedf, double rho_cut, double* vpart,
-                   double* hx, double* hy, double* hz, long long nr, double* partial, cudaStream_t st) {
+                   double* hx, double* hy, double* hz, long long nr, double* partial, bool fp32, cudaStream_t st) {
   count_launches(1);
   ProfScope prof_("k_pw_total", st);
-  k_pw_total<<<kRedBlocks, kRedThreads, 0, st>>>(rho, gp, xc_mode, kedf, rho_cut, vpart, hx, hy, hz, nr, partial);
+  if (fp32)
+    k_pw_total<float><<<kRedBlocks, kRedThreads, 0, st>>>(rho, gp, xc_mode, kedf, rho_cut, vpart, hx, hy, hz, nr,
+                                                          partial);
+  else
+    k_pw_total<double><<<kRedBlocks, kRedThreads, 0, st>>>(rho, gp, xc_mode, kedf, rho_cut, vpart, hx, hy, hz, nr,
+                                                           partial);
 }
 template <typename TD>
 void grid_pw_pair(const double* ra, const double* rb, const double2* Pa, const double2* Pb, const double2* Pz,

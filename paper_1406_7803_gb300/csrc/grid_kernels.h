@@ -49,8 +49,9 @@ struct GradPacks {  // real-space gradients of the subsystem densities, pairwise
 void grid_pack2(const double* a, const double* b, double2* c, long long n, cudaStream_t st);
 void grid_unpack_density(const double2* C, int has_b, double2* RT, int accumulate, double2* Pa, double2* Pb,
                          double2* Pz, const GridDims& g, const CellDev& c, double* partial, cudaStream_t st);
+// fp32: the pointwise functionals in FP32 arithmetic (mixed path), else FP64.
 void grid_pw_total(const double* rho, const GradPacks& gp, int xc_mode, int kedf, double rho_cut, double* vpart,
-                   double* hx, double* hy, double* hz, long long nr, double* partial, cudaStream_t st);
+                   double* hx, double* hy, double* hz, long long nr, double* partial, bool fp32, cudaStream_t st);
 // The divergence arguments (Da, Db, Dz), the reciprocal-space potentials F and their transforms
 // are in precision TD: FP64 in FP64 contexts (Da.. may alias Pa..), FP32 in mixed ones.
 template <typename TD>

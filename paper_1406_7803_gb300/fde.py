@@ -91,6 +91,7 @@ EXPORTS = {
     "fde_set_gemm_path": (C.c_int, [C.c_int]),
     "fde_set_tc_wait_limit": (C.c_int, [C.c_longlong]),
     "fde_set_precond_path": (C.c_int, [C.c_int]),
+    "fde_hot_step_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "fde_host_sphere": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
     "fde_host_ewald": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "fde_host_occupations": (C.c_int, [C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_int,
@@ -480,6 +481,23 @@ class Context:
 
     def get_hpsi(self, sub, k, out):
         return self._check(self.lib.fde_get_hpsi(self.h, sub, k, _dptr(out)), "fde_get_hpsi")
+
+    def hot_step_host(self, rhos, psis, hpsis):
+        """The hot path end to end with host arrays: rhos[nsub] (float64 grids), psis and hpsis
+        one complex128 [nbands][npw] array per (subsystem, k), subsystem-major.  The arrays stay
+        owned by the caller; page-locked ones (e.g. numpy views of pinned torch tensors) are
+        copied without staging."""
+        if len(psis) != len(hpsis) or len(rhos) == 0:
+            raise ValueError("one density per subsystem and one output per orbital block")
+        arrs = [np.ascontiguousarray(r, dtype=np.float64) for r in rhos]
+        ins = [np.ascontiguousarray(p, dtype=np.complex128) for p in psis]
+        for o in hpsis:
+            if o.dtype != np.complex128 or not o.flags["C_CONTIGUOUS"]:
+                raise ValueError("H psi outputs must be C-contiguous complex128 arrays")
+        tr = (C.c_void_p * len(arrs))(*[a.ctypes.data for a in arrs])
+        tp = (C.c_void_p * len(ins))(*[a.ctypes.data for a in ins])
+        to = (C.c_void_p * len(hpsis))(*[o.ctypes.data for o in hpsis])
+        return self._check(self.lib.fde_hot_step_host(self.h, tr, tp, to), "fde_hot_step_host")
 
     def hot_step(self, use_graph=False):
         return self._check(self.lib.fde_hot_step(self.h, int(bool(use_graph))), "fde_hot_step")

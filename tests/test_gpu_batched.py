@@ -121,8 +121,8 @@ def test_batched_uneven_hot_step_matches_oracle(cell, prec, tol, graph):
         s = wl.subsystems[I]
         npw = sy.basis[I][k][0].shape[0]
         out = torch.zeros((s.nbands, npw), dtype=torch.complex128, device="cuda")
+        torch.cuda.synchronize()  # the zero fill runs on torch's stream, the context writes on its own
         ctx.get_hpsi(I, k, out)
-        ctx.sync()  # the copy runs on the context's stream
         got = out.cpu().numpy()[[0, s.nbands // 2, s.nbands - 1]]
         want = sy.apply_h(I, k, c, pot["veff"][I])
         err = band_err(got, want)

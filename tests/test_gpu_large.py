@@ -65,6 +65,7 @@ def test_large_cell_veff_and_hot_step_match_oracle(cell):
     for I in range(wl.nsub):
         ctx.set_density(I, rhos[I])
     out = torch.zeros((wl.nsub,) + tuple(wl.grid), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()  # the zero fill runs on torch's stream, the context writes on its own
     ctx.build_vemb(out)
     torch.cuda.synchronize()
     for I in range(wl.nsub):
@@ -90,8 +91,8 @@ def test_large_cell_veff_and_hot_step_match_oracle(cell):
         npw = ctx.basis(I, k).shape[0]
         assert np.array_equal(ctx.basis(I, k), sy.basis[I][0][0])
         got = torch.zeros((s.nbands, npw), dtype=torch.complex128, device="cuda")
+        torch.cuda.synchronize()  # the zero fill runs on torch's stream, the context writes on its own
         ctx.get_hpsi(I, k, got)
-        ctx.sync()  # the copy runs on the context's stream
         g = got.cpu().numpy()[[0, s.nbands // 2, s.nbands - 1]]
         want = sy.apply_h(I, 0, c, pot["veff"][I])
         assert band_err(g, want) < 1e-5, (I, k, band_err(g, want))
