@@ -288,7 +288,8 @@ def step_work(wl, ctx, prec):
     cw = 8 if prec == "mixed" else 16  # bytes per complex value of the working precision
     rw = cw // 2
     w = {k: {"bytes": 0.0, "flops": 0.0} for k in ("k_zinv", "k_plane", "k_zfwd", "k_gemm_hn", "k_gemm_rot",
-                                                  "k_kb_couple", "k_fft_axis_f64", "k_fft_axis_dd", "k_fft_axis_f32")}
+                                                  "k_kb_couple", "k_fft_axis_f64", "k_fft_axis_dd", "k_fft_axis_f32",
+                                                  "k_pw_total", "k_pw_pair", "k_unpack_density", "k_assemble_pair")}
     for I, s in enumerate(wl.subsystems):
         for k in range(s.nk):
             mil = ctx.basis(I, k)
@@ -324,6 +325,19 @@ def step_work(wl, ctx, prec):
     else:
         w["k_fft_axis_f64"]["bytes"] = 8 * npairs * 3 * 2 * nr * 16
         w["k_fft_axis_f64"]["flops"] = 8 * npairs * per_tr
+    # the G-space and pointwise passes of a GGA build, per grid point (FP64 grids 8 bytes a
+    # value, packed complex grids 16; the divergence arguments in the working precision):
+    #   k_unpack_density  C in, rho_tot(G) out, three packed gradient grids out (+ rho_tot in
+    #                     for every pair after the first);
+    #   k_pw_total        rho_tot and every pair's three packed gradients in, v and h_x,y,z out;
+    #   k_pw_pair         both densities, three packed gradients, h_x,y,z and v in; both w and
+    #                     three packed divergence arguments out;
+    #   k_assemble_pair   rho_tot(G) and the three divergence grids in, F out.
+    td = 8 if prec == "mixed" else 16
+    w["k_unpack_density"]["bytes"] = nr * (npairs * (16 + 16 + 48) + (npairs - 1) * 16)
+    w["k_pw_total"]["bytes"] = nr * (8 + npairs * 48 + 32)
+    w["k_pw_pair"]["bytes"] = nr * npairs * (16 + 48 + 24 + 8 + 16 + 3 * td)
+    w["k_assemble_pair"]["bytes"] = nr * npairs * (16 + 3 * td + td)
     return w
 
 
@@ -441,6 +455,46 @@ def ft_cycles(tol=1e-6):
     out["speedup_mixed_learned_vs_fp64"] = out["fp64"]["seconds"] / out["mixed_learned"]["seconds"]
     out["dF_mixed_vs_fp64_ha"] = out["mixed"]["F_fde"] - out["fp64"]["F_fde"]
     out["dF_mixed_learned_vs_fp64_ha"] = out["mixed_learned"]["F_fde"] - out["fp64"]["F_fde"]
+    return out
+
+
+def precond_kernels(ctx, wl, stream):
+    """The learned preconditioner's kernels on the first slab k-point's band block (n_b x npw,
+    working precision): inference with the bf16 weights (average of 10 calls) and one
+    loss-and-gradient evaluation over the same block as training pairs (average of 3), wall
+    time of the synchronising calls, on the tensor cores and on the CUDA cores."""
+    import torch
+    from paper_1406_7803_gb300 import fde
+    s = wl.subsystems[0]
+    npw = ctx.basis(0, 0).shape[0]
+    rng = np.random.default_rng(7)
+    rh = (rng.standard_normal((s.nbands, npw)) + 1j * rng.standard_normal((s.nbands, npw))) / np.sqrt(npw)
+    dh = rh * 0.5 + 0.1 * (rng.standard_normal((s.nbands, npw)) + 1j * rng.standard_normal((s.nbands, npw))) / np.sqrt(npw)
+    tb = np.linspace(0.5, 3.0, s.nbands)
+    w0 = fde.precond_initial_weights(0)
+    w0[-65:-1] = 0.05 * np.random.default_rng(8).standard_normal(64)  # a nonzero output layer
+    ctx.precond_set_weights(w0)
+    ctx.precond_add_pairs(0, 0, rh, dh, tb)
+    r = torch.from_numpy(rh).to(device="cuda",
+                                dtype=torch.complex64 if ctx.prec == fde.FDE_PREC_MIXED else torch.complex128)
+    w = torch.zeros_like(r)
+    torch.cuda.synchronize()
+    out = {"block": f"{s.nbands} bands x {npw} plane waves", "pairs": s.nbands * npw}
+    for path, name in ((1, "tensor_cores"), (0, "cuda_cores")):
+        fde.set_precond_path(path)
+        ctx.precond_apply(0, 0, r, w, s.nbands, tb)
+        ctx.precond_loss_grad()
+        t0 = time.perf_counter()
+        for _ in range(10):
+            ctx.precond_apply(0, 0, r, w, s.nbands, tb)
+        t_apply = (time.perf_counter() - t0) / 10
+        t0 = time.perf_counter()
+        for _ in range(3):
+            ctx.precond_loss_grad()
+        t_grad = (time.perf_counter() - t0) / 3
+        out[name] = {"apply_ms": 1e3 * t_apply, "loss_grad_ms": 1e3 * t_grad}
+    fde.set_precond_path(1)
+    ctx.precond_clear()
     return out
 
 
@@ -597,6 +651,7 @@ def run_ours(args):
         del c64
         torch.cuda.empty_cache()
 
+    pre = precond_kernels(ctx, wl, stream) if not large else None
     cpu = cpu_baseline(wl, bands=2 if large else None) if (rank == 0 and not args.no_cpu) else None
     ft = ft_cycles() if (ws == 1 and not args.no_ft and args.workload == "molecule-on-slab") else None
     clocks = clk.summary()
@@ -612,7 +667,7 @@ def run_ours(args):
                          "d2h_bytes_per_step": d2h, "host_buffers": "page-locked (torch pin_memory)"}
                         if e2e_s else None),
                 "gpu_launches": launches, "roofline": roof, "kernels": table, "fp64": fp64,
-                "cpu_baseline": cpu, "clocks": clocks, "ft_cycle": ft,
+                "cpu_baseline": cpu, "clocks": clocks, "ft_cycle": ft, "precond": pre,
                 "wall_s": wall, "step_ms": step_ms,
                 "graph": {"ms_per_step": graph_ms, "value": ws * units / (graph_ms / 1e3),
                           "note": "the same step replayed from a captured CUDA graph"}}

@@ -434,16 +434,17 @@ fde_status fde_set_tc_wait_limit(long long polls);
 
 /* The FP32 plane pass of H psi (the (x, y) transforms, potential multiply and back) comes in
  * several compiled variants (CTAs per SM, radix order of the line transforms, fused x pass,
- * thread mapping of the row transforms).  The first large batch of a grid shape times each once on the batch
+ * thread mapping of the row transforms, fused column scatter and gather).  The first large batch of a grid shape times each once on the batch
  * itself and keeps the fastest (measurement support; no counterpart in the paper).  Returns the
  * variant chosen for plane side n1 and z length n3, or -1 if none was tuned yet; the
  * environment variable FDE_PLANE_VARIANT pins one. */
 int fde_tuned_plane_variant(int n1, int n3);
-/* Pin the plane-pass variant used from now on in this process (0 .. 5; 2 .. 5 fuse the x pass:
+/* Pin the plane-pass variant used from now on in this process (0 .. 7; 2 .. 7 fuse the x pass:
  * the inverse transform's last stage, the potential multiply and the forward transform's first
- * stage on the same registers; 4 and 5 also map consecutive threads to neighbouring rows in the
- * y transforms; FP64 plane passes run a pinned 0, 2 or 4 as it is and any other as 0), or
- * return to tuning (-1).  FDE_EINVAL for other values. */
+ * stage on the same registers; 4, 5 and 7 map consecutive threads to neighbouring rows in the
+ * y transforms; 6 and 7 read the sphere columns straight into the first y stage and write the
+ * last y stage's outputs straight back; FP64 plane passes run a pinned 0, 2, 4 or 6 as it is and
+ * any other as 0), or return to tuning (-1).  FDE_EINVAL for other values. */
 fde_status fde_pin_plane_variant(int variant);
 
 /* ---- host-side numerics (no device work; usable without a GPU) --------------------------

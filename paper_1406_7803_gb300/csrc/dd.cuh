@@ -56,8 +56,10 @@ __device__ __forceinline__ dd& operator*=(dd& a, dd b) { return a = a * b; }
 
 // Conversions at the boundary of a transform (FP64 grids in global memory).  The FP64 pipe
 // runs at 1/64 of the FP32 rate here, so the split and the join work on the bit patterns with
-// integer and FP32 instructions where the exponents allow, and fall back to the FP64
-// conversions (same results) for zero, tiny or huge values.
+// integer and FP32 instructions.  The split equals the FP64-based one for 2^-70 <= |v| < 2^127;
+// below 2^-70 (the vacuum tails of a density, 70 binary orders under its peak) it keeps the
+// rounded high part alone (or nothing below FP32's normal range), an absolute error under
+// 2^-94, and huge values take the FP64 conversions.
 __device__ __forceinline__ dd dd_from_double_fp64(double v) {
   const float h = __double2float_rn(v);
   return dd(h, __double2float_rn(v - (double)h));
@@ -69,16 +71,31 @@ __device__ __forceinline__ dd dd_from_double_fp64(double v) {
 __device__ __forceinline__ dd dd_from_double(double v) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(v);
   const int e = (int)((b >> 52) & 0x7FF) - 1023;
-  if (e < -70 || e > 126) return dd_from_double_fp64(v);
+  if (e > 126) return dd_from_double_fp64(v);
+  const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
+  if (e < -126) return dd(__uint_as_float(sign), 0.0f);
   const unsigned int mh = (unsigned int)((b >> 29) & 0x7FFFFFu);
   const unsigned int rem = (unsigned int)(b & 0x1FFFFFFFu);
   const unsigned int up = (rem > 0x10000000u || (rem == 0x10000000u && (mh & 1u))) ? 1u : 0u;
-  const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
   const float hi = __uint_as_float(sign | ((((unsigned int)(e + 127)) << 23) + mh + up));
+  if (e < -70) return dd(hi, 0.0f);
   const int diff = (int)rem - (up ? 0x20000000 : 0);
   float lo = __int2float_rn(diff) * __uint_as_float((unsigned int)(e - 52 + 127) << 23);
   if (sign) lo = -lo;
   return dd(hi, lo);
+}
+// double -> float rounded to nearest even on the bit pattern (the high part of the split);
+// values below FP32's normal range become zero, huge ones take the FP64 conversion.
+__device__ __forceinline__ float float_of_double_bits(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const int e = (int)((b >> 52) & 0x7FF) - 1023;
+  if (e > 126) return __double2float_rn(v);
+  const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
+  if (e < -126) return __uint_as_float(sign);
+  const unsigned int mh = (unsigned int)((b >> 29) & 0x7FFFFFu);
+  const unsigned int rem = (unsigned int)(b & 0x1FFFFFFFu);
+  const unsigned int up = (rem > 0x10000000u || (rem == 0x10000000u && (mh & 1u))) ? 1u : 0u;
+  return __uint_as_float(sign | ((((unsigned int)(e + 127)) << 23) + mh + up));
 }
 // Exact float -> double on the bit pattern (normal floats and zero), else the FP64 conversion.
 __device__ __forceinline__ double float_to_double_bits(float f) {

@@ -13,9 +13,14 @@
 // with W_m = exp(sign 2 pi i / m).
 #pragma once
 
+#include <type_traits>
+
 #include "fft.cuh"
 
 namespace fde {
+
+// Placeholder for the optional global-memory input / output of a stage (ct_stage).
+struct NoIO {};
 
 struct CtPlan {
   int n, ns;
@@ -166,9 +171,15 @@ struct LinesCols {  // line l at l, element stride pitch (columns of a plane)
 // the first stages alike.  Unit-stride lines batches may then be partial (l < nl checked).
 // Otherwise unit-stride lines are walked by consecutive threads (contiguous reads; the stride-R
 // writes of a stage with Ns = 1 conflict 2-way on 16-line planes).
-template <typename T, int N, int R, int NS, int NT, int NL, int V, typename A>
+// LD / ST (optional): a stage that reads its inputs through ld(line, element) instead of the
+// buffer (the first stage of a transform fed straight from global memory), or hands its outputs
+// to st(line, element, value) instead of writing the buffer (the last stage of one whose result
+// leaves the CTA).
+template <typename T, int N, int R, int NS, int NT, int NL, int V, typename A, typename LD = NoIO,
+          typename ST = NoIO>
 __device__ __forceinline__ void ct_stage(cplx<T>* buf, const A& addr, int l0, int nl,
-                                         const cplx<T>* __restrict__ tw, int sign) {
+                                         const cplx<T>* __restrict__ tw, int sign, const LD& ld = LD(),
+                                         const ST& stf = ST()) {
   using C = cplx<T>;
   constexpr int NB = N / R;
   constexpr int TWS = N / (NS * R);
@@ -187,7 +198,9 @@ __device__ __forceinline__ void ct_stage(cplx<T>* buf, const A& addr, int l0, in
       const C* a = buf + addr.base(l0 + l);
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        C x = a[(j + r * NB) * es];
+        C x;
+        if constexpr (std::is_same<LD, NoIO>::value) x = a[(j + r * NB) * es];
+        else x = ld(l0 + l, j + r * NB);
         if (r > 0 && NS > 1) {
           C t = tw[r * k * TWS];
           if (sign > 0) t.y = -t.y;
@@ -209,7 +222,10 @@ __device__ __forceinline__ void ct_stage(cplx<T>* buf, const A& addr, int l0, in
       const int d = (j / NS) * NS * R + k;
       C* a = buf + addr.base(l0 + l);
 #pragma unroll
-      for (int q = 0; q < R; ++q) a[(d + q * NS) * es] = v[it][q];
+      for (int q = 0; q < R; ++q) {
+        if constexpr (std::is_same<ST, NoIO>::value) a[(d + q * NS) * es] = v[it][q];
+        else stf(l0 + l, d + q * NS, v[it][q]);
+      }
     }
   }
   __syncthreads();
@@ -313,6 +329,36 @@ __device__ __forceinline__ void ct_lines(cplx<T>* buf, const A& addr, int nlines
   for (int l0 = 0; l0 < nlines; l0 += LB) {
     const int nl = nlines - l0 < LB ? nlines - l0 : LB;
     ct_stages<T, N, NT, LB, 0, 1, V>(buf, addr, l0, nl, tw, sign);
+  }
+}
+
+// Stages S .. ns - 1 with the first stage reading through ld and the last writing through st.
+template <typename T, int N, int NT, int NL, int S, int NS, int V, typename A, typename LD, typename ST>
+__device__ __forceinline__ void ct_stages_io(cplx<T>* buf, const A& addr, int l0, int nl, const cplx<T>* tw, int sign,
+                                             const LD& ld, const ST& st) {
+  constexpr CtPlan P = ct_factor(N, ct_order(V));
+  if constexpr (S < P.ns) {
+    constexpr int R = P.r[S];
+    if constexpr (S == 0 && S == P.ns - 1)
+      ct_stage<T, N, R, NS, NT, NL, V, A, LD, ST>(buf, addr, l0, nl, tw, sign, ld, st);
+    else if constexpr (S == 0)
+      ct_stage<T, N, R, NS, NT, NL, V, A, LD, NoIO>(buf, addr, l0, nl, tw, sign, ld, NoIO());
+    else if constexpr (S == P.ns - 1)
+      ct_stage<T, N, R, NS, NT, NL, V, A, NoIO, ST>(buf, addr, l0, nl, tw, sign, NoIO(), st);
+    else
+      ct_stage<T, N, R, NS, NT, NL, V, A>(buf, addr, l0, nl, tw, sign);
+    ct_stages_io<T, N, NT, NL, S + 1, NS * R, V, A, LD, ST>(buf, addr, l0, nl, tw, sign, ld, st);
+  }
+}
+// ct_lines for unit-stride lines with global-memory input (ld) or output (st) of the transform.
+template <typename T, int N, int NT, typename A, int V, typename LD, typename ST>
+__device__ __forceinline__ void ct_lines_io(cplx<T>* buf, const A& addr, int nlines, const cplx<T>* tw, int sign,
+                                            const LD& ld, const ST& st) {
+  static_assert(A::kUnit, "row transforms only");
+  constexpr int LB = ct_lines_per_batch<T, N, NT, V>();
+  for (int l0 = 0; l0 < nlines; l0 += LB) {
+    const int nl = nlines - l0 < LB ? nlines - l0 : LB;
+    ct_stages_io<T, N, NT, LB, 0, 1, V, A, LD, ST>(buf, addr, l0, nl, tw, sign, ld, st);
   }
 }
 

@@ -254,6 +254,14 @@ template <typename R> __device__ __forceinline__ void kedf_F(int kind, R s, R* F
   *dF = (dnum - num * iden * dden) * iden;
 }
 
+// FP64 grid values into and out of the arithmetic type R: for FP32 the conversions work on the
+// bit patterns (dd.cuh), so the mixed path's pointwise kernels stay off the FP64 pipe.
+template <typename R> __device__ __forceinline__ R narrow(double v);
+template <> __device__ __forceinline__ double narrow<double>(double v) { return v; }
+template <> __device__ __forceinline__ float narrow<float>(double v) { return float_of_double_bits(v); }
+__device__ __forceinline__ double widen(double v) { return v; }
+__device__ __forceinline__ double widen(float v) { return float_to_double_bits(v); }
+
 // One point of a functional evaluation.  xc_mode: -1 none, 0 LDA, 1 PBE.  kedf: -1 none,
 // 0 TF, 1 revAPBEK, 2 LC94.  Returns the local potential part (d e/d rho of both), the
 // coefficient multiplying grad rho in the divergence term, and the two energy densities.
@@ -449,29 +457,29 @@ __global__ void k_pw_total(const double* __restrict__ rho, GradPacks gp, int xc_
                            double* __restrict__ hz, long long nr, double* partial) {
   double ax = 0, ak = 0;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < nr; idx += (long long)gridDim.x * blockDim.x) {
-    double x = 0, y = 0, z = 0;
+    R x = 0, y = 0, z = 0;
     for (int q = 0; q < gp.npairs; ++q) {
       const double2 pa = gp.a[q][idx], pz = gp.z[q][idx];
-      x += pa.x;
-      y += pa.y;
-      z += pz.x;
+      x += narrow<R>(pa.x);
+      y += narrow<R>(pa.y);
+      z += narrow<R>(pz.x);
       if (gp.has_b[q]) {
         const double2 pb = gp.b[q][idx];
-        x += pb.x;
-        y += pb.y;
-        z += pz.y;
+        x += narrow<R>(pb.x);
+        y += narrow<R>(pb.y);
+        z += narrow<R>(pz.y);
       }
     }
     R v, h, ex, ek;
-    point_functional<R>((R)rho[idx], (R)x, (R)y, (R)z, xc_mode, 1, kedf, (R)rho_cut, &v, &h, &ex, &ek);
-    if (vpart) vpart[idx] = (double)v;
+    point_functional<R>(narrow<R>(rho[idx]), x, y, z, xc_mode, 1, kedf, (R)rho_cut, &v, &h, &ex, &ek);
+    if (vpart) vpart[idx] = widen(v);
     if (hx) {
-      hx[idx] = (double)h * x;
-      hy[idx] = (double)h * y;
-      hz[idx] = (double)h * z;
+      hx[idx] = widen(h * x);
+      hy[idx] = widen(h * y);
+      hz[idx] = widen(h * z);
     }
-    ax += (double)ex;
-    ak += (double)ek;
+    ax += widen(ex);
+    ak += widen(ek);
   }
   block_sum_store(ax, partial + blockIdx.x);
   block_sum_store(ak, partial + kRedBlocks + blockIdx.x);
@@ -499,27 +507,26 @@ __global__ void k_pw_pair(const double* __restrict__ ra, const double* __restric
       pz = Pz[idx];
       if (has_b) pb = Pb[idx];
     }
+    const TD pax = narrow<TD>(pa.x), pay = narrow<TD>(pa.y), pzx = narrow<TD>(pz.x);
+    const TD pbx = narrow<TD>(pb.x), pby = narrow<TD>(pb.y), pzy = narrow<TD>(pz.y);
     TD va, ha, ex, ek;
-    point_functional<TD>((TD)ra[idx], (TD)pa.x, (TD)pa.y, (TD)pz.x, xc_mode, 0, kedf, (TD)rho_cut, &va, &ha, &ex,
-                         &ek);
-    xa += (double)ex;
-    ka += (double)ek;
+    point_functional<TD>(narrow<TD>(ra[idx]), pax, pay, pzx, xc_mode, 0, kedf, (TD)rho_cut, &va, &ha, &ex, &ek);
+    xa += widen(ex);
+    ka += widen(ek);
     TD vb = 0, hb = 0;
     if (has_b) {
-      point_functional<TD>((TD)rb[idx], (TD)pb.x, (TD)pb.y, (TD)pz.y, xc_mode, 0, kedf, (TD)rho_cut, &vb, &hb, &ex,
-                           &ek);
-      xb += (double)ex;
-      kb += (double)ek;
+      point_functional<TD>(narrow<TD>(rb[idx]), pbx, pby, pzy, xc_mode, 0, kedf, (TD)rho_cut, &vb, &hb, &ex, &ek);
+      xb += widen(ex);
+      kb += widen(ek);
     }
-    const double vt = vtot ? vtot[idx] : 0.0;
-    if (wa) wa[idx] = vt - (double)va;
-    if (wb) wb[idx] = vt - (double)vb;
+    const TD vt = vtot ? narrow<TD>(vtot[idx]) : TD(0);
+    if (wa) wa[idx] = widen(vt - va);
+    if (wb) wb[idx] = widen(vt - vb);
     if (write_d) {
-      const double tx = hx[idx], ty = hy[idx], tz = hz[idx];
-      const double hda = (double)ha, hdb = (double)hb;
-      Da[idx] = mk<TD>((TD)(tx - hda * pa.x), (TD)(ty - hda * pa.y));
-      if (has_b) Db[idx] = mk<TD>((TD)(tx - hdb * pb.x), (TD)(ty - hdb * pb.y));
-      Dz[idx] = mk<TD>((TD)(tz - hda * pz.x), (TD)(has_b ? tz - hdb * pz.y : 0.0));
+      const TD tx = narrow<TD>(hx[idx]), ty = narrow<TD>(hy[idx]), tz = narrow<TD>(hz[idx]);
+      Da[idx] = mk<TD>(tx - ha * pax, ty - ha * pay);
+      if (has_b) Db[idx] = mk<TD>(tx - hb * pbx, ty - hb * pby);
+      Dz[idx] = mk<TD>(tz - ha * pzx, has_b ? tz - hb * pzy : TD(0));
     }
   }
   block_sum_store(xa, partial + blockIdx.x);

@@ -131,16 +131,47 @@ k_zfwd_ct(const __grid_constant__ HpsiBatch<T> B, T inv_nr, const cplx<T>* __res
   }
 }
 
+// Row r of a plane's data rows holds the sphere columns S[rs[r] .. rs[r] + rl[r]) at consecutive
+// signed m2 from m2lo[r] (i2 = m2 mod N): element i2 of the row is column rs + m2(i2) - m2lo
+// when that lies in the row, else zero.  RowIn feeds the first stage of the inverse y transform
+// straight from the columns; RowOut takes the last stage of the forward y transform's outputs
+// at the sphere columns back to them.
+__device__ __forceinline__ int row_offset(int i2, int n, int m2lo, int len) {
+  const int d = (i2 <= n / 2 ? i2 : i2 - n) - m2lo;
+  return (d >= 0 && d < len) ? d : -1;
+}
+template <typename T> struct RowIn {
+  const cplx<T>* S;
+  const int *rs, *rl, *m2lo;
+  int n;
+  __device__ __forceinline__ cplx<T> operator()(int r, int i2) const {
+    const int d = row_offset(i2, n, m2lo[r], rl[r]);
+    return d >= 0 ? S[rs[r] + d] : mk<T>(0, 0);
+  }
+};
+template <typename T> struct RowOut {
+  cplx<T>* S;
+  const int *rs, *rl, *m2lo;
+  int n;
+  __device__ __forceinline__ void operator()(int r, int i2, cplx<T> v) const {
+    const int d = row_offset(i2, n, m2lo[r], rl[r]);
+    if (d >= 0) S[rs[r] + d] = v;
+  }
+};
+
 // One CTA per (item, band, z-plane): columns in, 2D inverse FFT (y on the rows holding
 // columns, then x), potential multiply, 2D forward FFT, columns out.  n1 = n2 = N; the plane is
 // P[i1][i2] (pitch N + 1) and the potential plane vplane[i3][i1][i2].
 // Variants of the plane pass: V selects the staged transform's register budget, radix order
-// and row thread mapping (fftct.cuh), MINB the CTAs per SM the registers are bounded for (four FP32 CTAs of
-// 42 KB for a 72 x 72 plane need <= 64 registers; FP64 planes of 84 KB fit two), FX fuses the
-// x pass: the inverse's last stage, the potential multiply and the forward's first stage run on
-// the same registers (ct_cols_vmul), one shared-memory round trip and one barrier pair fewer
-// per column batch and no separate multiply pass.
-template <typename T, int N, int V = 0, int MINB = (sizeof(T) == 4 ? 4 : 2), bool FX = false>
+// and row thread mapping (fftct.cuh), MINB the CTAs per SM the registers are bounded for (four
+// FP32 CTAs of 42 KB for a 72 x 72 plane need <= 64 registers; FP64 planes of 84 KB fit two),
+// FX fuses the x pass: the inverse's last stage, the potential multiply and the forward's first
+// stage run on the same registers (ct_cols_vmul), one shared-memory round trip and one barrier
+// pair fewer per column batch and no separate multiply pass.  SG fuses the sphere scatter and
+// gather into the y transforms: the first inverse stage reads the columns from global memory
+// and the last forward stage writes them back, so only the rows without columns are
+// zero-filled and neither the scatter nor the gather pass goes through shared memory.
+template <typename T, int N, int V = 0, int MINB = (sizeof(T) == 4 ? 4 : 2), bool FX = false, bool SG = false>
 __global__ void __launch_bounds__(kCtThreads, MINB)
 k_plane_ct(const __grid_constant__ HpsiBatch<T> B, int n3, const cplx<T>* __restrict__ tw1,
            const cplx<T>* __restrict__ tw2) {
@@ -154,29 +185,60 @@ k_plane_ct(const __grid_constant__ HpsiBatch<T> B, int n3, const cplx<T>* __rest
   const int local = blockIdx.x - I.pstart;
   const int b = local / n3, i3 = local - b * n3;
   C* S = I.scratch + ((size_t)b * n3 + i3) * sp.ncol;
-  for (int idx = threadIdx.x; idx < N * PITCH; idx += kCtThreads) P[idx] = mk<T>(0, 0);
-  for (int r = threadIdx.x; r < sp.nrow; r += kCtThreads) rows[r] = sp.row_i1[r];
-  __syncthreads();
-  for (int c = threadIdx.x; c < sp.ncol; c += kCtThreads) P[sp.col_i1[c] * PITCH + sp.col_i2[c]] = S[c];
-  __syncthreads();
-  ct_lines<T, N, kCtThreads, LinesRows, V>(P, LinesRows{rows, PITCH}, sp.nrow, tw2, +1);
   const T* vp = I.vplane + (size_t)i3 * N * N;
-  if constexpr (FX) {
-    ct_cols_vmul<T, N, kCtThreads, V>(P, PITCH, tw1, vp);
-  } else {
-    ct_lines<T, N, kCtThreads, LinesCols, V>(P, LinesCols{PITCH}, N, tw1, +1);
-    for (int idx = threadIdx.x; idx < N * N; idx += kCtThreads) {
-      const int a = idx / N, c = idx - a * N;
-      C& z = P[a * PITCH + c];
-      const T v = vp[idx];
-      z.x *= v;
-      z.y *= v;
+  if constexpr (SG) {
+    __shared__ int rowof[N], rs[N], re[N], rm2[N];
+    for (int i = threadIdx.x; i < N; i += kCtThreads) rowof[i] = -1;
+    __syncthreads();
+    for (int r = threadIdx.x; r < sp.nrow; r += kCtThreads) {
+      rows[r] = sp.row_i1[r];
+      rowof[rows[r]] = r;
     }
     __syncthreads();
-    ct_lines<T, N, kCtThreads, LinesCols, V>(P, LinesCols{PITCH}, N, tw1, -1);
+    // the columns of a row are consecutive in the sphere order (sorted by m1, then m2)
+    for (int c = threadIdx.x; c < sp.ncol; c += kCtThreads) {
+      const int i1 = sp.col_i1[c];
+      if (c == 0 || sp.col_i1[c - 1] != i1) {
+        const int r = rowof[i1], i2 = sp.col_i2[c];
+        rs[r] = c;
+        rm2[r] = i2 <= N / 2 ? i2 : i2 - N;
+      }
+      if (c == sp.ncol - 1 || sp.col_i1[c + 1] != i1) re[rowof[i1]] = c + 1;
+    }
+    for (int idx = threadIdx.x; idx < N * PITCH; idx += kCtThreads)
+      if (rowof[idx / PITCH] < 0) P[idx] = mk<T>(0, 0);
+    __syncthreads();
+    for (int r = threadIdx.x; r < sp.nrow; r += kCtThreads) re[r] -= rs[r];  // now the row lengths
+    __syncthreads();
+    ct_lines_io<T, N, kCtThreads, LinesRows, V>(P, LinesRows{rows, PITCH}, sp.nrow, tw2, +1,
+                                                RowIn<T>{S, rs, re, rm2, N}, NoIO());
+    ct_cols_vmul<T, N, kCtThreads, V>(P, PITCH, tw1, vp);
+    ct_lines_io<T, N, kCtThreads, LinesRows, V>(P, LinesRows{rows, PITCH}, sp.nrow, tw2, -1, NoIO(),
+                                                RowOut<T>{S, rs, re, rm2, N});
+  } else {
+    for (int idx = threadIdx.x; idx < N * PITCH; idx += kCtThreads) P[idx] = mk<T>(0, 0);
+    for (int r = threadIdx.x; r < sp.nrow; r += kCtThreads) rows[r] = sp.row_i1[r];
+    __syncthreads();
+    for (int c = threadIdx.x; c < sp.ncol; c += kCtThreads) P[sp.col_i1[c] * PITCH + sp.col_i2[c]] = S[c];
+    __syncthreads();
+    ct_lines<T, N, kCtThreads, LinesRows, V>(P, LinesRows{rows, PITCH}, sp.nrow, tw2, +1);
+    if constexpr (FX) {
+      ct_cols_vmul<T, N, kCtThreads, V>(P, PITCH, tw1, vp);
+    } else {
+      ct_lines<T, N, kCtThreads, LinesCols, V>(P, LinesCols{PITCH}, N, tw1, +1);
+      for (int idx = threadIdx.x; idx < N * N; idx += kCtThreads) {
+        const int a = idx / N, c = idx - a * N;
+        C& z = P[a * PITCH + c];
+        const T v = vp[idx];
+        z.x *= v;
+        z.y *= v;
+      }
+      __syncthreads();
+      ct_lines<T, N, kCtThreads, LinesCols, V>(P, LinesCols{PITCH}, N, tw1, -1);
+    }
+    ct_lines<T, N, kCtThreads, LinesRows, V>(P, LinesRows{rows, PITCH}, sp.nrow, tw2, -1);
+    for (int c = threadIdx.x; c < sp.ncol; c += kCtThreads) S[c] = P[sp.col_i1[c] * PITCH + sp.col_i2[c]];
   }
-  ct_lines<T, N, kCtThreads, LinesRows, V>(P, LinesRows{rows, PITCH}, sp.nrow, tw2, -1);
-  for (int c = threadIdx.x; c < sp.ncol; c += kCtThreads) S[c] = P[sp.col_i1[c] * PITCH + sp.col_i2[c]];
 }
 
 template <typename T, int N>
@@ -313,7 +375,7 @@ static void ct_zfwd(int n3, unsigned blocks, cudaStream_t st, const HpsiBatch<T>
   }
 }
 
-// Plane-pass variants tried by the tuner (FP32; FP64 tries 0, 2 and 4 at 2 CTAs/SM):
+// Plane-pass variants tried by the tuner (FP32; FP64 tries 0, 2, 4 and 6):
 //   0: register budget 16, odd radices first, 4 CTAs/SM    1: largest radix first, 4 CTAs/SM
 //   2: fused x pass (FX), 4 CTAs/SM                         3: fused x pass, 3 CTAs/SM
 //   4: fused x pass, line-fastest row mapping, 4 CTAs/SM    5: the same, 3 CTAs/SM
@@ -322,18 +384,19 @@ static void ct_zfwd(int n3, unsigned blocks, cudaStream_t st, const HpsiBatch<T>
 // 288-thread CTAs (1.75 / 2.30 ms); warp-local line transforms, each line owned by one warp so
 // that a stage synchronises only that warp (2.21 ms: the pass is bound by shared-memory
 // bandwidth, not by its barriers, and the transposed layout conflicts on more banks).
-constexpr int kPlaneVariants = 6;
+//   6: fused x pass and fused scatter / gather (SG), 3 CTAs/SM    7: the same with the row mapping
+constexpr int kPlaneVariants = 8;
 template <typename T> constexpr bool plane_variant_ok(int v) {
-  return sizeof(T) == 4 ? (v >= 0 && v < kPlaneVariants) : (v == 0 || v == 2 || v == 4);
+  return sizeof(T) == 4 ? (v >= 0 && v < kPlaneVariants) : (v == 0 || v == 2 || v == 4 || v == 6);
 }
 
-template <typename T, int N, int V, int MINB, bool FX = false>
+template <typename T, int N, int V, int MINB, bool FX = false, bool SG = false>
 static void ct_plane_launch(unsigned blocks, cudaStream_t st, const HpsiBatch<T>& B, int n3, const cplx<T>* tw1,
                             const cplx<T>* tw2) {
   const size_t sm = (size_t)N * (N + 1) * sizeof(cplx<T>);
-  ct_allow_smem(k_plane_ct<T, N, V, MINB, FX>, sm);
+  ct_allow_smem(k_plane_ct<T, N, V, MINB, FX, SG>, sm);
   count_launches(1);
-  k_plane_ct<T, N, V, MINB, FX><<<blocks, kCtThreads, sm, st>>>(B, n3, tw1, tw2);
+  k_plane_ct<T, N, V, MINB, FX, SG><<<blocks, kCtThreads, sm, st>>>(B, n3, tw1, tw2);
 }
 
 // CTAs of the plane pass that fit an SM's 228 KB of shared memory (the plane plus ~2 KB of
@@ -364,6 +427,10 @@ static void ct_plane_variant(int variant, unsigned blocks, cudaStream_t st, cons
     case 5:
       if constexpr (sizeof(T) == 4) return ct_plane_launch<T, N, 32, M3, true>(blocks, st, B, n3, tw1, tw2);
       break;
+    case 6: return ct_plane_launch<T, N, 0, M3, true, true>(blocks, st, B, n3, tw1, tw2);
+    case 7:
+      if constexpr (sizeof(T) == 4) return ct_plane_launch<T, N, 32, M3, true, true>(blocks, st, B, n3, tw1, tw2);
+      break;
   }
   ct_plane_launch<T, N, 0, M4>(blocks, st, B, n3, tw1, tw2);
 }
@@ -387,7 +454,7 @@ static void ct_plane(int n, unsigned blocks, cudaStream_t st, const HpsiBatch<T>
 // for that shape.  Smaller batches (the eigensolver's residual blocks) use the tuned choice
 // when there is one, else variant 0.  Never runs while the stream is being captured.
 // FDE_PLANE_VARIANT=<v> in the environment pins the variant (reproducible rounding across
-// machines); an FP64 plane pass runs a pinned 0, 2 or 4 as it is and every other pin as 0.
+// machines); an FP64 plane pass runs a pinned 0, 2, 4 or 6 as it is and every other pin as 0.
 constexpr unsigned kTuneMinPlanes = 4096;
 struct PlaneTuner {
   std::mutex mu;

@@ -132,6 +132,11 @@ constexpr int sW1 = 0, sb1 = sW1 + 3 * kH, sb2 = sb1 + kH, sb3 = sb2 + kH, sW4 =
 __device__ unsigned g_pc_status;
 __device__ long long g_pc_spin = kTcSpin;
 
+// Operands of the tensor-core kernels to FP32 on the bit patterns (dd.cuh), keeping their
+// per-point work off the FP64 pipe.
+__device__ __forceinline__ float tof(float v) { return v; }
+__device__ __forceinline__ float tof(double v) { return float_of_double_bits(v); }
+
 __device__ __forceinline__ float tanh_tc(float x) {
   const float t = __expf(2.f * fminf(fmaxf(x, -15.f), 15.f));
   return __fdividef(t - 1.f, t + 1.f);
@@ -291,10 +296,10 @@ k_precond_apply_tc(const cplx<T>* __restrict__ R, int ldr, const T* __restrict__
     const int g = (int)(tile - (long long)j * tiles_per_band) * kPcThreads + t;
     const bool valid = g < K;
     const cplx<T> r = valid ? R[(size_t)j * ldr + g] : mk<T>(0, 0);
-    const float rx = (float)r.x, ry = (float)r.y;
+    const float rx = tof(r.x), ry = tof(r.y);
     float f[3], y;
-    features(valid ? (float)kin[g] : 0.f, (float)tband[j], sqrtf(rx * rx + ry * ry),
-             (float)sqrt(sumsq[j] / (double)K), f, &y);
+    features(valid ? tof(kin[g]) : 0.f, tof(tband[j]), sqrtf(rx * rx + ry * ry), sqrtf(tof(sumsq[j]) / (float)K), f,
+             &y);
     float h[kH];
 #pragma unroll
     for (int i = 0; i < kH; ++i)
@@ -465,10 +470,10 @@ k_precond_grad_tc(const cplx<T>* __restrict__ R, const cplx<T>* __restrict__ D, 
     const bool valid = e < total;
     const int j = valid ? (int)(e / K) : 0, g = valid ? (int)(e - (long long)j * K) : 0;
     const cplx<T> r = valid ? R[e] : mk<T>(0, 0), dv = valid ? D[e] : mk<T>(0, 0);
-    const float rx = (float)r.x, ry = (float)r.y;
+    const float rx = tof(r.x), ry = tof(r.y);
     float f[3], y;
-    features(valid ? (float)kin[g] : 0.f, (float)tband[j], sqrtf(rx * rx + ry * ry),
-             (float)sqrt(sumsq[j] / (double)K), f, &y);
+    features(valid ? tof(kin[g]) : 0.f, tof(tband[j]), sqrtf(rx * rx + ry * ry), sqrtf(tof(sumsq[j]) / (float)K), f,
+             &y);
     float h[kH];
 #pragma unroll
     for (int i = 0; i < kH; ++i)
@@ -513,10 +518,10 @@ k_precond_grad_tc(const cplx<T>* __restrict__ R, const cplx<T>* __restrict__ D, 
     const float m = tpa_f(y) * expf(o);
     float go = 0.f;
     if (valid) {
-      const float ax = (float)alpha[2 * j], ay = (float)alpha[2 * j + 1];
+      const float ax = tof(alpha[2 * j]), ay = tof(alpha[2 * j + 1]);
       const float qx = ax * rx - ay * ry, qy = ax * ry + ay * rx;
-      const float ex = m * qx - (float)dv.x, ey = m * qy - (float)dv.y;
-      const float nd = (float)dnorm2[j];
+      const float ex = m * qx - tof(dv.x), ey = m * qy - tof(dv.y);
+      const float nd = tof(dnorm2[j]);
       accl += (ex * ex + ey * ey) / nd;
       go = 2.f * (ex * qx + ey * qy) / nd * m;
     }

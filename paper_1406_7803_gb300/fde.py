@@ -163,9 +163,9 @@ def tuned_plane_variant(n1: int, n3: int) -> int:
 
 
 def pin_plane_variant(variant: int) -> None:
-    """Pin the FP32 plane-pass variant (0..5) for this process, or -1 to return to tuning."""
+    """Pin the FP32 plane-pass variant (0..7) for this process, or -1 to return to tuning."""
     if load().fde_pin_plane_variant(int(variant)) != FDE_OK:
-        raise FDEError(FDE_EINVAL, "fde_pin_plane_variant: variant must be -1..5")
+        raise FDEError(FDE_EINVAL, "fde_pin_plane_variant: variant must be -1..7")
 
 
 def host_sphere(lengths, kfrac, ecut):

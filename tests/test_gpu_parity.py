@@ -175,10 +175,10 @@ def slab_system():
     return wl, ofde.System(wl)
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7])
 def test_every_plane_variant_matches_oracle(slab_system, variant):
     """Each compiled variant of the FP32 plane pass (CTAs per SM, radix order, fused x pass, row
-    thread mapping), pinned in turn, gives the oracle's H psi on the full-size molecule-on-slab cell's batched
+    thread mapping, fused column scatter and gather), pinned in turn, gives the oracle's H psi on the full-size molecule-on-slab cell's batched
     pass within the mixed-precision tolerance (sampled bands of each (subsystem, k))."""
     wl, sy = slab_system
     rhos = np.array([workloads.initial_density(wl, I) for I in range(wl.nsub)])
@@ -213,12 +213,12 @@ def test_every_plane_variant_matches_oracle(slab_system, variant):
             assert band_err(got, want) < 1e-5, (variant, I, k)
 
 
-@pytest.mark.parametrize("variant", [0, 2, 4])
+@pytest.mark.parametrize("variant", [0, 2, 4, 6])
 def test_fp64_plane_variants_match_oracle(variant):
     """The FP64 plane pass, plain, with the fused x pass (inverse last stage, potential
-    multiply and forward first stage on the same registers) and with the line-fastest row
-    mapping too, gives the oracle's H psi to 1e-10 per band on the small molecule-on-slab cell
-    (24 x 24 x 60)."""
+    multiply and forward first stage on the same registers), with the line-fastest row mapping
+    and with the fused column scatter and gather, gives the oracle's H psi to 1e-10 per band on
+    the small molecule-on-slab cell (24 x 24 x 60)."""
     wl = workloads.molecule_on_slab_small()
     sy = ofde.System(wl)
     rhos = np.array([workloads.initial_density(wl, I) for I in range(wl.nsub)])
