@@ -361,8 +361,8 @@ fde_status fde_launch_count(fde_ctx* ctx, long long* launches);
  * checked on the device: (m1, m2) strictly increasing from column to column, m3 contiguous
  * within a column, every m3 in [-n3, n3), no column longer than n3 and m1, m2 spans within
  * n1, n2; a list that breaks any of these returns FDE_EINVAL and writes nothing to d_hpsi.  The first
- * call on a device resolves the arrays' device addresses (cudaGetSymbolAddress) and must
- * come before any stream capture.  Calls share the arrays: calls that overlap on the GPU
+ * call on a device resolves the arrays' device addresses (cudaGetSymbolAddress).  Calls share
+ * the arrays: calls that overlap on the GPU
  * (other streams, other host threads) race and must be serialised by the caller.  The call
  * synchronises the stream once (to read the column count).  Errors: FDE_EINVAL (null or
  * non-positive arguments, a sphere list that fails the checks above), FDE_EUNSUPPORTED

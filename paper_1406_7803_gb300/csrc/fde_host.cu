@@ -1316,6 +1316,21 @@ template <typename T> struct EngineT : Engine {
       CK(cudaMemcpyAsync(V.p, V2.p, nb * rowsz, cudaMemcpyDeviceToDevice, st));
       CK(cudaMemcpyAsync(HV.p, HV2.p, nb * rowsz, cudaMemcpyDeviceToDevice, st));
       if (use_s) CK(cudaMemcpyAsync(SV.p, SV2.p, nb * rowsz, cudaMemcpyDeviceToDevice, st));
+      if constexpr (sizeof(T) == 4) {
+        // FP32: one more Rayleigh-Ritz step on the kept block alone.  The big step's inverse
+        // Cholesky factor scales the split-TF32 Gram matrix's rounding into the kept basis; its
+        // own Gram matrix is near the identity, so this step re-orthonormalises it and makes
+        // the Ritz values those of an orthonormal basis (without it, solves near the FP32
+        // residual floor returned Ritz values below the true eigenvalues)
+        try {
+          rayleigh_ritz(q, nb, nb, eps);
+          CK(cudaMemcpyAsync(V.p, V2.p, nb * rowsz, cudaMemcpyDeviceToDevice, st));
+          CK(cudaMemcpyAsync(HV.p, HV2.p, nb * rowsz, cudaMemcpyDeviceToDevice, st));
+          if (use_s) CK(cudaMemcpyAsync(SV.p, SV2.p, nb * rowsz, cudaMemcpyDeviceToDevice, st));
+        } catch (Err& e) {
+          if (e.st != FDE_ENOCONV) throw;
+        }
+      }
       havep = true;
     }
     if (conv) {
@@ -1878,7 +1893,11 @@ template <typename T> struct EngineT : Engine {
       CK(cudaMemcpyAsync(frozen.p + I * nr, subs[I]->rho.p, nr * sizeof(double), cudaMemcpyDeviceToDevice, st));
     fresh.ensure(ns * nr);  // the output densities, stacked for the joint mixing
     pulay_reset(hist_all);
-    const double dtol = davidson_tol(tol);
+    // Every refresh step mixes the output densities of eigensolves that start from the previous
+    // step's orbitals, so their residual floor becomes the density residual's floor (about 30
+    // times the eigensolver tolerance on the two-layer slab's Methfessel-Paxton meshes): FP64
+    // solves go to 1/100 of tol to let the density residual reach 10 tol.
+    const double dtol = sizeof(T) == 8 ? std::max(1e-12, std::min(1e-6, 0.01 * tol)) : davidson_tol(tol);
     std::vector<double> dres_prev(ns, 1.0), dres(ns, 0.0);
     double Fprev = 0;
     bool have_prev = false;

@@ -73,19 +73,9 @@ def test_refresh_with_methfessel_paxton_matches_oracle(golden, mesh):
     else:
         run, sym = _mesh(wl, (1, 2, 3), True), ops
         assert run.subsystems[0].nk == 1
-    # The oracle's stored run converged to 1e-10 with exact (dense) eigensolves.  On the 4- and
-    # 2-point meshes the library's refreshed SCF reaches the same free energy to 1e-12 Ha within
-    # ~200 steps, but its density residual int|rho_out - rho_in| then settles at 1e-8 - 5e-8
-    # instead of falling further; those meshes run to 1e-8 here.  The free energy (variational)
-    # is compared at 1e-9 Ha, the other terms -- first order in the density residual -- at 2e-7 Ha;
-    # the single-point mirror mesh, which converges to 1e-10, checks every term at 1e-8 Ha.
-    ctx, got = _run(run, "fp64", 1e-10 if mesh == "mirrors" else 1e-8, sym)
+    ctx, got = _run(run, "fp64", 1e-10, sym)
     diffs = {k: got[k] - rec["energies"][k] for k in KEYS}
-    if mesh == "mirrors":
-        assert all(abs(d) < 1e-8 for d in diffs.values()), (mesh, diffs)
-    else:
-        assert abs(diffs["F_fde"]) < 1e-9, (mesh, diffs)
-        assert all(abs(d) < 2e-7 for d in diffs.values()), (mesh, diffs)
+    assert all(abs(d) < 1e-8 for d in diffs.values()), (mesh, diffs)
     if mesh == "mirrors":
         # <Delta rho> against the supersystem KS run, itself on the reduced mesh
         sup = workloads.supersystem(run, extra_bands=4)
