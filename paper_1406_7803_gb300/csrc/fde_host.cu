@@ -1322,6 +1322,13 @@ template <typename T> struct EngineT : Engine {
         // own Gram matrix is near the identity, so this step re-orthonormalises it and makes
         // the Ritz values those of an orthonormal basis (without it, solves near the FP32
         // residual floor returned Ritz values below the true eigenvalues)
+        // every eighth iteration the kept block's H- and S-images are recomputed rather than
+        // carried: they are rotated by the inverse Cholesky factors of every step, which scale
+        // their FP32 rounding up, and a drifted image shifts the Ritz values
+        if (it % 8 == 0) {
+          apply_h_dev(s, q, V.p, HV.p, nb);
+          if (use_s) apply_s(s, q, V.p, SV.p, nb);
+        }
         try {
           rayleigh_ritz(q, nb, nb, eps);
           CK(cudaMemcpyAsync(V.p, V2.p, nb * rowsz, cudaMemcpyDeviceToDevice, st));
