@@ -33,6 +33,22 @@ def test_zero_output_layer_is_the_kinetic_preconditioner():
     assert np.isclose(precond.tpa(np.array([1e6]))[0] * 2e6, 1.0, rtol=1e-5)
 
 
+def test_kinetic_preconditioner_values_fix_every_coefficient():
+    """The numerator of K is 27 sum_{n<4} (2y/3)^n, so K(3/2) = 4 x 27 / (4 x 27 + 81) = 4/7
+    and K(1) = 65/81 (hand-evaluated); with K(0) = 1, the 1/(2y) tail and 1 - K = 16 y^4 / 27
+    + O(y^5) at small y these values fix all five coefficients: a wrong one fails here."""
+    K = precond.tpa(np.array([0.0, 1.0, 1.5, 1e-3, 1e7]))
+    assert K[0] == 1.0
+    assert abs(K[1] - 65.0 / 81.0) < 1e-15
+    assert abs(K[2] - 4.0 / 7.0) < 1e-15
+    assert abs((1.0 - K[3]) / 1e-12 - 16.0 / 27.0) < 1e-3
+    assert abs(K[4] * 2e7 - 1.0) < 1e-6
+    # monotone decreasing between the limits, never negative
+    y = np.linspace(0.0, 50.0, 5001)
+    k = precond.tpa(y)
+    assert np.all(np.diff(k) < 0) and np.all(k > 0)
+
+
 def test_backward_matches_central_differences():
     rng = np.random.default_rng(2)
     kin = rng.uniform(0, 10, 40)
