@@ -196,14 +196,11 @@ def _gauss_overlap(s1, s2, d2):
     return (2.0 * s1 * s2 / w) ** 1.5 * math.exp(-d2 / (2.0 * w))
 
 
-def test_kinetic_and_nonlocal_energy_of_an_atom_centred_gaussian():
-    """<psi|H|psi> with v_eff = 0 for the Bloch sum psi_k(r) = sum_T e^{ik.T} g(r - R_A - T) of
-    a unit-norm Gaussian of width 0.8 bohr, sampled in real space and transformed with numpy's
-    FFT (not the oracle's), at a general k-point: the kinetic part is 3/(4 sigma^2), and the
-    nonlocal part is sum_a sum_i D_ii |<beta_ai|psi>|^2 with <beta_ai|psi> = sum_T e^{ik.T}
-    <g_sigma_i(. - R_a)|g(. - R_A - T)> from the Gaussian product theorem.  A second atom 4.5
-    bohr away has two nearly equidistant images, so a wrong sign of the projector phase, a
-    dropped atom, a transposed coupling or a missing 1/2 in the kinetic term fails here."""
+def _gaussian_cell(**uspp):
+    """One Bloch-summed unit-norm Gaussian orbital (width 0.8 bohr, centred on atom A) in a 9
+    bohr cube at a general k-point, sampled in real space and transformed with numpy's FFT
+    (not the oracle's), and the closed-form projections <beta_ai|psi> = sum_T e^{ik.T}
+    <g_sigma_i(. - R_a)|g(. - R_A - T)> (Gaussian product theorem) on both atoms."""
     L, n, sig = 9.0, 64, 0.8
     lat = np.diag([L] * 3)
     kfrac = np.array([0.1, 0.2, 0.3])
@@ -211,12 +208,11 @@ def test_kinetic_and_nonlocal_energy_of_an_atom_centred_gaussian():
     RB = RA + np.array([4.5, 0.3, -0.2])
     sub = workloads.Subsystem("pair", np.array([RA, RB]), np.array([1.0, 1.0]), 0.5, 1,
                               kfrac[None, :], np.ones(1), 2.0, 0.0,
-                              workloads.KB_SIGMA, workloads.KB_D)
+                              workloads.KB_SIGMA, workloads.KB_D, **uspp)
     wl = workloads.Workload(name="gauss", lattice=lat, grid=(n, n, n), ecut=40.0, subsystems=[sub],
                             xc=workloads.XC_LDA, kedf=workloads.KEDF_TF, seed=0, tol=1e-6)
     sy = fde.System(wl)
     kc = 2.0 * math.pi * kfrac / L
-    # real-space Bloch sum on the grid, then the periodic part u = e^{-ik.r} psi
     x = np.arange(n) * (L / n)
     r = np.stack(np.meshgrid(x, x, x, indexing="ij"), axis=-1)
     psi = np.zeros((n, n, n), dtype=np.complex128)
@@ -224,23 +220,50 @@ def test_kinetic_and_nonlocal_energy_of_an_atom_centred_gaussian():
         T = (np.array(t) - 1) * L
         d2 = ((r - RA - T) ** 2).sum(-1)
         psi += np.exp(1j * kc @ T) * (math.pi ** 1.5 * sig ** 3) ** -0.5 * np.exp(-d2 / (2 * sig * sig))
-    u = np.exp(-1j * (r @ kc)) * psi
+    u = np.exp(-1j * (r @ kc)) * psi  # the periodic part
     F = np.fft.fftn(u) * math.sqrt(L ** 3) / n ** 3  # c_G = Omega^{-1/2} int u e^{-iG.r}
     mil, _ = sy.basis[0][0]
     c = F[mil[:, 0] % n, mil[:, 1] % n, mil[:, 2] % n][None, :]
+    P = np.zeros((2, len(workloads.KB_SIGMA)), dtype=np.complex128)
+    for a, Ra in enumerate((RA, RB)):
+        for i, si in enumerate(workloads.KB_SIGMA):
+            for t in np.ndindex(5, 5, 5):
+                T = (np.array(t) - 2) * L
+                P[a, i] += np.exp(1j * kc @ T) * _gauss_overlap(si, sig, float(((RA + T - Ra) ** 2).sum()))
+    return sy, c, P, sig
+
+
+def test_kinetic_and_nonlocal_energy_of_an_atom_centred_gaussian():
+    """<psi|H|psi> with v_eff = 0 for the Gaussian orbital of the cell above: the kinetic part
+    is 3/(4 sigma^2) and the nonlocal part sum_a P_a^H D P_a.  The second atom, 4.5 bohr away,
+    has two nearly equidistant images, so a wrong sign of the projector phase, a dropped atom,
+    a transposed coupling or a missing 1/2 in the kinetic term fails here."""
+    sy, c, P, sig = _gaussian_cell()
+    n = sy.grid[0]
     assert abs(np.sum(np.abs(c) ** 2) - 1.0) < 1e-10  # the sphere holds the whole Gaussian
     hc = sy.apply_h(0, 0, c, np.zeros((n, n, n)))
     e = np.vdot(c, hc)
     assert abs(e.imag) < 1e-12
     want_kin = 3.0 / (4.0 * sig * sig)
-    want_nl = 0.0
-    for Ra in (RA, RB):
-        for si, Dii in zip(workloads.KB_SIGMA, np.diag(workloads.KB_D)):
-            P = 0.0j
-            for t in np.ndindex(5, 5, 5):
-                T = (np.array(t) - 2) * L
-                P += np.exp(1j * kc @ T) * _gauss_overlap(si, sig, float(((RA + T - Ra) ** 2).sum()))
-            want_nl += Dii * abs(P) ** 2
+    D = np.array(workloads.KB_D)
+    want_nl = float(sum(np.real(np.vdot(Pa, D @ Pa)) for Pa in P))
     kin_only = np.vdot(c, sy.basis[0][0][1][None, :] * c).real
     assert abs(kin_only - want_kin) < 1e-10, (kin_only, want_kin)
     assert abs(e.real - (want_kin + want_nl)) < 1e-10, (e.real - want_kin, want_nl)
+
+
+def test_overlap_of_an_atom_centred_gaussian():
+    """<psi|S|psi> = 1 + sum_a P_a^H q P_a for the ultrasoft-like model (Appendix, subsystem-
+    specific projectors) with the off-diagonal q of the synthetic cells, and with v_eff = 0 the
+    screening vanishes so H keeps the bare coupling D."""
+    q = np.array(workloads.USPP_Q)
+    sy, c, P, sig = _gaussian_cell(proj_Q=workloads.USPP_Q, aug_sigma=workloads.USPP_SIGMA)
+    n = sy.grid[0]
+    sc = sy.apply_s(0, 0, c)
+    want = 1.0 + float(sum(np.real(np.vdot(Pa, q @ Pa)) for Pa in P))
+    got = np.vdot(c, sc)
+    assert abs(got.imag) < 1e-12 and abs(got.real - want) < 1e-10, (got, want)
+    D = np.array(workloads.KB_D)
+    e = np.vdot(c, sy.apply_h(0, 0, c, np.zeros((n, n, n)))).real
+    want_h = 3.0 / (4.0 * sig * sig) + float(sum(np.real(np.vdot(Pa, D @ Pa)) for Pa in P))
+    assert abs(e - want_h) < 1e-10
