@@ -53,8 +53,10 @@ typedef enum {
 
 typedef enum {
   FDE_PREC_FP64 = 0,  /* everything in FP64 */
-  FDE_PREC_MIXED = 1  /* FP32 orbitals, FFTs and grid arithmetic; FP64 dense algebra,
-                         densities and energies */
+  FDE_PREC_MIXED = 1  /* FP32 orbitals, H psi transforms, subspace products and pointwise
+                         functionals; double-float density and gradient transforms; FP64
+                         dense algebra, densities, potentials in memory and energies; a
+                         freeze-and-thaw cycle ends with an FP64 refinement */
 } fde_prec;
 
 enum { FDE_XC_LDA = 0, FDE_XC_PBE = 1 };                         /* exchange-correlation */
@@ -301,6 +303,10 @@ fde_status fde_scf_subsystem(fde_ctx* ctx, int sub, double tol_ha, int max_scf,
 /* One Jacobi freeze-and-thaw cycle (Fig. 1b: each subsystem's SCF runs to self-consistency
  * before the densities are exchanged): every subsystem runs fde_scf_subsystem against the
  * densities frozen at the start of the cycle, then every rho_I is refreshed together.
+ * Mixed-precision contexts run the cycle twice: first in the FP32 engine with the subsystem
+ * SCFs to max(tol_ha, 1e-5), then in the FP64 engine (created on first use) against the same
+ * frozen densities, each subsystem's SCF starting from the FP32 cycle's orbitals and output
+ * density, to tol_ha; the FP64 result is copied back to the context's state.
  * out (nullable) receives the energies of the refreshed state. */
 fde_status fde_freeze_thaw_cycle(fde_ctx* ctx, double tol_ha, int max_scf, fde_energies* out);
 
