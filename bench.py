@@ -43,7 +43,7 @@ from paper_1406_7803_gb300 import workloads  # noqa: E402
 METRIC = "Embedded H·ψ band-applies/s"
 UNIT = "band-applies/s"
 WORKLOADS = {"molecule-on-slab": workloads.molecule_on_slab, "batched": workloads.batched_uneven,
-             "large": workloads.large_cell}
+             "large": workloads.large_cell, "plain": workloads.plain_fde_32}
 REFERENCE_BUDGET_S = 150.0  # wall time the reference arm's K + W steps should stay within
 
 
