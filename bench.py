@@ -6,6 +6,10 @@ Workloads (seeded synthetic inputs, paper_1406_7803_gb300.workloads):
     at Gamma, PBE + revAPBEK, 2 Gaussian KB projectors per atom: 268 band-applies per step.
   batched (--workload batched): 24^3 bohr, 96^3 grid, 20 Ha; a 54-atom slab with 96 bands x
     2 k-points plus 16 molecules of 8..64 bands at Gamma: 778 band-applies per step.
+  large (--workload large): 30 x 30 x 60 bohr, 144 x 144 x 288 grid, 25 Ha; a 216-atom slab
+    with 512 bands x 8 k-points plus 32 molecules of 16..48 bands: 5209 band-applies per step.
+  plain (--workload plain): 10^3 bohr, 32^3 grid, 15 Ha; two 3-atom subsystems with 4 bands
+    each, LDA + Thomas-Fermi: 8 band-applies per step.
 
 One step = one pass of the hot path over the whole cell: the embedding-potential build
 (rho = sum rho_I, FFT Poisson, FFT gradients, pointwise xc and GGA kinetic potentials,
@@ -20,8 +24,8 @@ the molecule-on-slab cell: mixed precision with and without the learned precondi
 against the plain FP64 GPU path ("ft_cycle").
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--prec mixed|fp64]
-                       [--workload molecule-on-slab|batched] [--impl ours|reference]
-                       [--no-cpu] [--no-ft]
+                       [--workload molecule-on-slab|batched|large|plain] [--impl ours|reference]
+                       [--no-cpu] [--no-fp64] [--no-ft]
 """
 from __future__ import annotations
 
