@@ -5,8 +5,9 @@ The device split (dd.cuh) reads the bit pattern of v = (-1)^s 2^e (1 + m 2^-52):
 float keeps the top 23 mantissa bits rounded to nearest even, and the low float is the
 remaining 29 bits minus the rounding increment, converted to float and scaled by 2^(e - 52).
 That must equal hi = float(v), lo = float(v - hi) for 2^-70 <= |v| < 2^127, keep hi alone
-below 2^-70 (an absolute error under 2^-94) and give (0, 0) below FP32's normal range.  The GPU parity tests check the transforms that use it; this
-test pins the rule itself over the whole exponent range, ties included."""
+below 2^-70 (an absolute error under 2^-94) and give (0, 0) below FP32's normal range.
+The GPU parity tests check the transforms that use it; this test pins the rule itself over
+the whole exponent range, ties included."""
 import numpy as np
 
 
